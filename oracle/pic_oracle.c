@@ -1,0 +1,515 @@
+/*
+ * CPU oracle for the spin-dependent PIC hot-electron step (arXiv:1807.04733).
+ *
+ * TEST INFRASTRUCTURE ONLY: called by tests, by the smoke check and by the
+ * benchmark's CPU-baseline leg.  Never part of the product path.
+ *
+ * One time step follows the Strang splitting of Eq. strang (Sec. III.A):
+ *
+ *   Source(dt/2) -> Transport(dt/2) -> Scattering(dt) -> Transport(dt/2)
+ *   -> Source(dt/2)
+ *
+ * with the superparticle rules of Sec. III:
+ *   - particle number: carriers are created by a Gaussian pulse at the start
+ *     and the end of every step (Sec. III, "Number of Particles");
+ *   - transport: dz/dt = v_sigma(E) cos(theta); full reflection at the vacuum
+ *     surfaces; stochastic transmission with probability T at an interface
+ *     (Sec. III, transport part);
+ *   - scattering: Monte-Carlo test against tau_eff of Eq. lifetimes within dt;
+ *     elastic events redraw the direction and keep E and spin (Eq. split_w,
+ *     Eq. elastic_scattering); inelastic events pick the final energy
+ *     uniformly below the initial one (Eq. inelastic_collision) and lift a
+ *     secondary whose spin follows the equilibrium polarisation P0
+ *     (Eq. eq_pol); a lowest-bin carrier that scatters inelastically is
+ *     removed (Sec. III, scattering part);
+ *   - moments (Eq. firstmoment): spin- and energy-resolved densities per cell
+ *     and the net spin-resolved particle flux through every cell face.
+ *
+ * Readings of points the paper leaves open are the ones listed in the design
+ * notes (energy split k' ~ U{1..k-1} with the secondary taking k - k';
+ * direction kept on transmission and mirrored on reflection; the flux as a
+ * net crossing count; thresholds floor(p * 2^32) compared with Philox words).
+ *
+ * Processing order: particles in slot order; a secondary takes its second
+ * half flight as soon as it is created and is appended after the slots that
+ * existed at the start of the step, in parent order; dead slots stay until
+ * the stable compaction every `compact_every` steps.
+ */
+#include "pic_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- Philox4x32-10 (Salmon et al., SC'11, "Parallel random numbers: as
+ * easy as 1, 2, 3"): ten rounds of two 32x32->64 multiplies with the round
+ * multipliers below; the key is bumped by the Weyl constants between rounds. */
+#define PH_M0 0xD2511F53u
+#define PH_M1 0xCD9E8D57u
+#define PH_W0 0x9E3779B9u
+#define PH_W1 0xBB67AE85u
+
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += PH_W0; k1 += PH_W1; }
+        uint64_t p0 = (uint64_t)PH_M0 * c0;
+        uint64_t p1 = (uint64_t)PH_M1 * c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* substreams: the fourth counter word */
+#define SUB_SCAT 0x000u
+#define SUB_SEC  0x001u
+#define SUB_IF   0x100u   /* + 16*half + hit : primary flights */
+#define SUB_SIF  0x200u   /* + hit           : secondary's second-half flight */
+#define SUB_INJ  0x300u   /* + j             : injection draws */
+
+/* ---- packed word: k:8 | spin:1 | layer:4 | gen:8 | id_hi:11 ---- */
+#define PK_K(w)     ((w) & 0xFFu)
+#define PK_S(w)     (((w) >> 8) & 1u)
+#define PK_L(w)     (((w) >> 9) & 0xFu)
+#define PK_G(w)     (((w) >> 13) & 0xFFu)
+#define PK_E(w)     ((w) >> 21)
+static uint32_t pk(uint32_t k, uint32_t s, uint32_t l, uint32_t g, uint32_t e)
+{
+    return k | (s << 8) | (l << 9) | (g << 13) | (e << 21);
+}
+
+struct or_sim {
+    or_config cfg;
+    /* owned copies of the physical tables */
+    float *v; double *tau_in, *tau_el, *T, *p0;
+    /* geometry */
+    float edge[OR_MAX_LAYERS + 1];
+    int32_t n_cells;
+    /* derived thresholds */
+    uint32_t *P_thr, *Q_thr, *T_thr, *P0_thr, up_thr;
+    int32_t n_cdf; int32_t *cdf_cell, *cdf_layer; uint32_t *cdf_thr;
+    int64_t *inj;                 /* per half step */
+    /* particles */
+    or_rec *recs; int64_t n_slots; uint64_t next_id; uint32_t step;
+    /* moments */
+    int32_t n_out; uint32_t *nh; int32_t *Jh;
+    or_ledger led;
+    int err;
+};
+
+static uint32_t to_thr(double p)
+{
+    if (!(p > 0.0)) return 0u;
+    if (p >= 1.0) return 0xFFFFFFFFu;
+    double t = floor(p * 4294967296.0);
+    if (t >= 4294967295.0) return 0xFFFFFFFFu;
+    return (uint32_t)t;
+}
+
+/* direction cosine from a word: odd multiples of 2^-23 in (-1, 1), exact */
+static float mu_from(uint32_t x)
+{
+    int32_t n = (int32_t)(2u * (x >> 9) + 1u) - 8388608;
+    return (float)n * (1.0f / 8388608.0f);
+}
+
+/* uniform in (0,1): odd multiples of 2^-24, exact */
+static float unit_from(uint32_t x)
+{
+    return (float)(2u * (x >> 9) + 1u) * (1.0f / 16777216.0f);
+}
+
+/* uniform integer in 0..n-1 from a word */
+static uint32_t below(uint32_t x, uint32_t n)
+{
+    return (uint32_t)(((uint64_t)x * n) >> 32);
+}
+
+static double Phi(double x) { return 0.5 * erfc(-x / sqrt(2.0)); }
+
+/* normalised pulse CDF on [0, 2 t0] (a Gaussian of the given FWHM centred
+ * at t0, truncated symmetrically so that exactly n0 carriers are created) */
+static double pulse_F(const or_config *c, double t)
+{
+    if (t <= 0.0) return 0.0;
+    if (t >= 2.0 * c->t0) return 1.0;
+    double s = c->fwhm / (2.0 * sqrt(2.0 * log(2.0)));
+    double a = Phi(-c->t0 / s), b = Phi(c->t0 / s);
+    return (Phi((t - c->t0) / s) - a) / (b - a);
+}
+
+static void draw(const or_sim *s, uint64_t id, uint32_t step, uint32_t sub, uint32_t r[4])
+{
+    uint32_t ctr[4] = { (uint32_t)id, (uint32_t)(id >> 32) | (s->cfg.stack_index << 16),
+                        step, sub };
+    uint32_t key[2] = { (uint32_t)s->cfg.seed, (uint32_t)(s->cfg.seed >> 32) };
+    or_philox4x32_10(ctr, key, r);
+}
+
+static int32_t cell_of(const or_sim *s, float z)
+{
+    float q = floorf(z / s->cfg.dz);
+    int32_t c = (int32_t)q;
+    if (q < 0.0f) c = 0;
+    if (c > s->n_cells - 1) c = s->n_cells - 1;
+    return c;
+}
+
+static int idx3(const or_sim *s, int m, int sg, int k) { return (m * 2 + sg) * s->cfg.n_e + (k - 1); }
+
+/* net flux through the cell faces between the start cell a and end cell b */
+static void flux(or_sim *s, int sg, int a, int b)
+{
+    int32_t *J = s->Jh + ((int64_t)(s->step / s->cfg.moment_every) * 2 + sg) * (s->n_cells + 1);
+    if (b > a) for (int f = a + 1; f <= b; ++f) J[f] += 1;
+    else       for (int f = b + 1; f <= a; ++f) J[f] -= 1;
+}
+
+/* Transport for a time tau (Eq. Strang-transport): free flight inside the
+ * current layer; at a vacuum surface the carrier is reflected; at an
+ * interface a uniform draw against T decides transmission (layer changes,
+ * direction kept) or reflection (direction mirrored); the remaining time is
+ * then flown with the velocity of the layer the carrier is in. */
+static void half_flight(or_sim *s, or_rec *p, float tau, uint64_t id, uint32_t sub0)
+{
+    const or_config *c = &s->cfg;
+    uint32_t w0 = p->packed;
+    int k = (int)PK_K(w0), sg = (int)PK_S(w0), layer = (int)PK_L(w0);
+    for (int hit = 0;; ++hit) {
+        int m = c->layer_mat[layer];
+        float v = s->v[idx3(s, m, sg, k)];
+        float w = v * p->mu;
+        float d = w * tau;
+        float z1 = p->z + d;
+        float lo = s->edge[layer], hi = s->edge[layer + 1];
+        float zb; int up;
+        if (p->mu > 0.0f && z1 > hi) { zb = hi; up = 1; }
+        else if (p->mu < 0.0f && z1 < lo) { zb = lo; up = 0; }
+        else { p->z = z1; break; }
+        if (hit == OR_MAX_HITS) { p->z = zb; s->led.truncated++; break; }
+        float tb = (zb - p->z) / w;
+        tau = tau - tb;
+        if (!(tau > 0.0f)) tau = 0.0f;
+        p->z = zb;
+        int vacuum = up ? (layer == c->n_layers - 1) : (layer == 0);
+        if (vacuum) {
+            p->mu = -p->mu;
+        } else {
+            int iface = up ? layer : layer - 1, dir = up ? 0 : 1;
+            int trans = 1;
+            s->led.iface_hits++;
+            if (!(c->flags & OR_F_TRANSPARENT)) {
+                uint32_t r[4];
+                draw(s, id, s->step, sub0 + (uint32_t)hit, r);
+                trans = r[0] < s->T_thr[((iface * 2 + dir) * 2 + sg) * c->n_e + (k - 1)];
+            }
+            if (trans) { layer += up ? 1 : -1; s->led.iface_transmit++; }
+            else p->mu = -p->mu;
+        }
+    }
+    p->packed = (w0 & ~(0xFu << 9)) | ((uint32_t)layer << 9);
+}
+
+static int append(or_sim *s, or_rec r)
+{
+    if (s->n_slots >= s->cfg.capacity) return 0;
+    s->recs[s->n_slots++] = r;
+    return 1;
+}
+
+/* Source(dt/2), Eq. Strang-source: carriers created in half step h = 2*step+half */
+static void inject(or_sim *s, int half)
+{
+    const or_config *c = &s->cfg;
+    int64_t h = 2 * (int64_t)s->step + half;
+    int64_t n = s->inj[h];
+    for (int64_t j = 0; j < n; ++j) {
+        if (s->n_slots >= c->capacity) {
+            s->led.inject_dropped += (uint64_t)(n - j);
+            if (c->flags & OR_F_STRICT_CAPACITY) s->err = 3;
+            return;
+        }
+        uint64_t id = s->next_id++;
+        uint32_t a[4], b[4];
+        draw(s, id, s->step, SUB_INJ + 0, a);
+        draw(s, id, s->step, SUB_INJ + 1, b);
+        int i = 0;
+        while (i < s->n_cdf - 1 && !(a[0] < s->cdf_thr[i])) ++i;
+        float z = ((float)s->cdf_cell[i] + unit_from(a[1])) * c->dz;
+        uint32_t sg = a[2] < s->up_thr ? 0u : 1u;
+        uint32_t k = c->e_mode == 1 ? (uint32_t)c->k_mono[sg] : 1u + below(a[3], (uint32_t)c->n_e);
+        or_rec r;
+        r.z = z;
+        r.mu = mu_from(b[0]);
+        r.id = (uint32_t)id;
+        r.packed = pk(k, sg, (uint32_t)s->cdf_layer[i], 1u, (uint32_t)(id >> 32));
+        append(s, r);
+        s->led.injected++;
+        s->led.q_injected += k;
+    }
+}
+
+static void absorb(or_sim *s, or_rec *p)
+{
+    p->packed &= ~0xFFu;       /* k = 0 marks a removed carrier */
+    s->led.absorbed++;
+    s->led.q_bath += 1;
+}
+
+static void step_once(or_sim *s)
+{
+    const or_config *c = &s->cfg;
+    const float half = c->dt * 0.5f;
+    inject(s, 0);
+    int64_t n_start = s->n_slots;
+    for (int64_t i = 0; i < n_start; ++i) {
+        or_rec *p = &s->recs[i];
+        if (PK_K(p->packed) == 0) continue;
+        s->led.particle_steps++;
+        uint64_t id = (uint64_t)p->id | ((uint64_t)PK_E(p->packed) << 32);
+        int c_start = cell_of(s, p->z);
+        int sg = (int)PK_S(p->packed);
+
+        half_flight(s, p, half, id, SUB_IF + 0);
+
+        /* Scattering(dt): one Monte-Carlo test against tau_eff (Eq. lifetimes) */
+        uint32_t x[4];
+        draw(s, id, s->step, SUB_SCAT, x);
+        int k = (int)PK_K(p->packed), layer = (int)PK_L(p->packed);
+        int m = c->layer_mat[layer];
+        int t = idx3(s, m, sg, k);
+        if (x[0] < s->P_thr[t]) {
+            int inel = x[1] < s->Q_thr[t];
+            if (k == 1 && (inel || (c->flags & OR_F_LOWEST_BIN_ANY))) {
+                absorb(s, p);
+                flux(s, sg, c_start, cell_of(s, p->z));
+                continue;
+            }
+            p->mu = mu_from(x[2]);
+            if (inel) {
+                uint32_t kp = 1u + below(x[3], (uint32_t)(k - 1));
+                uint32_t ks = (uint32_t)k - kp;
+                p->packed = (p->packed & ~0xFFu) | kp;
+                if (c->flags & OR_F_NO_SECONDARIES) {
+                    s->led.q_bath += ks;
+                } else {
+                    /* secondary: same place, spin from P0 of this material,
+                     * isotropic direction, one generation more */
+                    uint32_t y[4];
+                    draw(s, id, s->step, SUB_SEC, y);
+                    uint32_t g = PK_G(p->packed);
+                    uint32_t sgs = y[0] < s->P0_thr[m] ? 0u : 1u;
+                    or_rec q;
+                    q.z = p->z;
+                    q.mu = mu_from(y[1]);
+                    q.id = 0;
+                    q.packed = pk(ks, sgs, (uint32_t)layer, g < 255u ? g + 1u : 255u, 0u);
+                    int cs = cell_of(s, q.z);
+                    half_flight(s, &q, half, id, SUB_SIF);
+                    if (s->n_slots < c->capacity) {
+                        uint64_t nid = s->next_id++;
+                        q.id = (uint32_t)nid;
+                        q.packed |= (uint32_t)(nid >> 32) << 21;
+                        append(s, q);
+                        s->led.spawned++;
+                        flux(s, (int)sgs, cs, cell_of(s, q.z));
+                    } else {
+                        s->led.spawn_dropped++;
+                        s->led.q_dropped += ks;
+                        if (c->flags & OR_F_STRICT_CAPACITY) s->err = 3;
+                    }
+                }
+            }
+        }
+
+        half_flight(s, p, half, id, SUB_IF + 16);
+        flux(s, sg, c_start, cell_of(s, p->z));
+    }
+    inject(s, 1);
+
+    if ((s->step + 1) % (uint32_t)c->moment_every == 0) {
+        int64_t tout = (int64_t)(s->step + 1) / c->moment_every - 1;
+        for (int64_t i = 0; i < s->n_slots; ++i) {
+            const or_rec *p = &s->recs[i];
+            uint32_t k = PK_K(p->packed);
+            if (k == 0) continue;
+            int64_t b = ((tout * 2 + PK_S(p->packed)) * c->n_e + (k - 1)) * s->n_cells
+                        + cell_of(s, p->z);
+            s->nh[b] += 1;
+        }
+    }
+    if ((s->step + 1) % (uint32_t)c->compact_every == 0) {
+        int64_t j = 0;
+        for (int64_t i = 0; i < s->n_slots; ++i)
+            if (PK_K(s->recs[i].packed) != 0) s->recs[j++] = s->recs[i];
+        s->n_slots = j;
+    }
+    s->step++;
+}
+
+int or_step(or_sim *s, int n_steps)
+{
+    for (int i = 0; i < n_steps; ++i) {
+        if ((int64_t)s->step >= s->cfg.n_steps_max) return 2;
+        step_once(s);
+        if (s->err) return s->err;
+    }
+    return 0;
+}
+
+static void derive(or_sim *s)
+{
+    const or_config *c = &s->cfg;
+    int ne = c->n_e;
+    for (int m = 0; m < c->n_mat; ++m)
+        for (int sg = 0; sg < 2; ++sg)
+            for (int k = 1; k <= ne; ++k) {
+                int t = idx3(s, m, sg, k);
+                double ti = s->tau_in[t], te = s->tau_el[m];
+                double r_in = isinf(ti) ? 0.0 : 1.0 / ti;
+                double r_el = isinf(te) ? 0.0 : 1.0 / te;
+                double r = r_el + r_in;
+                double a = (double)c->dt * r;
+                s->P_thr[t] = to_thr(-expm1(-a));
+                s->Q_thr[t] = to_thr(r > 0.0 ? r_in / r : 0.0);
+            }
+    for (int i = 0; i < (c->n_layers - 1) * 2 * 2 * ne; ++i) s->T_thr[i] = to_thr(s->T[i]);
+    for (int m = 0; m < c->n_mat; ++m) s->P0_thr[m] = to_thr((1.0 + s->p0[m]) / 2.0);
+    s->up_thr = to_thr(c->up_frac);
+
+    /* excitation profile: cell masses of exp(-z/abs_len) (or uniform) over
+     * the excited layers, cumulated in cell order */
+    int n = 0, cell = 0;
+    double total = 0.0;
+    double *mass = (double *)malloc(sizeof(double) * (size_t)(s->n_cells > 0 ? s->n_cells : 1));
+    for (int l = 0; l < c->n_layers; ++l) {
+        for (int j = 0; j < c->layer_cells[l]; ++j, ++cell) {
+            if (!((c->excite_mask >> l) & 1u)) continue;
+            double zc = (double)cell * c->dz, dz = c->dz, m;
+            if (c->abs_len > 0.0) m = c->abs_len * (exp(-zc / c->abs_len) - exp(-(zc + dz) / c->abs_len));
+            else m = dz;
+            s->cdf_cell[n] = cell; s->cdf_layer[n] = l; mass[n] = m; total += m; ++n;
+        }
+    }
+    s->n_cdf = n;
+    double cum = 0.0;
+    for (int i = 0; i < n; ++i) {
+        cum += mass[i];
+        s->cdf_thr[i] = (i == n - 1) ? 0xFFFFFFFFu : to_thr(cum / total);
+    }
+    free(mass);
+
+    /* injected carriers per half step: floor(N0 F(t_{h+1})) - floor(N0 F(t_h)) */
+    int64_t nh = 2 * (int64_t)c->n_steps_max;
+    double n0 = (double)c->n0;
+    for (int64_t h = 0; h < nh; ++h) {
+        double ta = (double)h * 0.5 * (double)c->dt, tb = (double)(h + 1) * 0.5 * (double)c->dt;
+        if (c->n0 <= 0 || n == 0) { s->inj[h] = 0; continue; }
+        s->inj[h] = (int64_t)floor(n0 * pulse_F(c, tb)) - (int64_t)floor(n0 * pulse_F(c, ta));
+    }
+}
+
+int or_create(const or_config *cfg, or_sim **out)
+{
+    *out = NULL;
+    if (cfg->n_e < 1 || cfg->n_e > 255 || cfg->n_layers < 1 || cfg->n_layers > OR_MAX_LAYERS ||
+        cfg->capacity < 0 || cfg->moment_every < 1 || cfg->compact_every < 1 ||
+        cfg->n_steps_max < 0 || cfg->n_mat < 1 || !(cfg->dt > 0.0f) || !(cfg->dz > 0.0f))
+        return 1;
+    if (cfg->n0 > 0 && !(cfg->fwhm > 0.0 && cfg->t0 > 0.0)) return 1;
+    or_sim *s = (or_sim *)calloc(1, sizeof(or_sim));
+    s->cfg = *cfg;
+    int ne = cfg->n_e, nm = cfg->n_mat, nif = cfg->n_layers - 1;
+    size_t tab = (size_t)nm * 2 * ne;
+    s->v = (float *)malloc(sizeof(float) * tab); memcpy(s->v, cfg->v, sizeof(float) * tab);
+    s->tau_in = (double *)malloc(sizeof(double) * tab); memcpy(s->tau_in, cfg->tau_in, sizeof(double) * tab);
+    s->tau_el = (double *)malloc(sizeof(double) * nm); memcpy(s->tau_el, cfg->tau_el, sizeof(double) * nm);
+    s->p0 = (double *)malloc(sizeof(double) * nm); memcpy(s->p0, cfg->p0, sizeof(double) * nm);
+    s->T = (double *)malloc(sizeof(double) * (size_t)(nif * 4 * ne + 1));
+    if (nif > 0) memcpy(s->T, cfg->T, sizeof(double) * (size_t)(nif * 4 * ne));
+    s->cfg.v = s->v; s->cfg.tau_in = s->tau_in; s->cfg.tau_el = s->tau_el; s->cfg.T = s->T; s->cfg.p0 = s->p0;
+
+    int32_t cells = 0;
+    s->edge[0] = 0.0f;
+    for (int l = 0; l < cfg->n_layers; ++l) {
+        if (cfg->layer_cells[l] < 1 || cfg->layer_mat[l] < 0 || cfg->layer_mat[l] >= nm) { or_destroy(s); return 1; }
+        cells += cfg->layer_cells[l];
+        s->edge[l + 1] = (float)cells * cfg->dz;
+    }
+    s->n_cells = cells;
+    s->P_thr = (uint32_t *)malloc(sizeof(uint32_t) * tab);
+    s->Q_thr = (uint32_t *)malloc(sizeof(uint32_t) * tab);
+    s->T_thr = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(nif * 4 * ne + 1));
+    s->P0_thr = (uint32_t *)malloc(sizeof(uint32_t) * nm);
+    s->cdf_cell = (int32_t *)malloc(sizeof(int32_t) * cells);
+    s->cdf_layer = (int32_t *)malloc(sizeof(int32_t) * cells);
+    s->cdf_thr = (uint32_t *)malloc(sizeof(uint32_t) * cells);
+    s->inj = (int64_t *)calloc((size_t)(2 * (int64_t)cfg->n_steps_max + 1), sizeof(int64_t));
+    derive(s);
+
+    s->recs = (or_rec *)malloc(sizeof(or_rec) * (size_t)(cfg->capacity > 0 ? cfg->capacity : 1));
+    s->n_out = (cfg->n_steps_max + cfg->moment_every - 1) / cfg->moment_every;
+    s->nh = (uint32_t *)calloc((size_t)s->n_out * 2 * ne * cells + 1, sizeof(uint32_t));
+    s->Jh = (int32_t *)calloc((size_t)s->n_out * 2 * (cells + 1) + 1, sizeof(int32_t));
+    if (!s->recs || !s->nh || !s->Jh) { or_destroy(s); return 4; }
+    *out = s;
+    return 0;
+}
+
+void or_destroy(or_sim *s)
+{
+    if (!s) return;
+    free(s->v); free(s->tau_in); free(s->tau_el); free(s->T); free(s->p0);
+    free(s->P_thr); free(s->Q_thr); free(s->T_thr); free(s->P0_thr);
+    free(s->cdf_cell); free(s->cdf_layer); free(s->cdf_thr); free(s->inj);
+    free(s->recs); free(s->nh); free(s->Jh);
+    free(s);
+}
+
+int64_t or_n_slots(const or_sim *s) { return s->n_slots; }
+int32_t or_n_cells(const or_sim *s) { return s->n_cells; }
+int32_t or_n_out(const or_sim *s) { return s->n_out; }
+int32_t or_step_index(const or_sim *s) { return (int32_t)s->step; }
+uint64_t or_next_id(const or_sim *s) { return s->next_id; }
+
+void or_records(const or_sim *s, or_rec *out)
+{
+    memcpy(out, s->recs, sizeof(or_rec) * (size_t)s->n_slots);
+}
+
+int or_set_records(or_sim *s, const or_rec *in, int64_t n, uint64_t next_id)
+{
+    if (n < 0 || n > s->cfg.capacity) return 1;
+    memcpy(s->recs, in, sizeof(or_rec) * (size_t)n);
+    s->n_slots = n;
+    s->next_id = next_id;
+    return 0;
+}
+
+void or_moments(const or_sim *s, uint32_t *n_out, int32_t *J_out, or_ledger *led)
+{
+    size_t nn = (size_t)s->n_out * 2 * s->cfg.n_e * s->n_cells;
+    size_t nj = (size_t)s->n_out * 2 * (s->n_cells + 1);
+    if (n_out) memcpy(n_out, s->nh, sizeof(uint32_t) * nn);
+    if (J_out) memcpy(J_out, s->Jh, sizeof(int32_t) * nj);
+    if (led) *led = s->led;
+}
+
+void or_tables(const or_sim *s, uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_thr,
+               uint32_t *P0_thr, uint32_t *up_thr, int64_t *inj_counts)
+{
+    const or_config *c = &s->cfg;
+    size_t tab = (size_t)c->n_mat * 2 * c->n_e;
+    if (P_thr) memcpy(P_thr, s->P_thr, sizeof(uint32_t) * tab);
+    if (Q_thr) memcpy(Q_thr, s->Q_thr, sizeof(uint32_t) * tab);
+    if (T_thr) memcpy(T_thr, s->T_thr, sizeof(uint32_t) * (size_t)(c->n_layers - 1) * 4 * c->n_e);
+    if (P0_thr) memcpy(P0_thr, s->P0_thr, sizeof(uint32_t) * c->n_mat);
+    if (up_thr) *up_thr = s->up_thr;
+    if (inj_counts) memcpy(inj_counts, s->inj, sizeof(int64_t) * 2 * (size_t)c->n_steps_max);
+}

@@ -1,0 +1,94 @@
+/*
+ * CPU oracle for the spin-dependent particle-in-cell (PIC) hot-electron
+ * step of Nenno, Rethfeld and Schneider, "Particle-in-cell simulation of
+ * ultrafast hot-carrier transport in Fe/Au heterostructures" (arXiv:1807.04733).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, scalar implementation of
+ * the method, written to be checked against the paper by eye.  It is used by
+ * the test-suite, by the smoke check and by the timed CPU baseline of the
+ * benchmark.  It shares no code, header, table or constant generator with the
+ * CUDA library; the only thing both consume is the input generator module.
+ *
+ * Precision: particle state (z, mu) is float32, as the workload definition
+ * fixes FP32 superparticles; every table (probabilities, thresholds,
+ * injection counts) is derived here in double precision.  Build with
+ * -ffp-contract=off so that no multiply-add is fused.
+ */
+#ifndef PIC_ORACLE_H
+#define PIC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OR_MAX_LAYERS 16
+#define OR_MAX_HITS 8          /* boundary hits per half flight */
+
+/* flags (same bit values as the library's) */
+#define OR_F_DETERMINISTIC   1u
+#define OR_F_NO_SECONDARIES  2u
+#define OR_F_TRANSPARENT     4u
+#define OR_F_LOWEST_BIN_ANY  8u
+#define OR_F_STRICT_CAPACITY 16u
+
+typedef struct {
+    float z;          /* depth, nm */
+    float mu;         /* cos(theta) */
+    uint32_t id;      /* low 32 bits of the carrier id */
+    uint32_t packed;  /* k:8 | spin:1 | layer:4 | gen:8 | id_hi:11 */
+} or_rec;
+
+typedef struct {
+    int32_t n_e;
+    float dt, dz;
+    uint64_t seed;
+    uint32_t stack_index;
+    uint32_t flags;
+    int64_t capacity;
+    int32_t compact_every, moment_every, n_steps_max;
+    int32_t n_layers;
+    int32_t layer_cells[OR_MAX_LAYERS];
+    int32_t layer_mat[OR_MAX_LAYERS];
+    int32_t n_mat;
+    const float *v;        /* [n_mat][2][n_e] */
+    const double *tau_in;  /* [n_mat][2][n_e] */
+    const double *tau_el;  /* [n_mat] */
+    const double *T;       /* [n_layers-1][2][2][n_e] */
+    const double *p0;      /* [n_mat] */
+    int64_t n0;
+    double fwhm, t0, abs_len;
+    uint32_t excite_mask;
+    double up_frac;
+    int32_t e_mode;
+    int32_t k_mono[2];
+} or_config;
+
+typedef struct {
+    uint64_t injected, inject_dropped, spawned, spawn_dropped, absorbed;
+    uint64_t q_injected, q_bath, q_dropped;
+    uint64_t iface_hits, iface_transmit, truncated, particle_steps;
+} or_ledger;
+
+typedef struct or_sim or_sim;
+
+int  or_create(const or_config *cfg, or_sim **out);
+void or_destroy(or_sim *s);
+int  or_step(or_sim *s, int n_steps);             /* 0 ok, 3 capacity (strict) */
+int64_t or_n_slots(const or_sim *s);
+void or_records(const or_sim *s, or_rec *out);     /* n_slots records */
+int  or_set_records(or_sim *s, const or_rec *in, int64_t n, uint64_t next_id);
+void or_moments(const or_sim *s, uint32_t *n_out, int32_t *J_out, or_ledger *led);
+int32_t or_n_cells(const or_sim *s);
+int32_t or_n_out(const or_sim *s);
+int32_t or_step_index(const or_sim *s);
+uint64_t or_next_id(const or_sim *s);
+/* derived tables, for the test that the library derives the same ones */
+void or_tables(const or_sim *s, uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_thr,
+               uint32_t *P0_thr, uint32_t *up_thr, int64_t *inj_counts);
+void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
