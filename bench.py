@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Throughput of the hot-electron PIC step on GB300: particle-steps/s and the
+achieved fraction of the HBM roofline of the step kernel.
+
+Workload (default): the large Fe(15 nm)/Au(300 nm) bilayer, 2e8 carriers
+created by the pump pulse, capacity 4e8, dt = 0.5 fs, 60 energy bins,
+densities every 50 steps, compaction every 50 steps.  Set-up (untimed) runs
+the pulse window (t < 150 fs) so that the timed steps see the steady state.
+One benchmark step = one moment/compaction period of 50 time steps, i.e. one
+pass of every stage of the step (flight, scattering, secondaries, deposit,
+compaction).  The particle state (6.4 GB) is larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+`--impl reference` times the CPU oracle on the host cores on a bounded sample
+of the same workload (same metric and unit).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s"
+UNIT = "particle-steps/s"
+HBM_FALLBACK_GBS = 6800.0
+# algorithmic bytes: read 16 B of state + write z (4 B) per live carrier-step,
+# 8 B (mu, packed) per carrier whose record changed, 16 B per secondary placed
+B_STEP, B_CHANGED, B_SPAWN = 20, 8, 16
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", type=int, default=4)
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--period", type=int, default=0, help="time steps per benchmark step")
+    ap.add_argument("--deterministic", action="store_true")
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--hist-mode", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_1807_04733_gb300 import workloads as W
+    flags = W.FLAG_DETERMINISTIC if args.deterministic else 0
+    wl = W.config(args.config, scale=args.scale, flags=flags)
+    period = args.period if args.period else (wl.moment_every if wl.moment_every > 1 else 50)
+    st = wl.stacks[0]
+    pre = int(math.ceil(2 * st.t0 / wl.dt)) if st.n0 > 0 else 0
+    return wl, period, pre
+
+
+def config_dict(wl, period, pre, args):
+    st = wl.stacks[0]
+    mats = {0: "Fe", 1: "Au", 2: "Fe_AP"}
+    return {
+        "workload": wl.name,
+        "stack": "/".join("%s(%dnm)" % (mats[m], c) for c, m in zip(st.layer_cells, st.layer_mat)),
+        "n0": sum(s.n0 for s in wl.stacks),
+        "capacity": sum(s.capacity for s in wl.stacks),
+        "n_stacks": len(wl.stacks),
+        "dt_fs": wl.dt, "n_e": wl.n_e, "dz_nm": wl.dz,
+        "time_steps_per_step": period,
+        "moment_every": wl.moment_every, "compact_every": wl.compact_every,
+        "pre_roll_time_steps": pre,
+        "build": "deterministic (no FMA)" if args.deterministic else "fast (FMA)",
+        "l2": "inputs larger than L2 (16 B x capacity of particle state)",
+    }
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+# ncu DRAM traffic of one step-kernel launch (read + write bytes per live
+# carrier-step), valid for the kernel source whose hash is given; see
+# profiles/k_step_fe15_au300.md.  None until a capture exists.
+NCU_TRAFFIC = None   # {"bytes_per_particle_step": float, "src_sha": "..."}
+
+
+def kernel_sha():
+    with open(os.path.join(ROOT, "paper_1807_04733_gb300", "csrc", "pic_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%s.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r)
+                          if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# oracle workers (CPU baseline and the reference arm): one process per core,
+# each advancing its own replica of the workload
+# ---------------------------------------------------------------------------
+def _oracle_worker(conn, cfg_index, scale, seed, n_steps_max):
+    from oracle.oracle import OracleSim
+    from paper_1807_04733_gb300 import workloads as W
+    wl = W.config(cfg_index, scale=scale, seed=seed)
+    sim = OracleSim(wl, n_steps_max=n_steps_max)
+    while True:
+        cmd, n = conn.recv()
+        if cmd == "stop":
+            break
+        t = time.perf_counter()
+        rc = sim.step(n)
+        _, _, led = sim.moments()
+        conn.send((rc, led["particle_steps"], time.perf_counter() - t))
+
+
+class OraclePool:
+    def __init__(self, cfg_index, scale, workers, n_steps_max):
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for w in range(workers):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, cfg_index, scale, 1000 + w, n_steps_max),
+                            daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+
+    def step(self, n):
+        """Advance every replica by n time steps; returns the particle-steps done."""
+        for c in self.conns:
+            c.send(("step", n))
+        out = [c.recv() for c in self.conns]
+        if any(rc != 0 for rc, _, _ in out):
+            raise RuntimeError("oracle step failed")
+        total = sum(ps for _, ps, _ in out)
+        done = total - getattr(self, "_total", 0)
+        self._total = total
+        return done
+
+    def close(self):
+        for c in self.conns:
+            c.send(("stop", 0))
+        for p in self.procs:
+            p.join(10)
+
+
+def cpu_sample(args, wl, pre):
+    """Oracle replicas of a scaled copy of the workload on the host cores."""
+    cores = max(1, min(os.cpu_count() or 1, 64))
+    scale = 1e-3 * args.scale if args.config == 4 else 1e-2 * args.scale
+    n_each = max(1, int(round(wl.stacks[0].capacity * scale)))
+    return cores, scale, n_each
+
+
+def run_cpu_baseline(args, wl, period, pre, timed_steps=1):
+    cores, scale, cap_each = cpu_sample(args, wl, pre)
+    pool = OraclePool(args.config, scale, cores, pre + period * (timed_steps + 2) + 1)
+    try:
+        pool.step(pre)                      # pulse window, untimed
+        t = time.perf_counter()
+        ps = 0
+        n_steps = 0
+        while True:                          # timed: whole periods, ~cpu_seconds
+            ps += pool.step(period)
+            n_steps += 1
+            if time.perf_counter() - t > args.cpu_seconds or n_steps >= timed_steps:
+                break
+        dt = time.perf_counter() - t
+    finally:
+        pool.close()
+    sample = ("%d oracle replicas (one per core) of %s scaled by %g (capacity %d each): "
+              "%d pre-roll steps untimed, then %d x %d time steps timed"
+              % (cores, wl.name, scale, cap_each, pre, n_steps, period))
+    return {"value": ps / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl, period, pre = workload(args)
+    cores, scale, cap_each = cpu_sample(args, wl, pre)
+    pool = OraclePool(args.config, scale, cores, pre + period * (args.warmup + args.steps) + 1)
+    try:
+        pool.step(pre)
+        for _ in range(args.warmup):
+            pool.step(period)
+        t = time.perf_counter()
+        ps = 0
+        for _ in range(args.steps):
+            ps += pool.step(period)
+        dt = time.perf_counter() - t
+    finally:
+        pool.close()
+    value = ps / dt
+    sample = ("%d oracle replicas (one per core) of %s scaled by %g (capacity %d each), "
+              "%d pre-roll steps, %d warm-up and %d timed steps of %d time steps"
+              % (cores, wl.name, scale, cap_each, pre, args.warmup, args.steps, period))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config_dict(wl, period, pre, args), "impl": "reference",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_1807_04733_gb300 import pic
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    wl, period, pre = workload(args)
+    # replicas: every rank runs its own copy with its own seed (weak scaling)
+    wl = wl.replace(seed=wl.seed + rank)
+    total = pre + period * (args.warmup + 2 * args.steps) + 1
+    ctx = pic.Context(wl, n_steps_max=max(wl.n_steps, total), blocks_per_sm=args.blocks_per_sm,
+                      hist_mode=args.hist_mode)
+    stream = ctx.stream
+    # set-up: the pulse window (inputs resident in HBM before timing)
+    left = pre
+    while left > 0:
+        n = min(left, 100)
+        ctx.step(n)
+        left -= n
+    for _ in range(args.warmup):
+        ctx.step(period)
+    led0 = [ctx.ledger(s) for s in range(len(wl.stacks))]
+
+    # ---- device-timed region ----
+    try:
+        clk = Clocks("GPU-" + str(torch.cuda.get_device_properties(dev).uuid).replace("GPU-", ""))
+    except Exception:
+        clk = Clocks(str(dev))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    pic.pic_profile(ctx.ctx, True)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    launches = 0
+    for _ in range(args.steps):
+        ctx.step(period)
+        launches += ctx.launches
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    ktimes = pic.pic_profile_read(ctx.ctx)
+    pic.pic_profile(ctx.ctx, False)
+    led1 = [ctx.ledger(s) for s in range(len(wl.stacks))]
+    if dist is not None:
+        dist.barrier()
+    delta = {k: sum(b[k] - a[k] for a, b in zip(led0, led1)) for k in led1[0]}
+    ps = delta["particle_steps"]
+
+    # ---- end-to-end region: the public API with host read-back per step ----
+    nc, no, _ = ctx.shape(0)
+    n_dev = torch.empty((no, 2, wl.n_e, nc), dtype=torch.int32, device="cuda")
+    J_dev = torch.empty((no, 2, nc + 1), dtype=torch.int32, device="cuda")
+    n_host = torch.empty((2, wl.n_e, nc), dtype=torch.int32, pin_memory=True)
+    J_host = torch.empty((2, nc + 1), dtype=torch.int32, pin_memory=True)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    ps_e2e = 0
+    for _ in range(args.steps):
+        ctx.step(period)
+        led = pic.pic_moments(ctx.ctx, 0, n_dev.data_ptr(), J_dev.data_ptr())
+        w = ctx.shape(0)[2] // wl.moment_every - 1
+        n_host.copy_(n_dev[w], non_blocking=True)
+        J_host.copy_(J_dev[w], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        ps_e2e = led["particle_steps"]
+    e2e_s = time.perf_counter() - t
+    ps_e2e -= led1[0]["particle_steps"]
+    d2h = n_host.numel() * 4 + J_host.numel() * 4 + 13 * 8
+
+    # ---- reductions over ranks ----
+    vals = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device="cuda")
+    cnts = torch.tensor([ps, ps_e2e], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
+        dist.all_reduce(cnts, op=dist.ReduceOp.SUM)
+    ms_max, e2e_ms = float(vals[0]), float(vals[1])
+    ps_all, ps_e2e_all = float(cnts[0]), float(cnts[1])
+
+    peak, peak_kind = measured_peak()
+    n_k = ktimes["step"][0] + ktimes["step_moments"][0]
+    k_ms = ktimes["step"][1] + ktimes["step_moments"][1]
+    alg_bytes = B_STEP * delta["particle_steps"] + B_CHANGED * delta["changed"] + \
+        B_SPAWN * delta["spawned"]
+    achieved = (alg_bytes / n_k) / (k_ms / n_k * 1e-3) / 1e9 if n_k else 0.0
+    traffic = None
+    if NCU_TRAFFIC and NCU_TRAFFIC.get("src_sha") == kernel_sha():
+        traffic = NCU_TRAFFIC["bytes_per_particle_step"] * delta["particle_steps"] / n_k
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_step",
+                "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg_bytes / n_k if n_k else 0,
+                "avg_launch_ms": k_ms / n_k if n_k else 0,
+                "kernel_share_of_step_time": k_ms / ms if ms else 0}
+
+    line = {
+        "metric": METRIC, "value": ps_all / (ms_max * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(wl, period, pre, args),
+        "roofline": roofline,
+        "e2e": {"value": ps_e2e_all / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "ledger_delta": delta,
+        "kernel_ms": {k: v[1] for k, v in ktimes.items()},
+        "kernel_launches": {k: v[0] for k, v in ktimes.items()},
+    }
+    ctx.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = run_cpu_baseline(args, wl, period, pre, timed_steps=60)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,249 @@
+/*
+ * pic.h - C-ABI of the GB300 (sm_103a) hot-electron particle-in-cell step.
+ *
+ * The library advances the superparticle representation of the 1-D
+ * spin-dependent hot-electron Boltzmann equation of Nenno, Rethfeld and
+ * Schneider (arXiv:1807.04733), Eq. bte2 (Sec. II), with the PIC method of
+ * Eq. PIC and the Strang splitting of Eq. strang (Sec. III.A):
+ *
+ *   Source(dt/2) -> Transport(dt/2) -> Scattering(dt) -> Transport(dt/2)
+ *   -> Source(dt/2)
+ *
+ * Each superparticle carries depth z (nm), direction cosine mu, energy bin k
+ * (E_k = k dE above E_F), spin sigma, layer index and generation.  All
+ * device work runs in hand-written CUDA kernels on the stream given to
+ * pic_init.  PyTorch (or any caller) provides only memory and streams.
+ *
+ * Conventions for every call:
+ *   - Every call returns a pic_status; no call aborts or exits.
+ *   - "host" pointers are ordinary CPU memory, "device" pointers are CUDA
+ *     device memory of the current device (e.g. torch.Tensor.data_ptr()).
+ *   - The caller owns every buffer it passes; the library copies the tables
+ *     at pic_init and owns the particle state, histograms and scratch.
+ *   - Device-side faults (capacity overflow in strict mode, a bounded wait
+ *     that ran out) set a status word on the device; it is returned by the
+ *     next synchronising call (pic_moments, pic_records, pic_sync, pic_grad).
+ *   - A context is not thread-safe; calls on one context must be serialised.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_MAX_LAYERS 16   /* layers per stack */
+#define PIC_MAX_MAT 8       /* materials per table set */
+#define PIC_MAX_NE 255      /* energy bins */
+#define PIC_MAX_STACKS 256  /* stacks per context */
+#define PIC_MAX_HITS 8      /* boundary hits handled per half flight */
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,       /* invalid argument; nothing was changed */
+    PIC_ERR_ALLOC = 2,     /* device or host allocation failed */
+    PIC_ERR_CAPACITY = 3,  /* strict capacity mode: a carrier did not fit */
+    PIC_ERR_TIMEOUT = 4,   /* a bounded device wait ran out; results invalid */
+    PIC_ERR_CUDA = 5,      /* a CUDA runtime call failed (see pic_last_error) */
+    PIC_ERR_STATE = 6      /* call not valid in the current state */
+} pic_status;
+
+/* pic_params.flags */
+#define PIC_F_DETERMINISTIC   1u  /* no fused multiply-add in the flight: the
+                                     particle records are bit-identical to a
+                                     scalar IEEE float32 evaluation */
+#define PIC_F_NO_SECONDARIES  2u  /* Sec. V.A variant (3): inelastic events do
+                                     not create a secondary carrier */
+#define PIC_F_TRANSPARENT     4u  /* Sec. V.A variant (2): T = 1 everywhere */
+#define PIC_F_LOWEST_BIN_ANY  8u  /* remove a lowest-bin carrier on any
+                                     scattering event (default: inelastic only) */
+#define PIC_F_STRICT_CAPACITY 16u /* overflow is PIC_ERR_CAPACITY instead of
+                                     drop-and-count */
+
+/* Global parameters of a context. */
+typedef struct {
+    int32_t n_e;            /* energy bins, 1..PIC_MAX_NE; E_k = k*dE, k=1..n_e */
+    float dt;               /* time step, fs (> 0); Strang step of Eq. strang */
+    float dz;               /* moment cell width, nm (> 0); layer thicknesses
+                               are whole cells */
+    uint64_t seed;          /* Philox4x32-10 key */
+    uint32_t flags;         /* PIC_F_* */
+    int32_t compact_every;  /* stable removal of dead slots every N steps (>= 1) */
+    int32_t moment_every;   /* density snapshot every N steps (>= 1); the flux
+                               is accumulated over the same windows */
+    int32_t n_steps_max;    /* steps this context may run; sizes the moment
+                               buffers: n_out = ceil(n_steps_max/moment_every) */
+    int32_t blocks_per_sm;  /* persistent blocks per SM for the step kernel;
+                               0 = as many as fit */
+    int32_t hist_mode;      /* density deposit: 0 = shared-memory atomics,
+                               1 = warp-aggregated (match-any) atomics */
+} pic_params;
+
+/* One laterally homogeneous layer stack (Sec. II: 1-D transport along z).
+ * Layer l spans [sum_{j<l} cells_j, sum_{j<=l} cells_j) * dz; the outer
+ * surfaces z = 0 and z = L are vacuum (full reflection, Sec. III). */
+typedef struct {
+    int32_t n_layers;                       /* 1..PIC_MAX_LAYERS */
+    int32_t layer_cells[PIC_MAX_LAYERS];    /* thickness in cells (>= 1) */
+    int32_t layer_mat[PIC_MAX_LAYERS];      /* index into the material tables */
+    int64_t capacity;                       /* particle slots, < 2^30 */
+} pic_stack_desc;
+
+/* Physical tables of one stack (host pointers; copied by pic_init).
+ * The shapes follow the paper's Fig. 1 quantities; index order is
+ * [material][spin][k-1] with spin 0 = majority (up), 1 = minority (down). */
+typedef struct {
+    int32_t n_mat;          /* 1..PIC_MAX_MAT */
+    const float *v;         /* [n_mat][2][n_e] group velocity, nm/fs (> 0) */
+    const double *tau_in;   /* [n_mat][2][n_e] inelastic lifetime, fs; +inf = none */
+    const double *tau_el;   /* [n_mat] elastic lifetime, fs; +inf = none */
+    const double *T;        /* [n_layers-1][2 dir][2 spin][n_e] interface
+                               transmittance in [0,1]; dir 0 = towards +z
+                               (layer l -> l+1), dir 1 = towards -z */
+    const double *p0;       /* [n_mat] equilibrium polarisation P0 of Eq. eq_pol,
+                               in [-1,1]; spin of secondary carriers */
+} pic_tables;
+
+/* Excitation pulse of one stack (Sec. III, particle number; Sec. V.A). */
+typedef struct {
+    int64_t n0;             /* carriers created over the pulse (>= 0) */
+    double fwhm;            /* Gaussian FWHM, fs (> 0 when n0 > 0) */
+    double t0;              /* pulse centre, fs (> 0); the pulse is truncated
+                               symmetrically to [0, 2 t0] */
+    double abs_len;         /* absorption length, nm: profile exp(-z/abs_len);
+                               0 = homogeneous in the excited layers */
+    uint32_t excite_mask;   /* bit l set: layer l is excited */
+    double up_frac;         /* probability that a created carrier is spin up */
+    int32_t e_mode;         /* 0: k uniform on 1..n_e; 1: k = k_mono[spin] */
+    int32_t k_mono[2];      /* bins for e_mode 1 */
+} pic_pulse;
+
+/* Device-resident bookkeeping, per stack (exact integer counts). */
+typedef struct {
+    uint64_t injected, inject_dropped, spawned, spawn_dropped, absorbed;
+    uint64_t q_injected;    /* energy quanta (bins) created by the source */
+    uint64_t q_bath;        /* quanta handed to the thermal bath (removal,
+                               or the secondary's share without secondaries) */
+    uint64_t q_dropped;     /* quanta of secondaries dropped at capacity */
+    uint64_t iface_hits, iface_transmit, truncated;
+    uint64_t particle_steps;/* live carriers advanced, summed over steps */
+    uint64_t changed;       /* advanced carriers whose direction, energy, spin,
+                               layer or liveness changed (records rewritten) */
+} pic_ledger;
+
+/* Device time of the library's kernels, per kind: 0 = source, 1 = step,
+ * 2 = step with density deposit, 3 = compaction. */
+typedef struct {
+    int64_t launches[4];
+    double ms[4];
+} pic_kernel_times;
+
+/* One particle slot as returned by pic_records (16 bytes). */
+typedef struct {
+    float z;
+    float mu;
+    uint32_t id;            /* low 32 bits of the carrier id */
+    uint32_t packed;        /* k:8 | spin:1 | layer:4 | gen:8 | id_hi:11;
+                               k = 0 marks a removed carrier */
+} pic_record;
+
+typedef struct pic_ctx pic_ctx;
+
+/* Create a context with n_stacks independent stacks, each with its own
+ * tables (tables[n_stacks]).  Derives every probability threshold on the
+ * host in double precision, allocates the particle state (double-buffered
+ * structure of arrays), histograms and scratch on the current CUDA device,
+ * and uploads the tables.  cuda_stream is a cudaStream_t (NULL = legacy
+ * default stream); all later device work of the context is ordered on it.
+ * On error *out is NULL and nothing stays allocated. */
+pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *stacks,
+                    int n_stacks, const pic_tables *tables, void *cuda_stream);
+
+/* Set the excitation of one stack (Sec. III, "Number of Particles"): the
+ * source creates floor(n0 F(t_{h+1})) - floor(n0 F(t_h)) carriers in half
+ * step h, F the normalised pulse CDF; positions follow the absorption
+ * profile over the excited layers' cells, directions are isotropic.
+ * Host-side only (uploads a schedule); call before stepping through the
+ * pulse.  stack = -1 applies the same pulse to every stack. */
+pic_status pic_excite(pic_ctx *ctx, int stack, const pic_pulse *pulse);
+
+/* Advance every stack by n_steps Strang steps (Eq. strang).  Asynchronous
+ * on the context stream; returns PIC_ERR_ARG if the steps would exceed
+ * n_steps_max. */
+pic_status pic_step(pic_ctx *ctx, int n_steps);
+
+/* Moments of one stack (Eq. firstmoment).  n_dev (device, may be NULL):
+ * uint32 [n_out][2][n_e][n_cells] live carriers per (spin, bin, cell) at
+ * the end of each moment window.  J_dev (device, may be NULL): int32
+ * [n_out][2][n_cells+1] net number of carriers of each spin that crossed
+ * each cell face towards +z during the window (the time-integrated spin
+ * flux; face f sits at z = f*dz).  ledger_host (host, may be NULL).
+ * Synchronises the context stream; returns any pending device status. */
+pic_status pic_moments(pic_ctx *ctx, int stack, uint32_t *n_dev, int32_t *J_dev,
+                       pic_ledger *ledger_host);
+
+/* Score-function (likelihood-ratio) gradient of a linear functional of the
+ * moments with respect to the lifetime and transmittance tables of every
+ * stack.  grad_n_dev: float [n_stacks][n_out][2][n_e][n_cells_max] weights
+ * of the densities; grad_J_dev: float [n_stacks][n_out][2][n_cells_max+1]
+ * weights of the fluxes (either may be NULL = zero).  Outputs (device,
+ * double, overwritten): grad_tau_dev [n_stacks][n_mat][2][n_e] (d/d tau_in),
+ * grad_T_dev [n_stacks][PIC_MAX_LAYERS-1][2][2][n_e] (d/d T).  Replays the
+ * forward trajectories from the Philox counters; the forward pass stores
+ * nothing.  Requires a context that was stepped from an empty or loaded
+ * initial state with no intervening pic_set_records. */
+pic_status pic_grad(pic_ctx *ctx, const float *grad_n_dev, const float *grad_J_dev,
+                    double *grad_tau_dev, double *grad_T_dev);
+
+/* Copy the particle slots of one stack to host memory.  If host_out is NULL
+ * only the slot count is written to *n.  Synchronises. */
+pic_status pic_records(pic_ctx *ctx, int stack, pic_record *host_out, int64_t *n);
+
+/* Replace the particle slots of one stack (test set-up and resume from a
+ * saved state).  next_id is the id given to the next created carrier. */
+pic_status pic_set_records(pic_ctx *ctx, int stack, const pic_record *host_in,
+                           int64_t n, uint64_t next_id);
+
+/* Wait for the context stream and return the pending device status. */
+pic_status pic_sync(pic_ctx *ctx);
+
+/* Host-only (no device work): the integer tables pic_init and pic_excite
+ * derive for one stack.  P_thr, Q_thr: uint32 [n_mat][2][n_e]; T_thr:
+ * uint32 [n_layers-1][2][2][n_e]; P0_thr: uint32 [n_mat]; up_thr: uint32;
+ * inj_counts: int64 [2*n_steps_max] carriers created per half step.  Any
+ * output pointer may be NULL. */
+pic_status pic_derive_tables(const pic_params *p, const pic_stack_desc *stack,
+                             const pic_tables *tables, const pic_pulse *pulse,
+                             uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_thr,
+                             uint32_t *P0_thr, uint32_t *up_thr, int64_t *inj_counts);
+
+/* Sizes of one stack's outputs. */
+pic_status pic_shape(const pic_ctx *ctx, int stack, int32_t *n_cells, int32_t *n_out,
+                     int32_t *step);
+
+/* Start (enable = 1) or stop (0) recording CUDA events around every kernel
+ * launch on the context stream; starting clears earlier records. */
+pic_status pic_profile(pic_ctx *ctx, int enable);
+
+/* Sum the recorded kernel times (synchronises). */
+pic_status pic_profile_read(pic_ctx *ctx, pic_kernel_times *out);
+
+/* Device kernels launched by the last pic_step call (for accounting). */
+int64_t pic_launch_count(const pic_ctx *ctx);
+
+/* Free every resource of the context (NULL is allowed). */
+void pic_destroy(pic_ctx *ctx);
+
+/* Text of the last error on this context (never NULL). */
+const char *pic_last_error(const pic_ctx *ctx);
+
+/* Name of a status code. */
+const char *pic_status_string(pic_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIC_H */

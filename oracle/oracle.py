@@ -60,7 +60,7 @@ class Ledger(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "injected", "inject_dropped", "spawned", "spawn_dropped", "absorbed",
         "q_injected", "q_bath", "q_dropped", "iface_hits", "iface_transmit",
-        "truncated", "particle_steps")]
+        "truncated", "particle_steps", "changed")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}
@@ -84,6 +84,7 @@ def lib():
         L.or_n_cells.argtypes = [P]; L.or_n_cells.restype = C.c_int32
         L.or_n_out.argtypes = [P]; L.or_n_out.restype = C.c_int32
         L.or_step_index.argtypes = [P]; L.or_step_index.restype = C.c_int32
+        L.or_set_step.argtypes = [P, C.c_int32]
         L.or_next_id.argtypes = [P]; L.or_next_id.restype = C.c_uint64
         L.or_tables.argtypes = [P, P, P, P, P, P, P]
         L.or_philox4x32_10.argtypes = [P, P, P]
@@ -174,6 +175,9 @@ class OracleSim:
         led = Ledger()
         lib().or_moments(self.h, n.ctypes.data, J.ctypes.data, C.byref(led))
         return n, J, led.as_dict()
+
+    def set_step(self, step: int):
+        lib().or_set_step(self.h, step)
 
     @property
     def step_index(self) -> int:

@@ -273,6 +273,8 @@ static void step_once(or_sim *s)
         if (PK_K(p->packed) == 0) continue;
         s->led.particle_steps++;
         uint64_t id = (uint64_t)p->id | ((uint64_t)PK_E(p->packed) << 32);
+        const float mu_in = p->mu;
+        const uint32_t pk_in = p->packed;
         int c_start = cell_of(s, p->z);
         int sg = (int)PK_S(p->packed);
 
@@ -289,6 +291,7 @@ static void step_once(or_sim *s)
             if (k == 1 && (inel || (c->flags & OR_F_LOWEST_BIN_ANY))) {
                 absorb(s, p);
                 flux(s, sg, c_start, cell_of(s, p->z));
+                s->led.changed++;
                 continue;
             }
             p->mu = mu_from(x[2]);
@@ -311,6 +314,9 @@ static void step_once(or_sim *s)
                     q.id = 0;
                     q.packed = pk(ks, sgs, (uint32_t)layer, g < 255u ? g + 1u : 255u, 0u);
                     int cs = cell_of(s, q.z);
+                    /* boundary events are counted for carriers that exist
+                     * after the step: a dropped secondary's are taken back */
+                    or_ledger keep = s->led;
                     half_flight(s, &q, half, id, SUB_SIF);
                     if (s->n_slots < c->capacity) {
                         uint64_t nid = s->next_id++;
@@ -320,6 +326,9 @@ static void step_once(or_sim *s)
                         s->led.spawned++;
                         flux(s, (int)sgs, cs, cell_of(s, q.z));
                     } else {
+                        s->led.iface_hits = keep.iface_hits;
+                        s->led.iface_transmit = keep.iface_transmit;
+                        s->led.truncated = keep.truncated;
                         s->led.spawn_dropped++;
                         s->led.q_dropped += ks;
                         if (c->flags & OR_F_STRICT_CAPACITY) s->err = 3;
@@ -330,6 +339,7 @@ static void step_once(or_sim *s)
 
         half_flight(s, p, half, id, SUB_IF + 16);
         flux(s, sg, c_start, cell_of(s, p->z));
+        if (p->mu != mu_in || p->packed != pk_in) s->led.changed++;
     }
     inject(s, 1);
 
@@ -476,6 +486,7 @@ int64_t or_n_slots(const or_sim *s) { return s->n_slots; }
 int32_t or_n_cells(const or_sim *s) { return s->n_cells; }
 int32_t or_n_out(const or_sim *s) { return s->n_out; }
 int32_t or_step_index(const or_sim *s) { return (int32_t)s->step; }
+void or_set_step(or_sim *s, int32_t step) { s->step = (uint32_t)step; }
 uint64_t or_next_id(const or_sim *s) { return s->next_id; }
 
 void or_records(const or_sim *s, or_rec *out)

@@ -68,6 +68,7 @@ typedef struct {
     uint64_t injected, inject_dropped, spawned, spawn_dropped, absorbed;
     uint64_t q_injected, q_bath, q_dropped;
     uint64_t iface_hits, iface_transmit, truncated, particle_steps;
+    uint64_t changed;     /* advanced carriers whose mu or packed word changed */
 } or_ledger;
 
 typedef struct or_sim or_sim;
@@ -82,6 +83,7 @@ void or_moments(const or_sim *s, uint32_t *n_out, int32_t *J_out, or_ledger *led
 int32_t or_n_cells(const or_sim *s);
 int32_t or_n_out(const or_sim *s);
 int32_t or_step_index(const or_sim *s);
+void or_set_step(or_sim *s, int32_t step);          /* position in time (Philox counter) */
 uint64_t or_next_id(const or_sim *s);
 /* derived tables, for the test that the library derives the same ones */
 void or_tables(const or_sim *s, uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_thr,

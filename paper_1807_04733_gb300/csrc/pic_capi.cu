@@ -1,0 +1,733 @@
+// C-ABI of the GB300 hot-electron PIC library (declared in include/pic.h).
+//
+// Host responsibilities: argument checks, derivation of every probability
+// threshold in double precision (no transcendental function runs on the
+// device), allocation of the HBM state, and the per-step kernel sequence of
+// the Strang splitting (Eq. strang, Sec. III.A).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pic_internal.h"
+
+using namespace pic;
+
+struct HostStack {
+    pic_stack_desc d;
+    int n_cells = 0, n_out = 0;
+    int64_t base = 0, cap_round = 0;
+    std::vector<float> v;           // [n_mat][2][n_e]
+    std::vector<double> tau_in, tau_el, T, p0;
+    int n_mat = 0;
+    std::vector<uint32_t> P_thr, Q_thr, T_thr, P0_thr;   // material-indexed
+    std::vector<long long> inj;     // per half step
+    pic_pulse pulse{};
+    bool excited = false;
+};
+
+struct pic_ctx {
+    pic_params p{};
+    int n_stacks = 0;
+    std::vector<HostStack> hs;
+    std::vector<DevStack> ds;
+    cudaStream_t stream = nullptr;
+    // device memory
+    DevStack *d_stacks = nullptr;
+    TabEnt *d_ent = nullptr;
+    uint32_t *d_T = nullptr, *d_cdf_thr = nullptr;
+    int32_t *d_cdf_cell = nullptr, *d_cdf_layer = nullptr;
+    long long *d_inj = nullptr;
+    float *d_z[2] = {nullptr, nullptr}, *d_mu[2] = {nullptr, nullptr};
+    uint32_t *d_id[2] = {nullptr, nullptr}, *d_pk[2] = {nullptr, nullptr};
+    float4 *d_stage = nullptr;
+    unsigned long long *d_status = nullptr;
+    uint32_t *d_nh = nullptr;
+    int32_t *d_J = nullptr;
+    DevCounters *d_cnt = nullptr;
+    DevCtl *d_ctl = nullptr;
+    int64_t total_slots = 0, nh_total = 0, J_total = 0;
+    Args args{};
+    LaunchCfg lc{};
+    int step = 0;
+    int64_t launches = 0;
+    std::string err;
+    // kernel timing (pic_profile)
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, size_t>> ev_marks;   // (kind, index of start event)
+    size_t ev_used = 0;
+};
+
+namespace {
+
+thread_local std::string g_init_error;   // reason of the last failed pic_init
+
+const char *kStatusNames[] = {"PIC_OK", "PIC_ERR_ARG", "PIC_ERR_ALLOC", "PIC_ERR_CAPACITY",
+                              "PIC_ERR_TIMEOUT", "PIC_ERR_CUDA", "PIC_ERR_STATE"};
+
+// floor(p * 2^32) saturated to [0, 2^32-1]: "x < threshold" with a uniform
+// 32-bit word x happens with probability threshold / 2^32.
+uint32_t threshold_of(double p)
+{
+    if (!(p > 0.0)) return 0u;
+    if (p >= 1.0) return 0xFFFFFFFFu;
+    const double scaled = std::floor(p * 4294967296.0);
+    return scaled >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)scaled;
+}
+
+pic_status fail(pic_ctx *c, pic_status s, const std::string &msg)
+{
+    if (c) c->err = msg;
+    return s;
+}
+
+pic_status cuda_fail(pic_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool valid_params(const pic_params *p, std::string &why)
+{
+    if (!p) { why = "params is NULL"; return false; }
+    if (p->n_e < 1 || p->n_e > PIC_MAX_NE) { why = "n_e out of range"; return false; }
+    if (!(p->dt > 0.f) || !std::isfinite(p->dt)) { why = "dt must be > 0"; return false; }
+    if (!(p->dz > 0.f) || !std::isfinite(p->dz)) { why = "dz must be > 0"; return false; }
+    if (p->compact_every < 1 || p->moment_every < 1) { why = "compact_every/moment_every < 1"; return false; }
+    if (p->n_steps_max < 0) { why = "n_steps_max < 0"; return false; }
+    if (p->hist_mode < 0 || p->hist_mode > 1) { why = "hist_mode must be 0 or 1"; return false; }
+    if (p->blocks_per_sm < 0) { why = "blocks_per_sm < 0"; return false; }
+    return true;
+}
+
+bool valid_stack(const pic_params *p, const pic_stack_desc *s, const pic_tables *t, std::string &why)
+{
+    if (!s || !t) { why = "stack or tables is NULL"; return false; }
+    if (s->n_layers < 1 || s->n_layers > PIC_MAX_LAYERS) { why = "n_layers out of range"; return false; }
+    if (s->capacity < 0 || s->capacity >= (1ll << 30)) { why = "capacity must be in [0, 2^30)"; return false; }
+    if (t->n_mat < 1 || t->n_mat > PIC_MAX_MAT) { why = "n_mat out of range"; return false; }
+    if (!t->v || !t->tau_in || !t->tau_el || !t->p0 || (s->n_layers > 1 && !t->T)) {
+        why = "a table pointer is NULL"; return false;
+    }
+    int64_t cells = 0;
+    for (int l = 0; l < s->n_layers; ++l) {
+        if (s->layer_cells[l] < 1) { why = "layer thickness must be >= 1 cell"; return false; }
+        if (s->layer_mat[l] < 0 || s->layer_mat[l] >= t->n_mat) { why = "layer material out of range"; return false; }
+        cells += s->layer_cells[l];
+    }
+    if (cells > (1 << 20)) { why = "too many cells"; return false; }
+    const int ne = p->n_e;
+    for (int i = 0; i < t->n_mat * 2 * ne; ++i) {
+        if (!(t->v[i] > 0.f) || !std::isfinite(t->v[i])) { why = "v must be finite and > 0"; return false; }
+        if (!(t->tau_in[i] > 0.0)) { why = "tau_in must be > 0"; return false; }
+    }
+    for (int m = 0; m < t->n_mat; ++m) {
+        if (!(t->tau_el[m] > 0.0)) { why = "tau_el must be > 0"; return false; }
+        if (!(t->p0[m] >= -1.0 && t->p0[m] <= 1.0)) { why = "p0 must be in [-1,1]"; return false; }
+    }
+    for (int i = 0; i < (s->n_layers - 1) * 4 * ne; ++i)
+        if (!(t->T[i] >= 0.0 && t->T[i] <= 1.0)) { why = "T must be in [0,1]"; return false; }
+    return true;
+}
+
+// Thresholds of one material table set: scatter within dt with probability
+// p = 1 - exp(-dt (1/tau_el + 1/tau_in)) (Eq. lifetimes, Sec. III); the event
+// is inelastic with probability (1/tau_in) / (1/tau_el + 1/tau_in) (competing
+// rates, Eq. split_w); secondary spin up with probability (1 + P0)/2 (Eq. eq_pol).
+void material_thresholds(const pic_params &p, const pic_stack_desc &s, const pic_tables &t,
+                         std::vector<uint32_t> &P, std::vector<uint32_t> &Q,
+                         std::vector<uint32_t> &T, std::vector<uint32_t> &P0)
+{
+    const int ne = p.n_e, nm = t.n_mat;
+    P.assign((size_t)nm * 2 * ne, 0u);
+    Q.assign((size_t)nm * 2 * ne, 0u);
+    for (int m = 0; m < nm; ++m) {
+        const double rate_el = std::isinf(t.tau_el[m]) ? 0.0 : 1.0 / t.tau_el[m];
+        for (int sp = 0; sp < 2; ++sp)
+            for (int k = 0; k < ne; ++k) {
+                const size_t i = ((size_t)m * 2 + sp) * ne + k;
+                const double rate_in = std::isinf(t.tau_in[i]) ? 0.0 : 1.0 / t.tau_in[i];
+                const double rate = rate_el + rate_in;
+                P[i] = threshold_of(-std::expm1(-((double)p.dt * rate)));
+                Q[i] = threshold_of(rate > 0.0 ? rate_in / rate : 0.0);
+            }
+    }
+    const size_t nT = (size_t)(s.n_layers - 1) * 4 * ne;
+    T.resize(nT);
+    for (size_t i = 0; i < nT; ++i) T[i] = threshold_of(t.T[i]);
+    P0.resize(nm);
+    for (int m = 0; m < nm; ++m) P0[m] = threshold_of((1.0 + t.p0[m]) / 2.0);
+}
+
+double std_normal_cdf(double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); }
+
+// Fraction of the pulse delivered by time t: a Gaussian of the given FWHM
+// centred at t0, truncated to [0, 2 t0] and renormalised.
+double pulse_fraction(const pic_pulse &u, double t)
+{
+    if (t <= 0.0) return 0.0;
+    if (t >= 2.0 * u.t0) return 1.0;
+    const double sd = u.fwhm / (2.0 * std::sqrt(2.0 * std::log(2.0)));
+    const double lo = std_normal_cdf(-u.t0 / sd), hi = std_normal_cdf(u.t0 / sd);
+    return (std_normal_cdf((t - u.t0) / sd) - lo) / (hi - lo);
+}
+
+// Source schedule and depth profile of one stack.
+void source_tables(const pic_params &p, const pic_stack_desc &s, const pic_pulse &u,
+                   std::vector<uint32_t> &thr, std::vector<int32_t> &cell,
+                   std::vector<int32_t> &layer, std::vector<long long> &inj)
+{
+    thr.clear(); cell.clear(); layer.clear();
+    std::vector<double> mass;
+    double total = 0.0;
+    int c = 0;
+    for (int l = 0; l < s.n_layers; ++l)
+        for (int j = 0; j < s.layer_cells[l]; ++j, ++c) {
+            if (!((u.excite_mask >> l) & 1u)) continue;
+            const double z0 = (double)c * p.dz, w = p.dz;
+            const double m = u.abs_len > 0.0
+                                 ? u.abs_len * (std::exp(-z0 / u.abs_len) - std::exp(-(z0 + w) / u.abs_len))
+                                 : w;
+            mass.push_back(m); cell.push_back(c); layer.push_back(l);
+            total += m;
+        }
+    double run = 0.0;
+    for (size_t i = 0; i < mass.size(); ++i) {
+        run += mass[i];
+        thr.push_back(i + 1 == mass.size() ? 0xFFFFFFFFu : threshold_of(run / total));
+    }
+    const int64_t nh = 2 * (int64_t)p.n_steps_max;
+    inj.assign((size_t)nh, 0);
+    if (u.n0 <= 0 || mass.empty()) return;
+    const double n0 = (double)u.n0;
+    for (int64_t h = 0; h < nh; ++h) {
+        const double ta = (double)h * 0.5 * (double)p.dt, tb = (double)(h + 1) * 0.5 * (double)p.dt;
+        inj[h] = (long long)std::floor(n0 * pulse_fraction(u, tb)) -
+                 (long long)std::floor(n0 * pulse_fraction(u, ta));
+    }
+}
+
+bool valid_pulse(const pic_pulse *u, int n_layers, int n_e, std::string &why)
+{
+    if (!u) { why = "pulse is NULL"; return false; }
+    if (u->n0 < 0) { why = "n0 < 0"; return false; }
+    if (u->n0 > 0 && !(u->fwhm > 0.0 && u->t0 > 0.0)) { why = "fwhm and t0 must be > 0"; return false; }
+    if (!(u->abs_len >= 0.0)) { why = "abs_len < 0"; return false; }
+    if (!(u->up_frac >= 0.0 && u->up_frac <= 1.0)) { why = "up_frac not in [0,1]"; return false; }
+    if (u->e_mode != 0 && u->e_mode != 1) { why = "e_mode must be 0 or 1"; return false; }
+    if (u->e_mode == 1 && (u->k_mono[0] < 1 || u->k_mono[0] > n_e || u->k_mono[1] < 1 || u->k_mono[1] > n_e)) {
+        why = "k_mono out of range"; return false;
+    }
+    if (u->n0 > 0 && (u->excite_mask & ((1u << n_layers) - 1u)) == 0) { why = "no excited layer"; return false; }
+    return true;
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t n)
+{
+    return cudaMalloc((void **)p, sizeof(T) * (n ? n : 1));
+}
+
+void free_all(pic_ctx *c)
+{
+    cudaFree(c->d_stacks); cudaFree(c->d_ent); cudaFree(c->d_T); cudaFree(c->d_cdf_thr);
+    cudaFree(c->d_cdf_cell); cudaFree(c->d_cdf_layer); cudaFree(c->d_inj);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->d_z[b]); cudaFree(c->d_mu[b]); cudaFree(c->d_id[b]); cudaFree(c->d_pk[b]);
+    }
+    cudaFree(c->d_stage); cudaFree(c->d_status); cudaFree(c->d_nh); cudaFree(c->d_J);
+    cudaFree(c->d_cnt); cudaFree(c->d_ctl); cudaFree(c->d_status);
+}
+
+// Launch one kernel through `fn`, bracketed by events when profiling.
+template <class F>
+cudaError_t timed(pic_ctx *c, int kind, F fn)
+{
+    if (!c->profiling) return fn();
+    while (c->ev_used + 2 > c->ev_pool.size()) {
+        cudaEvent_t ev;
+        const cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) return e;
+        c->ev_pool.push_back(ev);
+    }
+    const size_t i = c->ev_used;
+    cudaError_t e = cudaEventRecord(c->ev_pool[i], c->stream);
+    if (e == cudaSuccess) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_pool[i + 1], c->stream);
+    if (e == cudaSuccess) {
+        c->ev_marks.push_back({kind, i});
+        c->ev_used += 2;
+    }
+    return e;
+}
+
+pic_status device_status(pic_ctx *c)
+{
+    DevCtl h{};
+    cudaError_t e = cudaMemcpyAsync(&h, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "device status");
+    if (h.status != 0) {
+        const pic_status s = (pic_status)h.status;
+        return fail(c, s, s == PIC_ERR_TIMEOUT ? "a bounded device wait ran out"
+                                               : "capacity exceeded in strict mode");
+    }
+    return PIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *pic_status_string(pic_status s)
+{
+    return (s >= 0 && s <= PIC_ERR_STATE) ? kStatusNames[s] : "PIC_UNKNOWN";
+}
+
+const char *pic_last_error(const pic_ctx *ctx)
+{
+    if (ctx) return ctx->err.c_str();
+    return g_init_error.empty() ? "no context" : g_init_error.c_str();
+}
+
+pic_status pic_derive_tables(const pic_params *p, const pic_stack_desc *stack,
+                             const pic_tables *tables, const pic_pulse *pulse, uint32_t *P_thr,
+                             uint32_t *Q_thr, uint32_t *T_thr, uint32_t *P0_thr, uint32_t *up_thr,
+                             int64_t *inj_counts)
+{
+    std::string why;
+    if (!valid_params(p, why) || !valid_stack(p, stack, tables, why)) return PIC_ERR_ARG;
+    std::vector<uint32_t> P, Q, T, P0;
+    material_thresholds(*p, *stack, *tables, P, Q, T, P0);
+    if (P_thr) std::memcpy(P_thr, P.data(), P.size() * 4);
+    if (Q_thr) std::memcpy(Q_thr, Q.data(), Q.size() * 4);
+    if (T_thr && !T.empty()) std::memcpy(T_thr, T.data(), T.size() * 4);
+    if (P0_thr) std::memcpy(P0_thr, P0.data(), P0.size() * 4);
+    if (pulse) {
+        if (!valid_pulse(pulse, stack->n_layers, p->n_e, why)) return PIC_ERR_ARG;
+        if (up_thr) *up_thr = threshold_of(pulse->up_frac);
+        std::vector<uint32_t> thr; std::vector<int32_t> cell, layer; std::vector<long long> inj;
+        source_tables(*p, *stack, *pulse, thr, cell, layer, inj);
+        if (inj_counts) for (size_t i = 0; i < inj.size(); ++i) inj_counts[i] = inj[i];
+    }
+    return PIC_OK;
+}
+
+pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *stacks, int n_stacks,
+                    const pic_tables *tables, void *cuda_stream)
+{
+    g_init_error.clear();
+    if (!out) { g_init_error = "out is NULL"; return PIC_ERR_ARG; }
+    *out = nullptr;
+    std::string why;
+    if (!valid_params(p, why)) { g_init_error = why; return PIC_ERR_ARG; }
+    if (n_stacks < 1 || n_stacks > PIC_MAX_STACKS || !stacks || !tables) {
+        g_init_error = "n_stacks out of range or NULL stacks/tables";
+        return PIC_ERR_ARG;
+    }
+    for (int s = 0; s < n_stacks; ++s)
+        if (!valid_stack(p, &stacks[s], &tables[s], why)) {
+            g_init_error = "stack " + std::to_string(s) + ": " + why;
+            return PIC_ERR_ARG;
+        }
+
+    pic_ctx *c = new pic_ctx();
+    c->p = *p;
+    c->n_stacks = n_stacks;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->hs.resize(n_stacks);
+    c->ds.resize(n_stacks);
+    const int ne = p->n_e;
+    int tab_max = 1, T_max = 1, nbin_max = 1, jbin_max = 1;
+    std::vector<TabEnt> ent;
+    std::vector<uint32_t> Tall;
+    for (int s = 0; s < n_stacks; ++s) {
+        HostStack &h = c->hs[s];
+        const pic_tables &t = tables[s];
+        h.d = stacks[s];
+        h.n_mat = t.n_mat;
+        const size_t nt = (size_t)t.n_mat * 2 * ne;
+        h.v.assign(t.v, t.v + nt);
+        h.tau_in.assign(t.tau_in, t.tau_in + nt);
+        h.tau_el.assign(t.tau_el, t.tau_el + t.n_mat);
+        h.p0.assign(t.p0, t.p0 + t.n_mat);
+        h.T.assign(t.T ? t.T : nullptr, t.T ? t.T + (size_t)(h.d.n_layers - 1) * 4 * ne : nullptr);
+        material_thresholds(*p, h.d, t, h.P_thr, h.Q_thr, h.T_thr, h.P0_thr);
+        DevStack &d = c->ds[s];
+        std::memset(&d, 0, sizeof(d));
+        d.n_layers = h.d.n_layers;
+        int cells = 0;
+        d.edge[0] = 0.f;
+        for (int l = 0; l < h.d.n_layers; ++l) {
+            cells += h.d.layer_cells[l];
+            d.edge[l + 1] = (float)cells * p->dz;
+            d.p0_thr[l] = h.P0_thr[h.d.layer_mat[l]];
+        }
+        h.n_cells = d.n_cells = cells;
+        h.n_out = (p->n_steps_max + p->moment_every - 1) / p->moment_every;
+        // layer-indexed {v, P, Q} entries
+        d.tab_n = h.d.n_layers * 2 * ne;
+        d.ent_off = (int64_t)ent.size();
+        for (int l = 0; l < h.d.n_layers; ++l)
+            for (int sp = 0; sp < 2; ++sp)
+                for (int k = 0; k < ne; ++k) {
+                    const size_t i = ((size_t)h.d.layer_mat[l] * 2 + sp) * ne + k;
+                    ent.push_back(TabEnt{h.v[i], h.P_thr[i], h.Q_thr[i], 0u});
+                }
+        d.T_n = (h.d.n_layers - 1) * 4 * ne;
+        d.T_off = (int64_t)Tall.size();
+        Tall.insert(Tall.end(), h.T_thr.begin(), h.T_thr.end());
+        d.cap = h.d.capacity;
+        h.cap_round = (h.d.capacity + TILE - 1) / TILE * TILE;
+        d.base = h.base = c->total_slots;
+        c->total_slots += h.cap_round;
+        d.n_off = c->nh_total;
+        c->nh_total += (int64_t)h.n_out * 2 * ne * cells;
+        d.J_off = c->J_total;
+        c->J_total += (int64_t)h.n_out * 2 * (cells + 1);
+        d.cdf_off = (int64_t)s * 0;      // set by pic_excite
+        d.n_cdf = 0;
+        d.inj_off = (int64_t)s * 2 * p->n_steps_max;
+        tab_max = std::max(tab_max, d.tab_n);
+        T_max = std::max(T_max, d.T_n);
+        nbin_max = std::max(nbin_max, 2 * ne * cells);
+        jbin_max = std::max(jbin_max, 2 * (cells + 1));
+        h.inj.assign((size_t)2 * p->n_steps_max, 0);
+    }
+    int64_t total_cells = 0;
+    for (int s = 0; s < n_stacks; ++s) {
+        c->ds[s].cdf_off = total_cells;
+        total_cells += c->hs[s].n_cells;
+    }
+
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, n) do { if (e == cudaSuccess) e = dalloc(&ptr, n); } while (0)
+    ALLOC(c->d_stacks, n_stacks);
+    ALLOC(c->d_ent, ent.size());
+    ALLOC(c->d_T, Tall.size());
+    ALLOC(c->d_cdf_thr, total_cells);
+    ALLOC(c->d_cdf_cell, total_cells);
+    ALLOC(c->d_cdf_layer, total_cells);
+    ALLOC(c->d_inj, (size_t)n_stacks * 2 * p->n_steps_max);
+    for (int b = 0; b < 2; ++b) {
+        ALLOC(c->d_z[b], c->total_slots);
+        ALLOC(c->d_mu[b], c->total_slots);
+        ALLOC(c->d_id[b], c->total_slots);
+        ALLOC(c->d_pk[b], c->total_slots);
+    }
+    ALLOC(c->d_stage, c->total_slots);
+    ALLOC(c->d_nh, c->nh_total);
+    ALLOC(c->d_J, c->J_total);
+    ALLOC(c->d_cnt, n_stacks);
+    ALLOC(c->d_ctl, 1);
+#undef ALLOC
+    if (e != cudaSuccess) {
+        g_init_error = std::string("device allocation: ") + cudaGetErrorString(e);
+        free_all(c);
+        delete c;
+        cudaGetLastError();
+        return PIC_ERR_ALLOC;
+    }
+
+    Args &a = c->args;
+    a.stacks = c->d_stacks; a.n_stacks = n_stacks;
+    a.ent = c->d_ent; a.T_thr = c->d_T;
+    a.cdf_thr = c->d_cdf_thr; a.cdf_cell = c->d_cdf_cell; a.cdf_layer = c->d_cdf_layer;
+    a.inj = c->d_inj;
+    for (int b = 0; b < 2; ++b) {
+        a.z[b] = c->d_z[b]; a.mu[b] = c->d_mu[b]; a.id[b] = c->d_id[b]; a.pk[b] = c->d_pk[b];
+    }
+    a.stage = c->d_stage;
+    a.n_hist = c->d_nh; a.J_hist = c->d_J; a.cnt = c->d_cnt; a.ctl = c->d_ctl;
+    a.seed_lo = (uint32_t)p->seed; a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.half_dt = p->dt * 0.5f;
+    a.dz = p->dz;
+    int ex = 0;
+    const float mant = std::frexp(p->dz, &ex);
+    a.dz_pow2 = mant == 0.5f;
+    a.inv_dz = a.dz_pow2 ? 1.0f / p->dz : 0.f;
+    a.flags = p->flags; a.n_e = ne; a.moment_every = p->moment_every;
+    a.step = 0;
+    a.tab_max = tab_max; a.T_max = T_max; a.nbin_max = nbin_max; a.jbin_max = jbin_max;
+    a.spin_limit = 1u << 24;
+
+    e = configure(a, p->blocks_per_sm, p->hist_mode, &c->lc);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("kernel configuration (moment grid too large for shared "
+                                   "memory, or no device): ") + cudaGetErrorString(e);
+        free_all(c);
+        delete c;
+        cudaGetLastError();
+        return PIC_ERR_ARG;   // moment grid too large for shared memory, or no device
+    }
+    const int gmax = std::max(std::max(c->lc.grid_step, c->lc.grid_step_dep), c->lc.grid_compact);
+    if (dalloc(&c->d_status, (size_t)gmax) != cudaSuccess) {
+        g_init_error = "device allocation of the look-back words";
+        free_all(c);
+        delete c;
+        cudaGetLastError();
+        return PIC_ERR_ALLOC;
+    }
+    a.status = c->d_status;
+
+    cudaStream_t st = c->stream;
+    DevCtl ctl{};
+    ctl.epoch = 1u;
+    std::vector<DevCounters> cnt(n_stacks);
+    std::memset(cnt.data(), 0, sizeof(DevCounters) * n_stacks);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_stacks, c->ds.data(), sizeof(DevStack) * n_stacks, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !ent.empty()) e = cudaMemcpyAsync(c->d_ent, ent.data(), sizeof(TabEnt) * ent.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !Tall.empty()) e = cudaMemcpyAsync(c->d_T, Tall.data(), 4 * Tall.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_inj, 0, sizeof(long long) * std::max<size_t>((size_t)n_stacks * 2 * p->n_steps_max, 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned long long) * gmax, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_nh, 0, 4 * (size_t)std::max<int64_t>(c->nh_total, 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_J, 0, 4 * (size_t)std::max<int64_t>(c->J_total, 1), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt, cnt.data(), sizeof(DevCounters) * n_stacks, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        g_init_error = std::string("initial upload: ") + cudaGetErrorString(e);
+        free_all(c);
+        delete c;
+        cudaGetLastError();
+        return PIC_ERR_CUDA;
+    }
+    *out = c;
+    return PIC_OK;
+}
+
+pic_status pic_excite(pic_ctx *c, int stack, const pic_pulse *u)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (stack < -1 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    const int s0 = stack < 0 ? 0 : stack, s1 = stack < 0 ? c->n_stacks : stack + 1;
+    std::string why;
+    for (int s = s0; s < s1; ++s)
+        if (!valid_pulse(u, c->hs[s].d.n_layers, c->p.n_e, why)) return fail(c, PIC_ERR_ARG, why);
+    for (int s = s0; s < s1; ++s) {
+        HostStack &h = c->hs[s];
+        DevStack &d = c->ds[s];
+        std::vector<uint32_t> thr; std::vector<int32_t> cell, layer;
+        source_tables(c->p, h.d, *u, thr, cell, layer, h.inj);
+        h.pulse = *u;
+        h.excited = true;
+        d.n_cdf = (int32_t)thr.size();
+        d.up_thr = threshold_of(u->up_frac);
+        d.e_mode = u->e_mode;
+        d.k_mono0 = u->k_mono[0];
+        d.k_mono1 = u->k_mono[1];
+        cudaError_t e = cudaSuccess;
+        if (!thr.empty()) {
+            e = cudaMemcpyAsync(c->d_cdf_thr + d.cdf_off, thr.data(), 4 * thr.size(), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cdf_cell + d.cdf_off, cell.data(), 4 * cell.size(), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cdf_layer + d.cdf_off, layer.data(), 4 * layer.size(), cudaMemcpyHostToDevice, c->stream);
+        }
+        if (e == cudaSuccess && !h.inj.empty())
+            e = cudaMemcpyAsync(c->d_inj + d.inj_off, h.inj.data(), sizeof(long long) * h.inj.size(), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(c->d_stacks + s, &d, sizeof(DevStack), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pic_excite upload");
+    }
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_ctx *c, int n_steps)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (n_steps < 0) return fail(c, PIC_ERR_ARG, "n_steps < 0");
+    if ((int64_t)c->step + n_steps > c->p.n_steps_max)
+        return fail(c, PIC_ERR_ARG, "steps would exceed n_steps_max");
+    const bool det = (c->p.flags & PIC_F_DETERMINISTIC) != 0;
+    c->launches = 0;
+    for (int i = 0; i < n_steps; ++i) {
+        const int s = c->step;
+        c->args.step = (uint32_t)s;
+        bool inj0 = false, inj1 = false;
+        for (const HostStack &h : c->hs) {
+            inj0 = inj0 || h.inj[2 * (size_t)s] > 0;
+            inj1 = inj1 || h.inj[2 * (size_t)s + 1] > 0;
+        }
+        const bool dep = ((s + 1) % c->p.moment_every) == 0;
+        cudaError_t e = cudaSuccess;
+        const Args &a = c->args;
+        const LaunchCfg &lc = c->lc;
+        cudaStream_t st = c->stream;
+        if (inj0) {
+            e = timed(c, 0, [&] { return launch_inject(a, lc, 0, false, st); });
+            ++c->launches;
+        }
+        if (e == cudaSuccess) {
+            e = timed(c, dep ? 2 : 1, [&] { return launch_step(a, lc, det, dep, c->p.hist_mode, st); });
+            ++c->launches;
+        }
+        if (e == cudaSuccess && inj1) {
+            e = timed(c, 0, [&] { return launch_inject(a, lc, 1, dep, st); });
+            ++c->launches;
+        }
+        if (e == cudaSuccess && ((s + 1) % c->p.compact_every) == 0) {
+            e = timed(c, 3, [&] { return launch_compact(a, lc, st); });
+            ++c->launches;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "pic_step launch");
+        c->step = s + 1;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_sync(pic_ctx *c)
+{
+    if (!c) return PIC_ERR_ARG;
+    return device_status(c);
+}
+
+pic_status pic_moments(pic_ctx *c, int stack, uint32_t *n_dev, int32_t *J_dev, pic_ledger *led)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    const HostStack &h = c->hs[stack];
+    const DevStack &d = c->ds[stack];
+    cudaError_t e = cudaSuccess;
+    const size_t nn = (size_t)h.n_out * 2 * c->p.n_e * h.n_cells;
+    const size_t nj = (size_t)h.n_out * 2 * (h.n_cells + 1);
+    if (n_dev && nn) e = cudaMemcpyAsync(n_dev, c->d_nh + d.n_off, 4 * nn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && J_dev && nj) e = cudaMemcpyAsync(J_dev, c->d_J + d.J_off, 4 * nj, cudaMemcpyDeviceToDevice, c->stream);
+    DevCounters hc{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, c->d_cnt + stack, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_moments copy");
+    const pic_status st = device_status(c);
+    if (led) {
+        static_assert(sizeof(pic_ledger) == sizeof(unsigned long long) * LEDGER_N, "ledger layout");
+        std::memcpy(led, hc.led, sizeof(pic_ledger));
+    }
+    return st;
+}
+
+pic_status pic_records(pic_ctx *c, int stack, pic_record *out, int64_t *n)
+{
+    if (!c || !n) return PIC_ERR_ARG;
+    if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    DevCounters hc{};
+    DevCtl ctl{};
+    cudaError_t e = cudaMemcpyAsync(&hc, c->d_cnt + stack, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_records");
+    const int64_t cnt = (int64_t)hc.n_slots;
+    if (!out) { *n = cnt; return PIC_OK; }
+    if (*n < cnt) { *n = cnt; return fail(c, PIC_ERR_ARG, "output buffer too small"); }
+    *n = cnt;
+    if (cnt == 0) return PIC_OK;
+    const int b = (int)ctl.cur;
+    const int64_t base = c->ds[stack].base;
+    std::vector<float> z(cnt), mu(cnt);
+    std::vector<uint32_t> id(cnt), pk(cnt);
+    e = cudaMemcpyAsync(z.data(), c->d_z[b] + base, 4 * cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mu.data(), c->d_mu[b] + base, 4 * cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(id.data(), c->d_id[b] + base, 4 * cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pk.data(), c->d_pk[b] + base, 4 * cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_records copy");
+    for (int64_t i = 0; i < cnt; ++i) out[i] = pic_record{z[i], mu[i], id[i], pk[i]};
+    return PIC_OK;
+}
+
+pic_status pic_set_records(pic_ctx *c, int stack, const pic_record *in, int64_t n, uint64_t next_id)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    if (n < 0 || n > c->hs[stack].d.capacity || (n > 0 && !in))
+        return fail(c, PIC_ERR_ARG, "record count exceeds capacity");
+    // every record must index valid tables: k in 0..n_e (0 = removed),
+    // layer in the stack, z inside the stack, mu a finite non-zero cosine
+    const HostStack &hs = c->hs[stack];
+    const float L = c->ds[stack].edge[hs.d.n_layers];
+    for (int64_t i = 0; i < n; ++i) {
+        const uint32_t w = in[i].packed;
+        const uint32_t k = w & 0xFFu, layer = (w >> 9) & 0xFu;
+        if (k > (uint32_t)c->p.n_e || (int)layer >= hs.d.n_layers || !(in[i].z >= 0.f) ||
+            !(in[i].z <= L) || !(in[i].mu >= -1.f && in[i].mu <= 1.f) || in[i].mu == 0.f)
+            return fail(c, PIC_ERR_ARG, "record " + std::to_string(i) + " is out of range");
+    }
+    DevCtl ctl{};
+    cudaError_t e = cudaMemcpyAsync(&ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_set_records");
+    const int b = (int)ctl.cur;
+    const int64_t base = c->ds[stack].base;
+    std::vector<float> z(n), mu(n);
+    std::vector<uint32_t> id(n), pk(n);
+    for (int64_t i = 0; i < n; ++i) { z[i] = in[i].z; mu[i] = in[i].mu; id[i] = in[i].id; pk[i] = in[i].packed; }
+    if (n) {
+        e = cudaMemcpyAsync(c->d_z[b] + base, z.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mu[b] + base, mu.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_id[b] + base, id.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_pk[b] + base, pk.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+    }
+    const unsigned long long vals[2] = {(unsigned long long)n, (unsigned long long)next_id};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt + stack, vals, sizeof(vals), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_set_records copy");
+    return PIC_OK;
+}
+
+pic_status pic_grad(pic_ctx *c, const float *, const float *, double *, double *)
+{
+    if (!c) return PIC_ERR_ARG;
+    return fail(c, PIC_ERR_STATE, "pic_grad: adjoint replay not available in this build");
+}
+
+pic_status pic_shape(const pic_ctx *c, int stack, int32_t *n_cells, int32_t *n_out, int32_t *step)
+{
+    if (!c || stack < 0 || stack >= c->n_stacks) return PIC_ERR_ARG;
+    if (n_cells) *n_cells = c->hs[stack].n_cells;
+    if (n_out) *n_out = c->hs[stack].n_out;
+    if (step) *step = c->step;
+    return PIC_OK;
+}
+
+int64_t pic_launch_count(const pic_ctx *c) { return c ? c->launches : 0; }
+
+pic_status pic_profile(pic_ctx *c, int enable)
+{
+    if (!c) return PIC_ERR_ARG;
+    const cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_profile");
+    c->profiling = enable != 0;
+    if (enable) {
+        c->ev_marks.clear();
+        c->ev_used = 0;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_profile_read(pic_ctx *c, pic_kernel_times *out)
+{
+    if (!c || !out) return PIC_ERR_ARG;
+    std::memset(out, 0, sizeof(*out));
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_profile_read");
+    for (const auto &m : c->ev_marks) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, c->ev_pool[m.second], c->ev_pool[m.second + 1]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pic_profile_read elapsed");
+        out->launches[m.first] += 1;
+        out->ms[m.first] += ms;
+    }
+    return PIC_OK;
+}
+
+void pic_destroy(pic_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t ev : c->ev_pool) cudaEventDestroy(ev);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

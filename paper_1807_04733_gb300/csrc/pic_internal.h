@@ -1,0 +1,119 @@
+// Internal structures of the GB300 PIC library (not part of the C-ABI).
+//
+// Data layout in HBM
+//   particles : structure of arrays, two buffers (ping-pong for compaction):
+//               z[f32], mu[f32], id[u32], packed[u32], each of length
+//               sum_s round_up(capacity_s, TILE); stack s owns slots
+//               [base_s, base_s + capacity_s).  One thread moves four
+//               consecutive slots with one 128-bit load/store per array.
+//   staging   : float4 per slot (z_end, mu, packed bits, z_spawn): secondary
+//               carriers of a step, in slot order, before their final place
+//               is known.
+//   tables    : per stack, per layer: {v, P_thr, Q_thr} (16 B) for
+//               [layer][spin][k], the interface thresholds, P0 per layer.
+//   moments   : uint32 densities and int32 fluxes per output window.
+#pragma once
+#include <cstdint>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+constexpr int TPB = 256;            // threads per block of the streaming kernels
+constexpr int VEC = 4;              // particles per thread per tile (128-bit)
+constexpr int TILE = TPB * VEC;     // particles per tile
+constexpr int LEDGER_N = 13;        // fields of pic_ledger
+
+// ledger field indices (order of pic_ledger)
+enum {
+    L_INJECTED, L_INJECT_DROPPED, L_SPAWNED, L_SPAWN_DROPPED, L_ABSORBED,
+    L_Q_INJECTED, L_Q_BATH, L_Q_DROPPED, L_IFACE_HITS, L_IFACE_TRANSMIT,
+    L_TRUNCATED, L_PARTICLE_STEPS, L_CHANGED
+};
+
+// Philox counter layout: ctr = {id_lo, id_hi | stack << 16, step, substream}
+enum : uint32_t {
+    SUB_SCAT = 0x000u,   // scattering test and event words
+    SUB_SEC = 0x001u,    // secondary spin and direction
+    SUB_IF = 0x100u,     // + 16*half + hit: interface draws of a carrier
+    SUB_SIF = 0x200u,    // + hit: the secondary's second-half flight
+    SUB_INJ = 0x300u,    // + j: source draws
+};
+
+struct TabEnt {          // one (layer, spin, k) entry
+    float v;             // nm/fs
+    uint32_t P;          // scatter iff x0 < P   (P = floor(p 2^32))
+    uint32_t Q;          // inelastic iff x1 < Q
+    uint32_t pad;
+};
+
+struct DevStack {        // immutable per-stack description (device copy)
+    int32_t n_layers, n_cells, tab_n, T_n;
+    float edge[PIC_MAX_LAYERS + 1];
+    uint32_t p0_thr[PIC_MAX_LAYERS];    // per layer
+    int64_t base, cap;                  // slot range
+    int64_t n_off, J_off;               // offsets in the moment arrays
+    int64_t ent_off, T_off;             // offsets in the table arrays
+    int64_t cdf_off; int32_t n_cdf;     // source profile
+    uint32_t up_thr;
+    int32_t e_mode, k_mono0, k_mono1;
+    int64_t inj_off;                    // source schedule, 2*n_steps_max
+};
+
+struct DevCounters {     // mutable per stack
+    unsigned long long n_slots, next_id, spawn_total, alive_total;
+    unsigned long long led[LEDGER_N];
+};
+
+struct DevCtl {
+    unsigned int status;     // first error code (0 = ok)
+    unsigned int epoch;      // tag of the look-back status words
+    unsigned int done;       // blocks finished in the current launch
+    unsigned int cur;        // current particle buffer (0/1)
+    unsigned int timeout_where;
+    unsigned int pad[3];
+};
+
+struct Args {            // everything a kernel needs, passed by value
+    const DevStack *stacks;
+    int n_stacks;
+    const TabEnt *ent;
+    const uint32_t *T_thr;
+    const uint32_t *cdf_thr;
+    const int32_t *cdf_cell;
+    const int32_t *cdf_layer;
+    const long long *inj;
+    float *z[2];
+    float *mu[2];
+    uint32_t *id[2];
+    uint32_t *pk[2];
+    float4 *stage;
+    unsigned long long *status;      // one look-back word per block
+    uint32_t *n_hist;
+    int32_t *J_hist;
+    DevCounters *cnt;
+    DevCtl *ctl;
+    uint32_t seed_lo, seed_hi;
+    float half_dt, dz, inv_dz;
+    int dz_pow2;
+    uint32_t flags;
+    int n_e;
+    int moment_every;
+    uint32_t step;
+    int tab_max, T_max, nbin_max, jbin_max;  // shared-memory sizing
+    unsigned int spin_limit;                 // look-back wait bound
+};
+
+// host-side launchers (pic_kernels.cu)
+struct LaunchCfg {
+    int grid_step, grid_step_dep, grid_compact, grid_inject;
+    size_t smem_step, smem_step_dep;
+};
+cudaError_t configure(const Args &a, int blocks_per_sm, int hist_mode, LaunchCfg *cfg);
+cudaError_t launch_inject(const Args &a, const LaunchCfg &c, int half, bool deposit,
+                          cudaStream_t s);
+cudaError_t launch_step(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
+                        int hist_mode, cudaStream_t s);
+cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s);
+
+}  // namespace pic

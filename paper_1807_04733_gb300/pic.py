@@ -1,0 +1,336 @@
+"""Thin Python binding of the C-ABI in ``include/pic.h`` (ctypes).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of ``libpic.so``.  The functions carry the C names (``pic_init``,
+``pic_excite``, ``pic_step``, ``pic_moments``, ``pic_grad`` ...).  Device
+buffers are torch tensors passed by ``data_ptr()``; streams are torch
+streams passed by their ``cuda_stream`` handle.
+
+There is no CPU fallback: if the library was not built, ``lib()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpic.so")
+
+MAX_LAYERS = 16
+MAX_MAT = 8
+LEDGER_FIELDS = ("injected", "inject_dropped", "spawned", "spawn_dropped", "absorbed",
+                 "q_injected", "q_bath", "q_dropped", "iface_hits", "iface_transmit",
+                 "truncated", "particle_steps", "changed")
+STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_ALLOC", 3: "PIC_ERR_CAPACITY",
+          4: "PIC_ERR_TIMEOUT", 5: "PIC_ERR_CUDA", 6: "PIC_ERR_STATE"}
+REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u4")])
+
+# symbols declared in include/pic.h
+EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_grad", "pic_records",
+           "pic_set_records", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
+           "pic_profile_read", "pic_launch_count", "pic_destroy", "pic_last_error",
+           "pic_status_string")
+KERNEL_KINDS = ("inject", "step", "step_moments", "compact")
+
+
+class pic_params(C.Structure):
+    _fields_ = [("n_e", C.c_int32), ("dt", C.c_float), ("dz", C.c_float),
+                ("seed", C.c_uint64), ("flags", C.c_uint32), ("compact_every", C.c_int32),
+                ("moment_every", C.c_int32), ("n_steps_max", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("hist_mode", C.c_int32)]
+
+
+class pic_stack_desc(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("layer_cells", C.c_int32 * MAX_LAYERS),
+                ("layer_mat", C.c_int32 * MAX_LAYERS), ("capacity", C.c_int64)]
+
+
+class pic_tables(C.Structure):
+    _fields_ = [("n_mat", C.c_int32), ("v", C.POINTER(C.c_float)),
+                ("tau_in", C.POINTER(C.c_double)), ("tau_el", C.POINTER(C.c_double)),
+                ("T", C.POINTER(C.c_double)), ("p0", C.POINTER(C.c_double))]
+
+
+class pic_pulse(C.Structure):
+    _fields_ = [("n0", C.c_int64), ("fwhm", C.c_double), ("t0", C.c_double),
+                ("abs_len", C.c_double), ("excite_mask", C.c_uint32), ("up_frac", C.c_double),
+                ("e_mode", C.c_int32), ("k_mono", C.c_int32 * 2)]
+
+
+class pic_ledger(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in LEDGER_FIELDS]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n in LEDGER_FIELDS}
+
+
+class pic_kernel_times(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4)]
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load the in-tree library; fails loudly when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libpic.so is missing (%s): run __graft_entry__.build() first"
+                               % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.pic_init.argtypes = [C.POINTER(P), C.POINTER(pic_params), C.POINTER(pic_stack_desc),
+                               C.c_int, C.POINTER(pic_tables), P]
+        L.pic_excite.argtypes = [P, C.c_int, C.POINTER(pic_pulse)]
+        L.pic_step.argtypes = [P, C.c_int]
+        L.pic_moments.argtypes = [P, C.c_int, P, P, C.POINTER(pic_ledger)]
+        L.pic_grad.argtypes = [P, P, P, P, P]
+        L.pic_records.argtypes = [P, C.c_int, P, C.POINTER(C.c_int64)]
+        L.pic_set_records.argtypes = [P, C.c_int, P, C.c_int64, C.c_uint64]
+        L.pic_sync.argtypes = [P]
+        L.pic_derive_tables.argtypes = [C.POINTER(pic_params), C.POINTER(pic_stack_desc),
+                                        C.POINTER(pic_tables), C.POINTER(pic_pulse),
+                                        P, P, P, P, P, P]
+        L.pic_shape.argtypes = [P, C.c_int, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                C.POINTER(C.c_int32)]
+        L.pic_profile.argtypes = [P, C.c_int]
+        L.pic_profile_read.argtypes = [P, C.POINTER(pic_kernel_times)]
+        L.pic_launch_count.argtypes = [P]
+        L.pic_launch_count.restype = C.c_int64
+        L.pic_destroy.argtypes = [P]
+        L.pic_destroy.restype = None
+        L.pic_last_error.argtypes = [P]
+        L.pic_last_error.restype = C.c_char_p
+        L.pic_status_string.argtypes = [C.c_int]
+        L.pic_status_string.restype = C.c_char_p
+        for name in EXPORTS:
+            if name not in ("pic_launch_count", "pic_destroy", "pic_last_error",
+                            "pic_status_string"):
+                getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        raise PicError(status, lib().pic_last_error(ctx).decode())
+
+
+# ---------------------------------------------------------------------------
+# marshalling of the workload description
+# ---------------------------------------------------------------------------
+def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hist_mode=0):
+    p = pic_params()
+    p.n_e = wl.n_e; p.dt = wl.dt; p.dz = wl.dz
+    p.seed = wl.seed if seed is None else seed
+    p.flags = wl.flags if flags is None else flags
+    p.compact_every = wl.compact_every; p.moment_every = wl.moment_every
+    p.n_steps_max = wl.n_steps if n_steps_max is None else n_steps_max
+    p.blocks_per_sm = blocks_per_sm; p.hist_mode = hist_mode
+    return p
+
+
+def make_stack(st, capacity=None):
+    d = pic_stack_desc()
+    d.n_layers = len(st.layer_cells)
+    for i, (c, m) in enumerate(zip(st.layer_cells, st.layer_mat)):
+        d.layer_cells[i] = c; d.layer_mat[i] = m
+    d.capacity = st.capacity if capacity is None else capacity
+    return d
+
+
+class _Tables:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, st):
+        self.v = np.ascontiguousarray(st.v, np.float32)
+        self.tau_in = np.ascontiguousarray(st.tau_in, np.float64)
+        self.tau_el = np.ascontiguousarray(st.tau_el, np.float64)
+        self.T = np.ascontiguousarray(st.T, np.float64).reshape(-1).copy() \
+            if st.T.size else np.zeros(1)
+        self.p0 = np.ascontiguousarray(st.p0, np.float64)
+        t = pic_tables()
+        t.n_mat = self.v.shape[0]
+        t.v = self.v.ctypes.data_as(C.POINTER(C.c_float))
+        t.tau_in = self.tau_in.ctypes.data_as(C.POINTER(C.c_double))
+        t.tau_el = self.tau_el.ctypes.data_as(C.POINTER(C.c_double))
+        t.T = self.T.ctypes.data_as(C.POINTER(C.c_double))
+        t.p0 = self.p0.ctypes.data_as(C.POINTER(C.c_double))
+        self.c = t
+
+
+def make_pulse(st):
+    u = pic_pulse()
+    u.n0 = st.n0; u.fwhm = st.fwhm; u.t0 = st.t0; u.abs_len = st.abs_len
+    u.excite_mask = st.excite_mask; u.up_frac = st.up_frac; u.e_mode = st.e_mode
+    u.k_mono[0] = st.k_mono[0]; u.k_mono[1] = st.k_mono[1]
+    return u
+
+
+# ---------------------------------------------------------------------------
+# C-named entry points
+# ---------------------------------------------------------------------------
+def pic_init(params, stacks, tables, stream=None):
+    n = len(stacks)
+    sarr = (pic_stack_desc * n)(*stacks)
+    tarr = (pic_tables * n)(*tables)
+    h = C.c_void_p()
+    st = lib().pic_init(C.byref(h), C.byref(params), sarr, n, tarr,
+                        C.c_void_p(stream) if stream else None)
+    _check(st)
+    return h
+
+
+def pic_excite(ctx, stack, pulse):
+    _check(lib().pic_excite(ctx, stack, C.byref(pulse)), ctx)
+
+
+def pic_step(ctx, n_steps):
+    _check(lib().pic_step(ctx, n_steps), ctx)
+
+
+def pic_moments(ctx, stack, n_dev_ptr, J_dev_ptr):
+    led = pic_ledger()
+    _check(lib().pic_moments(ctx, stack, C.c_void_p(n_dev_ptr or 0) if n_dev_ptr else None,
+                             C.c_void_p(J_dev_ptr) if J_dev_ptr else None, C.byref(led)), ctx)
+    return led.as_dict()
+
+
+def pic_grad(ctx, grad_n_ptr, grad_J_ptr, grad_tau_ptr, grad_T_ptr):
+    _check(lib().pic_grad(ctx, C.c_void_p(grad_n_ptr) if grad_n_ptr else None,
+                          C.c_void_p(grad_J_ptr) if grad_J_ptr else None,
+                          C.c_void_p(grad_tau_ptr), C.c_void_p(grad_T_ptr)), ctx)
+
+
+def pic_records(ctx, stack):
+    n = C.c_int64(0)
+    _check(lib().pic_records(ctx, stack, None, C.byref(n)), ctx)
+    out = np.zeros(n.value, REC_DTYPE)
+    if n.value:
+        _check(lib().pic_records(ctx, stack, C.c_void_p(out.ctypes.data), C.byref(n)), ctx)
+    return out[: n.value]
+
+
+def pic_set_records(ctx, stack, recs, next_id):
+    recs = np.ascontiguousarray(recs, REC_DTYPE)
+    _check(lib().pic_set_records(ctx, stack, C.c_void_p(recs.ctypes.data) if len(recs) else None,
+                                 len(recs), next_id), ctx)
+
+
+def pic_sync(ctx):
+    _check(lib().pic_sync(ctx), ctx)
+
+
+def pic_shape(ctx, stack):
+    nc, no, sp = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().pic_shape(ctx, stack, C.byref(nc), C.byref(no), C.byref(sp)), ctx)
+    return nc.value, no.value, sp.value
+
+
+def pic_profile(ctx, enable):
+    _check(lib().pic_profile(ctx, 1 if enable else 0), ctx)
+
+
+def pic_profile_read(ctx):
+    t = pic_kernel_times()
+    _check(lib().pic_profile_read(ctx, C.byref(t)), ctx)
+    return {k: (int(t.launches[i]), float(t.ms[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def pic_launch_count(ctx):
+    return int(lib().pic_launch_count(ctx))
+
+
+def pic_destroy(ctx):
+    if ctx is not None and ctx.value:
+        lib().pic_destroy(ctx)
+
+
+def pic_derive_tables(params, stack, tables, pulse, n_mat, n_e, n_steps_max):
+    nl = stack.n_layers
+    P = np.zeros((n_mat, 2, n_e), np.uint32); Q = np.zeros_like(P)
+    T = np.zeros((max(nl - 1, 0), 2, 2, n_e), np.uint32)
+    P0 = np.zeros(n_mat, np.uint32); up = np.zeros(1, np.uint32)
+    inj = np.zeros(2 * n_steps_max, np.int64)
+    _check(lib().pic_derive_tables(C.byref(params), C.byref(stack), C.byref(tables),
+                                   C.byref(pulse) if pulse is not None else None,
+                                   P.ctypes.data, Q.ctypes.data,
+                                   T.ctypes.data if T.size else None, P0.ctypes.data,
+                                   up.ctypes.data, inj.ctypes.data))
+    return dict(P_thr=P, Q_thr=Q, T_thr=T, P0_thr=P0, up_thr=int(up[0]), inj=inj)
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper: a context for a workload, torch tensors as device memory
+# ---------------------------------------------------------------------------
+class Context:
+    """All stacks of a workload in one context on the current CUDA device."""
+
+    def __init__(self, wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0,
+                 hist_mode=0, stream=None, excite=True, capacity=None):
+        import torch
+        self.wl = wl
+        self.torch = torch
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.params = make_params(wl, n_steps_max, flags, seed, blocks_per_sm, hist_mode)
+        self._tabs = [_Tables(st) for st in wl.stacks]
+        self.stacks = [make_stack(st, capacity) for st in wl.stacks]
+        self.ctx = pic_init(self.params, self.stacks, [t.c for t in self._tabs],
+                            self.stream.cuda_stream)
+        if excite:
+            for i, st in enumerate(wl.stacks):
+                if st.n0 > 0:
+                    pic_excite(self.ctx, i, make_pulse(st))
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None:
+            pic_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, n=1):
+        pic_step(self.ctx, n)
+
+    def shape(self, stack=0):
+        return pic_shape(self.ctx, stack)
+
+    def moments(self, stack=0):
+        torch = self.torch
+        nc, no, _ = self.shape(stack)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n = torch.empty((no, 2, self.wl.n_e, nc), dtype=torch.int32, device=dev)
+        J = torch.empty((no, 2, nc + 1), dtype=torch.int32, device=dev)
+        led = pic_moments(self.ctx, stack, n.data_ptr(), J.data_ptr())
+        return n, J, led
+
+    def ledger(self, stack=0):
+        return pic_moments(self.ctx, stack, None, None)
+
+    def records(self, stack=0):
+        return pic_records(self.ctx, stack)
+
+    def set_records(self, recs, next_id, stack=0):
+        pic_set_records(self.ctx, stack, recs, next_id)
+
+    def sync(self):
+        pic_sync(self.ctx)
+
+    @property
+    def launches(self):
+        return pic_launch_count(self.ctx)

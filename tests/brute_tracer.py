@@ -173,6 +173,7 @@ class Tracer:
                                  s=0 if y[0] < self.P0[m] else 1, l=p["l"],
                                  g=min(p["g"] + 1, 255))
                         cs = self.cell(q["z"])
+                        before = (self.counts["iface"], self.counts["trans"])
                         self.fly(q, half, pid, 0x200)
                         if len(self.parts) < self.st.capacity:
                             q["id"] = self.next_id
@@ -181,6 +182,7 @@ class Tracer:
                             self.counts["spawned"] += 1
                             self.add_flux(q["s"], cs, self.cell(q["z"]))
                         else:
+                            self.counts["iface"], self.counts["trans"] = before
                             self.counts["dropped"] += 1
             self.fly(p, half, pid, 0x110)
             self.add_flux(p["s"], c0, self.cell(p["z"]))
