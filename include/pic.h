@@ -231,6 +231,33 @@ pic_status pic_profile(pic_ctx *ctx, int enable);
 /* Sum the recorded kernel times (synchronises). */
 pic_status pic_profile_read(pic_ctx *ctx, pic_kernel_times *out);
 
+/* Stable removal of dead slots (k = 0) from particle arrays the caller owns,
+ * without any device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as an
+ * application whose device memory belongs entirely to its own allocator or
+ * pool, or a latency-critical loop that must not allocate.  It runs the same
+ * compaction kernel as pic_step, with that kernel's scratch (look-back words
+ * for up to 4096 blocks, counters, control block: about 33 KB) held in a
+ * static device array that every GPU which loads the library keeps until
+ * the process exits.
+ *   z, mu, id, packed (device, read): n slots in the pic_record field layout;
+ *     16-byte aligned and readable up to round_up(n, 4) elements.
+ *   z_out, mu_out, id_out, packed_out (device, written): the live slots in
+ *     their original order; each must hold n elements and must not overlap
+ *     the inputs.
+ *   n_alive (host, written): number of live slots.
+ *   cuda_stream: cudaStream_t the work is ordered on; the call synchronises it.
+ * n must be below 2^30 (the look-back words carry 30-bit counts); larger n,
+ * NULL pointers or a misaligned packed array return PIC_ERR_ARG.  The first
+ * call on a device looks up the array's device address (with that device
+ * current).  Calls share the array: each call resets the part that must
+ * start from zero, and calls whose kernels overlap on one GPU (different
+ * streams or host threads) race on it. */
+pic_status pic_compact_static(const float *z, const float *mu, const uint32_t *id,
+                              const uint32_t *packed, int64_t n, float *z_out, float *mu_out,
+                              uint32_t *id_out, uint32_t *packed_out, int64_t *n_alive,
+                              void *cuda_stream);
+
 /* Device kernels launched by the last pic_step call (for accounting). */
 int64_t pic_launch_count(const pic_ctx *ctx);
 

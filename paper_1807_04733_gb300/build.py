@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpic.so")
-SOURCES = ["pic_kernels.cu", "pic_capi.cu"]
+SOURCES = ["pic_kernels.cu", "pic_capi.cu", "pic_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "pic_internal.h"), os.path.join(ROOT, "include", "pic.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -32,8 +32,8 @@ REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u
 # symbols declared in include/pic.h
 EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_grad", "pic_records",
            "pic_set_records", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
-           "pic_profile_read", "pic_launch_count", "pic_destroy", "pic_last_error",
-           "pic_status_string")
+           "pic_profile_read", "pic_compact_static", "pic_launch_count", "pic_destroy",
+           "pic_last_error", "pic_status_string")
 KERNEL_KINDS = ("inject", "step", "step_moments", "compact")
 
 
@@ -106,6 +106,8 @@ def lib():
                                 C.POINTER(C.c_int32)]
         L.pic_profile.argtypes = [P, C.c_int]
         L.pic_profile_read.argtypes = [P, C.POINTER(pic_kernel_times)]
+        L.pic_compact_static.argtypes = [P, P, P, P, C.c_int64, P, P, P, P,
+                                         C.POINTER(C.c_int64), P]
         L.pic_launch_count.argtypes = [P]
         L.pic_launch_count.restype = C.c_int64
         L.pic_destroy.argtypes = [P]
@@ -246,6 +248,15 @@ def pic_profile_read(ctx):
     t = pic_kernel_times()
     _check(lib().pic_profile_read(ctx, C.byref(t)), ctx)
     return {k: (int(t.launches[i]), float(t.ms[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+
+def pic_compact_static(z, mu, id_, packed, n, z_out, mu_out, id_out, packed_out, stream=None):
+    """Allocation-free stable compaction of caller-owned device arrays (data
+    pointers); returns the number of live slots written to the outputs."""
+    alive = C.c_int64(0)
+    _check(lib().pic_compact_static(z, mu, id_, packed, n, z_out, mu_out, id_out, packed_out,
+                                    C.byref(alive), C.c_void_p(stream) if stream else None))
+    return alive.value
 
 
 def pic_launch_count(ctx):
