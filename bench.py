@@ -36,9 +36,11 @@ if ROOT not in sys.path:
 METRIC = "particle-steps/s"
 UNIT = "particle-steps/s"
 HBM_FALLBACK_GBS = 6800.0
-# algorithmic bytes: read 16 B of state + write z (4 B) per live carrier-step,
-# 8 B (mu, packed) per carrier whose record changed, 16 B per secondary placed
-B_STEP, B_CHANGED, B_SPAWN = 20, 8, 16
+# algorithmic bytes: read z, mu, packed (12 B) + write z (4 B) per live
+# carrier-step; the id (4 B) of every carrier that scatters or meets a
+# boundary (it keys that carrier's event draws); 8 B (mu, packed) per carrier
+# whose record changed; 16 B per secondary placed
+B_STEP, B_EVENTFUL, B_CHANGED, B_SPAWN = 16, 4, 8, 16
 
 
 def parse():
@@ -53,6 +55,7 @@ def parse():
     ap.add_argument("--deterministic", action="store_true")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--hist-mode", type=int, default=0)
+    ap.add_argument("--ring", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     return ap.parse_args()
@@ -298,7 +301,7 @@ def main():
     wl = wl.replace(seed=wl.seed + rank)
     total = pre + period * (args.warmup + 2 * args.steps) + 1
     ctx = pic.Context(wl, n_steps_max=max(wl.n_steps, total), blocks_per_sm=args.blocks_per_sm,
-                      hist_mode=args.hist_mode)
+                      hist_mode=args.hist_mode, ring_stages=args.ring)
     stream = ctx.stream
     # set-up: the pulse window (inputs resident in HBM before timing)
     left = pre
@@ -370,16 +373,19 @@ def main():
     ps_all, ps_e2e_all = float(cnts[0]), float(cnts[1])
 
     peak, peak_kind = measured_peak()
+    # the step is a kernel pair: the streaming pass (k_fast) and the event
+    # pass with the placement of secondaries (k_slow); one launch of each per
+    # time step, timed together
     n_k = ktimes["step"][0] + ktimes["step_moments"][0]
-    k_ms = ktimes["step"][1] + ktimes["step_moments"][1]
-    alg_bytes = B_STEP * delta["particle_steps"] + B_CHANGED * delta["changed"] + \
-        B_SPAWN * delta["spawned"]
+    k_ms = ktimes["step"][1] + ktimes["step_moments"][1] + ktimes["step_events"][1]
+    alg_bytes = B_STEP * delta["particle_steps"] + B_EVENTFUL * delta["eventful"] + \
+        B_CHANGED * delta["changed"] + B_SPAWN * delta["spawned"]
     achieved = (alg_bytes / n_k) / (k_ms / n_k * 1e-3) / 1e9 if n_k else 0.0
     traffic = None
     if NCU_TRAFFIC and NCU_TRAFFIC.get("src_sha") == kernel_sha():
         traffic = NCU_TRAFFIC["bytes_per_particle_step"] * delta["particle_steps"] / n_k
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_step",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_fast+k_slow",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes / n_k if n_k else 0,
                 "avg_launch_ms": k_ms / n_k if n_k else 0,
@@ -399,6 +405,7 @@ def main():
         "ledger_delta": delta,
         "kernel_ms": {k: v[1] for k, v in ktimes.items()},
         "kernel_launches": {k: v[0] for k, v in ktimes.items()},
+        "launch_config": ctx.launch_config(),
     }
     ctx.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

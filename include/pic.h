@@ -67,8 +67,8 @@ typedef enum {
 typedef struct {
     int32_t n_e;            /* energy bins, 1..PIC_MAX_NE; E_k = k*dE, k=1..n_e */
     float dt;               /* time step, fs (> 0); Strang step of Eq. strang */
-    float dz;               /* moment cell width, nm (> 0); layer thicknesses
-                               are whole cells */
+    float dz;               /* moment cell width, nm: a power of two (0.5, 1,
+                               2 ...); layer thicknesses are whole cells */
     uint64_t seed;          /* Philox4x32-10 key */
     uint32_t flags;         /* PIC_F_* */
     int32_t compact_every;  /* stable removal of dead slots every N steps (>= 1) */
@@ -80,7 +80,18 @@ typedef struct {
                                0 = as many as fit */
     int32_t hist_mode;      /* density deposit: 0 = shared-memory atomics,
                                1 = warp-aggregated (match-any) atomics */
+    int32_t ring_stages;    /* tiles in the step kernel's bulk-copy ring
+                               (2..8); 0 = chosen from the occupancy */
 } pic_params;
+
+/* Launch configuration a context chose (pic_launch_info). */
+typedef struct {
+    int32_t grid_step, grid_step_moments;   /* streaming pass */
+    int32_t grid_slow, grid_slow_moments;   /* event pass */
+    int32_t grid_compact, grid_inject;
+    int32_t ring_step, ring_step_moments;   /* bulk-copy ring depth (tiles) */
+    int64_t smem_step, smem_step_moments;   /* dynamic shared memory, bytes */
+} pic_launch_info;
 
 /* One laterally homogeneous layer stack (Sec. II: 1-D transport along z).
  * Layer l spans [sum_{j<l} cells_j, sum_{j<=l} cells_j) * dz; the outer
@@ -132,13 +143,16 @@ typedef struct {
     uint64_t particle_steps;/* live carriers advanced, summed over steps */
     uint64_t changed;       /* advanced carriers whose direction, energy, spin,
                                layer or liveness changed (records rewritten) */
+    uint64_t eventful;      /* advanced carriers that scattered or met a layer
+                               boundary or surface during the step */
 } pic_ledger;
 
-/* Device time of the library's kernels, per kind: 0 = source, 1 = step,
- * 2 = step with density deposit, 3 = compaction. */
+/* Device time of the library's kernels, per kind: 0 = source, 1 = step
+ * (streaming pass), 2 = step with density deposit (streaming pass),
+ * 3 = compaction, 4 = step (event pass and placement of secondaries). */
 typedef struct {
-    int64_t launches[4];
-    double ms[4];
+    int64_t launches[5];
+    double ms[5];
 } pic_kernel_times;
 
 /* One particle slot as returned by pic_records (16 bytes). */
@@ -257,6 +271,9 @@ pic_status pic_compact_static(const float *z, const float *mu, const uint32_t *i
                               const uint32_t *packed, int64_t n, float *z_out, float *mu_out,
                               uint32_t *id_out, uint32_t *packed_out, int64_t *n_alive,
                               void *cuda_stream);
+
+/* The launch configuration of a context's kernels. */
+pic_status pic_launch_config(const pic_ctx *ctx, pic_launch_info *out);
 
 /* Device kernels launched by the last pic_step call (for accounting). */
 int64_t pic_launch_count(const pic_ctx *ctx);

@@ -60,7 +60,7 @@ class Ledger(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in (
         "injected", "inject_dropped", "spawned", "spawn_dropped", "absorbed",
         "q_injected", "q_bath", "q_dropped", "iface_hits", "iface_transmit",
-        "truncated", "particle_steps", "changed")]
+        "truncated", "particle_steps", "changed", "eventful")]
 
     def as_dict(self):
         return {n: int(getattr(self, n)) for n, _ in self._fields_}

@@ -67,11 +67,12 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
 }
 
 /* substreams: the fourth counter word */
-#define SUB_SCAT 0x000u
+#define SUB_SCAT 0x000u   /* event words of a carrier that scatters */
 #define SUB_SEC  0x001u
 #define SUB_IF   0x100u   /* + 16*half + hit : primary flights */
 #define SUB_SIF  0x200u   /* + hit           : secondary's second-half flight */
 #define SUB_INJ  0x300u   /* + j             : injection draws */
+#define SUB_TEST 0x400u   /* scattering test: slot group of four, one word each */
 
 /* ---- packed word: k:8 | spin:1 | layer:4 | gen:8 | id_hi:11 ---- */
 #define PK_K(w)     ((w) & 0xFFu)
@@ -152,6 +153,17 @@ static void draw(const or_sim *s, uint64_t id, uint32_t step, uint32_t sub, uint
     or_philox4x32_10(ctr, key, r);
 }
 
+/* word of the scattering test of the carrier in slot i at this step: word
+ * i mod 4 of the call for the slot group i / 4 */
+static uint32_t test_word(const or_sim *s, int64_t slot)
+{
+    uint32_t ctr[4] = { (uint32_t)(slot >> 2), s->cfg.stack_index << 16, s->step, SUB_TEST };
+    uint32_t key[2] = { (uint32_t)s->cfg.seed, (uint32_t)(s->cfg.seed >> 32) };
+    uint32_t r[4];
+    or_philox4x32_10(ctr, key, r);
+    return r[slot & 3];
+}
+
 static int32_t cell_of(const or_sim *s, float z)
 {
     float q = floorf(z / s->cfg.dz);
@@ -176,8 +188,9 @@ static void flux(or_sim *s, int sg, int a, int b)
  * interface a uniform draw against T decides transmission (layer changes,
  * direction kept) or reflection (direction mirrored); the remaining time is
  * then flown with the velocity of the layer the carrier is in. */
-static void half_flight(or_sim *s, or_rec *p, float tau, uint64_t id, uint32_t sub0)
+static int half_flight(or_sim *s, or_rec *p, float tau, uint64_t id, uint32_t sub0)
 {
+    int met = 0;      /* boundaries met (surfaces and interfaces) */
     const or_config *c = &s->cfg;
     uint32_t w0 = p->packed;
     int k = (int)PK_K(w0), sg = (int)PK_S(w0), layer = (int)PK_L(w0);
@@ -192,6 +205,7 @@ static void half_flight(or_sim *s, or_rec *p, float tau, uint64_t id, uint32_t s
         if (p->mu > 0.0f && z1 > hi) { zb = hi; up = 1; }
         else if (p->mu < 0.0f && z1 < lo) { zb = lo; up = 0; }
         else { p->z = z1; break; }
+        ++met;
         if (hit == OR_MAX_HITS) { p->z = zb; s->led.truncated++; break; }
         float tb = (zb - p->z) / w;
         tau = tau - tb;
@@ -214,6 +228,7 @@ static void half_flight(or_sim *s, or_rec *p, float tau, uint64_t id, uint32_t s
         }
     }
     p->packed = (w0 & ~(0xFu << 9)) | ((uint32_t)layer << 9);
+    return met;
 }
 
 static int append(or_sim *s, or_rec r)
@@ -278,14 +293,20 @@ static void step_once(or_sim *s)
         int c_start = cell_of(s, p->z);
         int sg = (int)PK_S(p->packed);
 
-        half_flight(s, p, half, id, SUB_IF + 0);
+        const int met1 = half_flight(s, p, half, id, SUB_IF + 0);
 
-        /* Scattering(dt): one Monte-Carlo test against tau_eff (Eq. lifetimes) */
-        uint32_t x[4];
-        draw(s, id, s->step, SUB_SCAT, x);
+        /* Scattering(dt): one Monte-Carlo test against tau_eff (Eq. lifetimes);
+         * the event words are drawn only for a carrier that scatters */
+        uint32_t x[4] = { test_word(s, i), 0u, 0u, 0u };
+        if (x[0] < s->P_thr[idx3(s, c->layer_mat[PK_L(p->packed)], sg, (int)PK_K(p->packed))]) {
+            uint32_t ev[4];
+            draw(s, id, s->step, SUB_SCAT, ev);
+            x[1] = ev[1]; x[2] = ev[2]; x[3] = ev[3];
+        }
         int k = (int)PK_K(p->packed), layer = (int)PK_L(p->packed);
         int m = c->layer_mat[layer];
         int t = idx3(s, m, sg, k);
+        if (met1 || x[0] < s->P_thr[t]) s->led.eventful++;
         if (x[0] < s->P_thr[t]) {
             int inel = x[1] < s->Q_thr[t];
             if (k == 1 && (inel || (c->flags & OR_F_LOWEST_BIN_ANY))) {
@@ -337,7 +358,8 @@ static void step_once(or_sim *s)
             }
         }
 
-        half_flight(s, p, half, id, SUB_IF + 16);
+        const int met2 = half_flight(s, p, half, id, SUB_IF + 16);
+        if (met2 && !met1 && !(x[0] < s->P_thr[t])) s->led.eventful++;
         flux(s, sg, c_start, cell_of(s, p->z));
         if (p->mu != mu_in || p->packed != pk_in) s->led.changed++;
     }

@@ -69,6 +69,7 @@ typedef struct {
     uint64_t q_injected, q_bath, q_dropped;
     uint64_t iface_hits, iface_transmit, truncated, particle_steps;
     uint64_t changed;     /* advanced carriers whose mu or packed word changed */
+    uint64_t eventful;    /* advanced carriers that scattered or met a boundary */
 } or_ledger;
 
 typedef struct or_sim or_sim;

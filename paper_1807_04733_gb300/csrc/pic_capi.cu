@@ -44,7 +44,8 @@ struct pic_ctx {
     long long *d_inj = nullptr;
     float *d_z[2] = {nullptr, nullptr}, *d_mu[2] = {nullptr, nullptr};
     uint32_t *d_id[2] = {nullptr, nullptr}, *d_pk[2] = {nullptr, nullptr};
-    float4 *d_stage = nullptr;
+    float4 *d_stage = nullptr, *d_qrec = nullptr;
+    uint32_t *d_bits = nullptr, *d_qcnt = nullptr;
     unsigned long long *d_status = nullptr;
     uint32_t *d_nh = nullptr;
     int32_t *d_J = nullptr;
@@ -97,10 +98,15 @@ bool valid_params(const pic_params *p, std::string &why)
     if (p->n_e < 1 || p->n_e > PIC_MAX_NE) { why = "n_e out of range"; return false; }
     if (!(p->dt > 0.f) || !std::isfinite(p->dt)) { why = "dt must be > 0"; return false; }
     if (!(p->dz > 0.f) || !std::isfinite(p->dz)) { why = "dz must be > 0"; return false; }
+    int dz_exp = 0;
+    if (std::frexp(p->dz, &dz_exp) != 0.5f) { why = "dz must be a power of two"; return false; }
     if (p->compact_every < 1 || p->moment_every < 1) { why = "compact_every/moment_every < 1"; return false; }
     if (p->n_steps_max < 0) { why = "n_steps_max < 0"; return false; }
     if (p->hist_mode < 0 || p->hist_mode > 1) { why = "hist_mode must be 0 or 1"; return false; }
     if (p->blocks_per_sm < 0) { why = "blocks_per_sm < 0"; return false; }
+    if (p->ring_stages != 0 && (p->ring_stages < 2 || p->ring_stages > 8)) {
+        why = "ring_stages must be 0 or 2..8"; return false;
+    }
     return true;
 }
 
@@ -232,15 +238,26 @@ cudaError_t dalloc(T **p, size_t n)
     return cudaMalloc((void **)p, sizeof(T) * (n ? n : 1));
 }
 
+template <class T>
+void release(T *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+// Frees every device buffer of the context once; a failure here must not
+// linger as the runtime's pending error for an unrelated later call.
 void free_all(pic_ctx *c)
 {
-    cudaFree(c->d_stacks); cudaFree(c->d_ent); cudaFree(c->d_T); cudaFree(c->d_cdf_thr);
-    cudaFree(c->d_cdf_cell); cudaFree(c->d_cdf_layer); cudaFree(c->d_inj);
+    release(c->d_stacks); release(c->d_ent); release(c->d_T); release(c->d_cdf_thr);
+    release(c->d_cdf_cell); release(c->d_cdf_layer); release(c->d_inj);
     for (int b = 0; b < 2; ++b) {
-        cudaFree(c->d_z[b]); cudaFree(c->d_mu[b]); cudaFree(c->d_id[b]); cudaFree(c->d_pk[b]);
+        release(c->d_z[b]); release(c->d_mu[b]); release(c->d_id[b]); release(c->d_pk[b]);
     }
-    cudaFree(c->d_stage); cudaFree(c->d_status); cudaFree(c->d_nh); cudaFree(c->d_J);
-    cudaFree(c->d_cnt); cudaFree(c->d_ctl); cudaFree(c->d_status);
+    release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh);
+    release(c->d_qrec); release(c->d_qcnt); release(c->d_J); release(c->d_cnt);
+    release(c->d_ctl);
+    cudaGetLastError();
 }
 
 // Launch one kernel through `fn`, bracketed by events when profiling.
@@ -280,6 +297,10 @@ pic_status device_status(pic_ctx *c)
 }
 
 }  // namespace
+
+namespace pic {
+void pic_set_static_error(const char *msg) { g_init_error = msg ? msg : ""; }
+}
 
 extern "C" {
 
@@ -398,6 +419,11 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         jbin_max = std::max(jbin_max, 2 * (cells + 1));
         h.inj.assign((size_t)2 * p->n_steps_max, 0);
     }
+    if (c->total_slots >= (int64_t(1) << 32)) {
+        g_init_error = "total capacity of a context must stay below 2^32 slots";
+        delete c;
+        return PIC_ERR_ARG;
+    }
     int64_t total_cells = 0;
     for (int s = 0; s < n_stacks; ++s) {
         c->ds[s].cdf_off = total_cells;
@@ -420,6 +446,8 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         ALLOC(c->d_pk[b], c->total_slots);
     }
     ALLOC(c->d_stage, c->total_slots);
+    ALLOC(c->d_bits, c->total_slots / 32 + 1);
+    ALLOC(c->d_qrec, c->total_slots);
     ALLOC(c->d_nh, c->nh_total);
     ALLOC(c->d_J, c->J_total);
     ALLOC(c->d_cnt, n_stacks);
@@ -442,20 +470,24 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         a.z[b] = c->d_z[b]; a.mu[b] = c->d_mu[b]; a.id[b] = c->d_id[b]; a.pk[b] = c->d_pk[b];
     }
     a.stage = c->d_stage;
+    a.spawn_bits = c->d_bits;
+    a.qrec = c->d_qrec;
     a.n_hist = c->d_nh; a.J_hist = c->d_J; a.cnt = c->d_cnt; a.ctl = c->d_ctl;
     a.seed_lo = (uint32_t)p->seed; a.seed_hi = (uint32_t)(p->seed >> 32);
+    for (int r = 0; r < 10; ++r) {      // Philox4x32-10 round keys (Weyl sequence)
+        a.rk0[r] = a.seed_lo + (uint32_t)r * 0x9E3779B9u;
+        a.rk1[r] = a.seed_hi + (uint32_t)r * 0xBB67AE85u;
+    }
     a.half_dt = p->dt * 0.5f;
     a.dz = p->dz;
-    int ex = 0;
-    const float mant = std::frexp(p->dz, &ex);
-    a.dz_pow2 = mant == 0.5f;
-    a.inv_dz = a.dz_pow2 ? 1.0f / p->dz : 0.f;
+    a.dz_pow2 = 1;
+    a.inv_dz = 1.0f / p->dz;      // exact: dz is a power of two
     a.flags = p->flags; a.n_e = ne; a.moment_every = p->moment_every;
     a.step = 0;
     a.tab_max = tab_max; a.T_max = T_max; a.nbin_max = nbin_max; a.jbin_max = jbin_max;
     a.spin_limit = 1u << 24;
 
-    e = configure(a, p->blocks_per_sm, p->hist_mode, &c->lc);
+    e = configure(a, p->blocks_per_sm, p->ring_stages, p->hist_mode, &c->lc);
     if (e != cudaSuccess) {
         g_init_error = std::string("kernel configuration (moment grid too large for shared "
                                    "memory, or no device): ") + cudaGetErrorString(e);
@@ -464,8 +496,10 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         cudaGetLastError();
         return PIC_ERR_ARG;   // moment grid too large for shared memory, or no device
     }
-    const int gmax = std::max(std::max(c->lc.grid_step, c->lc.grid_step_dep), c->lc.grid_compact);
-    if (dalloc(&c->d_status, (size_t)gmax) != cudaSuccess) {
+    const int gmax = std::max({c->lc.grid_fast, c->lc.grid_fast_dep, c->lc.grid_slow,
+                               c->lc.grid_slow_dep, c->lc.grid_compact});
+    if (dalloc(&c->d_status, (size_t)gmax) != cudaSuccess ||
+        dalloc(&c->d_qcnt, (size_t)gmax) != cudaSuccess) {
         g_init_error = "device allocation of the look-back words";
         free_all(c);
         delete c;
@@ -473,6 +507,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         return PIC_ERR_ALLOC;
     }
     a.status = c->d_status;
+    a.qcnt = c->d_qcnt;
 
     cudaStream_t st = c->stream;
     DevCtl ctl{};
@@ -484,6 +519,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     if (e == cudaSuccess && !Tall.empty()) e = cudaMemcpyAsync(c->d_T, Tall.data(), 4 * Tall.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_inj, 0, sizeof(long long) * std::max<size_t>((size_t)n_stacks * 2 * p->n_steps_max, 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned long long) * gmax, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bits, 0, 4 * (size_t)(c->total_slots / 32 + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_nh, 0, 4 * (size_t)std::max<int64_t>(c->nh_total, 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_J, 0, 4 * (size_t)std::max<int64_t>(c->J_total, 1), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt, cnt.data(), sizeof(DevCounters) * n_stacks, cudaMemcpyHostToDevice, st);
@@ -562,7 +598,11 @@ pic_status pic_step(pic_ctx *c, int n_steps)
             ++c->launches;
         }
         if (e == cudaSuccess) {
-            e = timed(c, dep ? 2 : 1, [&] { return launch_step(a, lc, det, dep, c->p.hist_mode, st); });
+            e = timed(c, dep ? 2 : 1, [&] { return launch_fast(a, lc, det, dep, c->p.hist_mode, st); });
+            ++c->launches;
+        }
+        if (e == cudaSuccess) {
+            e = timed(c, 4, [&] { return launch_slow(a, lc, det, dep, st); });
             ++c->launches;
         }
         if (e == cudaSuccess && inj1) {
@@ -691,6 +731,22 @@ pic_status pic_shape(const pic_ctx *c, int stack, int32_t *n_cells, int32_t *n_o
 }
 
 int64_t pic_launch_count(const pic_ctx *c) { return c ? c->launches : 0; }
+
+pic_status pic_launch_config(const pic_ctx *c, pic_launch_info *out)
+{
+    if (!c || !out) return PIC_ERR_ARG;
+    out->grid_step = c->lc.grid_fast;
+    out->grid_step_moments = c->lc.grid_fast_dep;
+    out->grid_slow = c->lc.grid_slow;
+    out->grid_slow_moments = c->lc.grid_slow_dep;
+    out->grid_compact = c->lc.grid_compact;
+    out->grid_inject = c->lc.grid_inject;
+    out->ring_step = c->lc.ring_fast;
+    out->ring_step_moments = c->lc.ring_fast_dep;
+    out->smem_step = (int64_t)c->lc.smem_fast;
+    out->smem_step_moments = (int64_t)c->lc.smem_fast_dep;
+    return PIC_OK;
+}
 
 pic_status pic_profile(pic_ctx *c, int enable)
 {

@@ -6,29 +6,29 @@
 //               sum_s round_up(capacity_s, TILE); stack s owns slots
 //               [base_s, base_s + capacity_s).  One thread moves four
 //               consecutive slots with one 128-bit load/store per array.
-//   staging   : float4 per slot (z_end, mu, packed bits, z_spawn): secondary
-//               carriers of a step, in slot order, before their final place
-//               is known.
+//   staging   : float4 per slot (z_end, mu, packed bits, z_spawn): the
+//               secondary of the carrier at that position, before its final
+//               place is known, flagged by one bit per slot in spawn_bits.
 //   tables    : per stack, per layer: {v, P_thr, Q_thr} (16 B) for
 //               [layer][spin][k], the interface thresholds, P0 per layer.
 //   moments   : uint32 densities and int32 fluxes per output window.
 #pragma once
 #include <cstdint>
 
-#include "../../include/pic.h"
+#include "pic.h"
 
 namespace pic {
 
 constexpr int TPB = 256;            // threads per block of the streaming kernels
 constexpr int VEC = 4;              // particles per thread per tile (128-bit)
 constexpr int TILE = TPB * VEC;     // particles per tile
-constexpr int LEDGER_N = 13;        // fields of pic_ledger
+constexpr int LEDGER_N = 14;        // fields of pic_ledger
 
 // ledger field indices (order of pic_ledger)
 enum {
     L_INJECTED, L_INJECT_DROPPED, L_SPAWNED, L_SPAWN_DROPPED, L_ABSORBED,
     L_Q_INJECTED, L_Q_BATH, L_Q_DROPPED, L_IFACE_HITS, L_IFACE_TRANSMIT,
-    L_TRUNCATED, L_PARTICLE_STEPS, L_CHANGED
+    L_TRUNCATED, L_PARTICLE_STEPS, L_CHANGED, L_EVENTFUL
 };
 
 // Philox counter layout: ctr = {id_lo, id_hi | stack << 16, step, substream}
@@ -38,6 +38,7 @@ enum : uint32_t {
     SUB_IF = 0x100u,     // + 16*half + hit: interface draws of a carrier
     SUB_SIF = 0x200u,    // + hit: the secondary's second-half flight
     SUB_INJ = 0x300u,    // + j: source draws
+    SUB_TEST = 0x400u,   // scattering test: ctr.x = slot / 4, word slot % 4
 };
 
 struct TabEnt {          // one (layer, spin, k) entry
@@ -94,6 +95,7 @@ struct Args {            // everything a kernel needs, passed by value
     DevCounters *cnt;
     DevCtl *ctl;
     uint32_t seed_lo, seed_hi;
+    uint32_t rk0[10], rk1[10];               // Philox round keys (key + r * Weyl)
     float half_dt, dz, inv_dz;
     int dz_pow2;
     uint32_t flags;
@@ -101,19 +103,31 @@ struct Args {            // everything a kernel needs, passed by value
     int moment_every;
     uint32_t step;
     int tab_max, T_max, nbin_max, jbin_max;  // shared-memory sizing
-    unsigned int spin_limit;                 // look-back wait bound
+    unsigned int spin_limit;                 // bound of every device-side wait
+    int ring;                                // tiles in k_fast's copy ring
+    int grid_fast;                           // k_fast's grid (read by k_slow)
+    uint32_t *spawn_bits;                    // one bit per position: secondary staged
+    float4 *qrec;                            // eventful carriers: z, mu, packed, position
+    uint32_t *qcnt;                          // queue length per fast block
 };
+
+// reason of the last failure of a call without a context (pic_capi.cu);
+// returned by pic_last_error(NULL)
+void pic_set_static_error(const char *msg);
 
 // host-side launchers (pic_kernels.cu)
 struct LaunchCfg {
-    int grid_step, grid_step_dep, grid_compact, grid_inject;
-    size_t smem_step, smem_step_dep;
+    int grid_fast, grid_fast_dep, grid_slow, grid_slow_dep, grid_compact, grid_inject;
+    int ring_fast, ring_fast_dep;
+    size_t smem_fast, smem_fast_dep, smem_slow, smem_slow_dep;
 };
-cudaError_t configure(const Args &a, int blocks_per_sm, int hist_mode, LaunchCfg *cfg);
+cudaError_t configure(const Args &a, int blocks_per_sm, int ring, int hist_mode, LaunchCfg *cfg);
 cudaError_t launch_inject(const Args &a, const LaunchCfg &c, int half, bool deposit,
                           cudaStream_t s);
-cudaError_t launch_step(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
+cudaError_t launch_fast(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
                         int hist_mode, cudaStream_t s);
+cudaError_t launch_slow(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
+                        cudaStream_t s);
 cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s);
 
 }  // namespace pic

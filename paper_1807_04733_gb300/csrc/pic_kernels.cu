@@ -24,18 +24,20 @@
 namespace pic {
 
 // ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon et al., SC'11): two 32x32->64 products per round,
-// round multipliers 0xD2511F53 / 0xCD9E8D57, Weyl key increments
-// 0x9E3779B9 / 0xBB67AE85 between rounds.
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// with the round multipliers 0xD2511F53 / 0xCD9E8D57; the key of round r is
+// key + r * (0x9E3779B9, 0xBB67AE85).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
+// Philox4x32-10 with the ten round keys taken from the kernel arguments
+// (precomputed on the host), so no key arithmetic runs per call
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const Args &a)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        if (r) { k0 += 0x9E3779B9u; k1 += 0xBB67AE85u; }
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        const unsigned long long p0 = 0xD2511F53ull * c.x;
+        const unsigned long long p1 = 0xCD9E8D57ull * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ a.rk0[r], (uint32_t)p1,
+                       (uint32_t)(p0 >> 32) ^ c.w ^ a.rk1[r], (uint32_t)p0);
     }
     return c;
 }
@@ -72,29 +74,30 @@ struct Stk {
     uint32_t ctr_hi;     // stack << 16
 };
 
+// Cell of a depth z >= 0: floor(z / dz), clamped to the last cell.  dz is a
+// power of two, so q = z * (1/dz) is exact; adding 2^23 with rounding toward
+// -inf leaves floor(q) in the low mantissa bits (0 <= q < 2^23).
 __device__ __forceinline__ int cell_of(const Args &a, const Stk &s, float z)
 {
-    const float q = floorf(a.dz_pow2 ? __fmul_rn(z, a.inv_dz) : __fdiv_rn(z, a.dz));
-    int c = (int)q;
-    if (q < 0.f) c = 0;
-    if (c > s.n_cells - 1) c = s.n_cells - 1;
-    return c;
+    const float q = __fmul_rn(z, a.inv_dz);
+    const int c = __float_as_int(__fadd_rd(q, 8388608.0f)) - 0x4B000000;
+    return c < s.n_cells - 1 ? c : s.n_cells - 1;
 }
 
 // Transport for a time tau (Eq. Strang-transport, Sec. III): free flight in
 // the current layer, mirror reflection at the vacuum surfaces, a uniform
 // draw against T at an interface (transmit: layer changes, mu kept;
 // reflect: mu mirrored), the remaining time flown in the new layer.
+// e, lo, hi: table entry and edges of the current layer (updated on transmission).
 template <bool DET>
 __device__ __forceinline__ void flight(const Args &a, const Stk &s, float &z, float &mu,
-                                       int &layer, int sg, int k, float tau, uint32_t id_lo,
-                                       uint32_t ctr_y, uint32_t sub0, Tally &t)
+                                       int &layer, TabEnt &e, float &lo, float &hi, int sg,
+                                       int k, float tau, uint32_t id_lo, uint32_t ctr_y,
+                                       uint32_t sub0, Tally &t)
 {
     for (int hit = 0;; ++hit) {
-        const float v = s.ent[(layer * 2 + sg) * s.n_e + (k - 1)].v;
-        const float w = __fmul_rn(v, mu);
+        const float w = __fmul_rn(e.v, mu);
         const float z1 = DET ? __fadd_rn(z, __fmul_rn(w, tau)) : __fmaf_rn(w, tau, z);
-        const float lo = s.edge[layer], hi = s.edge[layer + 1];
         float zb;
         bool up;
         if (mu > 0.f && z1 > hi) { zb = hi; up = true; }
@@ -113,12 +116,18 @@ __device__ __forceinline__ void flight(const Args &a, const Stk &s, float &z, fl
             bool trans = true;
             ++t.hits;
             if (!(a.flags & PIC_F_TRANSPARENT)) {
-                const uint4 r = philox(make_uint4(id_lo, ctr_y, a.step, sub0 + (uint32_t)hit),
-                                       a.seed_lo, a.seed_hi);
+                const uint4 r = philox_rk(make_uint4(id_lo, ctr_y, a.step, sub0 + (uint32_t)hit), a);
                 trans = r.x < s.T[((iface * 2 + dir) * 2 + sg) * s.n_e + (k - 1)];
             }
-            if (trans) { layer += up ? 1 : -1; ++t.trans; }
-            else mu = -mu;
+            if (trans) {
+                layer += up ? 1 : -1;
+                ++t.trans;
+                e = s.ent[(layer * 2 + sg) * s.n_e + (k - 1)];
+                lo = s.edge[layer];
+                hi = s.edge[layer + 1];
+            } else {
+                mu = -mu;
+            }
         }
     }
 }
@@ -280,51 +289,200 @@ __device__ __forceinline__ void load_stack(const Args &a, int s, Stk &k, DevStac
 }
 
 // ---------------------------------------------------------------------------
-// k_step: Transport(dt/2) -> Scattering(dt) -> Transport(dt/2) for all slots
+// Tensor-memory-accelerator (bulk copy) helpers: 1-D cp.async.bulk of a tile
+// of each particle array into a shared-memory ring, completion tracked by an
+// mbarrier per ring stage.
 // ---------------------------------------------------------------------------
-template <bool DET, bool DEPN, bool WAGG>
-__global__ void __launch_bounds__(TPB) k_step(const Args a)
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    TabEnt *s_ent = reinterpret_cast<TabEnt *>(smem);
-    uint32_t *s_T = reinterpret_cast<uint32_t *>(s_ent + a.tab_max);
-    int32_t *s_J = reinterpret_cast<int32_t *>(s_T + a.T_max);
-    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + a.jbin_max);
-    __shared__ long long s_tpref[PIC_MAX_STACKS + 1];
-    __shared__ long long s_nsl[PIC_MAX_STACKS];
-    __shared__ float s_edge[PIC_MAX_LAYERS + 1];
-    __shared__ uint32_t s_p0[PIC_MAX_LAYERS];
-    __shared__ DevStack s_st;
-    __shared__ int s_w[TPB / 32];
-    __shared__ unsigned long long s_r[TPB / 32];
-    __shared__ long long s_prefix;
-    __shared__ int s_flag;
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
 
-    const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false if the copy did not land within `limit` polls
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity,
+                                          unsigned int limit)
+{
+    for (unsigned int it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
+                                          unsigned long long *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+constexpr int MAX_RING = 8;
+constexpr uint32_t TILE_BYTES = TILE * 4u;      // one array of one tile
+
+// Chunk of block j of a grid of G blocks over T tiles: [T*j/G, T*(j+1)/G).
+__device__ __forceinline__ long long chunk_lo(long long T, int j, int G)
+{
+    return T * j / G;
+}
+
+// Tiles of slow block j: the union of the chunks of the fast blocks
+// [Gf*j/Gs, Gf*(j+1)/Gs), so that it covers whole fast chunks.
+__device__ __forceinline__ long long slow_lo(long long T, int j, int Gs, int Gf)
+{
+    return chunk_lo(T, (int)((long long)Gf * j / Gs), Gf);
+}
+
+// Exclusive prefix of the secondaries of the stack segment that starts slow
+// block b's chunk (stack tiles start at ts): walk back over the blocks whose
+// chunks end inside the same stack.  Bounded wait.
+__device__ long long look_back_slow(const Args &a, unsigned int ep, long long T, long long ts,
+                                    int b, int Gs, int Gf)
+{
+    long long prefix = 0;
+    for (int j = b - 1; j >= 0; --j) {
+        const long long jt0 = slow_lo(T, j, Gs, Gf), jt1 = slow_lo(T, j + 1, Gs, Gf);
+        if (jt1 <= ts) break;
+        if (jt0 == jt1) continue;
+        unsigned long long w = 0;
+        unsigned int it = 0;
+        for (;;) {
+            w = ld_volatile_u64(&a.status[j]);
+            if ((unsigned int)(w >> 32) == ep && ((w >> 30) & 3ull)) break;
+            if (++it > a.spin_limit) {
+                atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+                a.ctl->timeout_where = 1u;
+                w = FLAG_P << 30;
+                break;
+            }
+            if (it > 64) __nanosleep(128);
+        }
+        prefix += (long long)(w & 0x3FFFFFFFull);
+        if (((w >> 30) & 3ull) == FLAG_P) break;
+    }
+    return prefix;
+}
+
+// tile prefix over the stacks, in dynamic shared memory
+__device__ __forceinline__ long long make_tiles(const Args &a, long long *s_tpref, long long *s_nsl)
+{
+    for (int i = threadIdx.x; i < a.n_stacks; i += TPB) s_nsl[i] = (long long)a.cnt[i].n_slots;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long acc = 0;
+        for (int i = 0; i < a.n_stacks; ++i) {
+            s_tpref[i] = acc;
+            acc += (s_nsl[i] + TILE - 1) / TILE;
+        }
+        s_tpref[a.n_stacks] = acc;
+    }
+    __syncthreads();
+    return s_tpref[a.n_stacks];
+}
+
+// ---------------------------------------------------------------------------
+// k_fast: the common case of Transport(dt/2) -> Scattering(dt) ->
+// Transport(dt/2), streamed.
+//
+// Each block streams its chunk of tiles through a ring of a.ring stages: one
+// thread issues the bulk copies of the four arrays of tile i + ring while the
+// block works on tile i.  A thread handles slots tid + r*TPB of a tile
+// (consecutive across a warp: conflict-free shared reads, coalesced writes).
+// A carrier that does not scatter and stays inside its layer for the whole
+// step is finished here: new depth, flux across the cell faces it passed,
+// density deposit.  Every other carrier ("eventful": it scatters or meets a
+// boundary) is copied, with its position, to the block's region of the
+// queue, in tile order, for k_slow.
+// ---------------------------------------------------------------------------
+#ifndef PIC_FAST_MIN_BLOCKS
+#define PIC_FAST_MIN_BLOCKS 4      // resident blocks per SM the register budget allows
+#endif
+template <bool DET, bool DEPN, bool WAGG>
+__global__ void __launch_bounds__(TPB, PIC_FAST_MIN_BLOCKS) k_fast(const Args a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *ring = reinterpret_cast<float *>(smem);                      // a.ring x 3 x TILE
+    TabEnt *s_ent = reinterpret_cast<TabEnt *>(ring + (size_t)a.ring * 3 * TILE);
+    int32_t *s_J = reinterpret_cast<int32_t *>(s_ent + a.tab_max);
+    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + a.jbin_max);
+    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max : 0) + 1) + 0;
+    s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
+    long long *s_nsl = s_tpref + a.n_stacks + 1;
+    __shared__ __align__(8) unsigned long long s_bar[MAX_RING];
+    __shared__ float s_edge[PIC_MAX_LAYERS + 1];
+    __shared__ DevStack s_st;
+    __shared__ unsigned long long s_r[TPB / 32];
+    __shared__ int s_qn, s_abort;
+
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
     const int b = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
-    Plan p;
-    make_plan(a, s_tpref, s_nsl, p);
+    const int lane = tid & 31;
+    const unsigned int lt_mask = (1u << lane) - 1u;
+    const long long T = make_tiles(a, s_tpref, s_nsl);
+    const long long t0 = chunk_lo(T, b, G), t1 = chunk_lo(T, b + 1, G);
+    const long long ntiles = t1 - t0;
+    const long long pos0 = t0 * TILE;                // queue region of this block
     const int tj = (int)(a.step / (uint32_t)a.moment_every);
     const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
     const float half = a.half_dt;
+    const int nring = a.ring;
+    float *Z = a.z[cur];
+    const float *MU = a.mu[cur];
+    const uint32_t *PK = a.pk[cur];
 
-    float *Z = a.z[cur], *MU = a.mu[cur];
-    const uint32_t *ID = a.id[cur];
-    uint32_t *PK = a.pk[cur];
+    if (tid == 0) {
+        for (int i = 0; i < nring; ++i) mbar_init(&s_bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_qn = 0;
+        s_abort = 0;
+    }
+    __syncthreads();
+    // the common path needs z, mu and the packed word only (ids key the event
+    // draws of eventful carriers, which k_slow reads itself)
+    auto issue = [&](long long t, int stg) {
+        const int s = stack_of(s_tpref, a.n_stacks, t);
+        const long long off = a.stacks[s].base + (t - s_tpref[s]) * TILE;
+        float *dst = ring + (size_t)stg * 3 * TILE;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&s_bar[stg], 3 * TILE_BYTES);
+        bulk_load(dst, Z + off, TILE_BYTES, &s_bar[stg]);
+        bulk_load(dst + TILE, MU + off, TILE_BYTES, &s_bar[stg]);
+        bulk_load(dst + 2 * TILE, PK + off, TILE_BYTES, &s_bar[stg]);
+    };
+    if (tid == 0)
+        for (long long i = 0; i < ntiles && i < nring; ++i) issue(t0 + i, (int)i);
 
-    // the first segment (stack of tile t0) may start inside its stack; its
-    // secondaries are staged until the look-back gives their prefix
     int seg_stack = -1;
-    long long seg_first = 0, seg_count = 0, stage0 = p.t0 * TILE, stage_cur = p.t0 * TILE;
-    bool staged_seg = false;          // current segment is the staged one
-    int staged_stack = -1;
-    long long staged_count = 0;
+    long long consumed = 0;
     Stk S{};
-    Tally ty{};
+    uint32_t n_steps = 0;            // advanced carriers of the segment
+    uint32_t n_queued = 0;           // of which eventful (queued)
 
-    auto flush_segment = [&](int s, bool deposit_hist) {
-        // moments and ledger of stack s
+    auto flush = [&](int s) {
         __syncthreads();
         const DevStack &st = s_st;
         const int nf = st.n_cells + 1;
@@ -333,7 +491,204 @@ __global__ void __launch_bounds__(TPB) k_step(const Args a)
             const int v = s_J[i];
             if (v) atomicAdd(&gJ[i], v);
         }
-        if (DEPN && deposit_hist) {
+        if (DEPN) {
+            const int nbins = 2 * a.n_e * st.n_cells;
+            uint32_t *gN = a.n_hist + st.n_off + (long long)tout * nbins;
+            for (int i = tid; i < nbins; i += TPB) {
+                const uint32_t v = s_n[i];
+                if (v) atomicAdd(&gN[i], v);
+            }
+        }
+        const unsigned long long v0 = block_sum_u64(n_steps, s_r);
+        if (tid == 0 && v0) atomicAdd(&a.cnt[s].led[L_PARTICLE_STEPS], v0);
+        const unsigned long long v1 = block_sum_u64(n_queued, s_r);
+        if (tid == 0 && v1) atomicAdd(&a.cnt[s].led[L_EVENTFUL], v1);
+        n_steps = 0;
+        n_queued = 0;
+        __syncthreads();
+    };
+
+    for (long long i = 0; i < ntiles; ++i) {
+        const long long t = t0 + i;
+        const int s = stack_of(s_tpref, a.n_stacks, t);
+        if (s != seg_stack) {
+            if (seg_stack >= 0) flush(seg_stack);
+            __syncthreads();
+            if (tid == 0) s_st = a.stacks[s];
+            __syncthreads();
+            const DevStack &st = s_st;
+            for (int q = tid; q < st.tab_n; q += TPB) s_ent[q] = a.ent[st.ent_off + q];
+            if (tid <= st.n_layers) s_edge[tid] = st.edge[tid];
+            for (int q = tid; q < 2 * (st.n_cells + 1); q += TPB) s_J[q] = 0;
+            if (DEPN)
+                for (int q = tid; q < 2 * a.n_e * st.n_cells; q += TPB) s_n[q] = 0u;
+            S.ent = s_ent; S.edge = s_edge; S.n_layers = st.n_layers; S.n_cells = st.n_cells;
+            S.n_e = a.n_e; S.ctr_hi = (uint32_t)s << 16;
+            seg_stack = s;
+            __syncthreads();
+        }
+        const long long nsl = s_nsl[s];
+        const long long tslot0 = (t - s_tpref[s]) * TILE;
+        const int stg = (int)(i % nring);
+        if (!mbar_wait(&s_bar[stg], (uint32_t)((i / nring) & 1), a.spin_limit)) {
+            atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+            a.ctl->timeout_where = 3u;
+            s_abort = 1;
+        }
+        consumed = i + 1;
+        const float *rz = ring + (size_t)stg * 3 * TILE;
+        const float *rmu = rz + TILE;
+        const uint32_t *rpk = reinterpret_cast<const uint32_t *>(rz + 2 * TILE);
+        float *gZ = Z + s_st.base + tslot0;
+        const int nvalid = nsl - tslot0 < TILE ? (int)(nsl - tslot0) : TILE;
+        // four consecutive slots per thread; one Philox call gives the four
+        // scattering-test words of the slot group
+        const int i0 = VEC * tid;
+        const float4 z4 = reinterpret_cast<const float4 *>(rz)[tid];
+        const float4 m4 = reinterpret_cast<const float4 *>(rmu)[tid];
+        const uint4 p4 = reinterpret_cast<const uint4 *>(rpk)[tid];
+        const uint4 xg = philox_rk(make_uint4((uint32_t)(tslot0 >> 2) + (uint32_t)tid, S.ctr_hi,
+                                              a.step, SUB_TEST), a);
+        const float zin[VEC] = {z4.x, z4.y, z4.z, z4.w};
+        const float min_[VEC] = {m4.x, m4.y, m4.z, m4.w};
+        const uint32_t pin[VEC] = {p4.x, p4.y, p4.z, p4.w};
+        const uint32_t xw[VEC] = {xg.x, xg.y, xg.z, xg.w};
+        float zo[VEC] = {z4.x, z4.y, z4.z, z4.w};
+        uint32_t slowbits = 0;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            int bin = -1;
+            const uint32_t pk = pin[j];
+            const int k = (int)(pk & 0xFFu);
+            if (i0 + j < nvalid && k != 0) {
+                ++n_steps;
+                const float z = zin[j], mu = min_[j];
+                const int sg = (int)((pk >> 8) & 1u), layer = (int)((pk >> 9) & 0xFu);
+                const TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
+                const float w = __fmul_rn(e.v, mu);
+                const float z1 = DET ? __fadd_rn(z, __fmul_rn(w, half)) : __fmaf_rn(w, half, z);
+                const float z2 = DET ? __fadd_rn(z1, __fmul_rn(w, half)) : __fmaf_rn(w, half, z1);
+                // the motion is monotone within the step: the end point decides
+                const bool cross = mu > 0.f ? (z2 > S.edge[layer + 1]) : (z2 < S.edge[layer]);
+                if (cross || xw[j] < e.P) {
+                    slowbits |= 1u << j;
+                } else {
+                    const int c0 = cell_of(a, S, z), c1 = cell_of(a, S, z2);
+                    const int nf = S.n_cells + 1;
+                    if (c1 == c0 + 1) atomicAdd(&s_J[sg * nf + c1], 1);
+                    else if (c1 == c0 - 1) atomicAdd(&s_J[sg * nf + c0], -1);
+                    else if (c1 != c0) add_flux(s_J, nf, sg, c0, c1);
+                    zo[j] = z2;
+                    if (DEPN) bin = (sg * S.n_e + (k - 1)) * S.n_cells + c1;
+                }
+            }
+            if (DEPN && !WAGG && bin >= 0) atomicAdd(&s_n[bin], 1u);
+            if (DEPN && WAGG) {
+                const unsigned int m = __match_any_sync(0xffffffffu, bin);
+                if (bin >= 0 && lane == __ffs(m) - 1) atomicAdd(&s_n[bin], (uint32_t)__popc(m));
+            }
+        }
+        // new depths (an eventful carrier keeps its old one here: k_slow
+        // writes its final state); only slots below n_slots are written
+        if (i0 + VEC <= nvalid) {
+            *reinterpret_cast<float4 *>(gZ + i0) = make_float4(zo[0], zo[1], zo[2], zo[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < VEC; ++j)
+                if (i0 + j < nvalid) gZ[i0 + j] = zo[j];
+        }
+        // queue the eventful carriers (record and position), in tile order
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            const bool slow = (slowbits >> j) & 1u;
+            const unsigned int m = __ballot_sync(0xffffffffu, slow);
+            if (m) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s_qn, __popc(m));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (slow) {
+                    const long long q = pos0 + base + __popc(m & lt_mask);
+                    a.qrec[q] = make_float4(zin[j], min_[j], __uint_as_float(pin[j]),
+                                            __uint_as_float((uint32_t)((t - t0) * TILE + i0 + j)));
+                    ++n_queued;
+                }
+            }
+        }
+        // every thread is done with ring stage stg: refill it with tile i + nring
+        __syncthreads();
+        if (s_abort) break;
+        if (tid == 0 && i + nring < ntiles) issue(t + nring, stg);
+    }
+    if (s_abort) {
+        // a copy did not land in time: wait (bounded) for the copies still in
+        // flight so no bulk copy writes into freed shared memory
+        if (tid == 0)
+            for (long long i = consumed; i < ntiles && i < consumed + nring - 1; ++i)
+                mbar_wait(&s_bar[i % nring], (uint32_t)((i / nring) & 1), a.spin_limit);
+        __syncthreads();
+    }
+    if (seg_stack >= 0) flush(seg_stack);
+    if (tid == 0) a.qcnt[b] = (uint32_t)s_qn;
+}
+
+// ---------------------------------------------------------------------------
+// k_slow: the general step for the queued (eventful) carriers, and the
+// placement of every secondary of the step.
+//
+// Slow block j works off the queues of fast blocks [Gf*j/Gs, Gf*(j+1)/Gs)
+// with all lanes busy on the event paths: interface draws against T, mirror
+// reflection, elastic and inelastic scattering, removal in the lowest bin
+// and secondary generation (Sec. III).  A secondary is staged at its
+// parent's position with one bit in a bitmap; its rank among the stack's
+// secondaries (slot order of the parents = the id order of a sequential
+// loop) is the popcount prefix of the bitmap, continued across blocks by a
+// decoupled look-back with a bounded wait.
+// ---------------------------------------------------------------------------
+template <bool DET, bool DEPN>
+__global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    TabEnt *s_ent = reinterpret_cast<TabEnt *>(smem);
+    uint32_t *s_T = reinterpret_cast<uint32_t *>(s_ent + a.tab_max);
+    int32_t *s_J = reinterpret_cast<int32_t *>(s_T + a.T_max);
+    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + a.jbin_max);
+    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max : 0) + 1);
+    s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
+    long long *s_nsl = s_tpref + a.n_stacks + 1;
+    __shared__ float s_edge[PIC_MAX_LAYERS + 1];
+    __shared__ uint32_t s_p0[PIC_MAX_LAYERS];
+    __shared__ DevStack s_st;
+    __shared__ int s_w[TPB / 32];
+    __shared__ unsigned long long s_r[TPB / 32];
+    __shared__ long long s_prefix, s_range[2];
+    __shared__ int s_flag, s_nspawn;
+
+    const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
+    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
+    const int b = blockIdx.x, Gs = gridDim.x, Gf = a.grid_fast, tid = threadIdx.x;
+    const long long T = make_tiles(a, s_tpref, s_nsl);
+    const int fb0 = (int)((long long)Gf * b / Gs), fb1 = (int)((long long)Gf * (b + 1) / Gs);
+    const long long t0 = chunk_lo(T, fb0, Gf), t1 = chunk_lo(T, fb1, Gf);
+    const int tj = (int)(a.step / (uint32_t)a.moment_every);
+    const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
+    const float half = a.half_dt;
+    float *Z = a.z[cur], *MU = a.mu[cur];
+    uint32_t *PK = a.pk[cur];
+    if (tid == 0) s_nspawn = 0;
+
+    Stk S{};
+    Tally ty{};
+
+    auto flush_segment = [&](int s) {
+        __syncthreads();
+        const DevStack &st = s_st;
+        const int nf = st.n_cells + 1;
+        int32_t *gJ = a.J_hist + st.J_off + (long long)tj * 2 * nf;
+        for (int i = tid; i < 2 * nf; i += TPB) {
+            const int v = s_J[i];
+            if (v) atomicAdd(&gJ[i], v);
+        }
+        if (DEPN) {
             const int nb = 2 * a.n_e * st.n_cells;
             uint32_t *gN = a.n_hist + st.n_off + (long long)tout * nb;
             for (int i = tid; i < nb; i += TPB) {
@@ -342,293 +697,287 @@ __global__ void __launch_bounds__(TPB) k_step(const Args a)
             }
         }
         unsigned long long *L = a.cnt[s].led;
-        const unsigned long long v0 = block_sum_u64(ty.steps, s_r);
-        if (tid == 0 && v0) atomicAdd(&L[L_PARTICLE_STEPS], v0);
-        const unsigned long long v1 = block_sum_u64(ty.absorbed, s_r);
-        if (tid == 0 && v1) atomicAdd(&L[L_ABSORBED], v1);
-        const unsigned long long v2 = block_sum_u64(ty.bath, s_r);
-        if (tid == 0 && v2) atomicAdd(&L[L_Q_BATH], v2);
-        const unsigned long long v3 = block_sum_u64(ty.hits, s_r);
-        if (tid == 0 && v3) atomicAdd(&L[L_IFACE_HITS], v3);
-        const unsigned long long v4 = block_sum_u64(ty.trans, s_r);
-        if (tid == 0 && v4) atomicAdd(&L[L_IFACE_TRANSMIT], v4);
-        const unsigned long long v5 = block_sum_u64(ty.trunc, s_r);
-        if (tid == 0 && v5) atomicAdd(&L[L_TRUNCATED], v5);
-        const unsigned long long v6 = block_sum_u64(ty.spawn_drop, s_r);
-        if (tid == 0 && v6) atomicAdd(&L[L_SPAWN_DROPPED], v6);
-        const unsigned long long v7 = block_sum_u64(ty.q_drop, s_r);
-        if (tid == 0 && v7) atomicAdd(&L[L_Q_DROPPED], v7);
-        const unsigned long long v8 = block_sum_u64(ty.changed, s_r);
-        if (tid == 0 && v8) atomicAdd(&L[L_CHANGED], v8);
+        const uint32_t vals[8] = {ty.absorbed, ty.bath, ty.hits, ty.trans, ty.trunc,
+                                  ty.spawn_drop, ty.q_drop, ty.changed};
+        const int idx[8] = {L_ABSORBED, L_Q_BATH, L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED,
+                            L_SPAWN_DROPPED, L_Q_DROPPED, L_CHANGED};
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const unsigned long long v = block_sum_u64(vals[q], s_r);
+            if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
+        }
         ty = Tally{};
         __syncthreads();
     };
 
-    // Place the staged secondaries [start, start+count) of stack s whose
-    // exclusive prefix among the stack's secondaries of this step is `prefix`.
-    // Deposits go to shared memory if `smem_hist`, else to global memory.
-    auto place = [&](int s, long long start, long long count, long long prefix, bool smem_hist) {
-        const DevStack &st = s_st;          // loaded stack == s when smem_hist
+    // Place the staged secondaries of stack s in tiles [tl0, tl1) in slot
+    // order, the first with rank `prefix` among the stack's secondaries of
+    // this step; clears the bitmap words it reads.  Deposits go to shared
+    // memory if `smem_hist`, else to global memory.
+    auto place = [&](int s, long long tl0, long long tl1, long long prefix, bool smem_hist) {
         const DevStack stg = a.stacks[s];
         const long long nsl = s_nsl[s];
         const long long room = stg.cap - nsl;
         const unsigned long long nid = a.cnt[s].next_id;
         const int nf = stg.n_cells + 1;
         uint32_t kept = 0;
-        for (long long i = tid; i < count; i += TPB) {
-            const float4 r = a.stage[start + i];
-            const long long g = prefix + i;
-            const uint32_t pk_staged = __float_as_uint(r.z);
-            const uint32_t pk = pk_staged & 0x1FFFFFu;
-            if (g < room) {
-                ty.hits += (pk_staged >> 21) & 0xFu;
-                ty.trans += (pk_staged >> 25) & 0xFu;
-                ty.trunc += (pk_staged >> 29) & 0x1u;
-                const unsigned long long id = nid + (unsigned long long)g;
-                const long long d = stg.base + nsl + g;
-                Z[d] = r.x;
-                MU[d] = r.y;
-                a.id[cur][d] = (uint32_t)id;
-                PK[d] = pk | ((uint32_t)(id >> 32) << 21);
-                ++kept;
-                const int sg = (int)((pk >> 8) & 1u), k = (int)(pk & 0xFFu);
-                Stk tmp; tmp.n_cells = stg.n_cells;
-                const int c0 = cell_of(a, tmp, r.w), c1 = cell_of(a, tmp, r.x);
-                if (smem_hist) {
-                    if (c0 != c1) add_flux(s_J, nf, sg, c0, c1);
-                    if (DEPN) atomicAdd(&s_n[(sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
-                } else {
-                    int32_t *gJ = a.J_hist + stg.J_off + (long long)tj * 2 * nf;
-                    if (c0 != c1) add_flux(gJ, nf, sg, c0, c1);
-                    if (DEPN)
-                        atomicAdd(&a.n_hist[stg.n_off + (long long)tout * 2 * a.n_e * stg.n_cells +
-                                            (sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
+        Stk tmp;
+        tmp.n_cells = stg.n_cells;
+        long long run = prefix;
+        const long long w0 = tl0 * (TILE / 32), w1 = tl1 * (TILE / 32);
+        for (long long wb = w0; wb < w1; wb += TPB) {
+            const long long w = wb + tid;
+            uint32_t bits = w < w1 ? a.spawn_bits[w] : 0u;
+            int excl;
+            const int tot = block_scan(__popc(bits), excl, s_w);
+            if (bits) {
+                a.spawn_bits[w] = 0u;
+                long long g = run + excl;
+                while (bits) {
+                    const int j = __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    const float4 r = a.stage[w * 32 + j];
+                    const uint32_t pk_staged = __float_as_uint(r.z);
+                    const uint32_t pk = pk_staged & 0x1FFFFFu;
+                    if (g < room) {
+                        ty.hits += (pk_staged >> 21) & 0xFu;
+                        ty.trans += (pk_staged >> 25) & 0xFu;
+                        ty.trunc += (pk_staged >> 29) & 0x1u;
+                        const unsigned long long id = nid + (unsigned long long)g;
+                        const long long d = stg.base + nsl + g;
+                        Z[d] = r.x;
+                        MU[d] = r.y;
+                        a.id[cur][d] = (uint32_t)id;
+                        PK[d] = pk | ((uint32_t)(id >> 32) << 21);
+                        ++kept;
+                        const int sg = (int)((pk >> 8) & 1u), k = (int)(pk & 0xFFu);
+                        const int c0 = cell_of(a, tmp, r.w), c1 = cell_of(a, tmp, r.x);
+                        if (smem_hist) {
+                            if (c0 != c1) add_flux(s_J, nf, sg, c0, c1);
+                            if (DEPN) atomicAdd(&s_n[(sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
+                        } else {
+                            int32_t *gJ = a.J_hist + stg.J_off + (long long)tj * 2 * nf;
+                            if (c0 != c1) add_flux(gJ, nf, sg, c0, c1);
+                            if (DEPN)
+                                atomicAdd(&a.n_hist[stg.n_off + (long long)tout * 2 * a.n_e * stg.n_cells +
+                                                    (sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
+                        }
+                    } else {
+                        ++ty.spawn_drop;
+                        ty.q_drop += pk & 0xFFu;
+                    }
+                    ++g;
                 }
-            } else {
-                ++ty.spawn_drop;
-                ty.q_drop += pk & 0xFFu;
             }
+            run += tot;
         }
-        (void)st;
         const unsigned long long kk = block_sum_u64(kept, s_r);
         if (tid == 0 && kk) atomicAdd(&a.cnt[s].led[L_SPAWNED], kk);
-        if (tid == 0 && (a.flags & PIC_F_STRICT_CAPACITY) && prefix + count > room)
+        if (tid == 0 && (a.flags & PIC_F_STRICT_CAPACITY) && run > room)
             atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
     };
 
-    for (long long t = p.t0; t < p.t1; ++t) {
-        const int s = stack_of(s_tpref, a.n_stacks, t);
-        if (s != seg_stack) {
-            if (seg_stack >= 0) {
-                // close the previous segment: place its secondaries if their
-                // prefix is known (segment started at its stack's first tile)
-                if (!staged_seg) {
-                    place(seg_stack, seg_first, seg_count, 0, true);
-                    if (s_tpref[seg_stack + 1] == t && tid == 0)
-                        a.cnt[seg_stack].spawn_total = (unsigned long long)seg_count;
-                } else {
-                    staged_count = seg_count;
-                }
-                flush_segment(seg_stack, true);
-            }
-            load_stack(a, s, S, &s_st, s_ent, s_T, s_edge, s_p0);
-            const int nf = s_st.n_cells + 1;
-            for (int i = tid; i < 2 * nf; i += TPB) s_J[i] = 0;
-            if (DEPN)
-                for (int i = tid; i < 2 * a.n_e * s_st.n_cells; i += TPB) s_n[i] = 0u;
-            __syncthreads();
-            staged_seg = (t > s_tpref[s]);
-            if (staged_seg) staged_stack = s;
-            seg_stack = s;
-            seg_first = stage_cur;
-            seg_count = 0;
-        }
+    // the general step for queue entries [q_lo, q_hi) of fast block f, all of
+    // stack s (whose tables are loaded)
+    auto work = [&](int s, int f, long long q_lo, long long q_hi) {
         const DevStack &st = s_st;
-        const long long nsl = s_nsl[s];
-        const bool room0 = (st.cap - nsl) <= 0;        // every secondary is dropped
-        const long long slot0 = (t - s_tpref[s]) * TILE + (long long)tid * VEC;
-        float4 sp[VEC];
-        uint32_t spm = 0;
-        if (slot0 < nsl) {
-            const long long g = st.base + slot0;
-            float4 z4 = *reinterpret_cast<const float4 *>(Z + g);
-            float4 m4 = *reinterpret_cast<const float4 *>(MU + g);
-            const uint4 i4 = *reinterpret_cast<const uint4 *>(ID + g);
-            uint4 p4 = *reinterpret_cast<const uint4 *>(PK + g);
-            const float4 m4_in = m4;
-            const uint4 p4_in = p4;
-            float *zz = &z4.x, *mm = &m4.x;
-            const uint32_t *ii = &i4.x;
-            uint32_t *pp = &p4.x;
-            int bins[VEC];
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-                bins[j] = -1;
-                uint32_t pk = pp[j];
-                int k = (int)(pk & 0xFFu);
-                if (slot0 + j >= nsl || k == 0) continue;
-                ++ty.steps;
-                float z = zz[j], mu = mm[j];
-                const int sg = (int)((pk >> 8) & 1u);
-                int layer = (int)((pk >> 9) & 0xFu);
-                const uint32_t id_lo = ii[j];
-                const uint32_t ctr_y = (pk >> 21) | S.ctr_hi;
-                const int c_start = cell_of(a, S, z);
-                flight<DET>(a, S, z, mu, layer, sg, k, half, id_lo, ctr_y, SUB_IF, ty);
-                // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes)
-                const uint4 x = philox(make_uint4(id_lo, ctr_y, a.step, SUB_SCAT),
-                                       a.seed_lo, a.seed_hi);
-                const TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
-                bool dead = false;
-                if (x.x < e.P) {
-                    const bool inel = x.y < e.Q;
-                    if (k == 1 && (inel || (a.flags & PIC_F_LOWEST_BIN_ANY))) {
-                        dead = true;
-                        ++ty.absorbed;
-                        ++ty.bath;
-                    } else {
-                        mu = mu_of(x.z);
-                        if (inel) {
-                            const int kp = 1 + (int)__umulhi(x.w, (uint32_t)(k - 1));
-                            const int ks = k - kp;
-                            k = kp;
-                            if (a.flags & PIC_F_NO_SECONDARIES) {
-                                ty.bath += (uint32_t)ks;
-                            } else {
-                                // secondary: same place, spin from P0, isotropic
-                                const uint4 y = philox(make_uint4(id_lo, ctr_y, a.step, SUB_SEC),
-                                                       a.seed_lo, a.seed_hi);
-                                const uint32_t g0 = (pk >> 13) & 0xFFu;
-                                const int sgs = y.x < S.p0[layer] ? 0 : 1;
-                                const uint32_t gen = g0 < 255u ? g0 + 1u : 255u;
-                                if (room0) {
-                                    ++ty.spawn_drop;
-                                    ty.q_drop += (uint32_t)ks;
-                                    if (a.flags & PIC_F_STRICT_CAPACITY)
-                                        atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
-                                } else {
-                                    float zs = z, mus = mu_of(y.y);
-                                    int ls = layer;
-                                    Tally ts{};
-                                    flight<DET>(a, S, zs, mus, ls, sgs, ks, half, id_lo, ctr_y,
-                                                SUB_SIF, ts);
-                                    // the secondary's boundary events ride in the
-                                    // (not yet used) id_hi bits until it is placed
-                                    const uint32_t pks = (uint32_t)ks | ((uint32_t)sgs << 8) |
-                                                         ((uint32_t)ls << 9) | (gen << 13) |
-                                                         (ts.hits << 21) | (ts.trans << 25) |
-                                                         (ts.trunc << 29);
-                                    sp[j] = make_float4(zs, mus, __uint_as_float(pks), z);
-                                    spm |= 1u << j;
-                                }
-                            }
+        const long long fpos0 = chunk_lo(T, f, Gf) * TILE;
+        const long long sbase = st.base - s_tpref[s] * TILE;     // position -> slot
+        const bool room0 = (st.cap - s_nsl[s]) <= 0;
+        int nsp = 0;
+#pragma unroll 1
+        for (long long q = q_lo + tid; q < q_hi; q += TPB) {
+            const float4 rec = a.qrec[fpos0 + q];
+            float z = rec.x, mu = rec.y;
+            uint32_t pk = __float_as_uint(rec.z);
+            const long long vpos = fpos0 + __float_as_uint(rec.w);
+            const long long gslot = sbase + vpos;
+            const long long slot = vpos - s_tpref[s] * TILE;       // slot within the stack
+            const uint32_t id_lo = a.id[cur][gslot];
+            int k = (int)(pk & 0xFFu);
+            const float mu_in = mu;
+            const uint32_t pk_in = pk;
+            const int sg = (int)((pk >> 8) & 1u);
+            int layer = (int)((pk >> 9) & 0xFu);
+            const uint32_t ctr_y = (pk >> 21) | S.ctr_hi;
+            TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
+            float lo = S.edge[layer], hi = S.edge[layer + 1];
+            const int c_start = cell_of(a, S, z);
+            flight<DET>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y, SUB_IF, ty);
+            // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes):
+            // the slot group's test word, then the carrier's event words
+            const uint4 xg = philox_rk(make_uint4((uint32_t)(slot >> 2), S.ctr_hi, a.step,
+                                                  SUB_TEST), a);
+            const uint32_t xs = (slot & 3) == 0 ? xg.x : (slot & 3) == 1 ? xg.y
+                              : (slot & 3) == 2 ? xg.z : xg.w;
+            bool dead = false;
+            if (xs < e.P) {
+                const uint4 x = philox_rk(make_uint4(id_lo, ctr_y, a.step, SUB_SCAT), a);
+                const bool inel = x.y < e.Q;
+                if (k == 1 && (inel || (a.flags & PIC_F_LOWEST_BIN_ANY))) {
+                    dead = true;
+                    ++ty.absorbed;
+                    ++ty.bath;
+                } else {
+                    mu = mu_of(x.z);
+                    if (inel) {
+                        const int kp = 1 + (int)__umulhi(x.w, (uint32_t)(k - 1));
+                        const int ks = k - kp;
+                        k = kp;
+                        e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
+                        if (a.flags & PIC_F_NO_SECONDARIES) {
+                            ty.bath += (uint32_t)ks;
+                        } else if (room0) {
+                            ++ty.spawn_drop;
+                            ty.q_drop += (uint32_t)ks;
+                            if (a.flags & PIC_F_STRICT_CAPACITY)
+                                atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
+                        } else {
+                            // secondary: same place, spin from P0, isotropic
+                            const uint4 y = philox_rk(make_uint4(id_lo, ctr_y, a.step, SUB_SEC), a);
+                            const uint32_t g0 = (pk >> 13) & 0xFFu;
+                            const int sgs = y.x < S.p0[layer] ? 0 : 1;
+                            const uint32_t gen = g0 < 255u ? g0 + 1u : 255u;
+                            float zs = z, mus = mu_of(y.y), los = lo, his = hi;
+                            int ls = layer;
+                            TabEnt es = S.ent[(ls * 2 + sgs) * S.n_e + (ks - 1)];
+                            Tally ts{};
+                            flight<DET>(a, S, zs, mus, ls, es, los, his, sgs, ks, half, id_lo,
+                                        ctr_y, SUB_SIF, ts);
+                            // the secondary's boundary events ride in the (not yet
+                            // used) id_hi bits until it is placed
+                            const uint32_t pks = (uint32_t)ks | ((uint32_t)sgs << 8) |
+                                                 ((uint32_t)ls << 9) | (gen << 13) |
+                                                 (ts.hits << 21) | (ts.trans << 25) |
+                                                 (ts.trunc << 29);
+                            a.stage[vpos] = make_float4(zs, mus, __uint_as_float(pks), z);
+                            atomicOr(&a.spawn_bits[vpos >> 5], 1u << (vpos & 31));
+                            ++nsp;
                         }
                     }
                 }
-                if (dead) {
-                    pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
-                    const int c_end = cell_of(a, S, z);
-                    if (c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
-                } else {
-                    flight<DET>(a, S, z, mu, layer, sg, k, half, id_lo, ctr_y, SUB_IF + 16, ty);
-                    const int c_end = cell_of(a, S, z);
-                    if (c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
-                    pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) |
-                         ((uint32_t)layer << 9);
-                    if (DEPN) bins[j] = (sg * S.n_e + (k - 1)) * S.n_cells + c_end;
-                }
-                ty.changed += (__float_as_uint(mu) != __float_as_uint(mm[j]) || pk != pp[j]) ? 1u : 0u;
-                zz[j] = z; mm[j] = mu; pp[j] = pk;
             }
-            if (slot0 + VEC <= nsl) {
-                *reinterpret_cast<float4 *>(Z + g) = z4;
-                if (__float_as_uint(m4.x) != __float_as_uint(m4_in.x) ||
-                    __float_as_uint(m4.y) != __float_as_uint(m4_in.y) ||
-                    __float_as_uint(m4.z) != __float_as_uint(m4_in.z) ||
-                    __float_as_uint(m4.w) != __float_as_uint(m4_in.w))
-                    *reinterpret_cast<float4 *>(MU + g) = m4;
-                if (p4.x != p4_in.x || p4.y != p4_in.y || p4.z != p4_in.z || p4.w != p4_in.w)
-                    *reinterpret_cast<uint4 *>(PK + g) = p4;
+            if (dead) {
+                pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
+                const int c_end = cell_of(a, S, z);
+                if (c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
             } else {
-                // ragged end of the stack: the slots past n_slots receive this
-                // step's secondaries from other blocks, so only valid lanes
-                // are written back
-                const int nv = (int)(nsl - slot0);
-#pragma unroll
-                for (int j = 0; j < VEC; ++j)
-                    if (j < nv) { Z[g + j] = zz[j]; MU[g + j] = mm[j]; PK[g + j] = pp[j]; }
+                flight<DET>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
+                            SUB_IF + 16, ty);
+                const int c_end = cell_of(a, S, z);
+                if (c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
+                pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
+                if (DEPN) atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
             }
-            if (DEPN && !WAGG) {
-#pragma unroll
-                for (int j = 0; j < VEC; ++j)
-                    if (bins[j] >= 0) atomicAdd(&s_n[bins[j]], 1u);
-            }
-            if (DEPN && WAGG) {
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) {
-                    const unsigned int act = __activemask();
-                    const unsigned int m = __match_any_sync(act, bins[j]);
-                    if (bins[j] >= 0 && (threadIdx.x & 31) == __ffs(m) - 1)
-                        atomicAdd(&s_n[bins[j]], (uint32_t)__popc(m));
-                }
+            Z[gslot] = z;
+            if (__float_as_uint(mu) != __float_as_uint(mu_in) || pk != pk_in) {
+                ++ty.changed;
+                MU[gslot] = mu;
+                PK[gslot] = pk;
             }
         }
-        // append this tile's secondaries to the segment, in slot order
-        int excl;
-        const int tot = block_scan(__popc(spm), excl, s_w);
-#pragma unroll
-        for (int j = 0; j < VEC; ++j)
-            if ((spm >> j) & 1u) a.stage[stage_cur + excl++] = sp[j];
-        stage_cur += tot;
-        seg_count += tot;
+        if (nsp) atomicAdd(&s_nspawn, nsp);
+    };
+
+    // first entry of fast block f's queue (ascending by tile) with tile >= tb
+    auto lower = [&](int f, long long tb) -> long long {
+        const long long ft0 = chunk_lo(T, f, Gf), fpos0 = ft0 * TILE;
+        long long lo = 0, hi = a.qcnt[f];
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if (ft0 + __float_as_uint(a.qrec[fpos0 + mid].w) / TILE < tb) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
+    };
+
+    int staged_stack = -1;
+    long long staged_t0 = 0, staged_t1 = 0, staged_count = 0;
+    bool have_last = false, last_staged = false;
+    int last_stack = -1;
+    long long last_t0 = 0, last_count = 0;
+    if (t0 < t1) {
+        const int s_first = stack_of(s_tpref, a.n_stacks, t0);
+        const int s_last = stack_of(s_tpref, a.n_stacks, t1 - 1);
+        for (int s = s_first; s <= s_last; ++s) {
+            const long long sg0 = s_tpref[s] > t0 ? s_tpref[s] : t0;
+            const long long sg1 = s_tpref[s + 1] < t1 ? s_tpref[s + 1] : t1;
+            if (sg0 >= sg1) continue;               // a stack with no tiles
+            load_stack(a, s, S, &s_st, s_ent, s_T, s_edge, s_p0);
+            for (int q = tid; q < 2 * (s_st.n_cells + 1); q += TPB) s_J[q] = 0;
+            if (DEPN)
+                for (int q = tid; q < 2 * a.n_e * s_st.n_cells; q += TPB) s_n[q] = 0u;
+            if (tid == 0) s_nspawn = 0;
+            __syncthreads();
+            for (int f = fb0; f < fb1; ++f) {
+                if (tid == 0) {
+                    s_range[0] = lower(f, sg0);
+                    s_range[1] = lower(f, sg1);
+                }
+                __syncthreads();
+                const long long q_lo = s_range[0], q_hi = s_range[1];
+                __syncthreads();
+                if (q_lo < q_hi) work(s, f, q_lo, q_hi);
+            }
+            __syncthreads();
+            const long long cnt = s_nspawn;
+            const bool inside = sg0 > s_tpref[s];   // segment starts inside its stack
+            if (s < s_last) {
+                // a segment that ends its stack inside the chunk
+                if (!inside) {
+                    if (cnt) place(s, sg0, sg1, 0, true);
+                    if (tid == 0) a.cnt[s].spawn_total = (unsigned long long)cnt;
+                } else {
+                    staged_stack = s; staged_t0 = sg0; staged_t1 = sg1; staged_count = cnt;
+                }
+                flush_segment(s);
+            } else {
+                have_last = true; last_staged = inside; last_stack = s;
+                last_t0 = sg0; last_count = cnt;
+            }
+        }
     }
 
-    // close the last segment and publish its running count
-    const bool have = seg_stack >= 0;
-    long long lb_prefix = 0;
-    if (have) {
-        const bool ends_stack = s_tpref[seg_stack + 1] == p.t1;
-        if (!staged_seg) {
-            if (tid == 0) publish(&a.status[b], ep, FLAG_P, seg_count);
-            place(seg_stack, seg_first, seg_count, 0, true);
-            if (ends_stack && tid == 0) a.cnt[seg_stack].spawn_total = (unsigned long long)seg_count;
-            flush_segment(seg_stack, true);
+    // close the last segment and publish its count of secondaries
+    if (have_last) {
+        const long long cnt = last_count;
+        const bool ends_stack = s_tpref[last_stack + 1] == t1;
+        if (!last_staged) {
+            if (tid == 0) publish(&a.status[b], ep, FLAG_P, cnt);
+            if (cnt) place(last_stack, last_t0, t1, 0, true);
+            if (ends_stack && tid == 0) a.cnt[last_stack].spawn_total = (unsigned long long)cnt;
+            flush_segment(last_stack);
         } else {
-            // single segment starting inside its stack
             if (tid == 0) {
-                publish(&a.status[b], ep, FLAG_A, seg_count);
-                s_prefix = look_back(a, ep, p.T, s_tpref[seg_stack], b, G);
-                publish(&a.status[b], ep, FLAG_P, s_prefix + seg_count);
+                publish(&a.status[b], ep, FLAG_A, cnt);
+                s_prefix = look_back_slow(a, ep, T, s_tpref[last_stack], b, Gs, Gf);
+                publish(&a.status[b], ep, FLAG_P, s_prefix + cnt);
             }
             __syncthreads();
-            lb_prefix = s_prefix;
-            place(seg_stack, seg_first, seg_count, lb_prefix, true);
+            const long long pre = s_prefix;
+            if (cnt) place(last_stack, last_t0, t1, pre, true);
             if (ends_stack && tid == 0)
-                a.cnt[seg_stack].spawn_total = (unsigned long long)(lb_prefix + seg_count);
-            flush_segment(seg_stack, true);
-            staged_stack = -1;
+                a.cnt[last_stack].spawn_total = (unsigned long long)(pre + cnt);
+            flush_segment(last_stack);
         }
-        // an earlier staged segment (block spanning stacks): its prefix now
+        // an earlier segment (block spanning stacks) that waited for its prefix
         if (staged_stack >= 0) {
-            if (tid == 0) s_prefix = look_back(a, ep, p.T, s_tpref[staged_stack], b, G);
+            __syncthreads();
+            if (tid == 0) s_prefix = look_back_slow(a, ep, T, s_tpref[staged_stack], b, Gs, Gf);
             __syncthreads();
             const long long pre = s_prefix;
-            place(staged_stack, stage0, staged_count, pre, false);
-            if (s_tpref[staged_stack + 1] <= p.t1 && tid == 0)
+            if (staged_count) place(staged_stack, staged_t0, staged_t1, pre, false);
+            if (tid == 0)
                 a.cnt[staged_stack].spawn_total = (unsigned long long)(pre + staged_count);
-            __syncthreads();
-            // its counts belong to the staged stack
             unsigned long long *L = a.cnt[staged_stack].led;
-            const unsigned long long v3 = block_sum_u64(ty.hits, s_r);
-            if (tid == 0 && v3) atomicAdd(&L[L_IFACE_HITS], v3);
-            const unsigned long long v4 = block_sum_u64(ty.trans, s_r);
-            if (tid == 0 && v4) atomicAdd(&L[L_IFACE_TRANSMIT], v4);
-            const unsigned long long v5 = block_sum_u64(ty.trunc, s_r);
-            if (tid == 0 && v5) atomicAdd(&L[L_TRUNCATED], v5);
-            const unsigned long long v6 = block_sum_u64(ty.spawn_drop, s_r);
-            if (tid == 0 && v6) atomicAdd(&L[L_SPAWN_DROPPED], v6);
-            const unsigned long long v7 = block_sum_u64(ty.q_drop, s_r);
-            if (tid == 0 && v7) atomicAdd(&L[L_Q_DROPPED], v7);
+            const uint32_t vals[5] = {ty.hits, ty.trans, ty.trunc, ty.spawn_drop, ty.q_drop};
+            const int idx[5] = {L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED, L_SPAWN_DROPPED,
+                                L_Q_DROPPED};
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                const unsigned long long v = block_sum_u64(vals[q], s_r);
+                if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
+            }
             ty = Tally{};
         }
     }
@@ -686,10 +1035,8 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
         const DevStack &st = a.stacks[s];
         const unsigned long long id = a.cnt[s].next_id + (unsigned long long)j;
         const uint32_t cy = (uint32_t)(id >> 32) | ((uint32_t)s << 16);
-        const uint4 r0 = philox(make_uint4((uint32_t)id, cy, a.step, SUB_INJ + 0), a.seed_lo,
-                                a.seed_hi);
-        const uint4 r1 = philox(make_uint4((uint32_t)id, cy, a.step, SUB_INJ + 1), a.seed_lo,
-                                a.seed_hi);
+        const uint4 r0 = philox_rk(make_uint4((uint32_t)id, cy, a.step, SUB_INJ + 0), a);
+        const uint4 r1 = philox_rk(make_uint4((uint32_t)id, cy, a.step, SUB_INJ + 1), a);
         int i = 0;
         const uint32_t *thr = a.cdf_thr + st.cdf_off;
         while (i < st.n_cdf - 1 && !(r0.x < thr[i])) ++i;
@@ -846,60 +1193,95 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-template <bool DET, bool DEPN, bool WAGG>
-static cudaError_t occupancy(size_t smem, int *blocks)
+// Occupancy of a kernel with `smem` bytes of dynamic shared memory; the
+// largest dynamic shared memory the device offers is allowed, so that
+// contexts with different moment grids never lower each other's cap.
+template <class K>
+static cudaError_t occupancy(K kernel, size_t smem, int *blocks)
 {
-    // allow the largest dynamic shared memory the device offers, so that
-    // contexts with different moment grids never lower each other's cap
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
         e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaFuncAttributes fa{};
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_step<DET, DEPN, WAGG>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
     if (e != cudaSuccess) return e;
     const int cap = optin - (int)fa.sharedSizeBytes;
-    if ((int)smem > cap) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(k_step<DET, DEPN, WAGG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             cap);
+    *blocks = 0;
+    if ((int)smem > cap) return cudaSuccess;       // does not fit: zero blocks
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k_step<DET, DEPN, WAGG>, TPB,
-                                                         smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, TPB, smem);
 }
 
-cudaError_t configure(const Args &a, int blocks_per_sm, int hist_mode, LaunchCfg *cfg)
+// Ring depth of k_fast for one variant, both builds (with and without fused
+// multiply-add) fitting: the most resident blocks per SM (warps to hide the
+// arithmetic latency) such that at least three tiles per SM are in flight
+// (blocks x (stages - 1) >= 3, about 48 KB), then the deepest ring.
+template <bool DEPN, bool WAGG>
+static cudaError_t pick_ring(size_t fixed, int blocks_per_sm, int ring_req, int *ring, int *blocks,
+                             size_t *smem)
+{
+    int best = -1;
+    for (int r = 2; r <= MAX_RING; ++r) {
+        if (ring_req > 0 && r != ring_req) continue;
+        const size_t sm = fixed + (size_t)r * 3 * TILE_BYTES;
+        int o1 = 0, o2 = 0;
+        cudaError_t e = occupancy(k_fast<false, DEPN, WAGG>, sm, &o1);
+        if (e == cudaSuccess) e = occupancy(k_fast<true, DEPN, WAGG>, sm, &o2);
+        if (e != cudaSuccess) return e;
+        int o = o1 < o2 ? o1 : o2;
+        if (blocks_per_sm > 0 && o > blocks_per_sm) o = blocks_per_sm;
+        if (o < 1) continue;
+        const int enough = o * (r - 1) >= 3 ? 1 : 0;
+        const int score = enough * 10000 + o * 100 + r;
+        if (score > best) { best = score; *ring = r; *blocks = o; *smem = sm; }
+    }
+    return best < 0 ? cudaErrorInvalidConfiguration : cudaSuccess;
+}
+
+template <bool DEPN>
+static cudaError_t slow_cfg(size_t sm, int *grid, int sms)
+{
+    int o1 = 0, o2 = 0;
+    cudaError_t e = occupancy(k_slow<false, DEPN>, sm, &o1);
+    if (e == cudaSuccess) e = occupancy(k_slow<true, DEPN>, sm, &o2);
+    if (e != cudaSuccess) return e;
+    const int o = o1 < o2 ? o1 : o2;
+    if (o < 1) return cudaErrorInvalidConfiguration;
+    *grid = sms * o;
+    return cudaSuccess;
+}
+
+cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_mode, LaunchCfg *cfg)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    const size_t base = (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.T_max * 4 +
-                        (size_t)a.jbin_max * 4;
-    cfg->smem_step = (base + 15) & ~(size_t)15;
-    cfg->smem_step_dep = (base + (size_t)a.nbin_max * 4 + 15) & ~(size_t)15;
-    int occ[4] = {0, 0, 0, 0};
-    // every template instance gets the attribute; the grids use the smallest
-    // occupancy among the instances that share a shared-memory size
-    const bool w = hist_mode == 1;
-    if ((e = occupancy<false, false, false>(cfg->smem_step, &occ[0])) != cudaSuccess) return e;
-    if ((e = occupancy<true, false, false>(cfg->smem_step, &occ[1])) != cudaSuccess) return e;
-    if (w) {
-        if ((e = occupancy<false, true, true>(cfg->smem_step_dep, &occ[2])) != cudaSuccess) return e;
-        if ((e = occupancy<true, true, true>(cfg->smem_step_dep, &occ[3])) != cudaSuccess) return e;
-    } else {
-        if ((e = occupancy<false, true, false>(cfg->smem_step_dep, &occ[2])) != cudaSuccess) return e;
-        if ((e = occupancy<true, true, false>(cfg->smem_step_dep, &occ[3])) != cudaSuccess) return e;
-    }
-    int o_plain = occ[0] < occ[1] ? occ[0] : occ[1];
-    int o_dep = occ[2] < occ[3] ? occ[2] : occ[3];
-    if (o_plain < 1 || o_dep < 1) return cudaErrorInvalidConfiguration;
-    if (blocks_per_sm > 0) {
-        o_plain = blocks_per_sm < o_plain ? blocks_per_sm : o_plain;
-        o_dep = blocks_per_sm < o_dep ? blocks_per_sm : o_dep;
-    }
-    cfg->grid_step = sms * o_plain;
-    cfg->grid_step_dep = sms * o_dep;
+    const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;      // tile prefix, counts
+    const size_t fixed = (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.jbin_max * 4 + 4 + tiles;
+    const size_t fixed_dep = fixed + (size_t)a.nbin_max * 4;
+    int o_plain = 0, o_dep = 0;
+    if ((e = pick_ring<false, false>(fixed, blocks_per_sm, ring_req, &cfg->ring_fast, &o_plain,
+                                     &cfg->smem_fast)) != cudaSuccess)
+        return e;
+    if (hist_mode == 1)
+        e = pick_ring<true, true>(fixed_dep, blocks_per_sm, 0, &cfg->ring_fast_dep, &o_dep,
+                                  &cfg->smem_fast_dep);
+    else
+        e = pick_ring<true, false>(fixed_dep, blocks_per_sm, 0, &cfg->ring_fast_dep, &o_dep,
+                                   &cfg->smem_fast_dep);
+    if (e != cudaSuccess) return e;
+    cfg->grid_fast = sms * o_plain;
+    cfg->grid_fast_dep = sms * o_dep;
+    const size_t slow = (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.T_max * 4 +
+                        (size_t)a.jbin_max * 4 + 4 + tiles;
+    cfg->smem_slow = slow;
+    cfg->smem_slow_dep = slow + (size_t)a.nbin_max * 4;
+    if ((e = slow_cfg<false>(cfg->smem_slow, &cfg->grid_slow, sms)) != cudaSuccess) return e;
+    if ((e = slow_cfg<true>(cfg->smem_slow_dep, &cfg->grid_slow_dep, sms)) != cudaSuccess) return e;
     int oc = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_compact, TPB, 0)) != cudaSuccess)
         return e;
@@ -908,26 +1290,44 @@ cudaError_t configure(const Args &a, int blocks_per_sm, int hist_mode, LaunchCfg
     return cudaSuccess;
 }
 
-cudaError_t launch_step(const Args &a, const LaunchCfg &c, bool det, bool dep, int hist_mode,
+cudaError_t launch_fast(const Args &a0, const LaunchCfg &c, bool det, bool dep, int hist_mode,
                         cudaStream_t s)
 {
-    const int g = dep ? c.grid_step_dep : c.grid_step;
-    const size_t sm = dep ? c.smem_step_dep : c.smem_step;
+    Args a = a0;
+    a.ring = dep ? c.ring_fast_dep : c.ring_fast;
+    const int g = dep ? c.grid_fast_dep : c.grid_fast;
+    const size_t sm = dep ? c.smem_fast_dep : c.smem_fast;
     const bool w = hist_mode == 1;
     if (det) {
         if (dep) {
-            if (w) k_step<true, true, true><<<g, TPB, sm, s>>>(a);
-            else k_step<true, true, false><<<g, TPB, sm, s>>>(a);
+            if (w) k_fast<true, true, true><<<g, TPB, sm, s>>>(a);
+            else k_fast<true, true, false><<<g, TPB, sm, s>>>(a);
         } else {
-            k_step<true, false, false><<<g, TPB, sm, s>>>(a);
+            k_fast<true, false, false><<<g, TPB, sm, s>>>(a);
         }
     } else {
         if (dep) {
-            if (w) k_step<false, true, true><<<g, TPB, sm, s>>>(a);
-            else k_step<false, true, false><<<g, TPB, sm, s>>>(a);
+            if (w) k_fast<false, true, true><<<g, TPB, sm, s>>>(a);
+            else k_fast<false, true, false><<<g, TPB, sm, s>>>(a);
         } else {
-            k_step<false, false, false><<<g, TPB, sm, s>>>(a);
+            k_fast<false, false, false><<<g, TPB, sm, s>>>(a);
         }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slow(const Args &a0, const LaunchCfg &c, bool det, bool dep, cudaStream_t s)
+{
+    Args a = a0;
+    a.grid_fast = dep ? c.grid_fast_dep : c.grid_fast;
+    const int g = dep ? c.grid_slow_dep : c.grid_slow;
+    const size_t sm = dep ? c.smem_slow_dep : c.smem_slow;
+    if (det) {
+        if (dep) k_slow<true, true><<<g, TPB, sm, s>>>(a);
+        else k_slow<true, false><<<g, TPB, sm, s>>>(a);
+    } else {
+        if (dep) k_slow<false, true><<<g, TPB, sm, s>>>(a);
+        else k_slow<false, false><<<g, TPB, sm, s>>>(a);
     }
     return cudaGetLastError();
 }

@@ -18,6 +18,7 @@
 
 #include <cstring>
 #include <mutex>
+#include <string>
 
 #include "pic_internal.h"
 
@@ -47,6 +48,12 @@ struct DeviceSetup {
 std::mutex g_mu;
 DeviceSetup g_dev[kMaxDevices];
 
+pic_status cuda_error(cudaError_t e, const char *where)
+{
+    pic_set_static_error((std::string(where) + ": " + cudaGetErrorString(e)).c_str());
+    return PIC_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" pic_status pic_compact_static(const float *z, const float *mu, const uint32_t *id,
@@ -62,7 +69,9 @@ extern "C" pic_status pic_compact_static(const float *z, const float *mu, const 
     if (n > 0 && (reinterpret_cast<uintptr_t>(packed) & 15u)) return PIC_ERR_ARG;
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PIC_ERR_CUDA;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_error(e, "pic_compact_static: current device");
+    if (dev < 0 || dev >= kMaxDevices) return PIC_ERR_ARG;
 
     Scratch *scr = nullptr;
     int grid = 0;
@@ -74,10 +83,11 @@ extern "C" pic_status pic_compact_static(const float *z, const float *mu, const 
         DeviceSetup &d = g_dev[dev];
         if (!d.ready) {
             void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_compact_scratch) != cudaSuccess) return PIC_ERR_CUDA;
+            e = cudaGetSymbolAddress(&p, g_compact_scratch);
+            if (e != cudaSuccess) return cuda_error(e, "pic_compact_static: scratch address");
             int sms = 0;
-            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-                return PIC_ERR_CUDA;
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return cuda_error(e, "pic_compact_static: SM count");
             d.addr = static_cast<Scratch *>(p);
             d.grid = sms * (2048 / TPB);
             if (d.grid > kMaxBlocks) d.grid = kMaxBlocks;
@@ -101,8 +111,8 @@ extern "C" pic_status pic_compact_static(const float *z, const float *mu, const 
     static_assert(offsetof(Scratch, ctl) == offsetof(Header, ctl), "layout");
     static_assert(offsetof(Scratch, cnt) == offsetof(Header, cnt), "layout");
     static_assert(offsetof(Scratch, stack) == offsetof(Header, stack), "layout");
-    cudaError_t e = cudaMemcpyAsync(scr, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return PIC_ERR_CUDA;
+    e = cudaMemcpyAsync(scr, &h, sizeof(h), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_error(e, "pic_compact_static: scratch reset");
 
     Args a{};
     a.stacks = &scr->stack;
@@ -118,7 +128,7 @@ extern "C" pic_status pic_compact_static(const float *z, const float *mu, const 
     LaunchCfg c{};
     c.grid_compact = grid;
     e = launch_compact(a, c, stream);
-    if (e != cudaSuccess) return PIC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_error(e, "pic_compact_static: launch");
 
     unsigned long long alive = 0;
     unsigned int status = 0;
@@ -126,7 +136,7 @@ extern "C" pic_status pic_compact_static(const float *z, const float *mu, const 
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&status, &scr->ctl.status, sizeof(status), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
-    if (e != cudaSuccess) return PIC_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_error(e, "pic_compact_static: result");
     if (status != 0) return (pic_status)status;
     *n_alive = (int64_t)alive;
     return PIC_OK;

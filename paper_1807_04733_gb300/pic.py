@@ -24,7 +24,7 @@ MAX_LAYERS = 16
 MAX_MAT = 8
 LEDGER_FIELDS = ("injected", "inject_dropped", "spawned", "spawn_dropped", "absorbed",
                  "q_injected", "q_bath", "q_dropped", "iface_hits", "iface_transmit",
-                 "truncated", "particle_steps", "changed")
+                 "truncated", "particle_steps", "changed", "eventful")
 STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_ALLOC", 3: "PIC_ERR_CAPACITY",
           4: "PIC_ERR_TIMEOUT", 5: "PIC_ERR_CUDA", 6: "PIC_ERR_STATE"}
 REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u4")])
@@ -32,16 +32,17 @@ REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u
 # symbols declared in include/pic.h
 EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_grad", "pic_records",
            "pic_set_records", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
-           "pic_profile_read", "pic_compact_static", "pic_launch_count", "pic_destroy",
-           "pic_last_error", "pic_status_string")
-KERNEL_KINDS = ("inject", "step", "step_moments", "compact")
+           "pic_profile_read", "pic_compact_static", "pic_launch_config", "pic_launch_count",
+           "pic_destroy", "pic_last_error", "pic_status_string")
+KERNEL_KINDS = ("inject", "step", "step_moments", "compact", "step_events")
 
 
 class pic_params(C.Structure):
     _fields_ = [("n_e", C.c_int32), ("dt", C.c_float), ("dz", C.c_float),
                 ("seed", C.c_uint64), ("flags", C.c_uint32), ("compact_every", C.c_int32),
                 ("moment_every", C.c_int32), ("n_steps_max", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("hist_mode", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("hist_mode", C.c_int32),
+                ("ring_stages", C.c_int32)]
 
 
 class pic_stack_desc(C.Structure):
@@ -68,8 +69,19 @@ class pic_ledger(C.Structure):
         return {n: int(getattr(self, n)) for n in LEDGER_FIELDS}
 
 
+class pic_launch_info(C.Structure):
+    _fields_ = [("grid_step", C.c_int32), ("grid_step_moments", C.c_int32),
+                ("grid_slow", C.c_int32), ("grid_slow_moments", C.c_int32),
+                ("grid_compact", C.c_int32), ("grid_inject", C.c_int32),
+                ("ring_step", C.c_int32), ("ring_step_moments", C.c_int32),
+                ("smem_step", C.c_int64), ("smem_step_moments", C.c_int64)]
+
+    def as_dict(self):
+        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+
+
 class pic_kernel_times(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 4), ("ms", C.c_double * 4)]
+    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5)]
 
 
 class PicError(RuntimeError):
@@ -108,6 +120,7 @@ def lib():
         L.pic_profile_read.argtypes = [P, C.POINTER(pic_kernel_times)]
         L.pic_compact_static.argtypes = [P, P, P, P, C.c_int64, P, P, P, P,
                                          C.POINTER(C.c_int64), P]
+        L.pic_launch_config.argtypes = [P, C.POINTER(pic_launch_info)]
         L.pic_launch_count.argtypes = [P]
         L.pic_launch_count.restype = C.c_int64
         L.pic_destroy.argtypes = [P]
@@ -132,14 +145,15 @@ def _check(status, ctx=None):
 # ---------------------------------------------------------------------------
 # marshalling of the workload description
 # ---------------------------------------------------------------------------
-def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hist_mode=0):
+def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hist_mode=0,
+                ring_stages=0):
     p = pic_params()
     p.n_e = wl.n_e; p.dt = wl.dt; p.dz = wl.dz
     p.seed = wl.seed if seed is None else seed
     p.flags = wl.flags if flags is None else flags
     p.compact_every = wl.compact_every; p.moment_every = wl.moment_every
     p.n_steps_max = wl.n_steps if n_steps_max is None else n_steps_max
-    p.blocks_per_sm = blocks_per_sm; p.hist_mode = hist_mode
+    p.blocks_per_sm = blocks_per_sm; p.hist_mode = hist_mode; p.ring_stages = ring_stages
     return p
 
 
@@ -259,6 +273,12 @@ def pic_compact_static(z, mu, id_, packed, n, z_out, mu_out, id_out, packed_out,
     return alive.value
 
 
+def pic_launch_config(ctx):
+    info = pic_launch_info()
+    _check(lib().pic_launch_config(ctx, C.byref(info)), ctx)
+    return info.as_dict()
+
+
 def pic_launch_count(ctx):
     return int(lib().pic_launch_count(ctx))
 
@@ -289,12 +309,13 @@ class Context:
     """All stacks of a workload in one context on the current CUDA device."""
 
     def __init__(self, wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0,
-                 hist_mode=0, stream=None, excite=True, capacity=None):
+                 hist_mode=0, stream=None, excite=True, capacity=None, ring_stages=0):
         import torch
         self.wl = wl
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
-        self.params = make_params(wl, n_steps_max, flags, seed, blocks_per_sm, hist_mode)
+        self.params = make_params(wl, n_steps_max, flags, seed, blocks_per_sm, hist_mode,
+                                  ring_stages)
         self._tabs = [_Tables(st) for st in wl.stacks]
         self.stacks = [make_stack(st, capacity) for st in wl.stacks]
         self.ctx = pic_init(self.params, self.stacks, [t.c for t in self._tabs],
@@ -341,6 +362,9 @@ class Context:
 
     def sync(self):
         pic_sync(self.ctx)
+
+    def launch_config(self):
+        return pic_launch_config(self.ctx)
 
     @property
     def launches(self):

@@ -150,10 +150,12 @@ class Tracer:
             pid = p["id"]
             c0 = self.cell(p["z"])
             self.fly(p, half, pid, 0x100)
-            x = self.rand(pid, 0)
+            grp = philox([i >> 2, (self.sidx << 16) & MASK, self.step_no, 0x400], self.key)
             m = self.mat[p["l"]]
             k = p["k"]
+            x = [grp[i & 3], 0, 0, 0]
             if x[0] < self.P[m, p["s"], k]:
+                x = [x[0]] + self.rand(pid, 0)[1:]
                 inel = x[1] < self.Q[m, p["s"], k]
                 if k == 1 and (inel or wl.flags & 8):
                     p["k"] = 0
