@@ -39,6 +39,7 @@ struct pic_ctx {
     // device memory
     DevStack *d_stacks = nullptr;
     TabEnt *d_ent = nullptr;
+    FastEnt *d_fent = nullptr;
     uint32_t *d_T = nullptr, *d_cdf_thr = nullptr;
     int32_t *d_cdf_cell = nullptr, *d_cdf_layer = nullptr;
     long long *d_inj = nullptr;
@@ -249,7 +250,8 @@ void release(T *&p)
 // linger as the runtime's pending error for an unrelated later call.
 void free_all(pic_ctx *c)
 {
-    release(c->d_stacks); release(c->d_ent); release(c->d_T); release(c->d_cdf_thr);
+    release(c->d_stacks); release(c->d_ent); release(c->d_fent); release(c->d_T);
+    release(c->d_cdf_thr);
     release(c->d_cdf_cell); release(c->d_cdf_layer); release(c->d_inj);
     for (int b = 0; b < 2; ++b) {
         release(c->d_z[b]); release(c->d_mu[b]); release(c->d_id[b]); release(c->d_pk[b]);
@@ -365,6 +367,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     const int ne = p->n_e;
     int tab_max = 1, T_max = 1, nbin_max = 1, jbin_max = 1;
     std::vector<TabEnt> ent;
+    std::vector<FastEnt> fent;
     std::vector<uint32_t> Tall;
     for (int s = 0; s < n_stacks; ++s) {
         HostStack &h = c->hs[s];
@@ -398,6 +401,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
                 for (int k = 0; k < ne; ++k) {
                     const size_t i = ((size_t)h.d.layer_mat[l] * 2 + sp) * ne + k;
                     ent.push_back(TabEnt{h.v[i], h.P_thr[i], h.Q_thr[i], 0u});
+                    fent.push_back(FastEnt{h.v[i], h.P_thr[i], d.edge[l], d.edge[l + 1]});
                 }
         d.T_n = (h.d.n_layers - 1) * 4 * ne;
         d.T_off = (int64_t)Tall.size();
@@ -434,6 +438,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
 #define ALLOC(ptr, n) do { if (e == cudaSuccess) e = dalloc(&ptr, n); } while (0)
     ALLOC(c->d_stacks, n_stacks);
     ALLOC(c->d_ent, ent.size());
+    ALLOC(c->d_fent, fent.size());
     ALLOC(c->d_T, Tall.size());
     ALLOC(c->d_cdf_thr, total_cells);
     ALLOC(c->d_cdf_cell, total_cells);
@@ -463,7 +468,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
 
     Args &a = c->args;
     a.stacks = c->d_stacks; a.n_stacks = n_stacks;
-    a.ent = c->d_ent; a.T_thr = c->d_T;
+    a.ent = c->d_ent; a.fent = c->d_fent; a.T_thr = c->d_T;
     a.cdf_thr = c->d_cdf_thr; a.cdf_cell = c->d_cdf_cell; a.cdf_layer = c->d_cdf_layer;
     a.inj = c->d_inj;
     for (int b = 0; b < 2; ++b) {
@@ -516,6 +521,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     std::memset(cnt.data(), 0, sizeof(DevCounters) * n_stacks);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_stacks, c->ds.data(), sizeof(DevStack) * n_stacks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !ent.empty()) e = cudaMemcpyAsync(c->d_ent, ent.data(), sizeof(TabEnt) * ent.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !fent.empty()) e = cudaMemcpyAsync(c->d_fent, fent.data(), sizeof(FastEnt) * fent.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !Tall.empty()) e = cudaMemcpyAsync(c->d_T, Tall.data(), 4 * Tall.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_inj, 0, sizeof(long long) * std::max<size_t>((size_t)n_stacks * 2 * p->n_steps_max, 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned long long) * gmax, st);

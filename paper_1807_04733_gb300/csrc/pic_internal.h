@@ -48,6 +48,12 @@ struct TabEnt {          // one (layer, spin, k) entry
     uint32_t pad;
 };
 
+struct FastEnt {         // the common path's (layer, spin, k) entry
+    float v;             // nm/fs
+    uint32_t P;          // scatter iff test word < P
+    float lo, hi;        // edges of the layer, nm
+};
+
 struct DevStack {        // immutable per-stack description (device copy)
     int32_t n_layers, n_cells, tab_n, T_n;
     float edge[PIC_MAX_LAYERS + 1];
@@ -79,6 +85,7 @@ struct Args {            // everything a kernel needs, passed by value
     const DevStack *stacks;
     int n_stacks;
     const TabEnt *ent;
+    const FastEnt *fent;                     // same indexing as ent
     const uint32_t *T_thr;
     const uint32_t *cdf_thr;
     const int32_t *cdf_cell;

@@ -408,82 +408,145 @@ __device__ __forceinline__ long long make_tiles(const Args &a, long long *s_tpre
 // k_fast: the common case of Transport(dt/2) -> Scattering(dt) ->
 // Transport(dt/2), streamed.
 //
-// Each block streams its chunk of tiles through a ring of a.ring stages: one
-// thread issues the bulk copies of the four arrays of tile i + ring while the
-// block works on tile i.  A thread handles slots tid + r*TPB of a tile
-// (consecutive across a warp: conflict-free shared reads, coalesced writes).
-// A carrier that does not scatter and stays inside its layer for the whole
-// step is finished here: new depth, flux across the cell faces it passed,
-// density deposit.  Every other carrier ("eventful": it scatters or meets a
-// boundary) is copied, with its position, to the block's region of the
-// queue, in tile order, for k_slow.
+// Warp-specialised pipeline: one producer warp issues the bulk copies of the
+// z, mu and packed arrays of each tile into a ring of a.ring shared-memory
+// stages; eight consumer warps wait on the stage's "full" mbarrier, work on
+// four consecutive slots per thread, and release the stage with one arrival
+// per warp on its "empty" mbarrier, which gates the producer's next copy
+// into it.  No block-wide barrier runs per tile.  A carrier that does not
+// scatter and stays inside its layer for the whole step is finished here
+// (new depth, flux across the face it passed, density deposit).  Every other
+// carrier ("eventful": it scatters or meets a boundary) is copied, with its
+// position, to this block's region of the queue, in tile order, for k_slow.
 // ---------------------------------------------------------------------------
+constexpr int FAST_WARPS = TPB / 32;             // consumer warps
+constexpr int FAST_THREADS = TPB + 32;           // + the producer warp
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// barrier among the consumer warps only (the producer warp never joins)
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(TPB) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long consumer_sum_u64(unsigned long long v,
+                                                               unsigned long long *s_r)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = v;
+    consumer_sync();
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < FAST_WARPS; ++i) t += s_r[i];
+    consumer_sync();
+    return t;  // valid in thread 0
+}
+
 #ifndef PIC_FAST_MIN_BLOCKS
-#define PIC_FAST_MIN_BLOCKS 4      // resident blocks per SM the register budget allows
+#define PIC_FAST_MIN_BLOCKS 3      // resident blocks per SM the register budget allows
 #endif
 template <bool DET, bool DEPN, bool WAGG>
-__global__ void __launch_bounds__(TPB, PIC_FAST_MIN_BLOCKS) k_fast(const Args a)
+__global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(const Args a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     float *ring = reinterpret_cast<float *>(smem);                      // a.ring x 3 x TILE
-    TabEnt *s_ent = reinterpret_cast<TabEnt *>(ring + (size_t)a.ring * 3 * TILE);
+    FastEnt *s_ent = reinterpret_cast<FastEnt *>(ring + (size_t)a.ring * 3 * TILE);
     int32_t *s_J = reinterpret_cast<int32_t *>(s_ent + a.tab_max);
     uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + a.jbin_max);
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max : 0) + 1) + 0;
+    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max : 0) + 1);
     s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
     long long *s_nsl = s_tpref + a.n_stacks + 1;
-    __shared__ __align__(8) unsigned long long s_bar[MAX_RING];
-    __shared__ float s_edge[PIC_MAX_LAYERS + 1];
+    __shared__ __align__(8) unsigned long long s_full[MAX_RING], s_empty[MAX_RING];
     __shared__ DevStack s_st;
-    __shared__ unsigned long long s_r[TPB / 32];
+    __shared__ unsigned long long s_r[FAST_WARPS];
     __shared__ int s_qn, s_abort;
 
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
     const int b = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
-    const int lane = tid & 31;
+    const int warp = tid >> 5, lane = tid & 31;
     const unsigned int lt_mask = (1u << lane) - 1u;
-    const long long T = make_tiles(a, s_tpref, s_nsl);
-    const long long t0 = chunk_lo(T, b, G), t1 = chunk_lo(T, b + 1, G);
-    const long long ntiles = t1 - t0;
-    const long long pos0 = t0 * TILE;                // queue region of this block
-    const int tj = (int)(a.step / (uint32_t)a.moment_every);
-    const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
-    const float half = a.half_dt;
-    const int nring = a.ring;
-    float *Z = a.z[cur];
-    const float *MU = a.mu[cur];
-    const uint32_t *PK = a.pk[cur];
-
+    // tile prefix over the stacks (every thread of the block takes part)
+    for (int i = tid; i < a.n_stacks; i += FAST_THREADS) s_nsl[i] = (long long)a.cnt[i].n_slots;
     if (tid == 0) {
-        for (int i = 0; i < nring; ++i) mbar_init(&s_bar[i], 1);
+        for (int i = 0; i < a.ring; ++i) {
+            mbar_init(&s_full[i], 1);
+            mbar_init(&s_empty[i], FAST_WARPS);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_qn = 0;
         s_abort = 0;
     }
     __syncthreads();
-    // the common path needs z, mu and the packed word only (ids key the event
-    // draws of eventful carriers, which k_slow reads itself)
-    auto issue = [&](long long t, int stg) {
-        const int s = stack_of(s_tpref, a.n_stacks, t);
-        const long long off = a.stacks[s].base + (t - s_tpref[s]) * TILE;
-        float *dst = ring + (size_t)stg * 3 * TILE;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_expect_tx(&s_bar[stg], 3 * TILE_BYTES);
-        bulk_load(dst, Z + off, TILE_BYTES, &s_bar[stg]);
-        bulk_load(dst + TILE, MU + off, TILE_BYTES, &s_bar[stg]);
-        bulk_load(dst + 2 * TILE, PK + off, TILE_BYTES, &s_bar[stg]);
-    };
-    if (tid == 0)
-        for (long long i = 0; i < ntiles && i < nring; ++i) issue(t0 + i, (int)i);
+    if (tid == 0) {
+        long long acc = 0;
+        for (int i = 0; i < a.n_stacks; ++i) {
+            s_tpref[i] = acc;
+            acc += (s_nsl[i] + TILE - 1) / TILE;
+        }
+        s_tpref[a.n_stacks] = acc;
+    }
+    __syncthreads();
+    const long long T = s_tpref[a.n_stacks];
+    const long long t0 = chunk_lo(T, b, G), t1 = chunk_lo(T, b + 1, G);
+    const long long ntiles = t1 - t0;
+    const int nring = a.ring;
+    float *Z = a.z[cur];
+    const float *MU = a.mu[cur];
+    const uint32_t *PK = a.pk[cur];
 
-    int seg_stack = -1;
-    long long consumed = 0;
-    Stk S{};
-    uint32_t n_steps = 0;            // advanced carriers of the segment
-    uint32_t n_queued = 0;           // of which eventful (queued)
+    // ---------------- producer warp ----------------
+    if (warp == FAST_WARPS) {
+        if (lane == 0) {
+            long long issued = 0;
+            int stg = 0;
+            uint32_t phase = 0;          // completions of stage stg so far, mod 2
+            for (long long i = 0; i < ntiles; ++i) {
+                if (i >= nring &&
+                    !mbar_wait(&s_empty[stg], phase ^ 1u, a.spin_limit)) {
+                    atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+                    a.ctl->timeout_where = 4u;
+                    s_abort = 1;
+                }
+                if (*(volatile int *)&s_abort) break;
+                const long long t = t0 + i;
+                const int s = stack_of(s_tpref, a.n_stacks, t);
+                const long long off = a.stacks[s].base + (t - s_tpref[s]) * TILE;
+                float *dst = ring + (size_t)stg * 3 * TILE;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&s_full[stg], 3 * TILE_BYTES);
+                bulk_load(dst, Z + off, TILE_BYTES, &s_full[stg]);
+                bulk_load(dst + TILE, MU + off, TILE_BYTES, &s_full[stg]);
+                bulk_load(dst + 2 * TILE, PK + off, TILE_BYTES, &s_full[stg]);
+                issued = i + 1;
+                if (++stg == nring) { stg = 0; phase ^= 1u; }
+            }
+            if (*(volatile int *)&s_abort) {
+                // wait (bounded) for the copies that may still be in flight
+                // (the last `ring` issued), so that none lands in shared
+                // memory after the block has exited
+                for (long long i = issued > nring ? issued - nring : 0; i < issued; ++i)
+                    mbar_wait(&s_full[(int)(i % nring)], (uint32_t)((i / nring) & 1), a.spin_limit);
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
+    const int tj = (int)(a.step / (uint32_t)a.moment_every);
+    const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
+    const float half = a.half_dt;
+    const long long pos0 = t0 * TILE;                // queue region of this block
+    int seg_stack = -1, nc = 1, ne = a.n_e;
+    uint32_t ctr_hi = 0;
+    uint32_t n_steps = 0, n_queued = 0;
 
     auto flush = [&](int s) {
-        __syncthreads();
+        consumer_sync();
         const DevStack &st = s_st;
         const int nf = st.n_cells + 1;
         int32_t *gJ = a.J_hist + st.J_off + (long long)tj * 2 * nf;
@@ -499,43 +562,44 @@ __global__ void __launch_bounds__(TPB, PIC_FAST_MIN_BLOCKS) k_fast(const Args a)
                 if (v) atomicAdd(&gN[i], v);
             }
         }
-        const unsigned long long v0 = block_sum_u64(n_steps, s_r);
+        const unsigned long long v0 = consumer_sum_u64(n_steps, s_r);
         if (tid == 0 && v0) atomicAdd(&a.cnt[s].led[L_PARTICLE_STEPS], v0);
-        const unsigned long long v1 = block_sum_u64(n_queued, s_r);
+        const unsigned long long v1 = consumer_sum_u64(n_queued, s_r);
         if (tid == 0 && v1) atomicAdd(&a.cnt[s].led[L_EVENTFUL], v1);
         n_steps = 0;
         n_queued = 0;
-        __syncthreads();
+        consumer_sync();
     };
 
+    int stg = 0;
+    uint32_t phase = 0;                  // completions of full[stg] consumed, mod 2
     for (long long i = 0; i < ntiles; ++i) {
         const long long t = t0 + i;
         const int s = stack_of(s_tpref, a.n_stacks, t);
         if (s != seg_stack) {
             if (seg_stack >= 0) flush(seg_stack);
-            __syncthreads();
+            consumer_sync();
             if (tid == 0) s_st = a.stacks[s];
-            __syncthreads();
+            consumer_sync();
             const DevStack &st = s_st;
-            for (int q = tid; q < st.tab_n; q += TPB) s_ent[q] = a.ent[st.ent_off + q];
-            if (tid <= st.n_layers) s_edge[tid] = st.edge[tid];
+            for (int q = tid; q < st.tab_n; q += TPB) s_ent[q] = a.fent[st.ent_off + q];
             for (int q = tid; q < 2 * (st.n_cells + 1); q += TPB) s_J[q] = 0;
             if (DEPN)
                 for (int q = tid; q < 2 * a.n_e * st.n_cells; q += TPB) s_n[q] = 0u;
-            S.ent = s_ent; S.edge = s_edge; S.n_layers = st.n_layers; S.n_cells = st.n_cells;
-            S.n_e = a.n_e; S.ctr_hi = (uint32_t)s << 16;
+            nc = st.n_cells;
+            ctr_hi = (uint32_t)s << 16;
             seg_stack = s;
-            __syncthreads();
+            consumer_sync();
         }
         const long long nsl = s_nsl[s];
         const long long tslot0 = (t - s_tpref[s]) * TILE;
-        const int stg = (int)(i % nring);
-        if (!mbar_wait(&s_bar[stg], (uint32_t)((i / nring) & 1), a.spin_limit)) {
+        // after a failed wait every later wait is skipped: the warps run the
+        // same control flow to the end (results are invalid, the status says so)
+        if (!*(volatile int *)&s_abort && !mbar_wait(&s_full[stg], phase, a.spin_limit)) {
             atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
             a.ctl->timeout_where = 3u;
             s_abort = 1;
         }
-        consumed = i + 1;
         const float *rz = ring + (size_t)stg * 3 * TILE;
         const float *rmu = rz + TILE;
         const uint32_t *rpk = reinterpret_cast<const uint32_t *>(rz + 2 * TILE);
@@ -547,7 +611,11 @@ __global__ void __launch_bounds__(TPB, PIC_FAST_MIN_BLOCKS) k_fast(const Args a)
         const float4 z4 = reinterpret_cast<const float4 *>(rz)[tid];
         const float4 m4 = reinterpret_cast<const float4 *>(rmu)[tid];
         const uint4 p4 = reinterpret_cast<const uint4 *>(rpk)[tid];
-        const uint4 xg = philox_rk(make_uint4((uint32_t)(tslot0 >> 2) + (uint32_t)tid, S.ctr_hi,
+        // the stage is no longer needed by this warp
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[stg]);
+        if (++stg == nring) { stg = 0; phase ^= 1u; }
+        const uint4 xg = philox_rk(make_uint4((uint32_t)(tslot0 >> 2) + (uint32_t)tid, ctr_hi,
                                               a.step, SUB_TEST), a);
         const float zin[VEC] = {z4.x, z4.y, z4.z, z4.w};
         const float min_[VEC] = {m4.x, m4.y, m4.z, m4.w};
@@ -564,22 +632,28 @@ __global__ void __launch_bounds__(TPB, PIC_FAST_MIN_BLOCKS) k_fast(const Args a)
                 ++n_steps;
                 const float z = zin[j], mu = min_[j];
                 const int sg = (int)((pk >> 8) & 1u), layer = (int)((pk >> 9) & 0xFu);
-                const TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
+                const FastEnt e = s_ent[(layer * 2 + sg) * ne + (k - 1)];
                 const float w = __fmul_rn(e.v, mu);
                 const float z1 = DET ? __fadd_rn(z, __fmul_rn(w, half)) : __fmaf_rn(w, half, z);
                 const float z2 = DET ? __fadd_rn(z1, __fmul_rn(w, half)) : __fmaf_rn(w, half, z1);
                 // the motion is monotone within the step: the end point decides
-                const bool cross = mu > 0.f ? (z2 > S.edge[layer + 1]) : (z2 < S.edge[layer]);
+                const bool cross = mu > 0.f ? (z2 > e.hi) : (z2 < e.lo);
                 if (cross || xw[j] < e.P) {
                     slowbits |= 1u << j;
                 } else {
-                    const int c0 = cell_of(a, S, z), c1 = cell_of(a, S, z2);
-                    const int nf = S.n_cells + 1;
-                    if (c1 == c0 + 1) atomicAdd(&s_J[sg * nf + c1], 1);
-                    else if (c1 == c0 - 1) atomicAdd(&s_J[sg * nf + c0], -1);
-                    else if (c1 != c0) add_flux(s_J, nf, sg, c0, c1);
+                    // cells floor(z / dz): 2^23 added with rounding toward -inf
+                    const int c0u = __float_as_int(__fadd_rd(__fmul_rn(z, a.inv_dz), 8388608.0f)) - 0x4B000000;
+                    const int c1u = __float_as_int(__fadd_rd(__fmul_rn(z2, a.inv_dz), 8388608.0f)) - 0x4B000000;
+                    const int c1 = c1u < nc - 1 ? c1u : nc - 1;
+                    if (c0u != c1u) {
+                        const int c0 = c0u < nc - 1 ? c0u : nc - 1;
+                        const int nf = nc + 1;
+                        if (c1 == c0 + 1) atomicAdd(&s_J[sg * nf + c1], 1);
+                        else if (c1 == c0 - 1) atomicAdd(&s_J[sg * nf + c0], -1);
+                        else if (c1 != c0) add_flux(s_J, nf, sg, c0, c1);
+                    }
                     zo[j] = z2;
-                    if (DEPN) bin = (sg * S.n_e + (k - 1)) * S.n_cells + c1;
+                    if (DEPN) bin = (sg * ne + (k - 1)) * nc + c1;
                 }
             }
             if (DEPN && !WAGG && bin >= 0) atomicAdd(&s_n[bin], 1u);
@@ -598,36 +672,27 @@ __global__ void __launch_bounds__(TPB, PIC_FAST_MIN_BLOCKS) k_fast(const Args a)
                 if (i0 + j < nvalid) gZ[i0 + j] = zo[j];
         }
         // queue the eventful carriers (record and position), in tile order
+        if (__any_sync(0xffffffffu, slowbits != 0)) {
 #pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            const bool slow = (slowbits >> j) & 1u;
-            const unsigned int m = __ballot_sync(0xffffffffu, slow);
-            if (m) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&s_qn, __popc(m));
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (slow) {
-                    const long long q = pos0 + base + __popc(m & lt_mask);
-                    a.qrec[q] = make_float4(zin[j], min_[j], __uint_as_float(pin[j]),
-                                            __uint_as_float((uint32_t)((t - t0) * TILE + i0 + j)));
-                    ++n_queued;
+            for (int j = 0; j < VEC; ++j) {
+                const bool slow = (slowbits >> j) & 1u;
+                const unsigned int m = __ballot_sync(0xffffffffu, slow);
+                if (m) {
+                    int base = 0;
+                    if (lane == 0) base = atomicAdd(&s_qn, __popc(m));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (slow) {
+                        const long long q = pos0 + base + __popc(m & lt_mask);
+                        a.qrec[q] = make_float4(zin[j], min_[j], __uint_as_float(pin[j]),
+                                                __uint_as_float((uint32_t)((t - t0) * TILE + i0 + j)));
+                        ++n_queued;
+                    }
                 }
             }
         }
-        // every thread is done with ring stage stg: refill it with tile i + nring
-        __syncthreads();
-        if (s_abort) break;
-        if (tid == 0 && i + nring < ntiles) issue(t + nring, stg);
-    }
-    if (s_abort) {
-        // a copy did not land in time: wait (bounded) for the copies still in
-        // flight so no bulk copy writes into freed shared memory
-        if (tid == 0)
-            for (long long i = consumed; i < ntiles && i < consumed + nring - 1; ++i)
-                mbar_wait(&s_bar[i % nring], (uint32_t)((i / nring) & 1), a.spin_limit);
-        __syncthreads();
     }
     if (seg_stack >= 0) flush(seg_stack);
+    consumer_sync();
     if (tid == 0) a.qcnt[b] = (uint32_t)s_qn;
 }
 
@@ -660,7 +725,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
     __shared__ DevStack s_st;
     __shared__ int s_w[TPB / 32];
     __shared__ unsigned long long s_r[TPB / 32];
-    __shared__ long long s_prefix, s_range[2];
+    __shared__ long long s_prefix;
     __shared__ int s_flag, s_nspawn;
 
     const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
@@ -879,16 +944,20 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
         if (nsp) atomicAdd(&s_nspawn, nsp);
     };
 
-    // first entry of fast block f's queue (ascending by tile) with tile >= tb
+    // first entry of fast block f's queue (ascending by tile) with tile >=
+    // tb: the block counts the entries below tb (one pass, all threads)
     auto lower = [&](int f, long long tb) -> long long {
         const long long ft0 = chunk_lo(T, f, Gf), fpos0 = ft0 * TILE;
-        long long lo = 0, hi = a.qcnt[f];
-        while (lo < hi) {
-            const long long mid = (lo + hi) >> 1;
-            if (ft0 + __float_as_uint(a.qrec[fpos0 + mid].w) / TILE < tb) lo = mid + 1;
-            else hi = mid;
-        }
-        return lo;
+        const long long n = a.qcnt[f];
+        unsigned long long below = 0;
+        for (long long q = tid; q < n; q += TPB)
+            below += (ft0 + __float_as_uint(a.qrec[fpos0 + q].w) / TILE < tb) ? 1u : 0u;
+        const unsigned long long tot = block_sum_u64(below, s_r);
+        if (tid == 0) s_prefix = (long long)tot;
+        __syncthreads();
+        const long long r = s_prefix;
+        __syncthreads();
+        return r;
     };
 
     int staged_stack = -1;
@@ -910,13 +979,13 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
             if (tid == 0) s_nspawn = 0;
             __syncthreads();
             for (int f = fb0; f < fb1; ++f) {
-                if (tid == 0) {
-                    s_range[0] = lower(f, sg0);
-                    s_range[1] = lower(f, sg1);
+                // the queue entries of stack s (the whole queue when the chunk
+                // lies in one stack)
+                long long q_lo = 0, q_hi = a.qcnt[f];
+                if (s_first != s_last) {
+                    q_lo = lower(f, sg0);
+                    q_hi = lower(f, sg1);
                 }
-                __syncthreads();
-                const long long q_lo = s_range[0], q_hi = s_range[1];
-                __syncthreads();
                 if (q_lo < q_hi) work(s, f, q_lo, q_hi);
             }
             __syncthreads();
@@ -1197,7 +1266,7 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
 // largest dynamic shared memory the device offers is allowed, so that
 // contexts with different moment grids never lower each other's cap.
 template <class K>
-static cudaError_t occupancy(K kernel, size_t smem, int *blocks)
+static cudaError_t occupancy(K kernel, size_t smem, int *blocks, int threads = TPB)
 {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -1211,7 +1280,7 @@ static cudaError_t occupancy(K kernel, size_t smem, int *blocks)
     if ((int)smem > cap) return cudaSuccess;       // does not fit: zero blocks
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, TPB, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, threads, smem);
 }
 
 // Ring depth of k_fast for one variant, both builds (with and without fused
@@ -1227,8 +1296,8 @@ static cudaError_t pick_ring(size_t fixed, int blocks_per_sm, int ring_req, int 
         if (ring_req > 0 && r != ring_req) continue;
         const size_t sm = fixed + (size_t)r * 3 * TILE_BYTES;
         int o1 = 0, o2 = 0;
-        cudaError_t e = occupancy(k_fast<false, DEPN, WAGG>, sm, &o1);
-        if (e == cudaSuccess) e = occupancy(k_fast<true, DEPN, WAGG>, sm, &o2);
+        cudaError_t e = occupancy(k_fast<false, DEPN, WAGG>, sm, &o1, FAST_THREADS);
+        if (e == cudaSuccess) e = occupancy(k_fast<true, DEPN, WAGG>, sm, &o2, FAST_THREADS);
         if (e != cudaSuccess) return e;
         int o = o1 < o2 ? o1 : o2;
         if (blocks_per_sm > 0 && o > blocks_per_sm) o = blocks_per_sm;
@@ -1261,7 +1330,7 @@ cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_m
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
     const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;      // tile prefix, counts
-    const size_t fixed = (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.jbin_max * 4 + 4 + tiles;
+    const size_t fixed = (size_t)a.tab_max * sizeof(FastEnt) + (size_t)a.jbin_max * 4 + 4 + tiles;
     const size_t fixed_dep = fixed + (size_t)a.nbin_max * 4;
     int o_plain = 0, o_dep = 0;
     if ((e = pick_ring<false, false>(fixed, blocks_per_sm, ring_req, &cfg->ring_fast, &o_plain,
@@ -1300,17 +1369,17 @@ cudaError_t launch_fast(const Args &a0, const LaunchCfg &c, bool det, bool dep, 
     const bool w = hist_mode == 1;
     if (det) {
         if (dep) {
-            if (w) k_fast<true, true, true><<<g, TPB, sm, s>>>(a);
-            else k_fast<true, true, false><<<g, TPB, sm, s>>>(a);
+            if (w) k_fast<true, true, true><<<g, FAST_THREADS, sm, s>>>(a);
+            else k_fast<true, true, false><<<g, FAST_THREADS, sm, s>>>(a);
         } else {
-            k_fast<true, false, false><<<g, TPB, sm, s>>>(a);
+            k_fast<true, false, false><<<g, FAST_THREADS, sm, s>>>(a);
         }
     } else {
         if (dep) {
-            if (w) k_fast<false, true, true><<<g, TPB, sm, s>>>(a);
-            else k_fast<false, true, false><<<g, TPB, sm, s>>>(a);
+            if (w) k_fast<false, true, true><<<g, FAST_THREADS, sm, s>>>(a);
+            else k_fast<false, true, false><<<g, FAST_THREADS, sm, s>>>(a);
         } else {
-            k_fast<false, false, false><<<g, TPB, sm, s>>>(a);
+            k_fast<false, false, false><<<g, FAST_THREADS, sm, s>>>(a);
         }
     }
     return cudaGetLastError();
