@@ -88,6 +88,8 @@ def lib():
         L.or_next_id.argtypes = [P]; L.or_next_id.restype = C.c_uint64
         L.or_tables.argtypes = [P, P, P, P, P, P, P]
         L.or_philox4x32_10.argtypes = [P, P, P]
+        L.or_grad.argtypes = [C.POINTER(_Config), P, C.c_int64, C.c_uint64, C.c_int,
+                              P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -145,6 +147,9 @@ class OracleSim:
         self.h = h
         self.n_cells = lib().or_n_cells(h)
         self.n_out = lib().or_n_out(h)
+        # initial state the adjoint replays from (records loaded at step 0)
+        self._init = np.zeros(0, REC_DTYPE)
+        self._init_next_id = 0
 
     def __del__(self):
         h = getattr(self, "h", None)
@@ -167,6 +172,11 @@ class OracleSim:
         rc = lib().or_set_records(self.h, recs.ctypes.data, len(recs), next_id)
         if rc:
             raise ValueError("set_records failed")
+        if self.step_index == 0:
+            self._init = recs.copy()
+            self._init_next_id = int(next_id)
+        else:
+            self._init = None                # the run can no longer be replayed
 
     def moments(self):
         ne, nc = self.wl.n_e, self.n_cells
@@ -175,6 +185,34 @@ class OracleSim:
         led = Ledger()
         lib().or_moments(self.h, n.ctypes.data, J.ctypes.data, C.byref(led))
         return n, J, led.as_dict()
+
+    def grad(self, gn, gJ, n_steps: int | None = None):
+        """Score-function gradient of sum(gn * n) + sum(gJ * J) with respect to
+        tau_in [n_mat][2][n_e] and T [n_if][2][2][n_e], over the first n_steps
+        steps (default: the steps run so far) from the initial state.
+
+        Returns (g_tau, g_T, mag_tau, mag_T); mag_* sum |score| (|total| +
+        |earned|) per entry, the scale of rounding differences."""
+        if self._init is None:
+            raise ValueError("records were replaced after step 0: nothing to replay")
+        n_steps = self.step_index if n_steps is None else n_steps
+        ne, nc = self.wl.n_e, self.n_cells
+        gn = np.ascontiguousarray(np.broadcast_to(np.asarray(gn, np.float32),
+                                                  (self.n_out, 2, ne, nc)))
+        gJ = np.ascontiguousarray(np.broadcast_to(np.asarray(gJ, np.float32),
+                                                  (self.n_out, 2, nc + 1)))
+        nm, nif = self.cfg.n_mat, len(self.st.layer_cells) - 1
+        g_tau = np.zeros((nm, 2, ne)); m_tau = np.zeros_like(g_tau)
+        g_T = np.zeros((max(nif, 0), 2, 2, ne)); m_T = np.zeros_like(g_T)
+        init = np.ascontiguousarray(self._init, REC_DTYPE)
+        rc = lib().or_grad(C.byref(self.cfg), init.ctypes.data if len(init) else None,
+                           len(init), self._init_next_id, n_steps, gn.ctypes.data,
+                           gJ.ctypes.data, g_tau.ctypes.data,
+                           g_T.ctypes.data if g_T.size else None, m_tau.ctypes.data,
+                           m_T.ctypes.data if m_T.size else None)
+        if rc:
+            raise ValueError("or_grad failed with code %d" % rc)
+        return g_tau, g_T, m_tau, m_T
 
     def set_step(self, step: int):
         lib().or_set_step(self.h, step)

@@ -85,8 +85,31 @@ static uint32_t pk(uint32_t k, uint32_t s, uint32_t l, uint32_t g, uint32_t e)
     return k | (s << 8) | (l << 9) | (g << 13) | (e << 21);
 }
 
+/* State of the adjoint replay (or_grad).  Pass 1 sums every carrier's own
+ * reward (the weights of the densities it is counted in and of the faces it
+ * crosses) and records its parent; pass 2 weights the score of every random
+ * decision of a carrier by that carrier's reward-to-go. */
+typedef struct {
+    int pass;                     /* 1 or 2 */
+    const float *gn;              /* [n_out][2][n_e][n_cells] */
+    const float *gJ;              /* [n_out][2][n_cells+1] */
+    uint64_t n_ids;               /* size of the id-indexed arrays */
+    double *own;                  /* pass 1: own reward; then lineage total */
+    double *acc;                  /* pass 2: rewards and child totals so far */
+    uint64_t *parent;             /* UINT64_MAX: no parent */
+    /* d log p / d theta of each outcome, per table entry */
+    double *s_noscat, *s_scat, *s_el, *s_inel;   /* [n_mat][2][n_e], d/d tau_in */
+    double *s_tr, *s_rf;                         /* [n_if][2][2][n_e], d/d T */
+    double *g_tau, *g_T, *m_tau, *m_T;           /* sums of score x R and |score| x |R| */
+    double R, Rmag;               /* reward-to-go of the carrier being advanced */
+    int buffering, nbuf;          /* scores of a secondary wait for its id */
+    int buf_T[OR_MAX_HITS + 1], buf_bin[OR_MAX_HITS + 1];
+    double buf_s[OR_MAX_HITS + 1];
+} or_adj;
+
 struct or_sim {
     or_config cfg;
+    or_adj *adj;                  /* NULL: plain forward run */
     /* owned copies of the physical tables */
     float *v; double *tau_in, *tau_el, *T, *p0;
     /* geometry */
@@ -183,6 +206,61 @@ static void flux(or_sim *s, int sg, int a, int b)
     else       for (int f = b + 1; f <= a; ++f) J[f] -= 1;
 }
 
+/* ---- adjoint bookkeeping (used only when s->adj is set) ---- */
+
+/* make room in the id-indexed arrays for ids below n */
+static void adj_grow(or_sim *s, uint64_t n)
+{
+    or_adj *A = s->adj;
+    if (n <= A->n_ids) return;
+    uint64_t m = A->n_ids ? A->n_ids : 1024;
+    while (m < n) m *= 2;
+    A->own = (double *)realloc(A->own, sizeof(double) * m);
+    A->acc = (double *)realloc(A->acc, sizeof(double) * m);
+    A->parent = (uint64_t *)realloc(A->parent, sizeof(uint64_t) * m);
+    for (uint64_t i = A->n_ids; i < m; ++i) {
+        A->own[i] = 0.0; A->acc[i] = 0.0; A->parent[i] = UINT64_MAX;
+    }
+    A->n_ids = m;
+}
+
+/* weight of the flux a carrier of spin sg contributes when it moves from
+ * cell a to cell b in this step: the signed sum over the faces it crosses */
+static double flux_reward(const or_sim *s, int sg, int a, int b)
+{
+    const float *g = s->adj->gJ + ((int64_t)(s->step / s->cfg.moment_every) * 2 + sg) * (s->n_cells + 1);
+    double r = 0.0;
+    if (b > a) for (int f = a + 1; f <= b; ++f) r += g[f];
+    else       for (int f = b + 1; f <= a; ++f) r -= g[f];
+    return r;
+}
+
+/* a reward earned by carrier id: pass 1 sums it into the carrier's own
+ * total, pass 2 into what the carrier has earned so far */
+static void credit(or_sim *s, uint64_t id, double r)
+{
+    or_adj *A = s->adj;
+    if (A->pass == 1) A->own[id] += r;
+    else A->acc[id] += r;
+}
+
+/* the score of one decision (is_T: a transmittance entry, else a lifetime
+ * entry), weighted by the reward-to-go of the carrier being advanced, or
+ * held back while a secondary's flight has no id yet */
+static void add_score(or_sim *s, int is_T, int bin, double sc)
+{
+    or_adj *A = s->adj;
+    if (A->pass != 2) return;
+    if (A->buffering) {
+        A->buf_T[A->nbuf] = is_T; A->buf_bin[A->nbuf] = bin; A->buf_s[A->nbuf] = sc;
+        A->nbuf++;
+        return;
+    }
+    double *g = is_T ? A->g_T : A->g_tau, *m = is_T ? A->m_T : A->m_tau;
+    g[bin] += sc * A->R;
+    m[bin] += fabs(sc) * A->Rmag;
+}
+
 /* Transport for a time tau (Eq. Strang-transport): free flight inside the
  * current layer; at a vacuum surface the carrier is reflected; at an
  * interface a uniform draw against T decides transmission (layer changes,
@@ -221,7 +299,9 @@ static int half_flight(or_sim *s, or_rec *p, float tau, uint64_t id, uint32_t su
             if (!(c->flags & OR_F_TRANSPARENT)) {
                 uint32_t r[4];
                 draw(s, id, s->step, sub0 + (uint32_t)hit, r);
-                trans = r[0] < s->T_thr[((iface * 2 + dir) * 2 + sg) * c->n_e + (k - 1)];
+                int te = ((iface * 2 + dir) * 2 + sg) * c->n_e + (k - 1);
+                trans = r[0] < s->T_thr[te];
+                if (s->adj) add_score(s, 1, te, trans ? s->adj->s_tr[te] : s->adj->s_rf[te]);
             }
             if (trans) { layer += up ? 1 : -1; s->led.iface_transmit++; }
             else p->mu = -p->mu;
@@ -251,6 +331,7 @@ static void inject(or_sim *s, int half)
             return;
         }
         uint64_t id = s->next_id++;
+        if (s->adj) adj_grow(s, s->next_id);
         uint32_t a[4], b[4];
         draw(s, id, s->step, SUB_INJ + 0, a);
         draw(s, id, s->step, SUB_INJ + 1, b);
@@ -292,6 +373,13 @@ static void step_once(or_sim *s)
         const uint32_t pk_in = p->packed;
         int c_start = cell_of(s, p->z);
         int sg = (int)PK_S(p->packed);
+        or_adj *A = s->adj;
+        if (A && A->pass == 2) {
+            /* every decision of this step is weighted by what the carrier
+             * and its descendants still earn from the start of the step */
+            A->R = A->own[id] - A->acc[id];
+            A->Rmag = fabs(A->own[id]) + fabs(A->acc[id]);
+        }
 
         const int met1 = half_flight(s, p, half, id, SUB_IF + 0);
 
@@ -307,11 +395,19 @@ static void step_once(or_sim *s)
         int m = c->layer_mat[layer];
         int t = idx3(s, m, sg, k);
         if (met1 || x[0] < s->P_thr[t]) s->led.eventful++;
+        if (A) {
+            /* scores of the scattering test and, after a scattering, of the
+             * choice between the elastic and the inelastic channel */
+            double sc = A->s_noscat[t];
+            if (x[0] < s->P_thr[t]) sc = A->s_scat[t] + (x[1] < s->Q_thr[t] ? A->s_inel[t] : A->s_el[t]);
+            add_score(s, 0, t, sc);
+        }
         if (x[0] < s->P_thr[t]) {
             int inel = x[1] < s->Q_thr[t];
             if (k == 1 && (inel || (c->flags & OR_F_LOWEST_BIN_ANY))) {
                 absorb(s, p);
                 flux(s, sg, c_start, cell_of(s, p->z));
+                if (A) credit(s, id, flux_reward(s, sg, c_start, cell_of(s, p->z)));
                 s->led.changed++;
                 continue;
             }
@@ -338,7 +434,9 @@ static void step_once(or_sim *s)
                     /* boundary events are counted for carriers that exist
                      * after the step: a dropped secondary's are taken back */
                     or_ledger keep = s->led;
+                    if (A) { A->buffering = 1; A->nbuf = 0; }
                     half_flight(s, &q, half, id, SUB_SIF);
+                    if (A) A->buffering = 0;
                     if (s->n_slots < c->capacity) {
                         uint64_t nid = s->next_id++;
                         q.id = (uint32_t)nid;
@@ -346,6 +444,24 @@ static void step_once(or_sim *s)
                         append(s, q);
                         s->led.spawned++;
                         flux(s, (int)sgs, cs, cell_of(s, q.z));
+                        if (A) {
+                            adj_grow(s, s->next_id);
+                            if (A->pass == 1) {
+                                A->parent[nid] = id;
+                            } else {
+                                /* the secondary's own decisions of this half
+                                 * step, weighted by its whole lineage total;
+                                 * the parent has now earned that total */
+                                double Rp = A->R, Rm = A->Rmag;
+                                A->R = A->own[nid];
+                                A->Rmag = fabs(A->own[nid]);
+                                for (int b = 0; b < A->nbuf; ++b)
+                                    add_score(s, A->buf_T[b], A->buf_bin[b], A->buf_s[b]);
+                                A->R = Rp; A->Rmag = Rm;
+                                A->acc[id] += A->own[nid];
+                            }
+                            credit(s, nid, flux_reward(s, (int)sgs, cs, cell_of(s, q.z)));
+                        }
                     } else {
                         s->led.iface_hits = keep.iface_hits;
                         s->led.iface_transmit = keep.iface_transmit;
@@ -361,6 +477,7 @@ static void step_once(or_sim *s)
         const int met2 = half_flight(s, p, half, id, SUB_IF + 16);
         if (met2 && !met1 && !(x[0] < s->P_thr[t])) s->led.eventful++;
         flux(s, sg, c_start, cell_of(s, p->z));
+        if (A) credit(s, id, flux_reward(s, sg, c_start, cell_of(s, p->z)));
         if (p->mu != mu_in || p->packed != pk_in) s->led.changed++;
     }
     inject(s, 1);
@@ -374,6 +491,7 @@ static void step_once(or_sim *s)
             int64_t b = ((tout * 2 + PK_S(p->packed)) * c->n_e + (k - 1)) * s->n_cells
                         + cell_of(s, p->z);
             s->nh[b] += 1;
+            if (s->adj) credit(s, (uint64_t)p->id | ((uint64_t)PK_E(p->packed) << 32), s->adj->gn[b]);
         }
     }
     if ((s->step + 1) % (uint32_t)c->compact_every == 0) {
@@ -545,4 +663,101 @@ void or_tables(const or_sim *s, uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_th
     if (P0_thr) memcpy(P0_thr, s->P0_thr, sizeof(uint32_t) * c->n_mat);
     if (up_thr) *up_thr = s->up_thr;
     if (inj_counts) memcpy(inj_counts, s->inj, sizeof(int64_t) * 2 * (size_t)c->n_steps_max);
+}
+
+/* ---- adjoint: score-function gradient of a linear functional of the
+ * moments, O = sum gn * n + sum gJ * J, with respect to tau_in and T.
+ *
+ * Every random decision of the step has an outcome probability that
+ * depends on the tables: the scattering test (p = 1 - exp(-dt/tau_eff),
+ * Eq. lifetimes), the channel (inelastic with q = tau_eff/tau_in) and each
+ * interface draw (transmission with T).  The derivative of E[O] is the
+ * expectation of sum over decisions of d log P(outcome)/d theta times the
+ * reward that follows the decision.  The reward that may follow a decision
+ * of carrier i in step s is what i earns from the start of step s on plus
+ * the lineage totals of the secondaries it creates from then on (rewards
+ * that cannot depend on the outcome add only zero-mean terms).
+ *
+ * Pass 1 replays the run and sums each carrier's own rewards and records
+ * its parent; the lineage totals follow by adding every carrier's total to
+ * its parent's, children first (a child's id is larger than its parent's).
+ * Pass 2 replays the run again with the totals known. */
+int or_grad(const or_config *cfg, const or_rec *init, int64_t n_init, uint64_t next_id,
+            int n_steps, const float *gn, const float *gJ, double *g_tau, double *g_T,
+            double *mag_tau, double *mag_T)
+{
+    for (int64_t i = 0; i < n_init; ++i) {
+        uint64_t id = (uint64_t)init[i].id | ((uint64_t)PK_E(init[i].packed) << 32);
+        if (id >= next_id) return 1;
+    }
+    const int ne = cfg->n_e, nm = cfg->n_mat;
+    const size_t ntau = (size_t)nm * 2 * ne;
+    const size_t nT = (size_t)(cfg->n_layers > 1 ? cfg->n_layers - 1 : 0) * 4 * ne;
+    or_adj A;
+    memset(&A, 0, sizeof(A));
+    A.gn = gn; A.gJ = gJ;
+    A.s_noscat = (double *)calloc(ntau + 1, sizeof(double));
+    A.s_scat = (double *)calloc(ntau + 1, sizeof(double));
+    A.s_el = (double *)calloc(ntau + 1, sizeof(double));
+    A.s_inel = (double *)calloc(ntau + 1, sizeof(double));
+    A.s_tr = (double *)calloc(nT + 1, sizeof(double));
+    A.s_rf = (double *)calloc(nT + 1, sizeof(double));
+    A.g_tau = (double *)calloc(ntau + 1, sizeof(double));
+    A.m_tau = (double *)calloc(ntau + 1, sizeof(double));
+    A.g_T = (double *)calloc(nT + 1, sizeof(double));
+    A.m_T = (double *)calloc(nT + 1, sizeof(double));
+
+    /* d log P / d tau_in with rates r_in = 1/tau_in, r_el = 1/tau_el,
+     * r = r_in + r_el and d r_in / d tau_in = -r_in^2:
+     *   no scattering  log(1-p) = -dt r          ->  dt r_in^2
+     *   scattering     log p                     -> -dt r_in^2 e^{-dt r} / p
+     *   inelastic      log(r_in/r)               -> -r_in r_el / r
+     *   elastic        log(r_el/r)               ->  r_in^2 / r
+     * d log P / d T: transmission 1/T, reflection -1/(1-T). */
+    const double dt = (double)cfg->dt;
+    for (int m = 0; m < nm; ++m)
+        for (int sg = 0; sg < 2; ++sg)
+            for (int k = 0; k < ne; ++k) {
+                size_t t = ((size_t)m * 2 + sg) * ne + k;
+                double ti = cfg->tau_in[t], te = cfg->tau_el[m];
+                double r_in = isinf(ti) ? 0.0 : 1.0 / ti;
+                double r_el = isinf(te) ? 0.0 : 1.0 / te;
+                double r = r_in + r_el, a = dt * r, p = -expm1(-a);
+                A.s_noscat[t] = dt * r_in * r_in;
+                A.s_scat[t] = p > 0.0 ? -dt * r_in * r_in * exp(-a) / p : 0.0;
+                A.s_inel[t] = r > 0.0 ? -r_in * r_el / r : 0.0;
+                A.s_el[t] = (r > 0.0 && r_el > 0.0) ? r_in * r_in / r : 0.0;
+            }
+    for (size_t i = 0; i < nT; ++i) {
+        double T = cfg->T[i];
+        A.s_tr[i] = T > 0.0 ? 1.0 / T : 0.0;
+        A.s_rf[i] = T < 1.0 ? -1.0 / (1.0 - T) : 0.0;
+    }
+
+    int rc = 0;
+    for (int pass = 1; pass <= 2 && rc == 0; ++pass) {
+        or_sim *s = NULL;
+        rc = or_create(cfg, &s);
+        if (rc) break;
+        s->adj = &A;
+        A.pass = pass;
+        adj_grow(s, next_id);
+        if (or_set_records(s, init, n_init, next_id)) rc = 1;
+        if (!rc) rc = or_step(s, n_steps);
+        s->adj = NULL;
+        or_destroy(s);
+        if (pass == 1 && !rc)
+            for (uint64_t i = A.n_ids; i-- > 0;)
+                if (A.parent[i] != UINT64_MAX) A.own[A.parent[i]] += A.own[i];
+    }
+    if (rc == 0) {
+        if (g_tau) memcpy(g_tau, A.g_tau, sizeof(double) * ntau);
+        if (mag_tau) memcpy(mag_tau, A.m_tau, sizeof(double) * ntau);
+        if (g_T && nT) memcpy(g_T, A.g_T, sizeof(double) * nT);
+        if (mag_T && nT) memcpy(mag_T, A.m_T, sizeof(double) * nT);
+    }
+    free(A.s_noscat); free(A.s_scat); free(A.s_el); free(A.s_inel); free(A.s_tr); free(A.s_rf);
+    free(A.g_tau); free(A.m_tau); free(A.g_T); free(A.m_T);
+    free(A.own); free(A.acc); free(A.parent);
+    return rc;
 }

@@ -91,6 +91,16 @@ void or_tables(const or_sim *s, uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_th
                uint32_t *P0_thr, uint32_t *up_thr, int64_t *inj_counts);
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
+/* Score-function gradient of O = sum gn*n + sum gJ*J (gn: [n_out][2][n_e]
+ * [n_cells], gJ: [n_out][2][n_cells+1], the moment layouts) over n_steps
+ * steps from the initial records (ids below next_id), with respect to
+ * tau_in ([n_mat][2][n_e]) and T ([n_layers-1][2][2][n_e]).  mag_*: the sums
+ * of |score| (|total| + |earned|), a scale for rounding comparisons.
+ * Returns 0, or non-zero on bad input. */
+int or_grad(const or_config *cfg, const or_rec *init, int64_t n_init, uint64_t next_id,
+            int n_steps, const float *gn, const float *gJ, double *g_tau, double *g_T,
+            double *mag_tau, double *mag_T);
+
 #ifdef __cplusplus
 }
 #endif
