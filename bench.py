@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--ring", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--adjoint-scale", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -274,6 +276,54 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------------------
+# adjoint leg: time(pic_grad) / time(pic_step) over the same run
+# ---------------------------------------------------------------------------
+def adjoint_leg(args):
+    """The Fe(15 nm)/Au(100 nm) workload with 1e7 carriers (capacity 5e7, 800
+    steps of 1 fs, densities every step): forward run, then the gradient of
+    O1 + O2 with respect to the lifetime and transmittance tables, where O1 =
+    sum over windows and cells 90..99 of (n_up - n_down) and O2 = sum over
+    windows of (J_up - J_down) at face 15."""
+    import torch
+    from paper_1807_04733_gb300 import pic
+    from paper_1807_04733_gb300 import workloads as W
+    wl = W.config(3, scale=args.adjoint_scale)
+    ctx = pic.Context(wl)
+    stream = ctx.stream
+    nc, n_out, _ = ctx.shape(0)
+    gn = torch.zeros((1, n_out, 2, wl.n_e, nc), dtype=torch.float32, device="cuda")
+    gJ = torch.zeros((1, n_out, 2, nc + 1), dtype=torch.float32, device="cuda")
+    gn[0, :, 0, :, 90:100] = 1.0
+    gn[0, :, 1, :, 90:100] = -1.0
+    gJ[0, :, 0, 15] = 1.0
+    gJ[0, :, 1, 15] = -1.0
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    ctx.step(wl.n_steps)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = ev[0].elapsed_time(ev[1])
+    led = ctx.ledger(0)
+    times = []
+    for _ in range(2):          # the first call also allocates the replay buffers
+        ev[2].record(stream)
+        g_tau, g_T = ctx.grad(gn, gJ)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        times.append(ev[2].elapsed_time(ev[3]))
+    grad_ms = min(times)
+    out = {"workload": "fe15_au100 (1e7 carriers, capacity 5e7, 800 x 1 fs, densities every step)"
+                       if args.adjoint_scale == 1.0 else "fe15_au100 scaled by %g" % args.adjoint_scale,
+           "observable": "O1 + O2 (spin density, cells 90..99; spin flux, face 15)",
+           "forward_ms": fwd_ms, "grad_ms": grad_ms, "grad_ms_first_call": times[0],
+           "ratio": grad_ms / fwd_ms, "particle_steps": led["particle_steps"],
+           "grad_tau_abs_sum": float(g_tau.abs().sum()), "grad_T_abs_sum": float(g_T.abs().sum())}
+    ctx.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -408,6 +458,8 @@ def main():
         "launch_config": ctx.launch_config(),
     }
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_adjoint:
+        line["adjoint"] = adjoint_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(args, wl, period, pre, timed_steps=60)
     if dist is not None:

@@ -1,6 +1,6 @@
 """Build the C-ABI library ``libpic.so`` for sm_103a (in-tree, no cmake).
 
-The two translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 ``paper_1807_04733_gb300/_build/libpic.so``.  The CUDA runtime is linked
 statically, so the library depends only on the driver.
 """
@@ -16,8 +16,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpic.so")
-SOURCES = ["pic_kernels.cu", "pic_capi.cu", "pic_noalloc.cu"]
-HEADERS = [os.path.join(CSRC, "pic_internal.h"), os.path.join(ROOT, "include", "pic.h")]
+SOURCES = ["pic_kernels.cu", "pic_adjoint.cu", "pic_capi.cu", "pic_noalloc.cu"]
+HEADERS = [os.path.join(CSRC, "pic_internal.h"), os.path.join(CSRC, "pic_step.cuh"),
+           os.path.join(ROOT, "include", "pic.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]

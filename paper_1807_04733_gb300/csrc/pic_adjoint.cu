@@ -1,0 +1,226 @@
+// Adjoint replay of the PIC step: launch configuration and launchers of the
+// replay variants of the step kernels (pic_step.cuh, ADJ = 1, 2) and the
+// small kernels of the score-function gradient (flux potential, end-of-pass
+// flush, lineage totals).
+//
+// The gradient of E[O], O = sum gn * n + sum gJ * J, with respect to the
+// lifetime and transmittance tables is the expectation of the sum, over the
+// random decisions of the run (scattering test, channel, interface draws),
+// of d log P(outcome)/d theta times the reward that can follow the decision.
+// The forward run stores nothing: both passes recompute the trajectories from
+// the initial state and the Philox counters.
+//   pass 1   every carrier's own reward (its density weights and the signed
+//            weights of the faces it crosses), into an id-indexed array when it
+//            is removed or the pass ends; each secondary's parent and depth
+//   lineage  totals: every carrier's total added to its parent's, deepest
+//            generation first
+//   pass 2   reward-to-go R per slot (total minus what the carrier and its
+//            secondaries have earned); every decision of a step adds its
+//            score times R to per-block gradient bins
+#include <cuda_runtime.h>
+
+#include "pic_step.cuh"
+
+namespace pic {
+
+namespace {
+
+// flux potential of one (stack, window, spin) row: gpot[c] = sum_{f=1..c} gJ[f]
+__global__ void k_flux_potential(const Args a, const float *gJ, int rows)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const int s = r / (2 * a.n_out);
+    const int nc = a.stacks[s].n_cells;
+    const float *g = gJ + (long long)r * (a.ncm + 1);
+    double *p = const_cast<double *>(a.gpot) + (long long)r * a.ncm;
+    double acc = 0.0;
+    p[0] = 0.0;
+    for (int c = 1; c < nc; ++c) {
+        acc += (double)g[c];
+        p[c] = acc;
+    }
+}
+
+// start of a pass: the loaded carriers' own reward so far (0, pass 1) or
+// reward-to-go (their lineage total, pass 2)
+__global__ void k_init_acc(const Args a, int pass)
+{
+    for (int s = 0; s < a.n_stacks; ++s) {
+        const DevStack &st = a.stacks[s];
+        const long long n = (long long)a.cnt[s].n_slots;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const long long slot = st.base + i;
+            const unsigned long long id = (unsigned long long)a.id[0][slot] |
+                                          ((unsigned long long)(a.pk[0][slot] >> 21) << 32);
+            double v = 0.0;
+            if (pass == 2) {
+                if (id < (unsigned long long)st.n_ids) v = a.tot[st.id_off + (long long)id];
+                else atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_STATE);
+            }
+            a.acc[0][slot] = v;
+        }
+    }
+}
+
+// end of pass 1: the own reward of every carrier still in a slot
+__global__ void k_flush_own(const Args a)
+{
+    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
+    for (int s = 0; s < a.n_stacks; ++s) {
+        const DevStack &st = a.stacks[s];
+        const long long n = (long long)a.cnt[s].n_slots;
+        for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const long long slot = st.base + i;
+            const unsigned long long id = (unsigned long long)a.id[cur][slot] |
+                                          ((unsigned long long)(a.pk[cur][slot] >> 21) << 32);
+            if (id < (unsigned long long)st.n_ids) a.tot[st.id_off + (long long)id] = a.acc[cur][slot];
+            else atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_STATE);
+        }
+    }
+}
+
+// lineage: the totals of the carriers at depth g are complete (all their
+// descendants are deeper); add them to their parents'
+__global__ void k_lineage(const Args a, long long n_ids, int g)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_ids;
+         i += (long long)gridDim.x * blockDim.x)
+        if (a.gen[i] == (uint8_t)g) atomicAdd(&a.tot[a.parent[i]], a.tot[i]);
+}
+
+template <int ADJ>
+cudaError_t configure_pass(const Args &a, LaunchCfg *cfg)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;
+    const size_t fixed = (size_t)a.tab_max * sizeof(FastEnt) +
+                         (ADJ == 2 ? (size_t)a.tab_max * 8 : 0) + 4 + tiles;
+    int o_plain = 0, o_dep = 0;
+    if ((e = pick_ring<false, false, ADJ>(fixed, 0, 0, &cfg->ring_fast, &o_plain,
+                                          &cfg->smem_fast)) != cudaSuccess)
+        return e;
+    if ((e = pick_ring<true, false, ADJ>(fixed, 0, 0, &cfg->ring_fast_dep, &o_dep,
+                                         &cfg->smem_fast_dep)) != cudaSuccess)
+        return e;
+    cfg->grid_fast = sms * o_plain;
+    cfg->grid_fast_dep = sms * o_dep;
+    const size_t slow = (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.T_max * 4 + 8 +
+                        (ADJ == 2 ? (size_t)(a.tab_max + a.T_max) * 8 : 0) + 4 + tiles;
+    cfg->smem_slow = cfg->smem_slow_dep = slow;
+    if ((e = slow_cfg<false, ADJ>(slow, &cfg->grid_slow, sms)) != cudaSuccess) return e;
+    if ((e = slow_cfg<true, ADJ>(slow, &cfg->grid_slow_dep, sms)) != cudaSuccess) return e;
+    int oc = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_compact<ADJ>, TPB, 0)) != cudaSuccess)
+        return e;
+    cfg->grid_compact = sms * (oc > 0 ? oc : 1);
+    cfg->grid_inject = sms * 4;
+    return cudaSuccess;
+}
+
+template <int ADJ>
+void fast_pass(const Args &a, const LaunchCfg &c, bool det, bool dep, cudaStream_t s)
+{
+    const int g = dep ? c.grid_fast_dep : c.grid_fast;
+    const size_t sm = dep ? c.smem_fast_dep : c.smem_fast;
+    if (det) {
+        if (dep) k_fast<true, true, false, ADJ><<<g, FAST_THREADS, sm, s>>>(a);
+        else k_fast<true, false, false, ADJ><<<g, FAST_THREADS, sm, s>>>(a);
+    } else {
+        if (dep) k_fast<false, true, false, ADJ><<<g, FAST_THREADS, sm, s>>>(a);
+        else k_fast<false, false, false, ADJ><<<g, FAST_THREADS, sm, s>>>(a);
+    }
+}
+
+template <int ADJ>
+void slow_pass(const Args &a, const LaunchCfg &c, bool det, bool dep, cudaStream_t s)
+{
+    const int g = dep ? c.grid_slow_dep : c.grid_slow;
+    const size_t sm = dep ? c.smem_slow_dep : c.smem_slow;
+    if (det) {
+        if (dep) k_slow<true, true, ADJ><<<g, TPB, sm, s>>>(a);
+        else k_slow<true, false, ADJ><<<g, TPB, sm, s>>>(a);
+    } else {
+        if (dep) k_slow<false, true, ADJ><<<g, TPB, sm, s>>>(a);
+        else k_slow<false, false, ADJ><<<g, TPB, sm, s>>>(a);
+    }
+}
+
+}  // namespace
+
+cudaError_t configure_adjoint(const Args &a, int pass, LaunchCfg *cfg)
+{
+    return pass == 1 ? configure_pass<1>(a, cfg) : configure_pass<2>(a, cfg);
+}
+
+cudaError_t launch_fast_adj(const Args &a0, const LaunchCfg &c, int pass, bool det, bool dep,
+                            cudaStream_t s)
+{
+    Args a = a0;
+    a.ring = dep ? c.ring_fast_dep : c.ring_fast;
+    if (pass == 1) fast_pass<1>(a, c, det, dep, s);
+    else fast_pass<2>(a, c, det, dep, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slow_adj(const Args &a0, const LaunchCfg &c, int pass, bool det, bool dep,
+                            cudaStream_t s)
+{
+    Args a = a0;
+    a.grid_fast = dep ? c.grid_fast_dep : c.grid_fast;
+    if (pass == 1) slow_pass<1>(a, c, det, dep, s);
+    else slow_pass<2>(a, c, det, dep, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject_adj(const Args &a, const LaunchCfg &c, int pass, int half, bool deposit,
+                              cudaStream_t s)
+{
+    if (pass == 1) k_inject<1><<<c.grid_inject, TPB, 0, s>>>(a, half, deposit ? 1 : 0);
+    else k_inject<2><<<c.grid_inject, TPB, 0, s>>>(a, half, deposit ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compact_adj(const Args &a, const LaunchCfg &c, int pass, cudaStream_t s)
+{
+    if (pass == 1) k_compact<1><<<c.grid_compact, TPB, 0, s>>>(a);
+    else k_compact<2><<<c.grid_compact, TPB, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux_potential(const Args &a, const float *gJ, int rows, cudaStream_t s)
+{
+    if (rows <= 0) return cudaSuccess;
+    k_flux_potential<<<(rows + TPB - 1) / TPB, TPB, 0, s>>>(a, gJ, rows);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_acc(const Args &a, const LaunchCfg &c, int pass, cudaStream_t s)
+{
+    k_init_acc<<<c.grid_compact, TPB, 0, s>>>(a, pass);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flush_own(const Args &a, const LaunchCfg &c, cudaStream_t s)
+{
+    k_flush_own<<<c.grid_compact, TPB, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lineage(const Args &a, const LaunchCfg &c, long long n_ids, int g,
+                           cudaStream_t s)
+{
+    if (n_ids <= 0) return cudaSuccess;
+    long long blocks = (n_ids + TPB - 1) / TPB;
+    if (blocks > c.grid_compact) blocks = c.grid_compact;
+    k_lineage<<<(int)blocks, TPB, 0, s>>>(a, n_ids, g);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

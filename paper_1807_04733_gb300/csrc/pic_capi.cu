@@ -30,6 +30,32 @@ struct HostStack {
     bool excited = false;
 };
 
+// Buffers of the adjoint replay, allocated by the first pic_grad: a second
+// particle state (the forward state stays untouched), one double per slot,
+// the id-indexed lineage arrays, score tables and gradient bins.
+struct Replay {
+    float *z[2] = {nullptr, nullptr}, *mu[2] = {nullptr, nullptr};
+    uint32_t *id[2] = {nullptr, nullptr}, *pk[2] = {nullptr, nullptr};
+    double *acc[2] = {nullptr, nullptr};
+    uint32_t *stage_l = nullptr;
+    unsigned long long *status = nullptr;
+    uint32_t *qcnt = nullptr;
+    DevCounters *cnt = nullptr;
+    DevCtl *ctl = nullptr;
+    DevStack *stacks = nullptr;
+    AdjEnt *aent = nullptr;
+    double2 *aT = nullptr;
+    double *g_ent = nullptr, *g_T = nullptr, *gpot = nullptr;
+    unsigned int *gen_max = nullptr;
+    double *tot = nullptr;
+    unsigned long long *parent = nullptr;
+    uint8_t *gen = nullptr;
+    int64_t ids_cap = 0;        // entries of tot / parent / gen
+    int n_status = 0;
+    LaunchCfg lc[2]{};
+    bool ready = false;
+};
+
 struct pic_ctx {
     pic_params p{};
     int n_stacks = 0;
@@ -58,6 +84,14 @@ struct pic_ctx {
     int step = 0;
     int64_t launches = 0;
     std::string err;
+    // initial state the adjoint replays from: records loaded at step 0
+    std::vector<std::vector<pic_record>> init_recs;
+    std::vector<uint64_t> init_next_id;
+    bool replayable = true;
+    std::string replay_why;
+    size_t n_ent = 0, n_T = 0;   // entries of the layer and interface tables
+    int n_mat_max = 1;
+    Replay rp;
     // kernel timing (pic_profile)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -259,6 +293,15 @@ void free_all(pic_ctx *c)
     release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh);
     release(c->d_qrec); release(c->d_qcnt); release(c->d_J); release(c->d_cnt);
     release(c->d_ctl);
+    Replay &r = c->rp;
+    for (int b = 0; b < 2; ++b) {
+        release(r.z[b]); release(r.mu[b]); release(r.id[b]); release(r.pk[b]); release(r.acc[b]);
+    }
+    release(r.stage_l); release(r.status); release(r.qcnt); release(r.cnt); release(r.ctl); release(r.stacks);
+    release(r.aent); release(r.aT); release(r.g_ent); release(r.g_T); release(r.gpot);
+    release(r.gen_max); release(r.tot); release(r.parent); release(r.gen);
+    r.ids_cap = 0;
+    r.ready = false;
     cudaGetLastError();
 }
 
@@ -292,8 +335,9 @@ pic_status device_status(pic_ctx *c)
     if (e != cudaSuccess) return cuda_fail(c, e, "device status");
     if (h.status != 0) {
         const pic_status s = (pic_status)h.status;
-        return fail(c, s, s == PIC_ERR_TIMEOUT ? "a bounded device wait ran out"
-                                               : "capacity exceeded in strict mode");
+        return fail(c, s, s == PIC_ERR_TIMEOUT    ? "a bounded device wait ran out"
+                          : s == PIC_ERR_CAPACITY ? "capacity exceeded in strict mode"
+                                                  : "the adjoint replay did not reproduce the forward run");
     }
     return PIC_OK;
 }
@@ -423,6 +467,11 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         jbin_max = std::max(jbin_max, 2 * (cells + 1));
         h.inj.assign((size_t)2 * p->n_steps_max, 0);
     }
+    c->n_ent = ent.size();
+    c->n_T = Tall.size();
+    for (int s = 0; s < n_stacks; ++s) c->n_mat_max = std::max(c->n_mat_max, c->hs[s].n_mat);
+    c->init_recs.assign(n_stacks, {});
+    c->init_next_id.assign(n_stacks, 0);
     if (c->total_slots >= (int64_t(1) << 32)) {
         g_init_error = "total capacity of a context must stay below 2^32 slots";
         delete c;
@@ -550,6 +599,10 @@ pic_status pic_excite(pic_ctx *c, int stack, const pic_pulse *u)
     std::string why;
     for (int s = s0; s < s1; ++s)
         if (!valid_pulse(u, c->hs[s].d.n_layers, c->p.n_e, why)) return fail(c, PIC_ERR_ARG, why);
+    if (c->step > 0) {
+        c->replayable = false;
+        c->replay_why = "pic_grad: the source changed after step 0";
+    }
     for (int s = s0; s < s1; ++s) {
         HostStack &h = c->hs[s];
         DevStack &d = c->ds[s];
@@ -718,13 +771,251 @@ pic_status pic_set_records(pic_ctx *c, int stack, const pic_record *in, int64_t 
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt + stack, vals, sizeof(vals), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pic_set_records copy");
+    // the adjoint replays from records loaded before the first step, whose
+    // ids all lie below next_id
+    bool ids_ok = true;
+    for (int64_t i = 0; i < n && ids_ok; ++i)
+        ids_ok = ((uint64_t)in[i].id | ((uint64_t)(in[i].packed >> 21) << 32)) < next_id;
+    if (c->step == 0 && ids_ok) {
+        c->init_recs[stack].assign(in, in + n);
+        c->init_next_id[stack] = next_id;
+    } else {
+        c->replayable = false;
+        c->replay_why = c->step == 0 ? "pic_grad: a loaded record has an id >= next_id"
+                                     : "pic_grad: records were replaced after step 0";
+    }
     return PIC_OK;
 }
 
-pic_status pic_grad(pic_ctx *c, const float *, const float *, double *, double *)
+pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double *grad_tau,
+                    double *grad_T)
 {
     if (!c) return PIC_ERR_ARG;
-    return fail(c, PIC_ERR_STATE, "pic_grad: adjoint replay not available in this build");
+    if (!grad_tau && !grad_T) return fail(c, PIC_ERR_ARG, "pic_grad: no output");
+    if (!c->replayable) return fail(c, PIC_ERR_STATE, c->replay_why);
+    const pic_status st0 = device_status(c);
+    if (st0 != PIC_OK) return st0;
+    const int S = c->n_stacks, ne = c->p.n_e;
+    cudaStream_t st = c->stream;
+    cudaError_t e = cudaSuccess;
+
+    // the forward run's counters: ids issued per stack and the ledger the
+    // replay must reproduce
+    std::vector<DevCounters> fwd(S);
+    e = cudaMemcpyAsync(fwd.data(), c->d_cnt, sizeof(DevCounters) * S, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_grad: counters");
+    std::vector<DevStack> ds = c->ds;
+    int64_t n_ids = 0;
+    for (int s = 0; s < S; ++s) {
+        ds[s].id_off = n_ids;
+        ds[s].n_ids = (int64_t)fwd[s].next_id;
+        n_ids += ds[s].n_ids;
+    }
+    int ncm = 1;
+    for (int s = 0; s < S; ++s) ncm = std::max(ncm, c->hs[s].n_cells);
+    const int n_out = c->hs[0].n_out;
+
+    Replay &r = c->rp;
+    Args a = c->args;
+#define RALLOC(ptr, n) do { if (e == cudaSuccess && !(ptr)) e = dalloc(&ptr, n); } while (0)
+    if (!r.ready) {
+        for (int b = 0; b < 2; ++b) {
+            RALLOC(r.z[b], c->total_slots); RALLOC(r.mu[b], c->total_slots);
+            RALLOC(r.id[b], c->total_slots); RALLOC(r.pk[b], c->total_slots);
+            RALLOC(r.acc[b], c->total_slots);
+        }
+        RALLOC(r.stage_l, c->total_slots);
+        RALLOC(r.cnt, S); RALLOC(r.ctl, 1); RALLOC(r.stacks, S);
+        RALLOC(r.aent, c->n_ent); RALLOC(r.aT, c->n_T);
+        RALLOC(r.g_ent, c->n_ent); RALLOC(r.g_T, c->n_T);
+        RALLOC(r.gpot, (size_t)S * n_out * 2 * ncm);
+        RALLOC(r.gen_max, 1);
+        a.n_out = n_out; a.ncm = ncm;
+        for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass)
+            e = configure_adjoint(a, pass, &r.lc[pass - 1]);
+        if (e == cudaSuccess) {
+            r.n_status = 1;
+            for (const LaunchCfg &l : r.lc)
+                r.n_status = std::max({r.n_status, l.grid_fast, l.grid_fast_dep, l.grid_slow,
+                                       l.grid_slow_dep, l.grid_compact});
+        }
+        RALLOC(r.status, (size_t)r.n_status);
+        RALLOC(r.qcnt, (size_t)r.n_status);
+        // d log P / d tau_in of each outcome per (layer, spin, k), with rates
+        // r_in = 1/tau_in, r_el = 1/tau_el, r = r_in + r_el, p = 1 - e^{-dt r}
+        // and d r_in / d tau_in = -r_in^2; d log P / d T per interface entry
+        std::vector<AdjEnt> aent;
+        std::vector<double2> aT;
+        for (int s = 0; s < S && e == cudaSuccess; ++s) {
+            const HostStack &h = c->hs[s];
+            for (int l = 0; l < h.d.n_layers; ++l) {
+                const int m = h.d.layer_mat[l];
+                const double r_el = std::isinf(h.tau_el[m]) ? 0.0 : 1.0 / h.tau_el[m];
+                for (int sp = 0; sp < 2; ++sp)
+                    for (int k = 0; k < ne; ++k) {
+                        const double ti = h.tau_in[((size_t)m * 2 + sp) * ne + k];
+                        const double r_in = std::isinf(ti) ? 0.0 : 1.0 / ti;
+                        const double rate = r_in + r_el, dtr = (double)c->p.dt * rate;
+                        const double pr = -std::expm1(-dtr);
+                        const double keep = (double)c->p.dt * r_in * r_in;
+                        const double hit = pr > 0.0 ? -keep * std::exp(-dtr) / pr : 0.0;
+                        const double inel = rate > 0.0 ? -r_in * r_el / rate : 0.0;
+                        const double el = (rate > 0.0 && r_el > 0.0) ? r_in * r_in / rate : 0.0;
+                        aent.push_back(AdjEnt{keep, hit + el, hit + inel, 0.0});
+                    }
+            }
+            for (double T : h.T)
+                aT.push_back(make_double2(T > 0.0 ? 1.0 / T : 0.0, T < 1.0 ? -1.0 / (1.0 - T) : 0.0));
+        }
+        if (e == cudaSuccess && !aent.empty())
+            e = cudaMemcpyAsync(r.aent, aent.data(), sizeof(AdjEnt) * aent.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && !aT.empty())
+            e = cudaMemcpyAsync(r.aT, aT.data(), sizeof(double2) * aT.size(), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PIC_ERR_ALLOC, std::string("pic_grad: replay buffers: ") + cudaGetErrorString(e));
+        }
+        r.ready = true;
+    }
+    if (n_ids > r.ids_cap) {
+        release(r.tot); release(r.parent); release(r.gen);
+        r.ids_cap = 0;
+        RALLOC(r.tot, (size_t)n_ids); RALLOC(r.parent, (size_t)n_ids); RALLOC(r.gen, (size_t)n_ids);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            release(r.tot); release(r.parent); release(r.gen);
+            return fail(c, PIC_ERR_ALLOC, "pic_grad: " + std::to_string(n_ids) +
+                                              " carrier ids do not fit in device memory");
+        }
+        r.ids_cap = n_ids;
+    }
+#undef RALLOC
+
+    for (int b = 0; b < 2; ++b) {
+        a.z[b] = r.z[b]; a.mu[b] = r.mu[b]; a.id[b] = r.id[b]; a.pk[b] = r.pk[b];
+        a.acc[b] = r.acc[b];
+    }
+    a.stacks = r.stacks; a.cnt = r.cnt; a.ctl = r.ctl; a.status = r.status; a.qcnt = r.qcnt;
+    a.n_hist = nullptr; a.J_hist = nullptr;
+    a.tot = r.tot; a.parent = r.parent; a.gen = r.gen; a.gen_max = r.gen_max;
+    a.aent = r.aent; a.aT = r.aT; a.g_ent = r.g_ent; a.g_T = r.g_T;
+    a.gn = grad_n; a.gpot = r.gpot; a.stage_l = r.stage_l;
+    a.n_out = n_out; a.ncm = ncm;
+
+    e = cudaMemcpyAsync(r.stacks, ds.data(), sizeof(DevStack) * S, cudaMemcpyHostToDevice, st);
+    const int rows = S * n_out * 2;
+    if (e == cudaSuccess) {
+        if (grad_J) e = launch_flux_potential(a, grad_J, rows, st);
+        else e = cudaMemsetAsync(r.gpot, 0, sizeof(double) * (size_t)rows * ncm, st);
+    }
+    const bool det = (c->p.flags & PIC_F_DETERMINISTIC) != 0;
+    for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass) {
+        const LaunchCfg &lc = r.lc[pass - 1];
+        // the initial state
+        DevCtl ctl{};
+        ctl.epoch = 1u;
+        std::vector<DevCounters> cnt(S);
+        std::memset(cnt.data(), 0, sizeof(DevCounters) * S);
+        for (int s = 0; s < S && e == cudaSuccess; ++s) {
+            const std::vector<pic_record> &ir = c->init_recs[s];
+            cnt[s].n_slots = ir.size();
+            cnt[s].next_id = c->init_next_id[s];
+            const int64_t n = (int64_t)ir.size();
+            if (!n) continue;
+            std::vector<float> z(n), mu(n);
+            std::vector<uint32_t> id(n), pk(n);
+            for (int64_t i = 0; i < n; ++i) { z[i] = ir[i].z; mu[i] = ir[i].mu; id[i] = ir[i].id; pk[i] = ir[i].packed; }
+            const int64_t base = c->ds[s].base;
+            e = cudaMemcpyAsync(r.z[0] + base, z.data(), 4 * n, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r.mu[0] + base, mu.data(), 4 * n, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r.id[0] + base, id.data(), 4 * n, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r.pk[0] + base, pk.data(), 4 * n, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) break;
+            e = cudaStreamSynchronize(st);          // host vectors go out of scope
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r.cnt, cnt.data(), sizeof(DevCounters) * S, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(r.ctl, &ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.status, 0, sizeof(unsigned long long) * r.n_status, st);
+        // the own reward (pass 1) or reward-to-go (pass 2) of a loaded carrier
+        // starts at 0 or at its lineage total
+        if (e == cudaSuccess) e = launch_init_acc(a, lc, pass, st);
+        if (e == cudaSuccess && pass == 1) {
+            e = cudaMemsetAsync(r.gen, 0, (size_t)n_ids, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(r.tot, 0, sizeof(double) * (size_t)n_ids, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(r.gen_max, 0, sizeof(unsigned int), st);
+        }
+        if (e == cudaSuccess && pass == 2) {
+            e = cudaMemsetAsync(r.g_ent, 0, sizeof(double) * std::max<size_t>(c->n_ent, 1), st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(r.g_T, 0, sizeof(double) * std::max<size_t>(c->n_T, 1), st);
+        }
+        // the steps of the forward run, in the same order
+        for (int step = 0; step < c->step && e == cudaSuccess; ++step) {
+            a.step = (uint32_t)step;
+            bool inj0 = false, inj1 = false;
+            for (const HostStack &h : c->hs) {
+                inj0 = inj0 || h.inj[2 * (size_t)step] > 0;
+                inj1 = inj1 || h.inj[2 * (size_t)step + 1] > 0;
+            }
+            const bool dep = ((step + 1) % c->p.moment_every) == 0;
+            if (inj0) e = launch_inject_adj(a, lc, pass, 0, false, st);
+            if (e == cudaSuccess) e = launch_fast_adj(a, lc, pass, det, dep, st);
+            if (e == cudaSuccess) e = launch_slow_adj(a, lc, pass, det, dep, st);
+            if (e == cudaSuccess && inj1) e = launch_inject_adj(a, lc, pass, 1, dep, st);
+            if (e == cudaSuccess && ((step + 1) % c->p.compact_every) == 0)
+                e = launch_compact_adj(a, lc, pass, st);
+        }
+        if (e == cudaSuccess && pass == 1) e = launch_flush_own(a, lc, st);
+        if (e != cudaSuccess) break;
+
+        // the replay must have reproduced the forward run exactly
+        std::vector<DevCounters> rc(S);
+        DevCtl rctl{};
+        unsigned int gmax = 0;
+        e = cudaMemcpyAsync(rc.data(), r.cnt, sizeof(DevCounters) * S, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&rctl, r.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&gmax, r.gen_max, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) break;
+        if (rctl.status != 0)
+            return fail(c, (pic_status)rctl.status,
+                        rctl.status == PIC_ERR_TIMEOUT ? "pic_grad: a bounded device wait ran out"
+                                                       : "pic_grad: the replay did not reproduce the forward run");
+        for (int s = 0; s < S; ++s)
+            if (rc[s].n_slots != fwd[s].n_slots || rc[s].next_id != fwd[s].next_id ||
+                std::memcmp(rc[s].led, fwd[s].led, sizeof(fwd[s].led)) != 0)
+                return fail(c, PIC_ERR_STATE, "pic_grad: the replay of stack " + std::to_string(s) +
+                                                  " did not reproduce the forward run");
+        // lineage totals, deepest generation first
+        if (pass == 1)
+            for (int g = (int)gmax; g >= 1 && e == cudaSuccess; --g)
+                e = launch_lineage(a, lc, n_ids, g, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_grad");
+
+    // per-layer bins to the per-material and per-interface outputs
+    std::vector<double> g_ent(c->n_ent), g_T(c->n_T);
+    if (c->n_ent) e = cudaMemcpyAsync(g_ent.data(), r.g_ent, 8 * c->n_ent, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && c->n_T) e = cudaMemcpyAsync(g_T.data(), r.g_T, 8 * c->n_T, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_grad: gradient bins");
+    const size_t per_tau = (size_t)c->n_mat_max * 2 * ne, per_T = (size_t)(PIC_MAX_LAYERS - 1) * 4 * ne;
+    std::vector<double> out_tau((size_t)S * per_tau, 0.0), out_T((size_t)S * per_T, 0.0);
+    for (int s = 0; s < S; ++s) {
+        const HostStack &h = c->hs[s];
+        const DevStack &d = c->ds[s];
+        for (int l = 0; l < h.d.n_layers; ++l)
+            for (int i = 0; i < 2 * ne; ++i)
+                out_tau[s * per_tau + (size_t)h.d.layer_mat[l] * 2 * ne + i] +=
+                    g_ent[d.ent_off + (size_t)l * 2 * ne + i];
+        for (int i = 0; i < d.T_n; ++i) out_T[s * per_T + i] = g_T[d.T_off + i];
+    }
+    if (grad_tau) e = cudaMemcpyAsync(grad_tau, out_tau.data(), 8 * out_tau.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && grad_T) e = cudaMemcpyAsync(grad_T, out_T.data(), 8 * out_T.size(), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_grad: outputs");
+    return PIC_OK;
 }
 
 pic_status pic_shape(const pic_ctx *c, int stack, int32_t *n_cells, int32_t *n_out, int32_t *step)

@@ -54,6 +54,13 @@ struct FastEnt {         // the common path's (layer, spin, k) entry
     float lo, hi;        // edges of the layer, nm
 };
 
+struct AdjEnt {          // d log P / d tau_in of the outcomes of one (layer, spin, k) entry
+    double noscat;       // no scattering in the step
+    double scat_el;      // scattering, elastic channel
+    double scat_inel;    // scattering, inelastic channel
+    double pad;
+};
+
 struct DevStack {        // immutable per-stack description (device copy)
     int32_t n_layers, n_cells, tab_n, T_n;
     float edge[PIC_MAX_LAYERS + 1];
@@ -65,6 +72,7 @@ struct DevStack {        // immutable per-stack description (device copy)
     uint32_t up_thr;
     int32_t e_mode, k_mono0, k_mono1;
     int64_t inj_off;                    // source schedule, 2*n_steps_max
+    int64_t id_off, n_ids;              // adjoint: range of the id-indexed arrays
 };
 
 struct DevCounters {     // mutable per stack
@@ -116,6 +124,21 @@ struct Args {            // everything a kernel needs, passed by value
     uint32_t *spawn_bits;                    // one bit per position: secondary staged
     float4 *qrec;                            // eventful carriers: z, mu, packed, position
     uint32_t *qcnt;                          // queue length per fast block
+    // adjoint replay (ADJ = 1, 2); unused by the forward step
+    double *acc[2];                          // per slot: own reward so far (pass 1),
+                                             // reward still to come (pass 2)
+    double *tot;                             // per id: own reward, then lineage total
+    unsigned long long *parent;              // per id: index of the parent's entry
+    uint8_t *gen;                            // per id: generation (1 = primary)
+    unsigned int *gen_max;                   // largest generation created
+    const AdjEnt *aent;                      // scores, ent indexing
+    const double2 *aT;                       // scores (transmit, reflect), T_thr indexing
+    double *g_ent;                           // gradient, ent indexing
+    double *g_T;                             // gradient, T_thr indexing
+    const float *gn;                         // density weights [stack][n_out][2][n_e][ncm]
+    const double *gpot;                      // flux potential [stack][n_out][2][ncm]
+    uint32_t *stage_l;                       // pass 2: start layer of a staged secondary
+    int n_out, ncm;                          // moment windows, cells of the widest stack
 };
 
 // reason of the last failure of a call without a context (pic_capi.cu);
@@ -136,5 +159,24 @@ cudaError_t launch_fast(const Args &a, const LaunchCfg &c, bool deterministic, b
 cudaError_t launch_slow(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
                         cudaStream_t s);
 cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s);
+
+// adjoint replay (pic_adjoint.cu); pass = 1 or 2
+cudaError_t configure_adjoint(const Args &a, int pass, LaunchCfg *cfg);
+cudaError_t launch_inject_adj(const Args &a, const LaunchCfg &c, int pass, int half,
+                              bool deposit, cudaStream_t s);
+cudaError_t launch_fast_adj(const Args &a, const LaunchCfg &c, int pass, bool deterministic,
+                            bool deposit, cudaStream_t s);
+cudaError_t launch_slow_adj(const Args &a, const LaunchCfg &c, int pass, bool deterministic,
+                            bool deposit, cudaStream_t s);
+cudaError_t launch_compact_adj(const Args &a, const LaunchCfg &c, int pass, cudaStream_t s);
+// flux potential from the flux weights gJ [stack][n_out][2][ncm+1]
+cudaError_t launch_flux_potential(const Args &a, const float *gJ, int rows, cudaStream_t s);
+// start of a pass: the double of every loaded carrier (0, or its lineage total)
+cudaError_t launch_init_acc(const Args &a, const LaunchCfg &c, int pass, cudaStream_t s);
+// pass 1 end: own reward of every carrier still in a slot
+cudaError_t launch_flush_own(const Args &a, const LaunchCfg &c, cudaStream_t s);
+// lineage totals of generation g added to their parents
+cudaError_t launch_lineage(const Args &a, const LaunchCfg &c, long long n_ids, int g,
+                           cudaStream_t s);
 
 }  // namespace pic

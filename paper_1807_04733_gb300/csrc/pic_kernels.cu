@@ -1,1327 +1,14 @@
-// CUDA kernels of the hot-electron PIC step (sm_103a).
-//
-// One Strang step (Eq. strang, Sec. III.A) is, per stack:
-//   k_inject(half 0)   Source(dt/2): append new carriers
-//   k_step             Transport(dt/2) -> Scattering(dt) -> Transport(dt/2)
-//                      for every live slot, secondaries appended in parent
-//                      slot order, densities and fluxes deposited
-//   k_inject(half 1)   Source(dt/2), deposited at moment steps
-//   k_compact          every compact_every steps: stable removal of dead slots
-//
-// The step kernel is a persistent streaming kernel: the tiles of all stacks
-// are concatenated and cut into one contiguous chunk per block.  Each thread
-// moves four consecutive slots with one 128-bit load and store per array.
-// Secondary carriers are placed by a decoupled look-back over the blocks'
-// chunks (the block's running count of secondaries, published as a tagged
-// 64-bit word), so slot order and ids equal those of a scalar loop over the
-// slots; every wait on another block is bounded and reports PIC_ERR_TIMEOUT.
-// Densities and fluxes are privatised in shared memory and flushed to the
-// global moment arrays once per block and stack segment.
+// Forward step of the hot-electron PIC method: launch configuration and
+// launchers of the kernels in pic_step.cuh.
 #include <cuda_runtime.h>
 
-#include "pic_internal.h"
+#include "pic_step.cuh"
 
 namespace pic {
 
 // ---------------------------------------------------------------------------
-// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
-// with the round multipliers 0xD2511F53 / 0xCD9E8D57; the key of round r is
-// key + r * (0x9E3779B9, 0xBB67AE85).
-// ---------------------------------------------------------------------------
-// Philox4x32-10 with the ten round keys taken from the kernel arguments
-// (precomputed on the host), so no key arithmetic runs per call
-__device__ __forceinline__ uint4 philox_rk(uint4 c, const Args &a)
-{
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const unsigned long long p0 = 0xD2511F53ull * c.x;
-        const unsigned long long p1 = 0xCD9E8D57ull * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ a.rk0[r], (uint32_t)p1,
-                       (uint32_t)(p0 >> 32) ^ c.w ^ a.rk1[r], (uint32_t)p0);
-    }
-    return c;
-}
-
-// direction cosine from a word: odd multiples of 2^-23 in (-1, 1), exact
-__device__ __forceinline__ float mu_of(uint32_t x)
-{
-    const int n = (int)(2u * (x >> 9) + 1u) - 8388608;
-    return __fmul_rn(__int2float_rn(n), 1.1920928955078125e-07f);
-}
-
-// uniform in (0, 1): odd multiples of 2^-24, exact
-__device__ __forceinline__ float unit_of(uint32_t x)
-{
-    return __fmul_rn(__uint2float_rn(2u * (x >> 9) + 1u), 5.9604644775390625e-08f);
-}
-
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p)
-{
-    return *(volatile const unsigned long long *)p;
-}
-
-struct Tally {           // per-thread event counts, reduced per segment
-    uint32_t steps, absorbed, bath, hits, trans, trunc, spawn_drop, q_drop, changed;
-};
-
-// Shared-memory view of the current stack.
-struct Stk {
-    const TabEnt *ent;
-    const uint32_t *T;
-    const float *edge;
-    const uint32_t *p0;
-    int n_layers, n_cells, n_e;
-    uint32_t ctr_hi;     // stack << 16
-};
-
-// Cell of a depth z >= 0: floor(z / dz), clamped to the last cell.  dz is a
-// power of two, so q = z * (1/dz) is exact; adding 2^23 with rounding toward
-// -inf leaves floor(q) in the low mantissa bits (0 <= q < 2^23).
-__device__ __forceinline__ int cell_of(const Args &a, const Stk &s, float z)
-{
-    const float q = __fmul_rn(z, a.inv_dz);
-    const int c = __float_as_int(__fadd_rd(q, 8388608.0f)) - 0x4B000000;
-    return c < s.n_cells - 1 ? c : s.n_cells - 1;
-}
-
-// Transport for a time tau (Eq. Strang-transport, Sec. III): free flight in
-// the current layer, mirror reflection at the vacuum surfaces, a uniform
-// draw against T at an interface (transmit: layer changes, mu kept;
-// reflect: mu mirrored), the remaining time flown in the new layer.
-// e, lo, hi: table entry and edges of the current layer (updated on transmission).
-template <bool DET>
-__device__ __forceinline__ void flight(const Args &a, const Stk &s, float &z, float &mu,
-                                       int &layer, TabEnt &e, float &lo, float &hi, int sg,
-                                       int k, float tau, uint32_t id_lo, uint32_t ctr_y,
-                                       uint32_t sub0, Tally &t)
-{
-    for (int hit = 0;; ++hit) {
-        const float w = __fmul_rn(e.v, mu);
-        const float z1 = DET ? __fadd_rn(z, __fmul_rn(w, tau)) : __fmaf_rn(w, tau, z);
-        float zb;
-        bool up;
-        if (mu > 0.f && z1 > hi) { zb = hi; up = true; }
-        else if (mu < 0.f && z1 < lo) { zb = lo; up = false; }
-        else { z = z1; return; }
-        if (hit == PIC_MAX_HITS) { z = zb; ++t.trunc; return; }
-        const float tb = __fdiv_rn(__fsub_rn(zb, z), w);
-        tau = __fsub_rn(tau, tb);
-        if (!(tau > 0.f)) tau = 0.f;
-        z = zb;
-        const bool vacuum = up ? (layer == s.n_layers - 1) : (layer == 0);
-        if (vacuum) {
-            mu = -mu;
-        } else {
-            const int iface = up ? layer : layer - 1, dir = up ? 0 : 1;
-            bool trans = true;
-            ++t.hits;
-            if (!(a.flags & PIC_F_TRANSPARENT)) {
-                const uint4 r = philox_rk(make_uint4(id_lo, ctr_y, a.step, sub0 + (uint32_t)hit), a);
-                trans = r.x < s.T[((iface * 2 + dir) * 2 + sg) * s.n_e + (k - 1)];
-            }
-            if (trans) {
-                layer += up ? 1 : -1;
-                ++t.trans;
-                e = s.ent[(layer * 2 + sg) * s.n_e + (k - 1)];
-                lo = s.edge[layer];
-                hi = s.edge[layer + 1];
-            } else {
-                mu = -mu;
-            }
-        }
-    }
-}
-
-__device__ __forceinline__ void add_flux(int32_t *sJ, int nf, int sg, int c0, int c1)
-{
-    if (c1 > c0) for (int f = c0 + 1; f <= c1; ++f) atomicAdd(&sJ[sg * nf + f], 1);
-    else         for (int f = c1 + 1; f <= c0; ++f) atomicAdd(&sJ[sg * nf + f], -1);
-}
-
-// Block-wide exclusive scan of small non-negative ints; returns the total.
-__device__ __forceinline__ int block_scan(int v, int &excl, int *s_w)
-{
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int x = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) s_w[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-        int w = lane < TPB / 32 ? s_w[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        if (lane < TPB / 32) s_w[lane] = w;        // inclusive warp totals
-    }
-    __syncthreads();
-    excl = x - v + (wid ? s_w[wid - 1] : 0);
-    const int total = s_w[TPB / 32 - 1];
-    __syncthreads();
-    return total;
-}
-
-__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
-                                                            unsigned long long *s_r)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = v;
-    __syncthreads();
-    unsigned long long t = 0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < TPB / 32; ++i) t += s_r[i];
-    __syncthreads();
-    return t;  // valid in thread 0
-}
-
-// Status word of the look-back: epoch:32 | flag:2 | value:30
-constexpr unsigned long long FLAG_A = 1ull, FLAG_P = 2ull;
-__device__ __forceinline__ void publish(unsigned long long *w, unsigned int ep,
-                                        unsigned long long flag, long long value)
-{
-    __threadfence();
-    atomicExch(w, ((unsigned long long)ep << 32) | (flag << 30) |
-                      ((unsigned long long)value & 0x3FFFFFFFull));
-}
-
-// Exclusive prefix of the running count of the stack segment that starts
-// this block's chunk at tile t0 (stack tiles start at ts): walk back over the
-// blocks whose chunks end inside the same stack.  Bounded wait.
-__device__ long long look_back(const Args &a, unsigned int ep, long long T, long long ts,
-                               int b, int G)
-{
-    long long prefix = 0;
-    for (int j = b - 1; j >= 0; --j) {
-        const long long jt0 = T * j / G, jt1 = T * (j + 1) / G;
-        if (jt1 <= ts) break;
-        if (jt0 == jt1) continue;
-        unsigned long long w = 0;
-        unsigned int it = 0;
-        for (;;) {
-            w = ld_volatile_u64(&a.status[j]);
-            if ((unsigned int)(w >> 32) == ep && ((w >> 30) & 3ull)) break;
-            if (++it > a.spin_limit) {
-                atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
-                a.ctl->timeout_where = 1u;
-                w = FLAG_P << 30;
-                break;
-            }
-            if (it > 64) __nanosleep(128);
-        }
-        prefix += (long long)(w & 0x3FFFFFFFull);
-        if (((w >> 30) & 3ull) == FLAG_P) break;
-    }
-    return prefix;
-}
-
-// Per-block plan shared by the streaming kernels: tiles of every stack
-// concatenated; this block owns tiles [t0, t1).
-struct Plan {
-    long long T, t0, t1;
-};
-
-__device__ __forceinline__ void make_plan(const Args &a, long long *s_tpref,
-                                          long long *s_nsl, Plan &p)
-{
-    for (int i = threadIdx.x; i < a.n_stacks; i += TPB)
-        s_nsl[i] = (long long)a.cnt[i].n_slots;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long acc = 0;
-        for (int i = 0; i < a.n_stacks; ++i) {
-            s_tpref[i] = acc;
-            acc += (s_nsl[i] + TILE - 1) / TILE;
-        }
-        s_tpref[a.n_stacks] = acc;
-    }
-    __syncthreads();
-    p.T = s_tpref[a.n_stacks];
-    p.t0 = p.T * blockIdx.x / gridDim.x;
-    p.t1 = p.T * (blockIdx.x + 1) / gridDim.x;
-}
-
-__device__ __forceinline__ int stack_of(const long long *s_tpref, int n, long long t)
-{
-    int lo = 0, hi = n - 1;              // last s with s_tpref[s] <= t
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_tpref[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-// Last-block-done: returns true in every thread of the block that finished last.
-__device__ __forceinline__ bool last_block(const Args &a, int *s_flag)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const unsigned int t = atomicAdd(&a.ctl->done, 1u);
-        *s_flag = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    const bool last = *s_flag != 0;
-    if (last) __threadfence();
-    return last;
-}
-
-__device__ __forceinline__ void load_stack(const Args &a, int s, Stk &k, DevStack *s_st,
-                                           TabEnt *s_ent, uint32_t *s_T, float *s_edge,
-                                           uint32_t *s_p0)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) *s_st = a.stacks[s];
-    __syncthreads();
-    const DevStack &st = *s_st;
-    for (int i = threadIdx.x; i < st.tab_n; i += TPB) s_ent[i] = a.ent[st.ent_off + i];
-    for (int i = threadIdx.x; i < st.T_n; i += TPB) s_T[i] = a.T_thr[st.T_off + i];
-    if (threadIdx.x <= st.n_layers) s_edge[threadIdx.x] = st.edge[threadIdx.x];
-    if (threadIdx.x < st.n_layers) s_p0[threadIdx.x] = st.p0_thr[threadIdx.x];
-    k.ent = s_ent; k.T = s_T; k.edge = s_edge; k.p0 = s_p0;
-    k.n_layers = st.n_layers; k.n_cells = st.n_cells; k.n_e = a.n_e;
-    k.ctr_hi = (uint32_t)s << 16;
-}
-
-// ---------------------------------------------------------------------------
-// Tensor-memory-accelerator (bulk copy) helpers: 1-D cp.async.bulk of a tile
-// of each particle array into a shared-memory ring, completion tracked by an
-// mbarrier per ring stage.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait: false if the copy did not land within `limit` polls
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity,
-                                          unsigned int limit)
-{
-    for (unsigned int it = 0; it < limit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    return false;
-}
-
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes,
-                                          unsigned long long *bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-        ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-constexpr int MAX_RING = 8;
-constexpr uint32_t TILE_BYTES = TILE * 4u;      // one array of one tile
-
-// Chunk of block j of a grid of G blocks over T tiles: [T*j/G, T*(j+1)/G).
-__device__ __forceinline__ long long chunk_lo(long long T, int j, int G)
-{
-    return T * j / G;
-}
-
-// Tiles of slow block j: the union of the chunks of the fast blocks
-// [Gf*j/Gs, Gf*(j+1)/Gs), so that it covers whole fast chunks.
-__device__ __forceinline__ long long slow_lo(long long T, int j, int Gs, int Gf)
-{
-    return chunk_lo(T, (int)((long long)Gf * j / Gs), Gf);
-}
-
-// Exclusive prefix of the secondaries of the stack segment that starts slow
-// block b's chunk (stack tiles start at ts): walk back over the blocks whose
-// chunks end inside the same stack.  Bounded wait.
-__device__ long long look_back_slow(const Args &a, unsigned int ep, long long T, long long ts,
-                                    int b, int Gs, int Gf)
-{
-    long long prefix = 0;
-    for (int j = b - 1; j >= 0; --j) {
-        const long long jt0 = slow_lo(T, j, Gs, Gf), jt1 = slow_lo(T, j + 1, Gs, Gf);
-        if (jt1 <= ts) break;
-        if (jt0 == jt1) continue;
-        unsigned long long w = 0;
-        unsigned int it = 0;
-        for (;;) {
-            w = ld_volatile_u64(&a.status[j]);
-            if ((unsigned int)(w >> 32) == ep && ((w >> 30) & 3ull)) break;
-            if (++it > a.spin_limit) {
-                atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
-                a.ctl->timeout_where = 1u;
-                w = FLAG_P << 30;
-                break;
-            }
-            if (it > 64) __nanosleep(128);
-        }
-        prefix += (long long)(w & 0x3FFFFFFFull);
-        if (((w >> 30) & 3ull) == FLAG_P) break;
-    }
-    return prefix;
-}
-
-// tile prefix over the stacks, in dynamic shared memory
-__device__ __forceinline__ long long make_tiles(const Args &a, long long *s_tpref, long long *s_nsl)
-{
-    for (int i = threadIdx.x; i < a.n_stacks; i += TPB) s_nsl[i] = (long long)a.cnt[i].n_slots;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long acc = 0;
-        for (int i = 0; i < a.n_stacks; ++i) {
-            s_tpref[i] = acc;
-            acc += (s_nsl[i] + TILE - 1) / TILE;
-        }
-        s_tpref[a.n_stacks] = acc;
-    }
-    __syncthreads();
-    return s_tpref[a.n_stacks];
-}
-
-// ---------------------------------------------------------------------------
-// k_fast: the common case of Transport(dt/2) -> Scattering(dt) ->
-// Transport(dt/2), streamed.
-//
-// Warp-specialised pipeline: one producer warp issues the bulk copies of the
-// z, mu and packed arrays of each tile into a ring of a.ring shared-memory
-// stages; eight consumer warps wait on the stage's "full" mbarrier, work on
-// four consecutive slots per thread, and release the stage with one arrival
-// per warp on its "empty" mbarrier, which gates the producer's next copy
-// into it.  No block-wide barrier runs per tile.  A carrier that does not
-// scatter and stays inside its layer for the whole step is finished here
-// (new depth, flux across the face it passed, density deposit).  Every other
-// carrier ("eventful": it scatters or meets a boundary) is copied, with its
-// position, to this block's region of the queue, in tile order, for k_slow.
-// ---------------------------------------------------------------------------
-constexpr int FAST_WARPS = TPB / 32;             // consumer warps
-constexpr int FAST_THREADS = TPB + 32;           // + the producer warp
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-// barrier among the consumer warps only (the producer warp never joins)
-__device__ __forceinline__ void consumer_sync()
-{
-    asm volatile("bar.sync 1, %0;" ::"n"(TPB) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long consumer_sum_u64(unsigned long long v,
-                                                               unsigned long long *s_r)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = v;
-    consumer_sync();
-    unsigned long long t = 0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < FAST_WARPS; ++i) t += s_r[i];
-    consumer_sync();
-    return t;  // valid in thread 0
-}
-
-#ifndef PIC_FAST_MIN_BLOCKS
-#define PIC_FAST_MIN_BLOCKS 3      // resident blocks per SM the register budget allows
-#endif
-template <bool DET, bool DEPN, bool WAGG>
-__global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(const Args a)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    float *ring = reinterpret_cast<float *>(smem);                      // a.ring x 3 x TILE
-    FastEnt *s_ent = reinterpret_cast<FastEnt *>(ring + (size_t)a.ring * 3 * TILE);
-    int32_t *s_J = reinterpret_cast<int32_t *>(s_ent + a.tab_max);
-    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + a.jbin_max);
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max : 0) + 1);
-    s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
-    long long *s_nsl = s_tpref + a.n_stacks + 1;
-    __shared__ __align__(8) unsigned long long s_full[MAX_RING], s_empty[MAX_RING];
-    __shared__ DevStack s_st;
-    __shared__ unsigned long long s_r[FAST_WARPS];
-    __shared__ int s_qn, s_abort;
-
-    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
-    const int b = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const unsigned int lt_mask = (1u << lane) - 1u;
-    // tile prefix over the stacks (every thread of the block takes part)
-    for (int i = tid; i < a.n_stacks; i += FAST_THREADS) s_nsl[i] = (long long)a.cnt[i].n_slots;
-    if (tid == 0) {
-        for (int i = 0; i < a.ring; ++i) {
-            mbar_init(&s_full[i], 1);
-            mbar_init(&s_empty[i], FAST_WARPS);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_qn = 0;
-        s_abort = 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        long long acc = 0;
-        for (int i = 0; i < a.n_stacks; ++i) {
-            s_tpref[i] = acc;
-            acc += (s_nsl[i] + TILE - 1) / TILE;
-        }
-        s_tpref[a.n_stacks] = acc;
-    }
-    __syncthreads();
-    const long long T = s_tpref[a.n_stacks];
-    const long long t0 = chunk_lo(T, b, G), t1 = chunk_lo(T, b + 1, G);
-    const long long ntiles = t1 - t0;
-    const int nring = a.ring;
-    float *Z = a.z[cur];
-    const float *MU = a.mu[cur];
-    const uint32_t *PK = a.pk[cur];
-
-    // ---------------- producer warp ----------------
-    if (warp == FAST_WARPS) {
-        if (lane == 0) {
-            long long issued = 0;
-            int stg = 0;
-            uint32_t phase = 0;          // completions of stage stg so far, mod 2
-            for (long long i = 0; i < ntiles; ++i) {
-                if (i >= nring &&
-                    !mbar_wait(&s_empty[stg], phase ^ 1u, a.spin_limit)) {
-                    atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
-                    a.ctl->timeout_where = 4u;
-                    s_abort = 1;
-                }
-                if (*(volatile int *)&s_abort) break;
-                const long long t = t0 + i;
-                const int s = stack_of(s_tpref, a.n_stacks, t);
-                const long long off = a.stacks[s].base + (t - s_tpref[s]) * TILE;
-                float *dst = ring + (size_t)stg * 3 * TILE;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&s_full[stg], 3 * TILE_BYTES);
-                bulk_load(dst, Z + off, TILE_BYTES, &s_full[stg]);
-                bulk_load(dst + TILE, MU + off, TILE_BYTES, &s_full[stg]);
-                bulk_load(dst + 2 * TILE, PK + off, TILE_BYTES, &s_full[stg]);
-                issued = i + 1;
-                if (++stg == nring) { stg = 0; phase ^= 1u; }
-            }
-            if (*(volatile int *)&s_abort) {
-                // wait (bounded) for the copies that may still be in flight
-                // (the last `ring` issued), so that none lands in shared
-                // memory after the block has exited
-                for (long long i = issued > nring ? issued - nring : 0; i < issued; ++i)
-                    mbar_wait(&s_full[(int)(i % nring)], (uint32_t)((i / nring) & 1), a.spin_limit);
-            }
-        }
-        return;
-    }
-
-    // ---------------- consumer warps ----------------
-    const int tj = (int)(a.step / (uint32_t)a.moment_every);
-    const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
-    const float half = a.half_dt;
-    const long long pos0 = t0 * TILE;                // queue region of this block
-    int seg_stack = -1, nc = 1, ne = a.n_e;
-    uint32_t ctr_hi = 0;
-    uint32_t n_steps = 0, n_queued = 0;
-
-    auto flush = [&](int s) {
-        consumer_sync();
-        const DevStack &st = s_st;
-        const int nf = st.n_cells + 1;
-        int32_t *gJ = a.J_hist + st.J_off + (long long)tj * 2 * nf;
-        for (int i = tid; i < 2 * nf; i += TPB) {
-            const int v = s_J[i];
-            if (v) atomicAdd(&gJ[i], v);
-        }
-        if (DEPN) {
-            const int nbins = 2 * a.n_e * st.n_cells;
-            uint32_t *gN = a.n_hist + st.n_off + (long long)tout * nbins;
-            for (int i = tid; i < nbins; i += TPB) {
-                const uint32_t v = s_n[i];
-                if (v) atomicAdd(&gN[i], v);
-            }
-        }
-        const unsigned long long v0 = consumer_sum_u64(n_steps, s_r);
-        if (tid == 0 && v0) atomicAdd(&a.cnt[s].led[L_PARTICLE_STEPS], v0);
-        const unsigned long long v1 = consumer_sum_u64(n_queued, s_r);
-        if (tid == 0 && v1) atomicAdd(&a.cnt[s].led[L_EVENTFUL], v1);
-        n_steps = 0;
-        n_queued = 0;
-        consumer_sync();
-    };
-
-    int stg = 0;
-    uint32_t phase = 0;                  // completions of full[stg] consumed, mod 2
-    for (long long i = 0; i < ntiles; ++i) {
-        const long long t = t0 + i;
-        const int s = stack_of(s_tpref, a.n_stacks, t);
-        if (s != seg_stack) {
-            if (seg_stack >= 0) flush(seg_stack);
-            consumer_sync();
-            if (tid == 0) s_st = a.stacks[s];
-            consumer_sync();
-            const DevStack &st = s_st;
-            for (int q = tid; q < st.tab_n; q += TPB) s_ent[q] = a.fent[st.ent_off + q];
-            for (int q = tid; q < 2 * (st.n_cells + 1); q += TPB) s_J[q] = 0;
-            if (DEPN)
-                for (int q = tid; q < 2 * a.n_e * st.n_cells; q += TPB) s_n[q] = 0u;
-            nc = st.n_cells;
-            ctr_hi = (uint32_t)s << 16;
-            seg_stack = s;
-            consumer_sync();
-        }
-        const long long nsl = s_nsl[s];
-        const long long tslot0 = (t - s_tpref[s]) * TILE;
-        // after a failed wait every later wait is skipped: the warps run the
-        // same control flow to the end (results are invalid, the status says so)
-        if (!*(volatile int *)&s_abort && !mbar_wait(&s_full[stg], phase, a.spin_limit)) {
-            atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
-            a.ctl->timeout_where = 3u;
-            s_abort = 1;
-        }
-        const float *rz = ring + (size_t)stg * 3 * TILE;
-        const float *rmu = rz + TILE;
-        const uint32_t *rpk = reinterpret_cast<const uint32_t *>(rz + 2 * TILE);
-        float *gZ = Z + s_st.base + tslot0;
-        const int nvalid = nsl - tslot0 < TILE ? (int)(nsl - tslot0) : TILE;
-        // four consecutive slots per thread; one Philox call gives the four
-        // scattering-test words of the slot group
-        const int i0 = VEC * tid;
-        const float4 z4 = reinterpret_cast<const float4 *>(rz)[tid];
-        const float4 m4 = reinterpret_cast<const float4 *>(rmu)[tid];
-        const uint4 p4 = reinterpret_cast<const uint4 *>(rpk)[tid];
-        // the stage is no longer needed by this warp
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[stg]);
-        if (++stg == nring) { stg = 0; phase ^= 1u; }
-        const uint4 xg = philox_rk(make_uint4((uint32_t)(tslot0 >> 2) + (uint32_t)tid, ctr_hi,
-                                              a.step, SUB_TEST), a);
-        const float zin[VEC] = {z4.x, z4.y, z4.z, z4.w};
-        const float min_[VEC] = {m4.x, m4.y, m4.z, m4.w};
-        const uint32_t pin[VEC] = {p4.x, p4.y, p4.z, p4.w};
-        const uint32_t xw[VEC] = {xg.x, xg.y, xg.z, xg.w};
-        float zo[VEC] = {z4.x, z4.y, z4.z, z4.w};
-        uint32_t slowbits = 0;
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            int bin = -1;
-            const uint32_t pk = pin[j];
-            const int k = (int)(pk & 0xFFu);
-            if (i0 + j < nvalid && k != 0) {
-                ++n_steps;
-                const float z = zin[j], mu = min_[j];
-                const int sg = (int)((pk >> 8) & 1u), layer = (int)((pk >> 9) & 0xFu);
-                const FastEnt e = s_ent[(layer * 2 + sg) * ne + (k - 1)];
-                const float w = __fmul_rn(e.v, mu);
-                const float z1 = DET ? __fadd_rn(z, __fmul_rn(w, half)) : __fmaf_rn(w, half, z);
-                const float z2 = DET ? __fadd_rn(z1, __fmul_rn(w, half)) : __fmaf_rn(w, half, z1);
-                // the motion is monotone within the step: the end point decides
-                const bool cross = mu > 0.f ? (z2 > e.hi) : (z2 < e.lo);
-                if (cross || xw[j] < e.P) {
-                    slowbits |= 1u << j;
-                } else {
-                    // cells floor(z / dz): 2^23 added with rounding toward -inf
-                    const int c0u = __float_as_int(__fadd_rd(__fmul_rn(z, a.inv_dz), 8388608.0f)) - 0x4B000000;
-                    const int c1u = __float_as_int(__fadd_rd(__fmul_rn(z2, a.inv_dz), 8388608.0f)) - 0x4B000000;
-                    const int c1 = c1u < nc - 1 ? c1u : nc - 1;
-                    if (c0u != c1u) {
-                        const int c0 = c0u < nc - 1 ? c0u : nc - 1;
-                        const int nf = nc + 1;
-                        if (c1 == c0 + 1) atomicAdd(&s_J[sg * nf + c1], 1);
-                        else if (c1 == c0 - 1) atomicAdd(&s_J[sg * nf + c0], -1);
-                        else if (c1 != c0) add_flux(s_J, nf, sg, c0, c1);
-                    }
-                    zo[j] = z2;
-                    if (DEPN) bin = (sg * ne + (k - 1)) * nc + c1;
-                }
-            }
-            if (DEPN && !WAGG && bin >= 0) atomicAdd(&s_n[bin], 1u);
-            if (DEPN && WAGG) {
-                const unsigned int m = __match_any_sync(0xffffffffu, bin);
-                if (bin >= 0 && lane == __ffs(m) - 1) atomicAdd(&s_n[bin], (uint32_t)__popc(m));
-            }
-        }
-        // new depths (an eventful carrier keeps its old one here: k_slow
-        // writes its final state); only slots below n_slots are written
-        if (i0 + VEC <= nvalid) {
-            *reinterpret_cast<float4 *>(gZ + i0) = make_float4(zo[0], zo[1], zo[2], zo[3]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < VEC; ++j)
-                if (i0 + j < nvalid) gZ[i0 + j] = zo[j];
-        }
-        // queue the eventful carriers (record and position), in tile order
-        if (__any_sync(0xffffffffu, slowbits != 0)) {
-#pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-                const bool slow = (slowbits >> j) & 1u;
-                const unsigned int m = __ballot_sync(0xffffffffu, slow);
-                if (m) {
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&s_qn, __popc(m));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (slow) {
-                        const long long q = pos0 + base + __popc(m & lt_mask);
-                        a.qrec[q] = make_float4(zin[j], min_[j], __uint_as_float(pin[j]),
-                                                __uint_as_float((uint32_t)((t - t0) * TILE + i0 + j)));
-                        ++n_queued;
-                    }
-                }
-            }
-        }
-    }
-    if (seg_stack >= 0) flush(seg_stack);
-    consumer_sync();
-    if (tid == 0) a.qcnt[b] = (uint32_t)s_qn;
-}
-
-// ---------------------------------------------------------------------------
-// k_slow: the general step for the queued (eventful) carriers, and the
-// placement of every secondary of the step.
-//
-// Slow block j works off the queues of fast blocks [Gf*j/Gs, Gf*(j+1)/Gs)
-// with all lanes busy on the event paths: interface draws against T, mirror
-// reflection, elastic and inelastic scattering, removal in the lowest bin
-// and secondary generation (Sec. III).  A secondary is staged at its
-// parent's position with one bit in a bitmap; its rank among the stack's
-// secondaries (slot order of the parents = the id order of a sequential
-// loop) is the popcount prefix of the bitmap, continued across blocks by a
-// decoupled look-back with a bounded wait.
-// ---------------------------------------------------------------------------
-template <bool DET, bool DEPN>
-__global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    TabEnt *s_ent = reinterpret_cast<TabEnt *>(smem);
-    uint32_t *s_T = reinterpret_cast<uint32_t *>(s_ent + a.tab_max);
-    int32_t *s_J = reinterpret_cast<int32_t *>(s_T + a.T_max);
-    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + a.jbin_max);
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max : 0) + 1);
-    s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
-    long long *s_nsl = s_tpref + a.n_stacks + 1;
-    __shared__ float s_edge[PIC_MAX_LAYERS + 1];
-    __shared__ uint32_t s_p0[PIC_MAX_LAYERS];
-    __shared__ DevStack s_st;
-    __shared__ int s_w[TPB / 32];
-    __shared__ unsigned long long s_r[TPB / 32];
-    __shared__ long long s_prefix;
-    __shared__ int s_flag, s_nspawn;
-
-    const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
-    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
-    const int b = blockIdx.x, Gs = gridDim.x, Gf = a.grid_fast, tid = threadIdx.x;
-    const long long T = make_tiles(a, s_tpref, s_nsl);
-    const int fb0 = (int)((long long)Gf * b / Gs), fb1 = (int)((long long)Gf * (b + 1) / Gs);
-    const long long t0 = chunk_lo(T, fb0, Gf), t1 = chunk_lo(T, fb1, Gf);
-    const int tj = (int)(a.step / (uint32_t)a.moment_every);
-    const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
-    const float half = a.half_dt;
-    float *Z = a.z[cur], *MU = a.mu[cur];
-    uint32_t *PK = a.pk[cur];
-    if (tid == 0) s_nspawn = 0;
-
-    Stk S{};
-    Tally ty{};
-
-    auto flush_segment = [&](int s) {
-        __syncthreads();
-        const DevStack &st = s_st;
-        const int nf = st.n_cells + 1;
-        int32_t *gJ = a.J_hist + st.J_off + (long long)tj * 2 * nf;
-        for (int i = tid; i < 2 * nf; i += TPB) {
-            const int v = s_J[i];
-            if (v) atomicAdd(&gJ[i], v);
-        }
-        if (DEPN) {
-            const int nb = 2 * a.n_e * st.n_cells;
-            uint32_t *gN = a.n_hist + st.n_off + (long long)tout * nb;
-            for (int i = tid; i < nb; i += TPB) {
-                const uint32_t v = s_n[i];
-                if (v) atomicAdd(&gN[i], v);
-            }
-        }
-        unsigned long long *L = a.cnt[s].led;
-        const uint32_t vals[8] = {ty.absorbed, ty.bath, ty.hits, ty.trans, ty.trunc,
-                                  ty.spawn_drop, ty.q_drop, ty.changed};
-        const int idx[8] = {L_ABSORBED, L_Q_BATH, L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED,
-                            L_SPAWN_DROPPED, L_Q_DROPPED, L_CHANGED};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const unsigned long long v = block_sum_u64(vals[q], s_r);
-            if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
-        }
-        ty = Tally{};
-        __syncthreads();
-    };
-
-    // Place the staged secondaries of stack s in tiles [tl0, tl1) in slot
-    // order, the first with rank `prefix` among the stack's secondaries of
-    // this step; clears the bitmap words it reads.  Deposits go to shared
-    // memory if `smem_hist`, else to global memory.
-    auto place = [&](int s, long long tl0, long long tl1, long long prefix, bool smem_hist) {
-        const DevStack stg = a.stacks[s];
-        const long long nsl = s_nsl[s];
-        const long long room = stg.cap - nsl;
-        const unsigned long long nid = a.cnt[s].next_id;
-        const int nf = stg.n_cells + 1;
-        uint32_t kept = 0;
-        Stk tmp;
-        tmp.n_cells = stg.n_cells;
-        long long run = prefix;
-        const long long w0 = tl0 * (TILE / 32), w1 = tl1 * (TILE / 32);
-        for (long long wb = w0; wb < w1; wb += TPB) {
-            const long long w = wb + tid;
-            uint32_t bits = w < w1 ? a.spawn_bits[w] : 0u;
-            int excl;
-            const int tot = block_scan(__popc(bits), excl, s_w);
-            if (bits) {
-                a.spawn_bits[w] = 0u;
-                long long g = run + excl;
-                while (bits) {
-                    const int j = __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                    const float4 r = a.stage[w * 32 + j];
-                    const uint32_t pk_staged = __float_as_uint(r.z);
-                    const uint32_t pk = pk_staged & 0x1FFFFFu;
-                    if (g < room) {
-                        ty.hits += (pk_staged >> 21) & 0xFu;
-                        ty.trans += (pk_staged >> 25) & 0xFu;
-                        ty.trunc += (pk_staged >> 29) & 0x1u;
-                        const unsigned long long id = nid + (unsigned long long)g;
-                        const long long d = stg.base + nsl + g;
-                        Z[d] = r.x;
-                        MU[d] = r.y;
-                        a.id[cur][d] = (uint32_t)id;
-                        PK[d] = pk | ((uint32_t)(id >> 32) << 21);
-                        ++kept;
-                        const int sg = (int)((pk >> 8) & 1u), k = (int)(pk & 0xFFu);
-                        const int c0 = cell_of(a, tmp, r.w), c1 = cell_of(a, tmp, r.x);
-                        if (smem_hist) {
-                            if (c0 != c1) add_flux(s_J, nf, sg, c0, c1);
-                            if (DEPN) atomicAdd(&s_n[(sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
-                        } else {
-                            int32_t *gJ = a.J_hist + stg.J_off + (long long)tj * 2 * nf;
-                            if (c0 != c1) add_flux(gJ, nf, sg, c0, c1);
-                            if (DEPN)
-                                atomicAdd(&a.n_hist[stg.n_off + (long long)tout * 2 * a.n_e * stg.n_cells +
-                                                    (sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
-                        }
-                    } else {
-                        ++ty.spawn_drop;
-                        ty.q_drop += pk & 0xFFu;
-                    }
-                    ++g;
-                }
-            }
-            run += tot;
-        }
-        const unsigned long long kk = block_sum_u64(kept, s_r);
-        if (tid == 0 && kk) atomicAdd(&a.cnt[s].led[L_SPAWNED], kk);
-        if (tid == 0 && (a.flags & PIC_F_STRICT_CAPACITY) && run > room)
-            atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
-    };
-
-    // the general step for queue entries [q_lo, q_hi) of fast block f, all of
-    // stack s (whose tables are loaded)
-    auto work = [&](int s, int f, long long q_lo, long long q_hi) {
-        const DevStack &st = s_st;
-        const long long fpos0 = chunk_lo(T, f, Gf) * TILE;
-        const long long sbase = st.base - s_tpref[s] * TILE;     // position -> slot
-        const bool room0 = (st.cap - s_nsl[s]) <= 0;
-        int nsp = 0;
-#pragma unroll 1
-        for (long long q = q_lo + tid; q < q_hi; q += TPB) {
-            const float4 rec = a.qrec[fpos0 + q];
-            float z = rec.x, mu = rec.y;
-            uint32_t pk = __float_as_uint(rec.z);
-            const long long vpos = fpos0 + __float_as_uint(rec.w);
-            const long long gslot = sbase + vpos;
-            const long long slot = vpos - s_tpref[s] * TILE;       // slot within the stack
-            const uint32_t id_lo = a.id[cur][gslot];
-            int k = (int)(pk & 0xFFu);
-            const float mu_in = mu;
-            const uint32_t pk_in = pk;
-            const int sg = (int)((pk >> 8) & 1u);
-            int layer = (int)((pk >> 9) & 0xFu);
-            const uint32_t ctr_y = (pk >> 21) | S.ctr_hi;
-            TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
-            float lo = S.edge[layer], hi = S.edge[layer + 1];
-            const int c_start = cell_of(a, S, z);
-            flight<DET>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y, SUB_IF, ty);
-            // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes):
-            // the slot group's test word, then the carrier's event words
-            const uint4 xg = philox_rk(make_uint4((uint32_t)(slot >> 2), S.ctr_hi, a.step,
-                                                  SUB_TEST), a);
-            const uint32_t xs = (slot & 3) == 0 ? xg.x : (slot & 3) == 1 ? xg.y
-                              : (slot & 3) == 2 ? xg.z : xg.w;
-            bool dead = false;
-            if (xs < e.P) {
-                const uint4 x = philox_rk(make_uint4(id_lo, ctr_y, a.step, SUB_SCAT), a);
-                const bool inel = x.y < e.Q;
-                if (k == 1 && (inel || (a.flags & PIC_F_LOWEST_BIN_ANY))) {
-                    dead = true;
-                    ++ty.absorbed;
-                    ++ty.bath;
-                } else {
-                    mu = mu_of(x.z);
-                    if (inel) {
-                        const int kp = 1 + (int)__umulhi(x.w, (uint32_t)(k - 1));
-                        const int ks = k - kp;
-                        k = kp;
-                        e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
-                        if (a.flags & PIC_F_NO_SECONDARIES) {
-                            ty.bath += (uint32_t)ks;
-                        } else if (room0) {
-                            ++ty.spawn_drop;
-                            ty.q_drop += (uint32_t)ks;
-                            if (a.flags & PIC_F_STRICT_CAPACITY)
-                                atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
-                        } else {
-                            // secondary: same place, spin from P0, isotropic
-                            const uint4 y = philox_rk(make_uint4(id_lo, ctr_y, a.step, SUB_SEC), a);
-                            const uint32_t g0 = (pk >> 13) & 0xFFu;
-                            const int sgs = y.x < S.p0[layer] ? 0 : 1;
-                            const uint32_t gen = g0 < 255u ? g0 + 1u : 255u;
-                            float zs = z, mus = mu_of(y.y), los = lo, his = hi;
-                            int ls = layer;
-                            TabEnt es = S.ent[(ls * 2 + sgs) * S.n_e + (ks - 1)];
-                            Tally ts{};
-                            flight<DET>(a, S, zs, mus, ls, es, los, his, sgs, ks, half, id_lo,
-                                        ctr_y, SUB_SIF, ts);
-                            // the secondary's boundary events ride in the (not yet
-                            // used) id_hi bits until it is placed
-                            const uint32_t pks = (uint32_t)ks | ((uint32_t)sgs << 8) |
-                                                 ((uint32_t)ls << 9) | (gen << 13) |
-                                                 (ts.hits << 21) | (ts.trans << 25) |
-                                                 (ts.trunc << 29);
-                            a.stage[vpos] = make_float4(zs, mus, __uint_as_float(pks), z);
-                            atomicOr(&a.spawn_bits[vpos >> 5], 1u << (vpos & 31));
-                            ++nsp;
-                        }
-                    }
-                }
-            }
-            if (dead) {
-                pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
-                const int c_end = cell_of(a, S, z);
-                if (c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
-            } else {
-                flight<DET>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
-                            SUB_IF + 16, ty);
-                const int c_end = cell_of(a, S, z);
-                if (c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
-                pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
-                if (DEPN) atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
-            }
-            Z[gslot] = z;
-            if (__float_as_uint(mu) != __float_as_uint(mu_in) || pk != pk_in) {
-                ++ty.changed;
-                MU[gslot] = mu;
-                PK[gslot] = pk;
-            }
-        }
-        if (nsp) atomicAdd(&s_nspawn, nsp);
-    };
-
-    // first entry of fast block f's queue (ascending by tile) with tile >=
-    // tb: the block counts the entries below tb (one pass, all threads)
-    auto lower = [&](int f, long long tb) -> long long {
-        const long long ft0 = chunk_lo(T, f, Gf), fpos0 = ft0 * TILE;
-        const long long n = a.qcnt[f];
-        unsigned long long below = 0;
-        for (long long q = tid; q < n; q += TPB)
-            below += (ft0 + __float_as_uint(a.qrec[fpos0 + q].w) / TILE < tb) ? 1u : 0u;
-        const unsigned long long tot = block_sum_u64(below, s_r);
-        if (tid == 0) s_prefix = (long long)tot;
-        __syncthreads();
-        const long long r = s_prefix;
-        __syncthreads();
-        return r;
-    };
-
-    int staged_stack = -1;
-    long long staged_t0 = 0, staged_t1 = 0, staged_count = 0;
-    bool have_last = false, last_staged = false;
-    int last_stack = -1;
-    long long last_t0 = 0, last_count = 0;
-    if (t0 < t1) {
-        const int s_first = stack_of(s_tpref, a.n_stacks, t0);
-        const int s_last = stack_of(s_tpref, a.n_stacks, t1 - 1);
-        for (int s = s_first; s <= s_last; ++s) {
-            const long long sg0 = s_tpref[s] > t0 ? s_tpref[s] : t0;
-            const long long sg1 = s_tpref[s + 1] < t1 ? s_tpref[s + 1] : t1;
-            if (sg0 >= sg1) continue;               // a stack with no tiles
-            load_stack(a, s, S, &s_st, s_ent, s_T, s_edge, s_p0);
-            for (int q = tid; q < 2 * (s_st.n_cells + 1); q += TPB) s_J[q] = 0;
-            if (DEPN)
-                for (int q = tid; q < 2 * a.n_e * s_st.n_cells; q += TPB) s_n[q] = 0u;
-            if (tid == 0) s_nspawn = 0;
-            __syncthreads();
-            for (int f = fb0; f < fb1; ++f) {
-                // the queue entries of stack s (the whole queue when the chunk
-                // lies in one stack)
-                long long q_lo = 0, q_hi = a.qcnt[f];
-                if (s_first != s_last) {
-                    q_lo = lower(f, sg0);
-                    q_hi = lower(f, sg1);
-                }
-                if (q_lo < q_hi) work(s, f, q_lo, q_hi);
-            }
-            __syncthreads();
-            const long long cnt = s_nspawn;
-            const bool inside = sg0 > s_tpref[s];   // segment starts inside its stack
-            if (s < s_last) {
-                // a segment that ends its stack inside the chunk
-                if (!inside) {
-                    if (cnt) place(s, sg0, sg1, 0, true);
-                    if (tid == 0) a.cnt[s].spawn_total = (unsigned long long)cnt;
-                } else {
-                    staged_stack = s; staged_t0 = sg0; staged_t1 = sg1; staged_count = cnt;
-                }
-                flush_segment(s);
-            } else {
-                have_last = true; last_staged = inside; last_stack = s;
-                last_t0 = sg0; last_count = cnt;
-            }
-        }
-    }
-
-    // close the last segment and publish its count of secondaries
-    if (have_last) {
-        const long long cnt = last_count;
-        const bool ends_stack = s_tpref[last_stack + 1] == t1;
-        if (!last_staged) {
-            if (tid == 0) publish(&a.status[b], ep, FLAG_P, cnt);
-            if (cnt) place(last_stack, last_t0, t1, 0, true);
-            if (ends_stack && tid == 0) a.cnt[last_stack].spawn_total = (unsigned long long)cnt;
-            flush_segment(last_stack);
-        } else {
-            if (tid == 0) {
-                publish(&a.status[b], ep, FLAG_A, cnt);
-                s_prefix = look_back_slow(a, ep, T, s_tpref[last_stack], b, Gs, Gf);
-                publish(&a.status[b], ep, FLAG_P, s_prefix + cnt);
-            }
-            __syncthreads();
-            const long long pre = s_prefix;
-            if (cnt) place(last_stack, last_t0, t1, pre, true);
-            if (ends_stack && tid == 0)
-                a.cnt[last_stack].spawn_total = (unsigned long long)(pre + cnt);
-            flush_segment(last_stack);
-        }
-        // an earlier segment (block spanning stacks) that waited for its prefix
-        if (staged_stack >= 0) {
-            __syncthreads();
-            if (tid == 0) s_prefix = look_back_slow(a, ep, T, s_tpref[staged_stack], b, Gs, Gf);
-            __syncthreads();
-            const long long pre = s_prefix;
-            if (staged_count) place(staged_stack, staged_t0, staged_t1, pre, false);
-            if (tid == 0)
-                a.cnt[staged_stack].spawn_total = (unsigned long long)(pre + staged_count);
-            unsigned long long *L = a.cnt[staged_stack].led;
-            const uint32_t vals[5] = {ty.hits, ty.trans, ty.trunc, ty.spawn_drop, ty.q_drop};
-            const int idx[5] = {L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED, L_SPAWN_DROPPED,
-                                L_Q_DROPPED};
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const unsigned long long v = block_sum_u64(vals[q], s_r);
-                if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
-            }
-            ty = Tally{};
-        }
-    }
-
-    if (last_block(a, &s_flag)) {
-        for (int s = tid; s < a.n_stacks; s += TPB) {
-            if (s_tpref[s + 1] == s_tpref[s]) continue;
-            DevCounters &c = a.cnt[s];
-            const long long room = a.stacks[s].cap - (long long)c.n_slots;
-            const long long tot = (long long)c.spawn_total;
-            const long long kept = tot < room ? tot : (room > 0 ? room : 0);
-            c.n_slots += (unsigned long long)kept;
-            c.next_id += (unsigned long long)kept;
-            c.spawn_total = 0;
-        }
-        if (tid == 0) {
-            a.ctl->done = 0u;
-            a.ctl->epoch = ep + 1u;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_inject: Source(dt/2) for half step h = 2*step + half (Eq. Strang-source)
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int deposit)
-{
-    __shared__ long long s_pref[PIC_MAX_STACKS + 1];
-    __shared__ long long s_n[PIC_MAX_STACKS];
-    __shared__ unsigned long long s_q[PIC_MAX_STACKS];
-    __shared__ int s_flag;
-    const int tid = threadIdx.x;
-    const long long h = 2 * (long long)a.step + half;
-    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
-    for (int s = tid; s < a.n_stacks; s += TPB) {
-        const DevStack &st = a.stacks[s];
-        const long long n = a.inj[st.inj_off + h];
-        const long long room = st.cap - (long long)a.cnt[s].n_slots;
-        s_n[s] = n < room ? n : (room > 0 ? room : 0);
-        s_q[s] = 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        long long acc = 0;
-        for (int s = 0; s < a.n_stacks; ++s) { s_pref[s] = acc; acc += s_n[s]; }
-        s_pref[a.n_stacks] = acc;
-    }
-    __syncthreads();
-    const long long total = s_pref[a.n_stacks];
-    const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
-    for (long long gidx = (long long)blockIdx.x * TPB + tid; gidx < total;
-         gidx += (long long)gridDim.x * TPB) {
-        const int s = stack_of(s_pref, a.n_stacks, gidx);
-        const long long j = gidx - s_pref[s];
-        const DevStack &st = a.stacks[s];
-        const unsigned long long id = a.cnt[s].next_id + (unsigned long long)j;
-        const uint32_t cy = (uint32_t)(id >> 32) | ((uint32_t)s << 16);
-        const uint4 r0 = philox_rk(make_uint4((uint32_t)id, cy, a.step, SUB_INJ + 0), a);
-        const uint4 r1 = philox_rk(make_uint4((uint32_t)id, cy, a.step, SUB_INJ + 1), a);
-        int i = 0;
-        const uint32_t *thr = a.cdf_thr + st.cdf_off;
-        while (i < st.n_cdf - 1 && !(r0.x < thr[i])) ++i;
-        const int cell = a.cdf_cell[st.cdf_off + i];
-        const float z = __fmul_rn(__fadd_rn((float)cell, unit_of(r0.y)), a.dz);
-        const uint32_t sg = r0.z < st.up_thr ? 0u : 1u;
-        const uint32_t k = st.e_mode == 1 ? (uint32_t)(sg ? st.k_mono1 : st.k_mono0)
-                                          : 1u + __umulhi(r0.w, (uint32_t)a.n_e);
-        const uint32_t layer = (uint32_t)a.cdf_layer[st.cdf_off + i];
-        const long long d = st.base + (long long)a.cnt[s].n_slots + j;
-        a.z[cur][d] = z;
-        a.mu[cur][d] = mu_of(r1.x);
-        a.id[cur][d] = (uint32_t)id;
-        a.pk[cur][d] = k | (sg << 8) | (layer << 9) | (1u << 13) | ((uint32_t)(id >> 32) << 21);
-        atomicAdd(&s_q[s], (unsigned long long)k);
-        if (deposit) {
-            Stk tmp; tmp.n_cells = st.n_cells;
-            const int c = cell_of(a, tmp, z);
-            atomicAdd(&a.n_hist[st.n_off + (long long)tout * 2 * a.n_e * st.n_cells +
-                                (sg * a.n_e + (k - 1)) * st.n_cells + c], 1u);
-        }
-    }
-    __syncthreads();
-    for (int s = tid; s < a.n_stacks; s += TPB)
-        if (s_q[s]) atomicAdd(&a.cnt[s].led[L_Q_INJECTED], s_q[s]);
-    if (last_block(a, &s_flag)) {
-        for (int s = tid; s < a.n_stacks; s += TPB) {
-            const DevStack &st = a.stacks[s];
-            const long long n = a.inj[st.inj_off + h];
-            DevCounters &c = a.cnt[s];
-            const long long kept = s_n[s];
-            c.n_slots += (unsigned long long)kept;
-            c.next_id += (unsigned long long)kept;
-            c.led[L_INJECTED] += (unsigned long long)kept;
-            c.led[L_INJECT_DROPPED] += (unsigned long long)(n - kept);
-            if (n > kept && (a.flags & PIC_F_STRICT_CAPACITY))
-                atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
-        }
-        if (tid == 0) a.ctl->done = 0u;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// k_compact: stable removal of dead slots (k = 0) into the other buffer
-// ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(TPB) k_compact(const Args a)
-{
-    __shared__ long long s_tpref[PIC_MAX_STACKS + 1];
-    __shared__ long long s_nsl[PIC_MAX_STACKS];
-    __shared__ int s_w[TPB / 32];
-    __shared__ long long s_prefix;
-    __shared__ int s_flag;
-    const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
-    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur, nxt = cur ^ 1;
-    const int b = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
-    Plan p;
-    make_plan(a, s_tpref, s_nsl, p);
-
-    auto alive4 = [&](int s, long long t, uint32_t &mask) {
-        const DevStack &st = a.stacks[s];
-        const long long nsl = s_nsl[s];
-        const long long slot0 = (t - s_tpref[s]) * TILE + (long long)tid * VEC;
-        mask = 0;
-        if (slot0 < nsl) {
-            const uint4 p4 = *reinterpret_cast<const uint4 *>(a.pk[cur] + st.base + slot0);
-            const uint32_t *pp = &p4.x;
-#pragma unroll
-            for (int j = 0; j < VEC; ++j)
-                if (slot0 + j < nsl && (pp[j] & 0xFFu)) mask |= 1u << j;
-        }
-    };
-
-    if (p.t0 < p.t1) {
-        const int s_first = stack_of(s_tpref, a.n_stacks, p.t0);
-        const int s_last = stack_of(s_tpref, a.n_stacks, p.t1 - 1);
-        const bool first_inside = p.t0 > s_tpref[s_first];
-        // phase 1: count the first segment (if it needs the look-back) and the
-        // last segment (its count is what later blocks need)
-        long long c_first = 0, c_last = 0;
-        for (long long t = p.t0; t < p.t1; ++t) {
-            const int s = stack_of(s_tpref, a.n_stacks, t);
-            const bool need = (s == s_first && first_inside) || s == s_last;
-            if (!need) { t = s_tpref[s + 1] - 1; continue; }
-            uint32_t m;
-            alive4(s, t, m);
-            int excl;
-            const int tot = block_scan(__popc(m), excl, s_w);
-            if (s == s_first) c_first += tot;
-            if (s == s_last) c_last += tot;
-        }
-        long long pre_first = 0;
-        if (tid == 0) {
-            if (s_last == s_first && first_inside) {
-                publish(&a.status[b], ep, FLAG_A, c_last);
-                s_prefix = look_back(a, ep, p.T, s_tpref[s_first], b, G);
-                publish(&a.status[b], ep, FLAG_P, s_prefix + c_last);
-            } else {
-                publish(&a.status[b], ep, FLAG_P, c_last);
-                s_prefix = first_inside ? look_back(a, ep, p.T, s_tpref[s_first], b, G) : 0;
-            }
-        }
-        __syncthreads();
-        pre_first = s_prefix;
-        (void)c_first;
-        // phase 2: scatter live slots, stable, into the other buffer
-        int seg = -1;
-        long long run = 0;
-        for (long long t = p.t0; t < p.t1; ++t) {
-            const int s = stack_of(s_tpref, a.n_stacks, t);
-            if (s != seg) {
-                if (seg >= 0 && s_tpref[seg + 1] <= p.t1 && tid == 0)
-                    a.cnt[seg].alive_total = (unsigned long long)run;
-                seg = s;
-                run = (s == s_first) ? pre_first : 0;
-            }
-            uint32_t m;
-            alive4(s, t, m);
-            int excl;
-            const int tot = block_scan(__popc(m), excl, s_w);
-            if (m) {
-                const DevStack &st = a.stacks[s];
-                const long long src = st.base + (t - s_tpref[s]) * TILE + (long long)tid * VEC;
-                long long d = st.base + run + excl;
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) {
-                    if (!((m >> j) & 1u)) continue;
-                    a.z[nxt][d] = a.z[cur][src + j];
-                    a.mu[nxt][d] = a.mu[cur][src + j];
-                    a.id[nxt][d] = a.id[cur][src + j];
-                    a.pk[nxt][d] = a.pk[cur][src + j];
-                    ++d;
-                }
-            }
-            run += tot;
-        }
-        if (seg >= 0 && s_tpref[seg + 1] <= p.t1 && tid == 0)
-            a.cnt[seg].alive_total = (unsigned long long)run;
-    }
-
-    if (last_block(a, &s_flag)) {
-        for (int s = tid; s < a.n_stacks; s += TPB) {
-            DevCounters &c = a.cnt[s];
-            c.n_slots = (s_tpref[s + 1] == s_tpref[s]) ? 0ull : c.alive_total;
-            c.alive_total = 0;
-        }
-        if (tid == 0) {
-            a.ctl->cur = (unsigned int)nxt;
-            a.ctl->done = 0u;
-            a.ctl->epoch = ep + 1u;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-// Occupancy of a kernel with `smem` bytes of dynamic shared memory; the
-// largest dynamic shared memory the device offers is allowed, so that
-// contexts with different moment grids never lower each other's cap.
-template <class K>
-static cudaError_t occupancy(K kernel, size_t smem, int *blocks, int threads = TPB)
-{
-    int dev = 0, optin = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess)
-        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa{};
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
-    if (e != cudaSuccess) return e;
-    const int cap = optin - (int)fa.sharedSizeBytes;
-    *blocks = 0;
-    if ((int)smem > cap) return cudaSuccess;       // does not fit: zero blocks
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, cap);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, threads, smem);
-}
-
-// Ring depth of k_fast for one variant, both builds (with and without fused
-// multiply-add) fitting: the most resident blocks per SM (warps to hide the
-// arithmetic latency) such that at least three tiles per SM are in flight
-// (blocks x (stages - 1) >= 3, about 48 KB), then the deepest ring.
-template <bool DEPN, bool WAGG>
-static cudaError_t pick_ring(size_t fixed, int blocks_per_sm, int ring_req, int *ring, int *blocks,
-                             size_t *smem)
-{
-    int best = -1;
-    for (int r = 2; r <= MAX_RING; ++r) {
-        if (ring_req > 0 && r != ring_req) continue;
-        const size_t sm = fixed + (size_t)r * 3 * TILE_BYTES;
-        int o1 = 0, o2 = 0;
-        cudaError_t e = occupancy(k_fast<false, DEPN, WAGG>, sm, &o1, FAST_THREADS);
-        if (e == cudaSuccess) e = occupancy(k_fast<true, DEPN, WAGG>, sm, &o2, FAST_THREADS);
-        if (e != cudaSuccess) return e;
-        int o = o1 < o2 ? o1 : o2;
-        if (blocks_per_sm > 0 && o > blocks_per_sm) o = blocks_per_sm;
-        if (o < 1) continue;
-        const int enough = o * (r - 1) >= 3 ? 1 : 0;
-        const int score = enough * 10000 + o * 100 + r;
-        if (score > best) { best = score; *ring = r; *blocks = o; *smem = sm; }
-    }
-    return best < 0 ? cudaErrorInvalidConfiguration : cudaSuccess;
-}
-
-template <bool DEPN>
-static cudaError_t slow_cfg(size_t sm, int *grid, int sms)
-{
-    int o1 = 0, o2 = 0;
-    cudaError_t e = occupancy(k_slow<false, DEPN>, sm, &o1);
-    if (e == cudaSuccess) e = occupancy(k_slow<true, DEPN>, sm, &o2);
-    if (e != cudaSuccess) return e;
-    const int o = o1 < o2 ? o1 : o2;
-    if (o < 1) return cudaErrorInvalidConfiguration;
-    *grid = sms * o;
-    return cudaSuccess;
-}
-
 cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_mode, LaunchCfg *cfg)
 {
     int dev = 0, sms = 0;
@@ -1352,7 +39,7 @@ cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_m
     if ((e = slow_cfg<false>(cfg->smem_slow, &cfg->grid_slow, sms)) != cudaSuccess) return e;
     if ((e = slow_cfg<true>(cfg->smem_slow_dep, &cfg->grid_slow_dep, sms)) != cudaSuccess) return e;
     int oc = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_compact, TPB, 0)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_compact<0>, TPB, 0)) != cudaSuccess)
         return e;
     cfg->grid_compact = sms * (oc > 0 ? oc : 1);
     cfg->grid_inject = sms * 4;
@@ -1404,13 +91,13 @@ cudaError_t launch_slow(const Args &a0, const LaunchCfg &c, bool det, bool dep, 
 cudaError_t launch_inject(const Args &a, const LaunchCfg &c, int half, bool deposit,
                           cudaStream_t s)
 {
-    k_inject<<<c.grid_inject, TPB, 0, s>>>(a, half, deposit ? 1 : 0);
+    k_inject<0><<<c.grid_inject, TPB, 0, s>>>(a, half, deposit ? 1 : 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s)
 {
-    k_compact<<<c.grid_compact, TPB, 0, s>>>(a);
+    k_compact<0><<<c.grid_compact, TPB, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -369,3 +369,108 @@ class Context:
     @property
     def launches(self):
         return pic_launch_count(self.ctx)
+
+    # ---- adjoint ----
+    @property
+    def n_mat_max(self):
+        return max(t.c.n_mat for t in self._tabs)
+
+    @property
+    def n_cells_max(self):
+        return max(self.shape(s)[0] for s in range(len(self.wl.stacks)))
+
+    def grad(self, grad_n=None, grad_J=None):
+        """Score-function gradient of sum(grad_n * n) + sum(grad_J * J) over the
+        steps run so far, with respect to tau_in [stack][mat][spin][k] and T
+        [stack][interface][dir][spin][k] (float64 tensors on the device).
+
+        grad_n: float [stacks][n_out][2][n_e][n_cells_max]; grad_J: float
+        [stacks][n_out][2][n_cells_max+1] (device tensors, None = zero)."""
+        torch = self.torch
+        S, ne = len(self.wl.stacks), self.wl.n_e
+        _, n_out, _ = self.shape(0)
+        ncm = self.n_cells_max
+        dev = torch.device("cuda", torch.cuda.current_device())
+        if grad_n is not None:
+            grad_n = grad_n.to(dev, torch.float32).contiguous()
+            assert grad_n.shape == (S, n_out, 2, ne, ncm), grad_n.shape
+        if grad_J is not None:
+            grad_J = grad_J.to(dev, torch.float32).contiguous()
+            assert grad_J.shape == (S, n_out, 2, ncm + 1), grad_J.shape
+        g_tau = torch.empty((S, self.n_mat_max, 2, ne), dtype=torch.float64, device=dev)
+        g_T = torch.empty((S, MAX_LAYERS - 1, 2, 2, ne), dtype=torch.float64, device=dev)
+        pic_grad(self.ctx, grad_n.data_ptr() if grad_n is not None else None,
+                 grad_J.data_ptr() if grad_J is not None else None,
+                 g_tau.data_ptr(), g_T.data_ptr())
+        return g_tau, g_T
+
+    def moments_all(self):
+        """Densities and fluxes of every stack, padded to the widest stack:
+        n [stacks][n_out][2][n_e][n_cells_max], J [stacks][n_out][2][n_cells_max+1]
+        (float32), the layouts grad() takes."""
+        torch = self.torch
+        S, ne = len(self.wl.stacks), self.wl.n_e
+        ncm = self.n_cells_max
+        _, n_out, _ = self.shape(0)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        n_all = torch.zeros((S, n_out, 2, ne, ncm), dtype=torch.float32, device=dev)
+        J_all = torch.zeros((S, n_out, 2, ncm + 1), dtype=torch.float32, device=dev)
+        for s in range(S):
+            n, J, _ = self.moments(s)
+            nc = n.shape[-1]
+            n_all[s, ..., :nc] = n.to(torch.float32)
+            J_all[s, ..., : nc + 1] = J.to(torch.float32)
+        return n_all, J_all
+
+
+class PicTransport:
+    """The PIC run as a differentiable function of the tables (torch autograd).
+
+    ``PicTransport.apply(tau_in, T, wl, n_steps)`` builds a context for the
+    workload with these lifetime ([stack][mat][2][n_e]) and transmittance
+    ([stack][n_layers-1][2][2][n_e]) tables, runs n_steps and returns the
+    densities and fluxes (padded layouts of Context.moments_all).  The
+    backward pass is the library's adjoint (pic_grad): a score-function
+    estimate of d E[moments] / d tables, contracted with the incoming
+    gradients."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, tau_in, T, wl, n_steps, **ctx_kw):
+        if cls._fn is None:
+            import torch
+
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, tau_in, T, wl, n_steps, ctx_kw):
+                    import copy
+                    w = copy.deepcopy(wl)
+                    ti = tau_in.detach().cpu().numpy()
+                    Tt = T.detach().cpu().numpy()
+                    for s, st in enumerate(w.stacks):
+                        st.tau_in = ti[s, : st.tau_in.shape[0]].copy()
+                        nif = len(st.layer_cells) - 1
+                        st.T = Tt[s, :nif].copy()
+                    c = Context(w, **ctx_kw)
+                    c.step(n_steps)
+                    n_all, J_all = c.moments_all()
+                    fctx.pic = c
+                    fctx.shapes = (tau_in.shape, T.shape)
+                    fctx.devs = (tau_in.device, T.device)
+                    return n_all, J_all
+
+                @staticmethod
+                def backward(fctx, g_n, g_J):
+                    c = fctx.pic
+                    g_tau, g_T = c.grad(g_n, g_J)
+                    sh_tau, sh_T = fctx.shapes
+                    gt = torch.zeros(sh_tau, dtype=torch.float64, device=g_tau.device)
+                    gt[:, : g_tau.shape[1]] = g_tau[:, : sh_tau[1]]
+                    gT = torch.zeros(sh_T, dtype=torch.float64, device=g_T.device)
+                    gT[:, : sh_T[1]] = g_T[:, : sh_T[1]]
+                    c.close()
+                    return gt.to(fctx.devs[0]), gT.to(fctx.devs[1]), None, None, None
+
+            cls._fn = _Fn
+        return cls._fn.apply(tau_in, T, wl, n_steps, ctx_kw)

@@ -1,0 +1,253 @@
+"""GPU adjoint (pic_grad) against the oracle's two-pass gradient.
+
+Deterministic build: the replay runs the forward trajectories bit for bit,
+so the gradient differs from the oracle's only by the order of the double
+sums: |g_gpu - g_oracle| <= 1e-9 (mag + 1), mag = the oracle's sum of
+|score| (|total| + |earned|) per entry.  Fast build: the per-sample survival
+identity (P1') and the closed form.
+"""
+import copy
+import math
+
+import numpy as np
+import pytest
+
+from oracle.oracle import OracleSim, REC_DTYPE, pack
+from paper_1807_04733_gb300 import pic
+from paper_1807_04733_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DET = W.FLAG_DETERMINISTIC
+TOL = 1e-9
+
+
+def random_weights(ctx, seed, density=1.0):
+    """Seeded density and flux weights in the padded layouts of Context.grad."""
+    S, ne = len(ctx.wl.stacks), ctx.wl.n_e
+    ncm = ctx.n_cells_max
+    _, n_out, _ = ctx.shape(0)
+    rng = np.random.default_rng(seed)
+    gn = rng.uniform(-1, 1, (S, n_out, 2, ne, ncm)).astype(np.float32)
+    gJ = rng.uniform(-1, 1, (S, n_out, 2, ncm + 1)).astype(np.float32)
+    if density < 1.0:
+        gn *= rng.uniform(0, 1, gn.shape) < density
+        gJ *= rng.uniform(0, 1, gJ.shape) < density
+    return gn, gJ
+
+
+def check_against_oracle(ctx, wl, gn, gJ, stacks=None, init=None):
+    g_tau, g_T = ctx.grad(torch.from_numpy(gn).cuda(), torch.from_numpy(gJ).cuda())
+    g_tau, g_T = g_tau.cpu().numpy(), g_T.cpu().numpy()
+    _, _, steps = ctx.shape(0)
+    for s in (range(len(wl.stacks)) if stacks is None else stacks):
+        ref = OracleSim(wl, stack=s)
+        if init is not None and s in init:
+            ref.set_records(*init[s])
+        nc = ref.n_cells
+        r_tau, r_T, m_tau, m_T = ref.grad(gn[s, :, :, :, :nc], gJ[s, :, :, : nc + 1], steps)
+        nm = r_tau.shape[0]
+        assert np.all(np.abs(g_tau[s, :nm] - r_tau) <= TOL * (m_tau + 1)), (s, g_tau[s, :nm], r_tau)
+        assert not g_tau[s, nm:].any()
+        nif = r_T.shape[0]
+        assert np.all(np.abs(g_T[s, :nif] - r_T) <= TOL * (m_T + 1)), (s, g_T[s, :nif], r_T)
+        assert not g_T[s, nif:].any()
+        assert np.abs(r_tau).max() > 0
+    return g_tau, g_T
+
+
+@pytest.mark.parametrize("rep", range(2))
+def test_det_grad_bilayer_pulse(rep):
+    wl = W.config(0, scale=0.02, flags=DET, seed=rep).replace(n_steps=160)
+    ctx = pic.Context(wl)
+    ctx.step(160)
+    gn, gJ = random_weights(ctx, 10 + rep)
+    check_against_oracle(ctx, wl, gn, gJ)
+    # a second call gives the same result (the replay leaves the forward state)
+    a1 = ctx.grad(torch.from_numpy(gn).cuda(), torch.from_numpy(gJ).cuda())
+    ctx.step(0)
+    n, J, led = ctx.moments(0)
+    ref = OracleSim(wl)
+    ref.step(160)
+    rn, rJ, rled = ref.moments()
+    assert led == rled and np.array_equal(J.cpu().numpy(), rJ)
+    ctx.close()
+
+
+def test_det_grad_through_capacity_and_compaction():
+    """Secondaries dropped at capacity, compaction, moments every 3 steps, a
+    stopped run (fewer steps than n_steps_max), sparse weights."""
+    wl = W.spin_valve(True, n0=20_000, capacity=40_000, n_steps=400, flags=DET,
+                      moment_every=3, compact_every=7)
+    ctx = pic.Context(wl)
+    ctx.step(250)
+    _, _, led = ctx.moments(0)
+    assert led["spawn_dropped"] > 0
+    gn, gJ = random_weights(ctx, 3, density=0.1)
+    check_against_oracle(ctx, wl, gn, gJ)
+    ctx.close()
+
+
+def test_det_grad_batched_stacks():
+    wl = W.batched(n_stacks=5, scale=2e-3, n_steps=150, flags=DET)
+    ctx = pic.Context(wl)
+    ctx.step(150)
+    gn, gJ = random_weights(ctx, 4)
+    check_against_oracle(ctx, wl, gn, gJ)
+    ctx.close()
+
+
+def test_det_grad_loaded_records_many_tiles():
+    """1.2M loaded carriers (hundreds of tiles, every block a multi-tile
+    chunk), fast scattering so that every tile spawns, ragged count."""
+    N = 1_200_003
+    wl = W.bilayer(n0=0, capacity=3_000_000, n_steps=12, flags=DET, compact_every=5,
+                   moment_every=2)
+    wl.stacks[0].tau_in *= 0.2
+    rng = np.random.default_rng(21)
+    r = np.zeros(N, REC_DTYPE)
+    r["z"] = rng.uniform(0, 115, N).astype(np.float32)
+    r["mu"] = rng.uniform(-1, 1, N).astype(np.float32)
+    r["id"] = np.arange(N, dtype=np.uint32)
+    k = rng.integers(1, 31, N)
+    r["packed"] = pack(k, rng.integers(0, 2, N), (r["z"] >= 15).astype(np.uint32), 1)
+    ctx = pic.Context(wl)
+    ctx.set_records(r, N)
+    ctx.step(12)
+    gn, gJ = random_weights(ctx, 5)
+    check_against_oracle(ctx, wl, gn, gJ, init={0: (r, N)})
+    ctx.close()
+
+
+@pytest.mark.parametrize("flags", [W.FLAG_NO_SECONDARIES, W.FLAG_TRANSPARENT,
+                                   W.FLAG_LOWEST_BIN_ANY])
+def test_det_grad_variants(flags):
+    wl = W.config(0, scale=0.01, flags=DET | flags).replace(n_steps=120)
+    ctx = pic.Context(wl)
+    ctx.step(120)
+    gn, gJ = random_weights(ctx, 6)
+    _, g_T = check_against_oracle(ctx, wl, gn, gJ)
+    if flags == W.FLAG_TRANSPARENT:
+        assert not g_T.any()
+    ctx.close()
+
+
+def test_fast_build_survival_identity():
+    """Default (fused multiply-add) build, 1e6 carriers: the per-sample P1'
+    identity grad = n dt/tau^2 N_live(n) and the closed form within 4 SE."""
+    N, tau, n, dt = 1_000_000, 30.0, 20, 1.0
+    wl = W.infinite_slab(n_e=4, dt=dt, cells=200, capacity=N, n_steps=n, moment_every=1,
+                         compact_every=1000, seed=0, flags=0, mat=W.MAT_AU)
+    st = wl.stacks[0]
+    st.tau_in[:] = tau
+    st.tau_el[:] = math.inf
+    r = np.zeros(N, REC_DTYPE)
+    rng = np.random.default_rng(1)
+    r["z"] = rng.uniform(0, 200, N).astype(np.float32)
+    r["mu"] = rng.uniform(-1, 1, N).astype(np.float32)
+    r["id"] = np.arange(N, dtype=np.uint32)
+    r["packed"] = pack(1, 0, 0, 1)
+    ctx = pic.Context(wl)
+    ctx.set_records(r, N)
+    ctx.step(n)
+    n_all, _ = ctx.moments_all()
+    alive = int(n_all[0, n - 1].sum().item())
+    gn = torch.zeros_like(n_all)
+    gn[0, n - 1] = 1.0
+    g_tau, g_T = ctx.grad(gn, None)
+    c = dt / tau ** 2
+    got = g_tau[0, W.MAT_AU, 0, 0].item()
+    assert got == pytest.approx(n * c * alive, rel=1e-9)
+    g_tau[0, W.MAT_AU, 0, 0] = 0
+    assert not g_tau.any() and not g_T.any()
+    surv = math.exp(-dt / tau) ** n
+    se = n * c * math.sqrt(N * surv * (1 - surv))
+    assert abs(got - N * n * c * math.exp(-n * dt / tau)) <= 4 * se
+    ctx.close()
+
+
+def test_grad_refused_after_records_replaced():
+    wl = W.config(0, scale=0.01, flags=DET).replace(n_steps=40)
+    ctx = pic.Context(wl)
+    ctx.step(10)
+    ctx.set_records(ctx.records(0), 10 ** 6)
+    ctx.step(5)
+    with pytest.raises(pic.PicError) as e:
+        ctx.grad(None, None)
+    assert e.value.status == 6
+    ctx.close()
+
+
+def test_autograd_function_backward_matches_grad():
+    wl = W.config(0, scale=0.01, flags=DET).replace(n_steps=80)
+    st = wl.stacks[0]
+    tau = torch.tensor(st.tau_in[None], dtype=torch.float64, requires_grad=True)
+    T = torch.tensor(st.T[None], dtype=torch.float64, requires_grad=True)
+    n_all, J_all = pic.PicTransport.apply(tau, T, wl, 80)
+    w_n = torch.rand_like(n_all)
+    w_J = torch.rand_like(J_all)
+    ((n_all * w_n).sum() + (J_all * w_J).sum()).backward()
+    ref = OracleSim(wl)
+    ref.step(80)
+    nc = ref.n_cells
+    r_tau, r_T, m_tau, m_T = ref.grad(w_n[0, ..., :nc].cpu().numpy(),
+                                      w_J[0, ..., : nc + 1].cpu().numpy())
+    assert np.all(np.abs(tau.grad[0].numpy() - r_tau) <= TOL * (m_tau + 1))
+    assert np.all(np.abs(T.grad[0].numpy() - r_T) <= TOL * (m_T + 1))
+
+
+def test_fast_build_finite_differences_common_random_numbers():
+    """Default build, Fe/Au bilayer with the pulse (2e5 carriers, capacity
+    raised so that nothing is dropped): central differences with the same
+    seed (the same Philox words) along tau_in and along T agree with the
+    adjoint's directional derivatives over 16 seeds within 3 SE."""
+    R, h = 16, 0.1
+    base = W.config(3, scale=0.02).replace(n_steps=300)
+    st0 = base.stacks[0]
+    st0.capacity = 40 * st0.n0
+
+    def O(wl, seed, ctx=None):
+        own = ctx is None
+        if own:
+            ctx = pic.Context(wl, seed=seed)
+            ctx.step(wl.n_steps)
+        n, J = ctx.moments_all()
+        val = float(n[0, :, 0, :, 90:100].sum() - n[0, :, 1, :, 90:100].sum()
+                    + J[0, :, 0, 15].sum() - J[0, :, 1, 15].sum())
+        if own:
+            ctx.close()
+        return val
+
+    d_tau, d_T = [], []
+    for rep in range(R):
+        ctx = pic.Context(base, seed=rep)
+        ctx.step(base.n_steps)
+        n, J = ctx.moments_all()
+        gn = torch.zeros_like(n)
+        gJ = torch.zeros_like(J)
+        gn[0, :, 0, :, 90:100] = 1.0
+        gn[0, :, 1, :, 90:100] = -1.0
+        gJ[0, :, 0, 15] = 1.0
+        gJ[0, :, 1, 15] = -1.0
+        g_tau, g_T = ctx.grad(gn, gJ)
+        _, _, led = ctx.moments(0)
+        assert led["spawn_dropped"] == 0
+        ctx.close()
+        g_tau, g_T = g_tau.cpu().numpy()[0], g_T.cpu().numpy()[0]
+        vals = []
+        for f in (1 + h, 1 - h):
+            wl = copy.deepcopy(base)
+            wl.stacks[0].tau_in = st0.tau_in * f
+            vals.append(O(wl, rep))
+        nm = st0.tau_in.shape[0]
+        d_tau.append((vals[0] - vals[1]) / (2 * h) - (g_tau[:nm] * st0.tau_in).sum())
+        vals = []
+        for f in (1 + h, 1 - h):
+            wl = copy.deepcopy(base)
+            wl.stacks[0].T = np.clip(st0.T * f, 0.0, 1.0)
+            vals.append(O(wl, rep))
+        nif = st0.T.shape[0]
+        d_T.append((vals[0] - vals[1]) / (2 * h) - (g_T[:nif] * st0.T).sum())
+    for d in (np.array(d_tau), np.array(d_T)):
+        assert abs(d.mean()) <= 3 * d.std(ddof=1) / math.sqrt(R), d
