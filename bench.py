@@ -299,25 +299,35 @@ def adjoint_leg(args):
     gJ[0, :, 1, 15] = -1.0
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     torch.cuda.synchronize()
+    pic.pic_profile(ctx.ctx, True)
     ev[0].record(stream)
     ctx.step(wl.n_steps)
     ev[1].record(stream)
     torch.cuda.synchronize()
     fwd_ms = ev[0].elapsed_time(ev[1])
+    kf = pic.pic_profile_read(ctx.ctx)
+    pic.pic_profile(ctx.ctx, False)
     led = ctx.ledger(0)
     times = []
-    for _ in range(2):          # the first call also allocates the replay buffers
+    for i in range(2):          # the first call also allocates the replay buffers
+        if i == 1:
+            pic.pic_profile(ctx.ctx, True)
         ev[2].record(stream)
         g_tau, g_T = ctx.grad(gn, gJ)
         ev[3].record(stream)
         torch.cuda.synchronize()
         times.append(ev[2].elapsed_time(ev[3]))
-    grad_ms = min(times)
+    kt = pic.pic_profile_read(ctx.ctx)
+    pic.pic_profile(ctx.ctx, False)
+    grad_ms = times[-1]
     out = {"workload": "fe15_au100 (1e7 carriers, capacity 5e7, 800 x 1 fs, densities every step)"
                        if args.adjoint_scale == 1.0 else "fe15_au100 scaled by %g" % args.adjoint_scale,
            "observable": "O1 + O2 (spin density, cells 90..99; spin flux, face 15)",
            "forward_ms": fwd_ms, "grad_ms": grad_ms, "grad_ms_first_call": times[0],
            "ratio": grad_ms / fwd_ms, "particle_steps": led["particle_steps"],
+           "forward_kernel_ms": {k: v[1] for k, v in kf.items() if not k.startswith("adjoint")},
+           "grad_kernel_ms": {k: v[1] for k, v in kt.items() if k.startswith("adjoint")},
+           "replay_launch_config": {k: v for k, v in ctx.launch_config().items() if "adj" in k},
            "grad_tau_abs_sum": float(g_tau.abs().sum()), "grad_T_abs_sum": float(g_T.abs().sum())}
     ctx.close()
     return out

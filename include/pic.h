@@ -91,6 +91,10 @@ typedef struct {
     int32_t grid_compact, grid_inject;
     int32_t ring_step, ring_step_moments;   /* bulk-copy ring depth (tiles) */
     int64_t smem_step, smem_step_moments;   /* dynamic shared memory, bytes */
+    /* pic_grad's replay passes 1 and 2 (zero before the first pic_grad):
+     * streaming pass with density weights, its ring depth and shared memory */
+    int32_t grid_adj_step[2], ring_adj_step[2];
+    int64_t smem_adj_step[2];
 } pic_launch_info;
 
 /* One laterally homogeneous layer stack (Sec. II: 1-D transport along z).
@@ -149,10 +153,13 @@ typedef struct {
 
 /* Device time of the library's kernels, per kind: 0 = source, 1 = step
  * (streaming pass), 2 = step with density deposit (streaming pass),
- * 3 = compaction, 4 = step (event pass and placement of secondaries). */
+ * 3 = compaction, 4 = step (event pass and placement of secondaries);
+ * pic_grad's replays: 5 = streaming pass, 6 = event pass, 7 = the rest
+ * (source, compaction, flux potential, flush, lineage totals). */
+#define PIC_KERNEL_KINDS 8
 typedef struct {
-    int64_t launches[5];
-    double ms[5];
+    int64_t launches[PIC_KERNEL_KINDS];
+    double ms[PIC_KERNEL_KINDS];
 } pic_kernel_times;
 
 /* One particle slot as returned by pic_records (16 bytes). */

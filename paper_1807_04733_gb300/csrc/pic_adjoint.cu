@@ -17,6 +17,11 @@
 //   pass 2   reward-to-go R per slot (total minus what the carrier and its
 //            secondaries have earned); every decision of a step adds its
 //            score times R to per-block gradient bins
+// Rewards are fixed-point integers: the weights are quantised to int32 in
+// units of 2^-F (F chosen on the host from the largest weight and a bound on
+// any lineage's reward), so that every reward sum, lineage total and
+// reward-to-go is exact and independent of the summation order, and the
+// streaming pass runs integer adds instead of double-precision arithmetic.
 #include <cuda_runtime.h>
 
 #include "pic_step.cuh"
@@ -25,21 +30,45 @@ namespace pic {
 
 namespace {
 
-// flux potential of one (stack, window, spin) row: gpot[c] = sum_{f=1..c} gJ[f]
-__global__ void k_flux_potential(const Args a, const float *gJ, int rows)
+// flux potential of one (stack, window, spin) row, in fixed point:
+// gpot[c] = sum_{f=1..c} rint(gJ[f] 2^F)
+__global__ void k_flux_potential(const Args a, const float *gJ, long long *gpot, int rows,
+                                 double scale)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
     const int s = r / (2 * a.n_out);
     const int nc = a.stacks[s].n_cells;
     const float *g = gJ + (long long)r * (a.ncm + 1);
-    double *p = const_cast<double *>(a.gpot) + (long long)r * a.ncm;
-    double acc = 0.0;
-    p[0] = 0.0;
+    long long *p = gpot + (long long)r * a.ncm;
+    long long acc = 0;
+    p[0] = 0;
     for (int c = 1; c < nc; ++c) {
-        acc += (double)g[c];
+        acc += (long long)rint((double)g[c] * scale);
         p[c] = acc;
     }
+}
+
+__global__ void k_absmax(const float *x, long long n, unsigned int *out)
+{
+    unsigned int m = 0;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned int b = __float_as_uint(x[i]) & 0x7FFFFFFFu;
+        m = b > m ? b : m;
+    }
+    for (int o = 16; o; o >>= 1) {
+        const unsigned int y = __shfl_down_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+__global__ void k_quantize(const float *x, long long n, int32_t *q, double scale)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        q[i] = (int32_t)rint((double)x[i] * scale);
 }
 
 // start of a pass: the loaded carriers' own reward so far (0, pass 1) or
@@ -54,7 +83,7 @@ __global__ void k_init_acc(const Args a, int pass)
             const long long slot = st.base + i;
             const unsigned long long id = (unsigned long long)a.id[0][slot] |
                                           ((unsigned long long)(a.pk[0][slot] >> 21) << 32);
-            double v = 0.0;
+            long long v = 0;
             if (pass == 2) {
                 if (id < (unsigned long long)st.n_ids) v = a.tot[st.id_off + (long long)id];
                 else atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_STATE);
@@ -88,7 +117,9 @@ __global__ void k_lineage(const Args a, long long n_ids, int g)
 {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n_ids;
          i += (long long)gridDim.x * blockDim.x)
-        if (a.gen[i] == (uint8_t)g) atomicAdd(&a.tot[a.parent[i]], a.tot[i]);
+        if (a.gen[i] == (uint8_t)g)
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.tot[a.parent[i]]),
+                      (unsigned long long)a.tot[i]);
 }
 
 template <int ADJ>
@@ -100,13 +131,17 @@ cudaError_t configure_pass(const Args &a, LaunchCfg *cfg)
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
     const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;
+    // tables, pass 2's sums of R, the flux potential slice and (with the
+    // density deposit) the density-weight slice
     const size_t fixed = (size_t)a.tab_max * sizeof(FastEnt) +
-                         (ADJ == 2 ? (size_t)a.tab_max * 8 : 0) + 4 + tiles;
+                         (ADJ == 2 ? (size_t)a.tab_max * 8 : 0) + (size_t)a.jbin_max * 8 + 4 +
+                         tiles;
+    const size_t fixed_dep = fixed + (size_t)a.nbin_max * 4;
     int o_plain = 0, o_dep = 0;
     if ((e = pick_ring<false, false, ADJ>(fixed, 0, 0, &cfg->ring_fast, &o_plain,
                                           &cfg->smem_fast)) != cudaSuccess)
         return e;
-    if ((e = pick_ring<true, false, ADJ>(fixed, 0, 0, &cfg->ring_fast_dep, &o_dep,
+    if ((e = pick_ring<true, false, ADJ>(fixed_dep, 0, 0, &cfg->ring_fast_dep, &o_dep,
                                          &cfg->smem_fast_dep)) != cudaSuccess)
         return e;
     cfg->grid_fast = sms * o_plain;
@@ -194,10 +229,29 @@ cudaError_t launch_compact_adj(const Args &a, const LaunchCfg &c, int pass, cuda
     return cudaGetLastError();
 }
 
-cudaError_t launch_flux_potential(const Args &a, const float *gJ, int rows, cudaStream_t s)
+cudaError_t launch_flux_potential(const Args &a, const float *gJ, long long *gpot, int rows,
+                                  double scale, cudaStream_t s)
 {
     if (rows <= 0) return cudaSuccess;
-    k_flux_potential<<<(rows + TPB - 1) / TPB, TPB, 0, s>>>(a, gJ, rows);
+    k_flux_potential<<<(rows + TPB - 1) / TPB, TPB, 0, s>>>(a, gJ, gpot, rows, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_absmax(const float *x, long long n, unsigned int *out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + TPB - 1) / TPB;
+    if (blocks > 4096) blocks = 4096;
+    k_absmax<<<(int)blocks, TPB, 0, s>>>(x, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quantize(const float *gn, long long n, int32_t *q, double scale, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + TPB - 1) / TPB;
+    if (blocks > 4096) blocks = 4096;
+    k_quantize<<<(int)blocks, TPB, 0, s>>>(gn, n, q, scale);
     return cudaGetLastError();
 }
 

@@ -36,7 +36,7 @@ struct HostStack {
 struct Replay {
     float *z[2] = {nullptr, nullptr}, *mu[2] = {nullptr, nullptr};
     uint32_t *id[2] = {nullptr, nullptr}, *pk[2] = {nullptr, nullptr};
-    double *acc[2] = {nullptr, nullptr};
+    long long *acc[2] = {nullptr, nullptr};
     uint32_t *stage_l = nullptr;
     unsigned long long *status = nullptr;
     uint32_t *qcnt = nullptr;
@@ -45,9 +45,11 @@ struct Replay {
     DevStack *stacks = nullptr;
     AdjEnt *aent = nullptr;
     double2 *aT = nullptr;
-    double *g_ent = nullptr, *g_T = nullptr, *gpot = nullptr;
-    unsigned int *gen_max = nullptr;
-    double *tot = nullptr;
+    double *g_ent = nullptr, *g_T = nullptr;
+    long long *gpot = nullptr;
+    int32_t *qgn = nullptr;          // quantised density weights
+    unsigned int *gen_max = nullptr, *absmax = nullptr;
+    long long *tot = nullptr;
     unsigned long long *parent = nullptr;
     uint8_t *gen = nullptr;
     int64_t ids_cap = 0;        // entries of tot / parent / gen
@@ -299,7 +301,8 @@ void free_all(pic_ctx *c)
     }
     release(r.stage_l); release(r.status); release(r.qcnt); release(r.cnt); release(r.ctl); release(r.stacks);
     release(r.aent); release(r.aT); release(r.g_ent); release(r.g_T); release(r.gpot);
-    release(r.gen_max); release(r.tot); release(r.parent); release(r.gen);
+    release(r.gen_max); release(r.absmax); release(r.qgn); release(r.tot); release(r.parent);
+    release(r.gen);
     r.ids_cap = 0;
     r.ready = false;
     cudaGetLastError();
@@ -830,7 +833,9 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
         RALLOC(r.aent, c->n_ent); RALLOC(r.aT, c->n_T);
         RALLOC(r.g_ent, c->n_ent); RALLOC(r.g_T, c->n_T);
         RALLOC(r.gpot, (size_t)S * n_out * 2 * ncm);
+        RALLOC(r.qgn, (size_t)S * n_out * 2 * ne * ncm);
         RALLOC(r.gen_max, 1);
+        RALLOC(r.absmax, 2);
         a.n_out = n_out; a.ncm = ncm;
         for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass)
             e = configure_adjoint(a, pass, &r.lc[pass - 1]);
@@ -901,14 +906,42 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
     a.n_hist = nullptr; a.J_hist = nullptr;
     a.tot = r.tot; a.parent = r.parent; a.gen = r.gen; a.gen_max = r.gen_max;
     a.aent = r.aent; a.aT = r.aT; a.g_ent = r.g_ent; a.g_T = r.g_T;
-    a.gn = grad_n; a.gpot = r.gpot; a.stage_l = r.stage_l;
+    a.gn = grad_n ? r.qgn : nullptr; a.gpot = r.gpot; a.stage_l = r.stage_l;
     a.n_out = n_out; a.ncm = ncm;
 
-    e = cudaMemcpyAsync(r.stacks, ds.data(), sizeof(DevStack) * S, cudaMemcpyHostToDevice, st);
+    // fixed-point scale 2^F: the largest weight maps to at most 2^30 (an
+    // int32), and no lineage's reward can reach 2^62: a lineage holds at most
+    // n_e carriers at a time, each earning at most (n_cells + 1) weights a step
     const int rows = S * n_out * 2;
+    const long long n_gn = (long long)rows * ne * ncm, n_gJ = (long long)rows * (ncm + 1);
+    unsigned int amax[2] = {0u, 0u};
+    e = cudaMemsetAsync(r.absmax, 0, 2 * sizeof(unsigned int), st);
+    if (e == cudaSuccess && grad_n) e = launch_absmax(grad_n, n_gn, r.absmax, st);
+    if (e == cudaSuccess && grad_J) e = launch_absmax(grad_J, n_gJ, r.absmax + 1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(amax, r.absmax, sizeof(amax), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_grad: weights");
+    if (amax[0] >= 0x7F800000u || amax[1] >= 0x7F800000u)
+        return fail(c, PIC_ERR_ARG, "pic_grad: the weights must be finite");
+    float wmax_f;
+    const unsigned int wbits = std::max(amax[0], amax[1]);
+    std::memcpy(&wmax_f, &wbits, 4);
+    int F = 0;
+    if (wmax_f > 0.f) {
+        int ex = 0;
+        std::frexp((double)wmax_f, &ex);                  // wmax < 2^ex
+        const double life = (double)ne * (double)std::max(c->step, 1) * (double)(ncm + 1);
+        F = std::min(30 - ex, (int)std::floor(62.0 - std::log2(life)) - ex);
+    }
+    const double scale = std::ldexp(1.0, F);
+    a.inv_q = std::ldexp(1.0, -F);
+
+    e = cudaMemcpyAsync(r.stacks, ds.data(), sizeof(DevStack) * S, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && grad_n)
+        e = timed(c, 7, [&] { return launch_quantize(grad_n, n_gn, r.qgn, scale, st); });
     if (e == cudaSuccess) {
-        if (grad_J) e = launch_flux_potential(a, grad_J, rows, st);
-        else e = cudaMemsetAsync(r.gpot, 0, sizeof(double) * (size_t)rows * ncm, st);
+        if (grad_J) e = timed(c, 7, [&] { return launch_flux_potential(a, grad_J, r.gpot, rows, scale, st); });
+        else e = cudaMemsetAsync(r.gpot, 0, sizeof(long long) * (size_t)rows * ncm, st);
     }
     const bool det = (c->p.flags & PIC_F_DETERMINISTIC) != 0;
     for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass) {
@@ -940,10 +973,10 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
         if (e == cudaSuccess) e = cudaMemsetAsync(r.status, 0, sizeof(unsigned long long) * r.n_status, st);
         // the own reward (pass 1) or reward-to-go (pass 2) of a loaded carrier
         // starts at 0 or at its lineage total
-        if (e == cudaSuccess) e = launch_init_acc(a, lc, pass, st);
+        if (e == cudaSuccess) e = timed(c, 7, [&] { return launch_init_acc(a, lc, pass, st); });
         if (e == cudaSuccess && pass == 1) {
             e = cudaMemsetAsync(r.gen, 0, (size_t)n_ids, st);
-            if (e == cudaSuccess) e = cudaMemsetAsync(r.tot, 0, sizeof(double) * (size_t)n_ids, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(r.tot, 0, sizeof(long long) * (size_t)n_ids, st);
             if (e == cudaSuccess) e = cudaMemsetAsync(r.gen_max, 0, sizeof(unsigned int), st);
         }
         if (e == cudaSuccess && pass == 2) {
@@ -959,14 +992,17 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
                 inj1 = inj1 || h.inj[2 * (size_t)step + 1] > 0;
             }
             const bool dep = ((step + 1) % c->p.moment_every) == 0;
-            if (inj0) e = launch_inject_adj(a, lc, pass, 0, false, st);
-            if (e == cudaSuccess) e = launch_fast_adj(a, lc, pass, det, dep, st);
-            if (e == cudaSuccess) e = launch_slow_adj(a, lc, pass, det, dep, st);
-            if (e == cudaSuccess && inj1) e = launch_inject_adj(a, lc, pass, 1, dep, st);
+            if (inj0) e = timed(c, 7, [&] { return launch_inject_adj(a, lc, pass, 0, false, st); });
+            if (e == cudaSuccess)
+                e = timed(c, 5, [&] { return launch_fast_adj(a, lc, pass, det, dep, st); });
+            if (e == cudaSuccess)
+                e = timed(c, 6, [&] { return launch_slow_adj(a, lc, pass, det, dep, st); });
+            if (e == cudaSuccess && inj1)
+                e = timed(c, 7, [&] { return launch_inject_adj(a, lc, pass, 1, dep, st); });
             if (e == cudaSuccess && ((step + 1) % c->p.compact_every) == 0)
-                e = launch_compact_adj(a, lc, pass, st);
+                e = timed(c, 7, [&] { return launch_compact_adj(a, lc, pass, st); });
         }
-        if (e == cudaSuccess && pass == 1) e = launch_flush_own(a, lc, st);
+        if (e == cudaSuccess && pass == 1) e = timed(c, 7, [&] { return launch_flush_own(a, lc, st); });
         if (e != cudaSuccess) break;
 
         // the replay must have reproduced the forward run exactly
@@ -990,7 +1026,7 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
         // lineage totals, deepest generation first
         if (pass == 1)
             for (int g = (int)gmax; g >= 1 && e == cudaSuccess; --g)
-                e = launch_lineage(a, lc, n_ids, g, st);
+                e = timed(c, 7, [&] { return launch_lineage(a, lc, n_ids, g, st); });
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "pic_grad");
 
@@ -1042,6 +1078,12 @@ pic_status pic_launch_config(const pic_ctx *c, pic_launch_info *out)
     out->ring_step_moments = c->lc.ring_fast_dep;
     out->smem_step = (int64_t)c->lc.smem_fast;
     out->smem_step_moments = (int64_t)c->lc.smem_fast_dep;
+    for (int i = 0; i < 2; ++i) {
+        const bool r = c->rp.ready;
+        out->grid_adj_step[i] = r ? c->rp.lc[i].grid_fast_dep : 0;
+        out->ring_adj_step[i] = r ? c->rp.lc[i].ring_fast_dep : 0;
+        out->smem_adj_step[i] = r ? (int64_t)c->rp.lc[i].smem_fast_dep : 0;
+    }
     return PIC_OK;
 }
 

@@ -124,21 +124,24 @@ struct Args {            // everything a kernel needs, passed by value
     uint32_t *spawn_bits;                    // one bit per position: secondary staged
     float4 *qrec;                            // eventful carriers: z, mu, packed, position
     uint32_t *qcnt;                          // queue length per fast block
-    // adjoint replay (ADJ = 1, 2); unused by the forward step
-    double *acc[2];                          // per slot: own reward so far (pass 1),
+    // adjoint replay (ADJ = 1, 2); unused by the forward step.  Rewards are
+    // fixed-point integers in units of 2^-F (the weights quantised to int32):
+    // sums are exact and independent of their order.
+    long long *acc[2];                       // per slot: own reward so far (pass 1),
                                              // reward still to come (pass 2)
-    double *tot;                             // per id: own reward, then lineage total
+    long long *tot;                          // per id: own reward, then lineage total
     unsigned long long *parent;              // per id: index of the parent's entry
-    uint8_t *gen;                            // per id: generation (1 = primary)
-    unsigned int *gen_max;                   // largest generation created
+    uint8_t *gen;                            // per id: lineage depth (0 = no parent)
+    unsigned int *gen_max;                   // largest depth created
     const AdjEnt *aent;                      // scores, ent indexing
     const double2 *aT;                       // scores (transmit, reflect), T_thr indexing
     double *g_ent;                           // gradient, ent indexing
     double *g_T;                             // gradient, T_thr indexing
-    const float *gn;                         // density weights [stack][n_out][2][n_e][ncm]
-    const double *gpot;                      // flux potential [stack][n_out][2][ncm]
+    const int32_t *gn;                       // density weights [stack][n_out][2][n_e][ncm]
+    const long long *gpot;                   // flux potential [stack][n_out][2][ncm]
     uint32_t *stage_l;                       // pass 2: start layer of a staged secondary
     int n_out, ncm;                          // moment windows, cells of the widest stack
+    double inv_q;                            // 2^-F: reward units to weight units
 };
 
 // reason of the last failure of a call without a context (pic_capi.cu);
@@ -169,8 +172,14 @@ cudaError_t launch_fast_adj(const Args &a, const LaunchCfg &c, int pass, bool de
 cudaError_t launch_slow_adj(const Args &a, const LaunchCfg &c, int pass, bool deterministic,
                             bool deposit, cudaStream_t s);
 cudaError_t launch_compact_adj(const Args &a, const LaunchCfg &c, int pass, cudaStream_t s);
-// flux potential from the flux weights gJ [stack][n_out][2][ncm+1]
-cudaError_t launch_flux_potential(const Args &a, const float *gJ, int rows, cudaStream_t s);
+// largest |x| of n floats, as its bit pattern (non-negative floats order as
+// their bits); NaN or infinity give 0x7F800000 or more
+cudaError_t launch_absmax(const float *x, long long n, unsigned int *out, cudaStream_t s);
+// density weights quantised: q[i] = rint(gn[i] * 2^F)
+cudaError_t launch_quantize(const float *gn, long long n, int32_t *q, double scale, cudaStream_t s);
+// flux potential from the flux weights gJ [stack][n_out][2][ncm+1], quantised
+cudaError_t launch_flux_potential(const Args &a, const float *gJ, long long *gpot, int rows,
+                                  double scale, cudaStream_t s);
 // start of a pass: the double of every loaded carrier (0, or its lineage total)
 cudaError_t launch_init_acc(const Args &a, const LaunchCfg &c, int pass, cudaStream_t s);
 // pass 1 end: own reward of every carrier still in a slot

@@ -151,20 +151,21 @@ __device__ __forceinline__ void flight(const Args &a, const Stk &s, float &z, fl
     }
 }
 
-// Adjoint rewards.  Flux: a carrier of spin sg moving from cell c0 to cell c1
-// in window tj earns the signed sum of the face weights it crosses, the
-// difference of the potential gpot[c] = sum_{f=1..c} gJ[f].  Density: the
-// weight of the (spin, k, cell) bin it is counted in at the end of window tout.
-__device__ __forceinline__ double flux_w(const Args &a, int s, int tj, int sg, int c0, int c1)
+// Adjoint rewards (fixed point).  Flux: a carrier of spin sg moving from cell
+// c0 to cell c1 in window tj earns the signed sum of the face weights it
+// crosses, the difference of the potential gpot[c] = sum_{f=1..c} gJ[f].
+// Density: the weight of the (spin, k, cell) bin it is counted in at the end
+// of window tout.
+__device__ __forceinline__ long long flux_w(const Args &a, int s, int tj, int sg, int c0, int c1)
 {
-    const double *g = a.gpot + ((long long)(s * a.n_out + tj) * 2 + sg) * a.ncm;
+    const long long *g = a.gpot + ((long long)(s * a.n_out + tj) * 2 + sg) * a.ncm;
     return g[c1] - g[c0];
 }
 
-__device__ __forceinline__ double dep_w(const Args &a, int s, int tout, int sg, int k, int c)
+__device__ __forceinline__ long long dep_w(const Args &a, int s, int tout, int sg, int k, int c)
 {
-    if (!a.gn) return 0.0;
-    return (double)a.gn[(((long long)(s * a.n_out + tout) * 2 + sg) * a.n_e + (k - 1)) * a.ncm + c];
+    if (!a.gn) return 0;
+    return a.gn[(((long long)(s * a.n_out + tout) * 2 + sg) * a.n_e + (k - 1)) * a.ncm + c];
 }
 
 __device__ __forceinline__ void add_flux(int32_t *sJ, int nf, int sg, int c0, int c1)
@@ -494,10 +495,16 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
     extern __shared__ __align__(128) unsigned char smem[];
     float *ring = reinterpret_cast<float *>(smem);                      // a.ring x STG x TILE
     FastEnt *s_ent = reinterpret_cast<FastEnt *>(ring + (size_t)a.ring * STG * TILE);
-    double *s_sr = reinterpret_cast<double *>(s_ent + a.tab_max);       // pass 2: sum of R
-    int32_t *s_J = reinterpret_cast<int32_t *>(s_sr + (ADJ == 2 ? a.tab_max : 0));
+    // pass 2: sum of the reward-to-go of the carriers that passed the
+    // scattering test, per entry (fixed point, two's complement)
+    unsigned long long *s_sr = reinterpret_cast<unsigned long long *>(s_ent + a.tab_max);
+    // replay: the window's flux potential [2][n_cells] and density weights
+    // [2][n_e][n_cells] of the stack, in place of the histograms
+    long long *s_gp = reinterpret_cast<long long *>(s_sr + (ADJ == 2 ? a.tab_max : 0));
+    int32_t *s_J = reinterpret_cast<int32_t *>(s_gp + (ADJ ? a.jbin_max : 0));
     uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + (ADJ ? 0 : a.jbin_max));
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN && !ADJ ? a.nbin_max : 0) + 1);
+    int32_t *s_gn = reinterpret_cast<int32_t *>(s_n);
+    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max : 0) + 1);
     s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     __shared__ __align__(8) unsigned long long s_full[MAX_RING], s_empty[MAX_RING];
@@ -608,8 +615,8 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
             // the no-scattering score of an entry times the sum of the
             // reward-to-go of the carriers that passed the test with it
             for (int i = tid; i < st.tab_n; i += TPB) {
-                const double v = s_sr[i];
-                if (v != 0.0) atomicAdd(&a.g_ent[st.ent_off + i], v * a.aent[st.ent_off + i].noscat);
+                const long long v = (long long)s_sr[i];
+                if (v) atomicAdd(&a.g_ent[st.ent_off + i], (double)v * a.inv_q * a.aent[st.ent_off + i].noscat);
             }
         }
         const unsigned long long v0 = consumer_sum_u64(n_steps, s_r);
@@ -638,7 +645,19 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
             if (DEPN && !ADJ)
                 for (int q = tid; q < 2 * a.n_e * st.n_cells; q += TPB) s_n[q] = 0u;
             if (ADJ == 2)
-                for (int q = tid; q < st.tab_n; q += TPB) s_sr[q] = 0.0;
+                for (int q = tid; q < st.tab_n; q += TPB) s_sr[q] = 0ull;
+            if (ADJ) {
+                const long long *gp = a.gpot + (long long)(s * a.n_out + tj) * 2 * a.ncm;
+                for (int q = tid; q < 2 * st.n_cells; q += TPB)
+                    s_gp[q] = gp[(q / st.n_cells) * a.ncm + q % st.n_cells];
+                if (DEPN) {
+                    const int rows = 2 * a.n_e;
+                    for (int q = tid; q < rows * st.n_cells; q += TPB)
+                        s_gn[q] = a.gn ? a.gn[((long long)(s * a.n_out + tout) * rows + q / st.n_cells) * a.ncm +
+                                              q % st.n_cells]
+                                       : 0;
+                }
+            }
             nc = st.n_cells;
             ctr_hi = (uint32_t)s << 16;
             seg_stack = s;
@@ -664,10 +683,10 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
         const float4 z4 = reinterpret_cast<const float4 *>(rz)[tid];
         const float4 m4 = reinterpret_cast<const float4 *>(rmu)[tid];
         const uint4 p4 = reinterpret_cast<const uint4 *>(rpk)[tid];
-        double av[VEC];
+        long long av[VEC];
         if (ADJ) {
-            const double2 *racc = reinterpret_cast<const double2 *>(rz + 3 * TILE);
-            const double2 a01 = racc[2 * tid], a23 = racc[2 * tid + 1];
+            const longlong2 *racc = reinterpret_cast<const longlong2 *>(rz + 3 * TILE);
+            const longlong2 a01 = racc[2 * tid], a23 = racc[2 * tid + 1];
             av[0] = a01.x; av[1] = a01.y; av[2] = a23.x; av[3] = a23.y;
         }
         bool achg = false;
@@ -717,10 +736,11 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
                     if (ADJ) {
                         // reward of the step: faces crossed, then the density bin
                         const int c0 = c0u < nc - 1 ? c0u : nc - 1;
-                        double r = c0 != c1 ? flux_w(a, s, tj, sg, c0, c1) : 0.0;
-                        if (DEPN) r += dep_w(a, s, tout, sg, k, c1);
-                        if (ADJ == 2) atomicAdd(&s_sr[(layer * 2 + sg) * ne + (k - 1)], av[j]);
-                        if (r != 0.0) {
+                        long long r = s_gp[sg * nc + c1] - s_gp[sg * nc + c0];
+                        if (DEPN) r += s_gn[(sg * ne + (k - 1)) * nc + c1];
+                        if (ADJ == 2)
+                            atomicAdd(&s_sr[(layer * 2 + sg) * ne + (k - 1)], (unsigned long long)av[j]);
+                        if (r != 0) {
                             av[j] = ADJ == 1 ? av[j] + r : av[j] - r;
                             achg = true;
                         }
@@ -743,10 +763,10 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
                 if (i0 + j < nvalid) gZ[i0 + j] = zo[j];
         }
         if (ADJ && achg) {
-            double *gA = a.acc[cur] + s_st.base + tslot0;
+            long long *gA = a.acc[cur] + s_st.base + tslot0;
             if (i0 + VEC <= nvalid) {
-                reinterpret_cast<double2 *>(gA + i0)[0] = make_double2(av[0], av[1]);
-                reinterpret_cast<double2 *>(gA + i0)[1] = make_double2(av[2], av[3]);
+                reinterpret_cast<longlong2 *>(gA + i0)[0] = make_longlong2(av[0], av[1]);
+                reinterpret_cast<longlong2 *>(gA + i0)[1] = make_longlong2(av[2], av[3]);
             } else {
 #pragma unroll
                 for (int j = 0; j < VEC; ++j)
@@ -884,7 +904,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
             atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_STATE);
             return;
         }
-        double rw = flux_w(a, s, tj, sg, c0, c1);
+        long long rw = flux_w(a, s, tj, sg, c0, c1);
         if (DEPN) rw += dep_w(a, s, tout, sg, k, c1);
         if (ADJ == 1) {
             const unsigned int depth = (unsigned int)a.gen[stg.id_off + pid] + 1u;
@@ -893,7 +913,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
             atomicMax(a.gen_max, depth);
             a.acc[cur][d] = rw;
         } else {
-            const double Rc = a.tot[stg.id_off + id];
+            const long long Rc = a.tot[stg.id_off + id];
             const uint32_t ctr_y = (ppk >> 21) | ((uint32_t)s << 16);
             const uint4 y = philox_rk(make_uint4(pid_lo, ctr_y, a.step, SUB_SEC), a);
             Stk gs;
@@ -907,7 +927,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
             float zs = r.w, mus = mu_of(y.y);
             Tally tq{};
             flight<DET, true>(a, gs, zs, mus, ls, es, los, his, sg, k, half, pid_lo, ctr_y,
-                              SUB_SIF, tq, Rc, a.g_T + stg.T_off);
+                              SUB_SIF, tq, (double)Rc * a.inv_q, a.g_T + stg.T_off);
             // the same words give the same flight: anything else means the
             // replay is not the forward run
             if (__float_as_uint(zs) != __float_as_uint(r.x))
@@ -1012,11 +1032,12 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
             TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
             float lo = S.edge[layer], hi = S.edge[layer + 1];
             const int c_start = cell_of(a, S, z);
-            // adjoint: the slot's double; in pass 2 the reward-to-go R that
-            // weights every decision of this step
-            const double R = ADJ ? a.acc[cur][gslot] : 0.0;
+            // adjoint: the slot's reward sum; in pass 2 the reward-to-go R
+            // that weights every decision of this step
+            const long long R = ADJ ? a.acc[cur][gslot] : 0;
+            const double Rd = ADJ == 2 ? (double)R * a.inv_q : 0.0;
             flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
-                                  SUB_IF, ty, R, s_gT);
+                                  SUB_IF, ty, Rd, s_gT);
             const int tb = (layer * 2 + sg) * S.n_e + (k - 1);     // entry of the test
             // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes):
             // the slot group's test word, then the carrier's event words
@@ -1025,14 +1046,14 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
             const uint32_t xs = (slot & 3) == 0 ? xg.x : (slot & 3) == 1 ? xg.y
                               : (slot & 3) == 2 ? xg.z : xg.w;
             bool dead = false;
-            if (ADJ == 2 && !(xs < e.P)) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * R);
+            if (ADJ == 2 && !(xs < e.P)) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * Rd);
             if (xs < e.P) {
                 const uint4 x = philox_rk(make_uint4(id_lo, ctr_y, a.step, SUB_SCAT), a);
                 const bool inel = x.y < e.Q;
                 // scores of the test (scattered) and of the channel
                 if (ADJ == 2) {
                     const AdjEnt &ae = a.aent[st.ent_off + tb];
-                    atomicAdd(&s_g[tb], (inel ? ae.scat_inel : ae.scat_el) * R);
+                    atomicAdd(&s_g[tb], (inel ? ae.scat_inel : ae.scat_el) * Rd);
                 }
                 if (k == 1 && (inel || (a.flags & PIC_F_LOWEST_BIN_ANY))) {
                     dead = true;
@@ -1078,7 +1099,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
                     }
                 }
             }
-            double rw = 0.0;         // adjoint: reward of the step
+            long long rw = 0;        // adjoint: reward of the step
             if (dead) {
                 pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
                 const int c_end = cell_of(a, S, z);
@@ -1086,7 +1107,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
                 if (ADJ) rw = flux_w(a, s, tj, sg, c_start, c_end);
             } else {
                 flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
-                                      SUB_IF + 16, ty, R, s_gT);
+                                      SUB_IF + 16, ty, Rd, s_gT);
                 const int c_end = cell_of(a, S, z);
                 if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
                 pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
@@ -1096,7 +1117,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
                     if (DEPN) rw += dep_w(a, s, tout, sg, k, c_end);
                 }
             }
-            if (ADJ && rw != 0.0) a.acc[cur][gslot] = ADJ == 1 ? R + rw : R - rw;
+            if (ADJ && rw != 0) a.acc[cur][gslot] = ADJ == 1 ? R + rw : R - rw;
             Z[gslot] = z;
             if (__float_as_uint(mu) != __float_as_uint(mu_in) || pk != pk_in) {
                 ++ty.changed;
@@ -1299,7 +1320,7 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
         if (ADJ) {
             // a new carrier: no parent (lineage depth 0, set when the replay
             // starts); its reward so far is its density weight if deposited
-            double rw = 0.0;
+            long long rw = 0;
             if (deposit) {
                 Stk tmp; tmp.n_cells = st.n_cells;
                 rw = dep_w(a, s, tout, (int)sg, (int)k, cell_of(a, tmp, z));

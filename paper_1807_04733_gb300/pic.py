@@ -34,7 +34,8 @@ EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_grad", "pic
            "pic_set_records", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
            "pic_profile_read", "pic_compact_static", "pic_launch_config", "pic_launch_count",
            "pic_destroy", "pic_last_error", "pic_status_string")
-KERNEL_KINDS = ("inject", "step", "step_moments", "compact", "step_events")
+KERNEL_KINDS = ("inject", "step", "step_moments", "compact", "step_events", "adjoint_step",
+                "adjoint_events", "adjoint_other")
 
 
 class pic_params(C.Structure):
@@ -74,14 +75,20 @@ class pic_launch_info(C.Structure):
                 ("grid_slow", C.c_int32), ("grid_slow_moments", C.c_int32),
                 ("grid_compact", C.c_int32), ("grid_inject", C.c_int32),
                 ("ring_step", C.c_int32), ("ring_step_moments", C.c_int32),
-                ("smem_step", C.c_int64), ("smem_step_moments", C.c_int64)]
+                ("smem_step", C.c_int64), ("smem_step_moments", C.c_int64),
+                ("grid_adj_step", C.c_int32 * 2), ("ring_adj_step", C.c_int32 * 2),
+                ("smem_adj_step", C.c_int64 * 2)]
 
     def as_dict(self):
-        return {n: int(getattr(self, n)) for n, _ in self._fields_}
+        out = {}
+        for n, t in self._fields_:
+            v = getattr(self, n)
+            out[n] = [int(x) for x in v] if hasattr(t, "_length_") else int(v)
+        return out
 
 
 class pic_kernel_times(C.Structure):
-    _fields_ = [("launches", C.c_int64 * 5), ("ms", C.c_double * 5)]
+    _fields_ = [("launches", C.c_int64 * len(KERNEL_KINDS)), ("ms", C.c_double * len(KERNEL_KINDS))]
 
 
 class PicError(RuntimeError):

@@ -1,10 +1,13 @@
 """GPU adjoint (pic_grad) against the oracle's two-pass gradient.
 
-Deterministic build: the replay runs the forward trajectories bit for bit,
-so the gradient differs from the oracle's only by the order of the double
-sums: |g_gpu - g_oracle| <= 1e-9 (mag + 1), mag = the oracle's sum of
+Deterministic build: the replay runs the forward trajectories bit for bit.
+The library sums rewards in fixed point (weights quantised to 2^-F); the
+weights here are multiples of 2^-10, which both sides add exactly, so the
+gradients differ only by the order of the final double sums of score x
+reward: |g_gpu - g_oracle| <= 1e-9 (mag + 1), mag = the oracle's sum of
 |score| (|total| + |earned|) per entry.  Fast build: the per-sample survival
-identity (P1') and the closed form.
+identity (P1'), the closed form, and central finite differences with common
+random numbers.
 """
 import copy
 import math
@@ -29,8 +32,8 @@ def random_weights(ctx, seed, density=1.0):
     ncm = ctx.n_cells_max
     _, n_out, _ = ctx.shape(0)
     rng = np.random.default_rng(seed)
-    gn = rng.uniform(-1, 1, (S, n_out, 2, ne, ncm)).astype(np.float32)
-    gJ = rng.uniform(-1, 1, (S, n_out, 2, ncm + 1)).astype(np.float32)
+    gn = (rng.integers(-1024, 1025, (S, n_out, 2, ne, ncm)) / 1024.0).astype(np.float32)
+    gJ = (rng.integers(-1024, 1025, (S, n_out, 2, ncm + 1)) / 1024.0).astype(np.float32)
     if density < 1.0:
         gn *= rng.uniform(0, 1, gn.shape) < density
         gJ *= rng.uniform(0, 1, gJ.shape) < density
@@ -185,8 +188,8 @@ def test_autograd_function_backward_matches_grad():
     tau = torch.tensor(st.tau_in[None], dtype=torch.float64, requires_grad=True)
     T = torch.tensor(st.T[None], dtype=torch.float64, requires_grad=True)
     n_all, J_all = pic.PicTransport.apply(tau, T, wl, 80)
-    w_n = torch.rand_like(n_all)
-    w_J = torch.rand_like(J_all)
+    w_n = torch.floor(torch.rand_like(n_all) * 1024) / 1024
+    w_J = torch.floor(torch.rand_like(J_all) * 1024) / 1024
     ((n_all * w_n).sum() + (J_all * w_J).sum()).backward()
     ref = OracleSim(wl)
     ref.step(80)
