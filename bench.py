@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-scale", type=float, default=1.0)
+    ap.add_argument("--batched-steps", type=int, default=0)
     ap.add_argument("--adjoint-scale", type=float, default=1.0)
     return ap.parse_args()
 
@@ -334,6 +337,53 @@ def adjoint_leg(args):
 
 
 # ---------------------------------------------------------------------------
+# batched leg: one context for 64 stacks, graph-replayed steps, against 64
+# one-stack contexts stepped one after another with single launches
+# ---------------------------------------------------------------------------
+def batched_leg(args):
+    """64 Fe(15 nm)/Au(round U[20,200] nm) stacks, P and AP emitters
+    alternating, N ~ logU[1e5, 1e7] per stack (sum ~1.4e8), capacity 4N,
+    tables perturbed by +-20 % per stack, 1 fs steps, densities every step."""
+    import torch
+    from paper_1807_04733_gb300 import pic
+    from paper_1807_04733_gb300 import workloads as W
+    wl = W.config(2, scale=args.batched_scale)
+    n = args.batched_steps or wl.n_steps
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    ctx = pic.Context(wl, use_graph=True)
+    torch.cuda.synchronize()
+    ev[0].record(ctx.stream)
+    ctx.step(n)
+    ev[1].record(ctx.stream)
+    torch.cuda.synchronize()
+    ms_b = ev[0].elapsed_time(ev[1])
+    launches_b = ctx.launches
+    ps_b = sum(ctx.ledger(s)["particle_steps"] for s in range(len(wl.stacks)))
+    ctx.close()
+
+    singles = [pic.Context(wl.replace(stacks=[st])) for st in wl.stacks]
+    torch.cuda.synchronize()
+    ev[0].record(singles[0].stream)
+    launches_s = 0
+    for c in singles:
+        c.step(n)
+        launches_s += c.launches
+    ev[1].record(singles[0].stream)
+    torch.cuda.synchronize()
+    ms_s = ev[0].elapsed_time(ev[1])
+    ps_s = sum(c.ledger(0)["particle_steps"] for c in singles)
+    for c in singles:
+        c.close()
+    return {"workload": "64 x Fe(15nm)/Au(20-200nm), sum n0 %d, %d x %g fs, densities every step"
+                        % (sum(st.n0 for st in wl.stacks), n, wl.dt),
+            "batched_graph_ms": ms_b, "sequential_plain_ms": ms_s, "speedup": ms_s / ms_b,
+            "batched_particle_steps_per_s": ps_b / (ms_b * 1e-3),
+            "sequential_particle_steps_per_s": ps_s / (ms_s * 1e-3),
+            "batched_launches": launches_b, "sequential_launches": launches_s}
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 def main():
@@ -470,6 +520,8 @@ def main():
     ctx.close()
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_leg(args)
+    if rank == 0 and world == 1 and not args.no_batched:
+        line["batched"] = batched_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = run_cpu_baseline(args, wl, period, pre, timed_steps=60)
     if dist is not None:

@@ -82,6 +82,13 @@ typedef struct {
                                1 = warp-aggregated (match-any) atomics */
     int32_t ring_stages;    /* tiles in the step kernel's bulk-copy ring
                                (2..8); 0 = chosen from the occupancy */
+    int32_t use_graph;      /* 1: pic_step replays whole periods (the least
+                               common multiple of moment_every and
+                               compact_every) from CUDA graphs captured once,
+                               the kernels reading the step index from device
+                               memory; 0: one launch per kernel.  Results are
+                               identical; kernel timing (pic_profile) always
+                               uses single launches. */
 } pic_params;
 
 /* Launch configuration a context chose (pic_launch_info). */

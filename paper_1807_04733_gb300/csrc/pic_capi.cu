@@ -94,6 +94,13 @@ struct pic_ctx {
     size_t n_ent = 0, n_T = 0;   // entries of the layer and interface tables
     int n_mat_max = 1;
     Replay rp;
+    // CUDA graphs of one period of steps (use_graph): [0] with the source
+    // kernels, [1] without (after the pulse); captured on a private stream
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t period_graph[2] = {nullptr, nullptr};
+    int64_t period_launches[2] = {0, 0};
+    int period = 0;
+    bool dev_step_valid = false;     // d_ctl->step == step
     // kernel timing (pic_profile)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -144,6 +151,7 @@ bool valid_params(const pic_params *p, std::string &why)
     if (p->ring_stages != 0 && (p->ring_stages < 2 || p->ring_stages > 8)) {
         why = "ring_stages must be 0 or 2..8"; return false;
     }
+    if (p->use_graph != 0 && p->use_graph != 1) { why = "use_graph must be 0 or 1"; return false; }
     return true;
 }
 
@@ -286,6 +294,12 @@ void release(T *&p)
 // linger as the runtime's pending error for an unrelated later call.
 void free_all(pic_ctx *c)
 {
+    for (cudaGraphExec_t &g : c->period_graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    c->cap_stream = nullptr;
     release(c->d_stacks); release(c->d_ent); release(c->d_fent); release(c->d_T);
     release(c->d_cdf_thr);
     release(c->d_cdf_cell); release(c->d_cdf_layer); release(c->d_inj);
@@ -634,49 +648,129 @@ pic_status pic_excite(pic_ctx *c, int stack, const pic_pulse *u)
     return PIC_OK;
 }
 
+namespace {
+
+// The kernels of time step s (Eq. strang): source half step, the streaming
+// and event passes, the second source half step, compaction.  `graph`: the
+// step is being captured; the source kernels run whatever the counts (they
+// read them on the device) and the step's last kernel advances the device
+// step counter.
+cudaError_t enqueue_step(pic_ctx *c, const Args &a0, int s, bool inj0, bool inj1, bool graph,
+                         cudaStream_t st, int64_t &launches)
+{
+    const bool det = (c->p.flags & PIC_F_DETERMINISTIC) != 0;
+    const bool dep = ((s + 1) % c->p.moment_every) == 0;
+    const LaunchCfg &lc = c->lc;
+    Args a = a0;
+    a.step = (uint32_t)s;
+    a.bump_step = 0;
+    cudaError_t e = cudaSuccess;
+    if (inj0) {
+        e = timed(c, 0, [&] { return launch_inject(a, lc, 0, false, st); });
+        ++launches;
+    }
+    if (e == cudaSuccess) {
+        e = timed(c, dep ? 2 : 1, [&] { return launch_fast(a, lc, det, dep, c->p.hist_mode, st); });
+        ++launches;
+    }
+    if (e == cudaSuccess) {
+        Args b = a;
+        b.bump_step = graph && !inj1;
+        e = timed(c, 4, [&] { return launch_slow(b, lc, det, dep, st); });
+        ++launches;
+    }
+    if (e == cudaSuccess && inj1) {
+        Args b = a;
+        b.bump_step = graph;
+        e = timed(c, 0, [&] { return launch_inject(b, lc, 1, dep, st); });
+        ++launches;
+    }
+    if (e == cudaSuccess && ((s + 1) % c->p.compact_every) == 0) {
+        e = timed(c, 3, [&] { return launch_compact(a, lc, st); });
+        ++launches;
+    }
+    return e;
+}
+
+bool any_source(const pic_ctx *c, int s0, int n)
+{
+    for (const HostStack &h : c->hs)
+        for (int64_t i = 2 * (int64_t)s0; i < 2 * (int64_t)(s0 + n); ++i)
+            if (h.inj[(size_t)i] > 0) return true;
+    return false;
+}
+
+// Capture one period of steps (starting at a step that is a multiple of the
+// period) into a graph; with_source: the source kernels of every half step.
+cudaError_t capture_period(pic_ctx *c, int which)
+{
+    if (!c->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    Args a = c->args;
+    a.step_dev = &c->d_ctl->step;
+    const bool src = which == 0;
+    cudaGraph_t g = nullptr;
+    int64_t n = 0;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < c->period && e == cudaSuccess; ++i)
+        e = enqueue_step(c, a, i, src, src, true, c->cap_stream, n);
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->period_graph[which], g, 0);
+    if (g) cudaGraphDestroy(g);
+    c->period_launches[which] = n;
+    return e;
+}
+
+int gcd_int(int x, int y) { return y ? gcd_int(y, x % y) : x; }
+
+}  // namespace
+
 pic_status pic_step(pic_ctx *c, int n_steps)
 {
     if (!c) return PIC_ERR_ARG;
     if (n_steps < 0) return fail(c, PIC_ERR_ARG, "n_steps < 0");
     if ((int64_t)c->step + n_steps > c->p.n_steps_max)
         return fail(c, PIC_ERR_ARG, "steps would exceed n_steps_max");
-    const bool det = (c->p.flags & PIC_F_DETERMINISTIC) != 0;
     c->launches = 0;
-    for (int i = 0; i < n_steps; ++i) {
+    const bool graphs = c->p.use_graph == 1 && !c->profiling;
+    if (graphs && c->period == 0) {
+        const int me = c->p.moment_every, ce = c->p.compact_every;
+        const long long l = (long long)me / gcd_int(me, ce) * ce;
+        c->period = l <= 100000 ? (int)l : -1;      // -1: no graphs for this context
+    }
+    int left = n_steps;
+    while (left > 0) {
         const int s = c->step;
-        c->args.step = (uint32_t)s;
+        cudaError_t e = cudaSuccess;
+        if (graphs && c->period > 0 && s % c->period == 0 && left >= c->period) {
+            const int which = any_source(c, s, c->period) ? 0 : 1;
+            if (!c->period_graph[which]) {
+                e = capture_period(c, which);
+                if (e != cudaSuccess) return cuda_fail(c, e, "pic_step graph capture");
+            }
+            if (!c->dev_step_valid) e = launch_set_step(c->d_ctl, (unsigned int)s, c->stream);
+            if (e == cudaSuccess) e = cudaGraphLaunch(c->period_graph[which], c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "pic_step graph launch");
+            c->dev_step_valid = true;
+            c->launches += c->period_launches[which];
+            c->step = s + c->period;
+            left -= c->period;
+            continue;
+        }
         bool inj0 = false, inj1 = false;
         for (const HostStack &h : c->hs) {
             inj0 = inj0 || h.inj[2 * (size_t)s] > 0;
             inj1 = inj1 || h.inj[2 * (size_t)s + 1] > 0;
         }
-        const bool dep = ((s + 1) % c->p.moment_every) == 0;
-        cudaError_t e = cudaSuccess;
-        const Args &a = c->args;
-        const LaunchCfg &lc = c->lc;
-        cudaStream_t st = c->stream;
-        if (inj0) {
-            e = timed(c, 0, [&] { return launch_inject(a, lc, 0, false, st); });
-            ++c->launches;
-        }
-        if (e == cudaSuccess) {
-            e = timed(c, dep ? 2 : 1, [&] { return launch_fast(a, lc, det, dep, c->p.hist_mode, st); });
-            ++c->launches;
-        }
-        if (e == cudaSuccess) {
-            e = timed(c, 4, [&] { return launch_slow(a, lc, det, dep, st); });
-            ++c->launches;
-        }
-        if (e == cudaSuccess && inj1) {
-            e = timed(c, 0, [&] { return launch_inject(a, lc, 1, dep, st); });
-            ++c->launches;
-        }
-        if (e == cudaSuccess && ((s + 1) % c->p.compact_every) == 0) {
-            e = timed(c, 3, [&] { return launch_compact(a, lc, st); });
-            ++c->launches;
-        }
+        e = enqueue_step(c, c->args, s, inj0, inj1, false, c->stream, c->launches);
         if (e != cudaSuccess) return cuda_fail(c, e, "pic_step launch");
+        c->dev_step_valid = false;
         c->step = s + 1;
+        --left;
     }
     return PIC_OK;
 }

@@ -86,7 +86,8 @@ struct DevCtl {
     unsigned int done;       // blocks finished in the current launch
     unsigned int cur;        // current particle buffer (0/1)
     unsigned int timeout_where;
-    unsigned int pad[3];
+    unsigned int step;       // time step of graph-replayed steps
+    unsigned int pad[2];
 };
 
 struct Args {            // everything a kernel needs, passed by value
@@ -116,7 +117,9 @@ struct Args {            // everything a kernel needs, passed by value
     uint32_t flags;
     int n_e;
     int moment_every;
-    uint32_t step;
+    uint32_t step;                           // time step (plain launches)
+    const unsigned int *step_dev;            // graph replay: the step is read here
+    int bump_step;                           // this kernel's last block advances *step_dev
     int tab_max, T_max, nbin_max, jbin_max;  // shared-memory sizing
     unsigned int spin_limit;                 // bound of every device-side wait
     int ring;                                // tiles in k_fast's copy ring
@@ -162,6 +165,8 @@ cudaError_t launch_fast(const Args &a, const LaunchCfg &c, bool deterministic, b
 cudaError_t launch_slow(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
                         cudaStream_t s);
 cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s);
+// set the device step counter read by graph-replayed steps
+cudaError_t launch_set_step(DevCtl *ctl, unsigned int step, cudaStream_t s);
 
 // adjoint replay (pic_adjoint.cu); pass = 1 or 2
 cudaError_t configure_adjoint(const Args &a, int pass, LaunchCfg *cfg);

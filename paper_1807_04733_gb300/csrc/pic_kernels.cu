@@ -95,6 +95,14 @@ cudaError_t launch_inject(const Args &a, const LaunchCfg &c, int half, bool depo
     return cudaGetLastError();
 }
 
+__global__ void k_set_step(DevCtl *ctl, unsigned int step) { ctl->step = step; }
+
+cudaError_t launch_set_step(DevCtl *ctl, unsigned int step, cudaStream_t s)
+{
+    k_set_step<<<1, 1, 0, s>>>(ctl, step);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s)
 {
     k_compact<0><<<c.grid_compact, TPB, 0, s>>>(a);

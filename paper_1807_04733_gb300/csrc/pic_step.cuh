@@ -64,6 +64,19 @@ __device__ __forceinline__ float unit_of(uint32_t x)
     return __fmul_rn(__uint2float_rn(2u * (x >> 9) + 1u), 5.9604644775390625e-08f);
 }
 
+// The time-step index: the kernel argument, or (steps replayed from a CUDA
+// graph) the device counter that the last kernel of every step advances.
+__device__ __forceinline__ uint32_t step_now(const Args &a)
+{
+    return a.step_dev ? *(volatile const unsigned int *)a.step_dev : a.step;
+}
+
+// advance the device step counter (last block of the step's last kernel)
+__device__ __forceinline__ void bump_step(const Args &a)
+{
+    if (a.bump_step && a.step_dev) *const_cast<unsigned int *>(a.step_dev) += 1u;
+}
+
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long *p)
 {
     return *(volatile const unsigned long long *)p;
@@ -106,7 +119,7 @@ template <bool DET, bool SC = false>
 __device__ __forceinline__ void flight(const Args &a, const Stk &s, float &z, float &mu,
                                        int &layer, TabEnt &e, float &lo, float &hi, int sg,
                                        int k, float tau, uint32_t id_lo, uint32_t ctr_y,
-                                       uint32_t sub0, Tally &t, double R = 0.0,
+                                       uint32_t step, uint32_t sub0, Tally &t, double R = 0.0,
                                        double *gT = nullptr)
 {
     for (int hit = 0;; ++hit) {
@@ -130,7 +143,7 @@ __device__ __forceinline__ void flight(const Args &a, const Stk &s, float &z, fl
             bool trans = true;
             ++t.hits;
             if (!(a.flags & PIC_F_TRANSPARENT)) {
-                const uint4 r = philox_rk(make_uint4(id_lo, ctr_y, a.step, sub0 + (uint32_t)hit), a);
+                const uint4 r = philox_rk(make_uint4(id_lo, ctr_y, step, sub0 + (uint32_t)hit), a);
                 const int ti = ((iface * 2 + dir) * 2 + sg) * s.n_e + (k - 1);
                 trans = r.x < s.T[ti];
                 if (SC) {
@@ -584,8 +597,9 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
     }
 
     // ---------------- consumer warps ----------------
-    const int tj = (int)(a.step / (uint32_t)a.moment_every);
-    const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
+    const uint32_t step = step_now(a);
+    const int tj = (int)(step / (uint32_t)a.moment_every);
+    const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
     const float half = a.half_dt;
     const long long pos0 = t0 * TILE;                // queue region of this block
     int seg_stack = -1, nc = 1, ne = a.n_e;
@@ -695,7 +709,7 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
         if (lane == 0) mbar_arrive(&s_empty[stg]);
         if (++stg == nring) { stg = 0; phase ^= 1u; }
         const uint4 xg = philox_rk(make_uint4((uint32_t)(tslot0 >> 2) + (uint32_t)tid, ctr_hi,
-                                              a.step, SUB_TEST), a);
+                                              step, SUB_TEST), a);
         const float zin[VEC] = {z4.x, z4.y, z4.z, z4.w};
         const float min_[VEC] = {m4.x, m4.y, m4.z, m4.w};
         const uint32_t pin[VEC] = {p4.x, p4.y, p4.z, p4.w};
@@ -839,8 +853,9 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
     const long long T = make_tiles(a, s_tpref, s_nsl);
     const int fb0 = (int)((long long)Gf * b / Gs), fb1 = (int)((long long)Gf * (b + 1) / Gs);
     const long long t0 = chunk_lo(T, fb0, Gf), t1 = chunk_lo(T, fb1, Gf);
-    const int tj = (int)(a.step / (uint32_t)a.moment_every);
-    const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
+    const uint32_t step = step_now(a);
+    const int tj = (int)(step / (uint32_t)a.moment_every);
+    const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
     const float half = a.half_dt;
     float *Z = a.z[cur], *MU = a.mu[cur];
     uint32_t *PK = a.pk[cur];
@@ -915,7 +930,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
         } else {
             const long long Rc = a.tot[stg.id_off + id];
             const uint32_t ctr_y = (ppk >> 21) | ((uint32_t)s << 16);
-            const uint4 y = philox_rk(make_uint4(pid_lo, ctr_y, a.step, SUB_SEC), a);
+            const uint4 y = philox_rk(make_uint4(pid_lo, ctr_y, step, SUB_SEC), a);
             Stk gs;
             gs.ent = a.ent + stg.ent_off; gs.T = a.T_thr + stg.T_off;
             gs.edge = a.stacks[s].edge; gs.p0 = nullptr;
@@ -927,7 +942,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
             float zs = r.w, mus = mu_of(y.y);
             Tally tq{};
             flight<DET, true>(a, gs, zs, mus, ls, es, los, his, sg, k, half, pid_lo, ctr_y,
-                              SUB_SIF, tq, (double)Rc * a.inv_q, a.g_T + stg.T_off);
+                              step, SUB_SIF, tq, (double)Rc * a.inv_q, a.g_T + stg.T_off);
             // the same words give the same flight: anything else means the
             // replay is not the forward run
             if (__float_as_uint(zs) != __float_as_uint(r.x))
@@ -1037,18 +1052,18 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
             const long long R = ADJ ? a.acc[cur][gslot] : 0;
             const double Rd = ADJ == 2 ? (double)R * a.inv_q : 0.0;
             flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
-                                  SUB_IF, ty, Rd, s_gT);
+                                  step, SUB_IF, ty, Rd, s_gT);
             const int tb = (layer * 2 + sg) * S.n_e + (k - 1);     // entry of the test
             // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes):
             // the slot group's test word, then the carrier's event words
-            const uint4 xg = philox_rk(make_uint4((uint32_t)(slot >> 2), S.ctr_hi, a.step,
+            const uint4 xg = philox_rk(make_uint4((uint32_t)(slot >> 2), S.ctr_hi, step,
                                                   SUB_TEST), a);
             const uint32_t xs = (slot & 3) == 0 ? xg.x : (slot & 3) == 1 ? xg.y
                               : (slot & 3) == 2 ? xg.z : xg.w;
             bool dead = false;
             if (ADJ == 2 && !(xs < e.P)) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * Rd);
             if (xs < e.P) {
-                const uint4 x = philox_rk(make_uint4(id_lo, ctr_y, a.step, SUB_SCAT), a);
+                const uint4 x = philox_rk(make_uint4(id_lo, ctr_y, step, SUB_SCAT), a);
                 const bool inel = x.y < e.Q;
                 // scores of the test (scattered) and of the channel
                 if (ADJ == 2) {
@@ -1075,7 +1090,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
                                 atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
                         } else {
                             // secondary: same place, spin from P0, isotropic
-                            const uint4 y = philox_rk(make_uint4(id_lo, ctr_y, a.step, SUB_SEC), a);
+                            const uint4 y = philox_rk(make_uint4(id_lo, ctr_y, step, SUB_SEC), a);
                             const uint32_t g0 = (pk >> 13) & 0xFFu;
                             const int sgs = y.x < S.p0[layer] ? 0 : 1;
                             const uint32_t gen = g0 < 255u ? g0 + 1u : 255u;
@@ -1084,7 +1099,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
                             TabEnt es = S.ent[(ls * 2 + sgs) * S.n_e + (ks - 1)];
                             Tally ts{};
                             flight<DET>(a, S, zs, mus, ls, es, los, his, sgs, ks, half, id_lo,
-                                        ctr_y, SUB_SIF, ts);
+                                        ctr_y, step, SUB_SIF, ts);
                             // the secondary's boundary events ride in the (not yet
                             // used) id_hi bits until it is placed
                             const uint32_t pks = (uint32_t)ks | ((uint32_t)sgs << 8) |
@@ -1107,7 +1122,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
                 if (ADJ) rw = flux_w(a, s, tj, sg, c_start, c_end);
             } else {
                 flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
-                                      SUB_IF + 16, ty, Rd, s_gT);
+                                      step, SUB_IF + 16, ty, Rd, s_gT);
                 const int c_end = cell_of(a, S, z);
                 if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
                 pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
@@ -1254,6 +1269,7 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
         if (tid == 0) {
             a.ctl->done = 0u;
             a.ctl->epoch = ep + 1u;
+            bump_step(a);
         }
     }
 }
@@ -1269,7 +1285,8 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
     __shared__ unsigned long long s_q[PIC_MAX_STACKS];
     __shared__ int s_flag;
     const int tid = threadIdx.x;
-    const long long h = 2 * (long long)a.step + half;
+    const uint32_t step = step_now(a);
+    const long long h = 2 * (long long)step + half;
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
     for (int s = tid; s < a.n_stacks; s += TPB) {
         const DevStack &st = a.stacks[s];
@@ -1286,7 +1303,7 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
     }
     __syncthreads();
     const long long total = s_pref[a.n_stacks];
-    const int tout = (int)((a.step + 1) / (uint32_t)a.moment_every) - 1;
+    const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
     for (long long gidx = (long long)blockIdx.x * TPB + tid; gidx < total;
          gidx += (long long)gridDim.x * TPB) {
         const int s = stack_of(s_pref, a.n_stacks, gidx);
@@ -1294,8 +1311,8 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
         const DevStack &st = a.stacks[s];
         const unsigned long long id = a.cnt[s].next_id + (unsigned long long)j;
         const uint32_t cy = (uint32_t)(id >> 32) | ((uint32_t)s << 16);
-        const uint4 r0 = philox_rk(make_uint4((uint32_t)id, cy, a.step, SUB_INJ + 0), a);
-        const uint4 r1 = philox_rk(make_uint4((uint32_t)id, cy, a.step, SUB_INJ + 1), a);
+        const uint4 r0 = philox_rk(make_uint4((uint32_t)id, cy, step, SUB_INJ + 0), a);
+        const uint4 r1 = philox_rk(make_uint4((uint32_t)id, cy, step, SUB_INJ + 1), a);
         int i = 0;
         const uint32_t *thr = a.cdf_thr + st.cdf_off;
         while (i < st.n_cdf - 1 && !(r0.x < thr[i])) ++i;
@@ -1348,7 +1365,10 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
             if (n > kept && (a.flags & PIC_F_STRICT_CAPACITY))
                 atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
         }
-        if (tid == 0) a.ctl->done = 0u;
+        if (tid == 0) {
+            a.ctl->done = 0u;
+            bump_step(a);
+        }
     }
 }
 
