@@ -289,6 +289,28 @@ pic_status pic_compact_static(const float *z, const float *mu, const uint32_t *i
 /* The launch configuration of a context's kernels. */
 pic_status pic_launch_config(const pic_ctx *ctx, pic_launch_info *out);
 
+/* One candidate launch configuration timed by pic_autotune. */
+typedef struct {
+    int32_t blocks_per_sm;  /* resident blocks per SM of the streaming pass */
+    int32_t ring_stages;    /* its bulk-copy ring depth */
+    int32_t hist_mode;      /* density deposit: 0 shared atomics, 1 warp-aggregated */
+    int32_t chosen;         /* 1 for the configuration the context keeps */
+    double ns_per_particle_step;  /* device time of the trial / carriers advanced */
+} pic_tune_entry;
+
+/* Time candidate launch configurations of the step kernels on the running
+ * simulation and keep the fastest.  Each candidate advances every stack by
+ * trial_steps ordinary steps (results do not depend on the launch
+ * configuration: the slot order and every random word are fixed by the
+ * run), timed with CUDA events on the context stream and divided by the
+ * carriers advanced.  Candidates: 1, 2 or 3 resident blocks per SM, ring
+ * depth 2, 3, 4, 6 or 8 where it fits, and both deposit modes when the
+ * trial contains density steps.  entries (host, may be NULL): up to
+ * max_entries results in the order tried; *n_entries (may be NULL): their
+ * number.  Needs steps left: up to 30 * trial_steps.  Synchronises. */
+pic_status pic_autotune(pic_ctx *ctx, int trial_steps, pic_tune_entry *entries,
+                        int max_entries, int *n_entries);
+
 /* Device kernels launched by the last pic_step call (for accounting). */
 int64_t pic_launch_count(const pic_ctx *ctx);
 

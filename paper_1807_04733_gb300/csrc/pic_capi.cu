@@ -81,6 +81,7 @@ struct pic_ctx {
     DevCounters *d_cnt = nullptr;
     DevCtl *d_ctl = nullptr;
     int64_t total_slots = 0, nh_total = 0, J_total = 0;
+    int n_status = 0;                // look-back words and queue counts allocated
     Args args{};
     LaunchCfg lc{};
     int step = 0;
@@ -569,6 +570,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     }
     const int gmax = std::max({c->lc.grid_fast, c->lc.grid_fast_dep, c->lc.grid_slow,
                                c->lc.grid_slow_dep, c->lc.grid_compact});
+    c->n_status = gmax;
     if (dalloc(&c->d_status, (size_t)gmax) != cudaSuccess ||
         dalloc(&c->d_qcnt, (size_t)gmax) != cudaSuccess) {
         g_init_error = "device allocation of the look-back words";
@@ -1178,6 +1180,104 @@ pic_status pic_launch_config(const pic_ctx *c, pic_launch_info *out)
         out->ring_adj_step[i] = r ? c->rp.lc[i].ring_fast_dep : 0;
         out->smem_adj_step[i] = r ? (int64_t)c->rp.lc[i].smem_fast_dep : 0;
     }
+    return PIC_OK;
+}
+
+pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, int max_entries,
+                        int *n_entries)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (trial_steps < 1) return fail(c, PIC_ERR_ARG, "pic_autotune: trial_steps < 1");
+    if (c->profiling) return fail(c, PIC_ERR_STATE, "pic_autotune: profiling is on");
+    struct Cand { int bps, ring, hm; };
+    std::vector<Cand> cands;
+    const bool dep_in_trial = trial_steps >= c->p.moment_every;
+    for (int hm = 0; hm <= (dep_in_trial ? 1 : 0); ++hm)
+        for (int bps = 1; bps <= 3; ++bps)
+            for (int ring : {2, 3, 4, 6, 8}) cands.push_back({bps, ring, hm});
+    if ((int64_t)c->step + (int64_t)trial_steps * (int64_t)cands.size() > c->p.n_steps_max)
+        return fail(c, PIC_ERR_ARG, "pic_autotune: not enough steps left for the trials");
+    const int use_graph = c->p.use_graph;
+    c->p.use_graph = 0;                       // trials use single launches
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    auto steps_done = [&](uint64_t &ps) {
+        std::vector<DevCounters> h(c->n_stacks);
+        cudaError_t r = cudaMemcpyAsync(h.data(), c->d_cnt, sizeof(DevCounters) * c->n_stacks,
+                                        cudaMemcpyDeviceToHost, c->stream);
+        if (r == cudaSuccess) r = cudaStreamSynchronize(c->stream);
+        ps = 0;
+        for (const DevCounters &x : h) ps += x.led[L_PARTICLE_STEPS];
+        return r;
+    };
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const LaunchCfg keep = c->lc;
+    const pic_params keep_p = c->p;
+    double best = 0.0;
+    LaunchCfg best_lc = keep;
+    Cand best_c{keep_p.blocks_per_sm, keep_p.ring_stages, keep_p.hist_mode};
+    std::vector<pic_tune_entry> res;
+    for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
+        const Cand &k = cands[i];
+        LaunchCfg lc{};
+        if (configure(c->args, k.bps, k.ring, k.hm, &lc) != cudaSuccess) {
+            cudaGetLastError();               // does not fit: not a candidate
+            continue;
+        }
+        const int gmax = std::max({lc.grid_fast, lc.grid_fast_dep, lc.grid_slow,
+                                   lc.grid_slow_dep, lc.grid_compact});
+        // a candidate whose ring leaves fewer resident blocks than asked for
+        // is another candidate's duplicate
+        if (gmax > c->n_status || lc.ring_fast != k.ring || lc.grid_fast != sms * k.bps ||
+            lc.grid_fast_dep == 0)
+            continue;
+        c->lc = lc;
+        c->p.hist_mode = k.hm;
+        uint64_t ps0 = 0, ps1 = 0;
+        e = steps_done(ps0);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[0], c->stream);
+        if (e != cudaSuccess) break;
+        const pic_status st = pic_step(c, trial_steps);
+        if (st != PIC_OK) { c->lc = keep; c->p = keep_p; c->p.use_graph = use_graph; return st; }
+        e = cudaEventRecord(ev[1], c->stream);
+        if (e == cudaSuccess) e = steps_done(ps1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (e != cudaSuccess) break;
+        const double ns = ps1 > ps0 ? 1e6 * (double)ms / (double)(ps1 - ps0) : 1e30;
+        res.push_back(pic_tune_entry{k.bps, k.ring, k.hm, 0, ns});
+        if (res.size() == 1 || ns < best) {
+            best = ns;
+            best_lc = lc;
+            best_c = k;
+        }
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    c->p = keep_p;
+    c->p.use_graph = use_graph;
+    if (e != cudaSuccess) {
+        c->lc = keep;
+        return cuda_fail(c, e, "pic_autotune");
+    }
+    c->lc = best_lc;
+    c->p.blocks_per_sm = best_c.bps;
+    c->p.ring_stages = best_c.ring;
+    c->p.hist_mode = best_c.hm;
+    // graphs captured with the old configuration are stale
+    for (cudaGraphExec_t &g : c->period_graph) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+    for (pic_tune_entry &r : res)
+        r.chosen = (r.blocks_per_sm == best_c.bps && r.ring_stages == best_c.ring &&
+                    r.hist_mode == best_c.hm) ? 1 : 0;
+    if (entries)
+        for (int i = 0; i < (int)res.size() && i < max_entries; ++i) entries[i] = res[i];
+    if (n_entries) *n_entries = (int)res.size();
     return PIC_OK;
 }
 

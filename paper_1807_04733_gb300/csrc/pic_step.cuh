@@ -65,10 +65,13 @@ __device__ __forceinline__ float unit_of(uint32_t x)
 }
 
 // The time-step index: the kernel argument, or (steps replayed from a CUDA
-// graph) the device counter that the last kernel of every step advances.
+// graph) the device counter that the last kernel of every step advances; it
+// changes only between kernels, so a plain L2 load reads it.  (A volatile
+// access here made the compiler copy the whole argument block to local
+// memory.)
 __device__ __forceinline__ uint32_t step_now(const Args &a)
 {
-    return a.step_dev ? *(volatile const unsigned int *)a.step_dev : a.step;
+    return a.step_dev ? __ldcg(a.step_dev) : a.step;
 }
 
 // advance the device step counter (last block of the step's last kernel)

@@ -33,7 +33,7 @@ REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u
 EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_grad", "pic_records",
            "pic_set_records", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
            "pic_profile_read", "pic_compact_static", "pic_launch_config", "pic_launch_count",
-           "pic_destroy", "pic_last_error", "pic_status_string")
+           "pic_destroy", "pic_last_error", "pic_status_string", "pic_autotune")
 KERNEL_KINDS = ("inject", "step", "step_moments", "compact", "step_events", "adjoint_step",
                 "adjoint_events", "adjoint_other")
 
@@ -87,6 +87,16 @@ class pic_launch_info(C.Structure):
         return out
 
 
+class pic_tune_entry(C.Structure):
+    _fields_ = [("blocks_per_sm", C.c_int32), ("ring_stages", C.c_int32),
+                ("hist_mode", C.c_int32), ("chosen", C.c_int32),
+                ("ns_per_particle_step", C.c_double)]
+
+    def as_dict(self):
+        return {n: (float(getattr(self, n)) if n.startswith("ns") else int(getattr(self, n)))
+                for n, _ in self._fields_}
+
+
 class pic_kernel_times(C.Structure):
     _fields_ = [("launches", C.c_int64 * len(KERNEL_KINDS)), ("ms", C.c_double * len(KERNEL_KINDS))]
 
@@ -128,6 +138,8 @@ def lib():
         L.pic_compact_static.argtypes = [P, P, P, P, C.c_int64, P, P, P, P,
                                          C.POINTER(C.c_int64), P]
         L.pic_launch_config.argtypes = [P, C.POINTER(pic_launch_info)]
+        L.pic_autotune.argtypes = [P, C.c_int, C.POINTER(pic_tune_entry), C.c_int,
+                                   C.POINTER(C.c_int)]
         L.pic_launch_count.argtypes = [P]
         L.pic_launch_count.restype = C.c_int64
         L.pic_destroy.argtypes = [P]
@@ -287,6 +299,13 @@ def pic_launch_config(ctx):
     return info.as_dict()
 
 
+def pic_autotune(ctx, trial_steps, max_entries=64):
+    buf = (pic_tune_entry * max_entries)()
+    n = C.c_int(0)
+    _check(lib().pic_autotune(ctx, trial_steps, buf, max_entries, C.byref(n)), ctx)
+    return [buf[i].as_dict() for i in range(min(n.value, max_entries))]
+
+
 def pic_launch_count(ctx):
     return int(lib().pic_launch_count(ctx))
 
@@ -378,6 +397,11 @@ class Context:
     @property
     def launches(self):
         return pic_launch_count(self.ctx)
+
+    def autotune(self, trial_steps):
+        """Time candidate launch configurations on the next steps of the run
+        and keep the fastest; returns the trials (pic_autotune)."""
+        return pic_autotune(self.ctx, trial_steps)
 
     # ---- adjoint ----
     @property
