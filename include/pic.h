@@ -303,11 +303,11 @@ typedef struct {
  * trial_steps ordinary steps (results do not depend on the launch
  * configuration: the slot order and every random word are fixed by the
  * run), timed with CUDA events on the context stream and divided by the
- * carriers advanced.  Candidates: 1, 2 or 3 resident blocks per SM, ring
+ * carriers advanced.  Candidates: 1 to 4 resident blocks per SM, ring
  * depth 2, 3, 4, 6 or 8 where it fits, and both deposit modes when the
  * trial contains density steps.  entries (host, may be NULL): up to
  * max_entries results in the order tried; *n_entries (may be NULL): their
- * number.  Needs steps left: up to 30 * trial_steps.  Synchronises. */
+ * number.  Needs steps left: up to 40 * trial_steps.  Synchronises. */
 pic_status pic_autotune(pic_ctx *ctx, int trial_steps, pic_tune_entry *entries,
                         int max_entries, int *n_entries);
 

@@ -90,6 +90,7 @@ def lib():
         L.or_philox4x32_10.argtypes = [P, P, P]
         L.or_grad.argtypes = [C.POINTER(_Config), P, C.c_int64, C.c_uint64, C.c_int,
                               P, P, P, P, P, P]
+        L.or_advance_one.argtypes = [P, P, C.c_int64, C.c_int, P, P]
         _lib = L
     return _lib
 
@@ -213,6 +214,16 @@ class OracleSim:
         if rc:
             raise ValueError("or_grad failed with code %d" % rc)
         return g_tau, g_T, m_tau, m_T
+
+    def advance_one(self, rec, slot: int, room: bool = True):
+        """One carrier (a REC_DTYPE record) in slot `slot` advanced by one step
+        at the current step index: (record after the step, secondary or None)."""
+        inp = np.ascontiguousarray(np.asarray(rec, REC_DTYPE).reshape(1))
+        out = np.zeros(1, REC_DTYPE)
+        sec = np.zeros(1, REC_DTYPE)
+        made = lib().or_advance_one(self.h, inp.ctypes.data, slot, 1 if room else 0,
+                                    out.ctypes.data, sec.ctypes.data)
+        return out[0], (sec[0] if made else None)
 
     def set_step(self, step: int):
         lib().or_set_step(self.h, step)

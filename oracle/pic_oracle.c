@@ -358,15 +358,13 @@ static void absorb(or_sim *s, or_rec *p)
     s->led.q_bath += 1;
 }
 
-static void step_once(or_sim *s)
+/* Transport(dt/2) -> Scattering(dt) -> Transport(dt/2) of the live carrier
+ * p that sits in slot i; a secondary is appended to the slots. */
+static void advance(or_sim *s, or_rec *p, int64_t i)
 {
     const or_config *c = &s->cfg;
     const float half = c->dt * 0.5f;
-    inject(s, 0);
-    int64_t n_start = s->n_slots;
-    for (int64_t i = 0; i < n_start; ++i) {
-        or_rec *p = &s->recs[i];
-        if (PK_K(p->packed) == 0) continue;
+    {
         s->led.particle_steps++;
         uint64_t id = (uint64_t)p->id | ((uint64_t)PK_E(p->packed) << 32);
         const float mu_in = p->mu;
@@ -409,7 +407,7 @@ static void step_once(or_sim *s)
                 flux(s, sg, c_start, cell_of(s, p->z));
                 if (A) credit(s, id, flux_reward(s, sg, c_start, cell_of(s, p->z)));
                 s->led.changed++;
-                continue;
+                return;
             }
             p->mu = mu_from(x[2]);
             if (inel) {
@@ -479,6 +477,18 @@ static void step_once(or_sim *s)
         flux(s, sg, c_start, cell_of(s, p->z));
         if (A) credit(s, id, flux_reward(s, sg, c_start, cell_of(s, p->z)));
         if (p->mu != mu_in || p->packed != pk_in) s->led.changed++;
+    }
+}
+
+static void step_once(or_sim *s)
+{
+    const or_config *c = &s->cfg;
+    inject(s, 0);
+    int64_t n_start = s->n_slots;
+    for (int64_t i = 0; i < n_start; ++i) {
+        or_rec *p = &s->recs[i];
+        if (PK_K(p->packed) == 0) continue;
+        advance(s, p, i);
     }
     inject(s, 1);
 
@@ -760,4 +770,24 @@ int or_grad(const or_config *cfg, const or_rec *init, int64_t n_init, uint64_t n
     free(A.g_tau); free(A.m_tau); free(A.g_T); free(A.m_T);
     free(A.own); free(A.acc); free(A.parent);
     return rc;
+}
+
+int or_advance_one(or_sim *s, const or_rec *in, int64_t slot, int room, or_rec *out, or_rec *sec)
+{
+    or_rec p = *in;
+    int64_t keep_n = s->n_slots, keep_cap = s->cfg.capacity;
+    uint64_t keep_id = s->next_id;
+    s->n_slots = 0;
+    s->cfg.capacity = room ? 1 : 0;
+    int made = 0;
+    if (PK_K(p.packed) != 0) {
+        advance(s, &p, slot);
+        made = s->n_slots == 1;
+        if (made && sec) *sec = s->recs[0];
+    }
+    s->n_slots = keep_n;
+    s->cfg.capacity = keep_cap;
+    s->next_id = keep_id;
+    if (out) *out = p;
+    return made;
 }

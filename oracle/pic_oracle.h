@@ -91,6 +91,14 @@ void or_tables(const or_sim *s, uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_th
                uint32_t *P0_thr, uint32_t *up_thr, int64_t *inj_counts);
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
+/* One carrier in slot `slot` advanced by one step (at the sim's step index,
+ * or_set_step) on its own: *out receives its record; if it creates a
+ * secondary and room != 0, *sec receives the secondary (its id fields are
+ * not meaningful; the id counter is left untouched) and 1 is returned.  Densities are not deposited;
+ * fluxes and the ledger of the sim are updated.  The sim's own records are
+ * left as they were (needs capacity >= 1). */
+int or_advance_one(or_sim *s, const or_rec *in, int64_t slot, int room, or_rec *out, or_rec *sec);
+
 /* Score-function gradient of O = sum gn*n + sum gJ*J (gn: [n_out][2][n_e]
  * [n_cells], gJ: [n_out][2][n_cells+1], the moment layouts) over n_steps
  * steps from the initial records (ids below next_id), with respect to

@@ -146,11 +146,15 @@ cudaError_t configure_pass(const Args &a, LaunchCfg *cfg)
         return e;
     cfg->grid_fast = sms * o_plain;
     cfg->grid_fast_dep = sms * o_dep;
-    const size_t slow = (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.T_max * 4 + 8 +
-                        (ADJ == 2 ? (size_t)(a.tab_max + a.T_max) * 8 : 0) + 4 + tiles;
-    cfg->smem_slow = cfg->smem_slow_dep = slow;
-    if ((e = slow_cfg<false, ADJ>(slow, &cfg->grid_slow, sms)) != cudaSuccess) return e;
-    if ((e = slow_cfg<true, ADJ>(slow, &cfg->grid_slow_dep, sms)) != cudaSuccess) return e;
+    const int gf_max = cfg->grid_fast > cfg->grid_fast_dep ? cfg->grid_fast : cfg->grid_fast_dep;
+    cfg->smem_slow = event_smem(a, false, ADJ, gf_max);
+    cfg->smem_slow_dep = event_smem(a, true, ADJ, gf_max);
+    if ((e = event_cfg<false, ADJ>(cfg->smem_slow, &cfg->grid_slow, sms)) != cudaSuccess) return e;
+    if ((e = event_cfg<true, ADJ>(cfg->smem_slow_dep, &cfg->grid_slow_dep, sms)) != cudaSuccess) return e;
+    cfg->smem_place = place_smem(a, false, ADJ);
+    cfg->smem_place_dep = place_smem(a, true, ADJ);
+    if ((e = place_cfg<false, ADJ>(cfg->smem_place, &cfg->grid_place, sms)) != cudaSuccess) return e;
+    if ((e = place_cfg<true, ADJ>(cfg->smem_place_dep, &cfg->grid_place_dep, sms)) != cudaSuccess) return e;
     int oc = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_compact<ADJ>, TPB, 0)) != cudaSuccess)
         return e;
@@ -178,12 +182,14 @@ void slow_pass(const Args &a, const LaunchCfg &c, bool det, bool dep, cudaStream
 {
     const int g = dep ? c.grid_slow_dep : c.grid_slow;
     const size_t sm = dep ? c.smem_slow_dep : c.smem_slow;
+    const int gp = dep ? c.grid_place_dep : c.grid_place;
+    const size_t smp = dep ? c.smem_place_dep : c.smem_place;
     if (det) {
-        if (dep) k_slow<true, true, ADJ><<<g, TPB, sm, s>>>(a);
-        else k_slow<true, false, ADJ><<<g, TPB, sm, s>>>(a);
+        if (dep) { k_event<true, true, ADJ><<<g, TPB, sm, s>>>(a); k_place<true, true, ADJ><<<gp, TPB, smp, s>>>(a); }
+        else { k_event<true, false, ADJ><<<g, TPB, sm, s>>>(a); k_place<true, false, ADJ><<<gp, TPB, smp, s>>>(a); }
     } else {
-        if (dep) k_slow<false, true, ADJ><<<g, TPB, sm, s>>>(a);
-        else k_slow<false, false, ADJ><<<g, TPB, sm, s>>>(a);
+        if (dep) { k_event<false, true, ADJ><<<g, TPB, sm, s>>>(a); k_place<false, true, ADJ><<<gp, TPB, smp, s>>>(a); }
+        else { k_event<false, false, ADJ><<<g, TPB, sm, s>>>(a); k_place<false, false, ADJ><<<gp, TPB, smp, s>>>(a); }
     }
 }
 

@@ -39,7 +39,7 @@ struct Replay {
     long long *acc[2] = {nullptr, nullptr};
     uint32_t *stage_l = nullptr;
     unsigned long long *status = nullptr;
-    uint32_t *qcnt = nullptr;
+    uint32_t *qcnt = nullptr, *fspawn = nullptr;
     DevCounters *cnt = nullptr;
     DevCtl *ctl = nullptr;
     DevStack *stacks = nullptr;
@@ -74,7 +74,7 @@ struct pic_ctx {
     float *d_z[2] = {nullptr, nullptr}, *d_mu[2] = {nullptr, nullptr};
     uint32_t *d_id[2] = {nullptr, nullptr}, *d_pk[2] = {nullptr, nullptr};
     float4 *d_stage = nullptr, *d_qrec = nullptr;
-    uint32_t *d_bits = nullptr, *d_qcnt = nullptr;
+    uint32_t *d_bits = nullptr, *d_qcnt = nullptr, *d_fspawn = nullptr;
     unsigned long long *d_status = nullptr;
     uint32_t *d_nh = nullptr;
     int32_t *d_J = nullptr;
@@ -308,13 +308,13 @@ void free_all(pic_ctx *c)
         release(c->d_z[b]); release(c->d_mu[b]); release(c->d_id[b]); release(c->d_pk[b]);
     }
     release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh);
-    release(c->d_qrec); release(c->d_qcnt); release(c->d_J); release(c->d_cnt);
+    release(c->d_qrec); release(c->d_qcnt); release(c->d_fspawn); release(c->d_J); release(c->d_cnt);
     release(c->d_ctl);
     Replay &r = c->rp;
     for (int b = 0; b < 2; ++b) {
         release(r.z[b]); release(r.mu[b]); release(r.id[b]); release(r.pk[b]); release(r.acc[b]);
     }
-    release(r.stage_l); release(r.status); release(r.qcnt); release(r.cnt); release(r.ctl); release(r.stacks);
+    release(r.stage_l); release(r.status); release(r.qcnt); release(r.fspawn); release(r.cnt); release(r.ctl); release(r.stacks);
     release(r.aent); release(r.aT); release(r.g_ent); release(r.g_T); release(r.gpot);
     release(r.gen_max); release(r.absmax); release(r.qgn); release(r.tot); release(r.parent);
     release(r.gen);
@@ -569,10 +569,12 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         return PIC_ERR_ARG;   // moment grid too large for shared memory, or no device
     }
     const int gmax = std::max({c->lc.grid_fast, c->lc.grid_fast_dep, c->lc.grid_slow,
-                               c->lc.grid_slow_dep, c->lc.grid_compact});
+                               c->lc.grid_slow_dep, c->lc.grid_place, c->lc.grid_place_dep,
+                               c->lc.grid_compact});
     c->n_status = gmax;
     if (dalloc(&c->d_status, (size_t)gmax) != cudaSuccess ||
-        dalloc(&c->d_qcnt, (size_t)gmax) != cudaSuccess) {
+        dalloc(&c->d_qcnt, (size_t)gmax) != cudaSuccess ||
+        dalloc(&c->d_fspawn, (size_t)gmax) != cudaSuccess) {
         g_init_error = "device allocation of the look-back words";
         free_all(c);
         delete c;
@@ -581,6 +583,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     }
     a.status = c->d_status;
     a.qcnt = c->d_qcnt;
+    a.fspawn = c->d_fspawn;
 
     cudaStream_t st = c->stream;
     DevCtl ctl{};
@@ -593,6 +596,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     if (e == cudaSuccess && !Tall.empty()) e = cudaMemcpyAsync(c->d_T, Tall.data(), 4 * Tall.size(), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_inj, 0, sizeof(long long) * std::max<size_t>((size_t)n_stacks * 2 * p->n_steps_max, 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned long long) * gmax, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_fspawn, 0, sizeof(uint32_t) * gmax, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bits, 0, 4 * (size_t)(c->total_slots / 32 + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_nh, 0, 4 * (size_t)std::max<int64_t>(c->nh_total, 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_J, 0, 4 * (size_t)std::max<int64_t>(c->J_total, 1), st);
@@ -939,10 +943,13 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
             r.n_status = 1;
             for (const LaunchCfg &l : r.lc)
                 r.n_status = std::max({r.n_status, l.grid_fast, l.grid_fast_dep, l.grid_slow,
-                                       l.grid_slow_dep, l.grid_compact});
+                                       l.grid_slow_dep, l.grid_place, l.grid_place_dep,
+                                       l.grid_compact});
         }
         RALLOC(r.status, (size_t)r.n_status);
         RALLOC(r.qcnt, (size_t)r.n_status);
+        RALLOC(r.fspawn, (size_t)r.n_status);
+        if (e == cudaSuccess) e = cudaMemsetAsync(r.fspawn, 0, sizeof(uint32_t) * r.n_status, st);
         // d log P / d tau_in of each outcome per (layer, spin, k), with rates
         // r_in = 1/tau_in, r_el = 1/tau_el, r = r_in + r_el, p = 1 - e^{-dt r}
         // and d r_in / d tau_in = -r_in^2; d log P / d T per interface entry
@@ -999,6 +1006,7 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
         a.acc[b] = r.acc[b];
     }
     a.stacks = r.stacks; a.cnt = r.cnt; a.ctl = r.ctl; a.status = r.status; a.qcnt = r.qcnt;
+    a.fspawn = r.fspawn;
     a.n_hist = nullptr; a.J_hist = nullptr;
     a.tot = r.tot; a.parent = r.parent; a.gen = r.gen; a.gen_max = r.gen_max;
     a.aent = r.aent; a.aT = r.aT; a.g_ent = r.g_ent; a.g_T = r.g_T;
@@ -1193,7 +1201,7 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
     std::vector<Cand> cands;
     const bool dep_in_trial = trial_steps >= c->p.moment_every;
     for (int hm = 0; hm <= (dep_in_trial ? 1 : 0); ++hm)
-        for (int bps = 1; bps <= 3; ++bps)
+        for (int bps = 1; bps <= 4; ++bps)
             for (int ring : {2, 3, 4, 6, 8}) cands.push_back({bps, ring, hm});
     if ((int64_t)c->step + (int64_t)trial_steps * (int64_t)cands.size() > c->p.n_steps_max)
         return fail(c, PIC_ERR_ARG, "pic_autotune: not enough steps left for the trials");
@@ -1228,7 +1236,8 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
             continue;
         }
         const int gmax = std::max({lc.grid_fast, lc.grid_fast_dep, lc.grid_slow,
-                                   lc.grid_slow_dep, lc.grid_compact});
+                                   lc.grid_slow_dep, lc.grid_place, lc.grid_place_dep,
+                                   lc.grid_compact});
         // a candidate whose ring leaves fewer resident blocks than asked for
         // is another candidate's duplicate
         if (gmax > c->n_status || lc.ring_fast != k.ring || lc.grid_fast != sms * k.bps ||

@@ -123,10 +123,11 @@ struct Args {            // everything a kernel needs, passed by value
     int tab_max, T_max, nbin_max, jbin_max;  // shared-memory sizing
     unsigned int spin_limit;                 // bound of every device-side wait
     int ring;                                // tiles in k_fast's copy ring
-    int grid_fast;                           // k_fast's grid (read by k_slow)
+    int grid_fast;                           // k_fast's grid (read by k_event, k_place)
     uint32_t *spawn_bits;                    // one bit per position: secondary staged
     float4 *qrec;                            // eventful carriers: z, mu, packed, position
     uint32_t *qcnt;                          // queue length per fast block
+    uint32_t *fspawn;                        // secondaries staged per fast block
     // adjoint replay (ADJ = 1, 2); unused by the forward step.  Rewards are
     // fixed-point integers in units of 2^-F (the weights quantised to int32):
     // sums are exact and independent of their order.
@@ -153,9 +154,12 @@ void pic_set_static_error(const char *msg);
 
 // host-side launchers (pic_kernels.cu)
 struct LaunchCfg {
-    int grid_fast, grid_fast_dep, grid_slow, grid_slow_dep, grid_compact, grid_inject;
+    int grid_fast, grid_fast_dep;          // k_fast (without / with density deposit)
+    int grid_slow, grid_slow_dep;          // k_event
+    int grid_place, grid_place_dep;        // k_place
+    int grid_compact, grid_inject;
     int ring_fast, ring_fast_dep;
-    size_t smem_fast, smem_fast_dep, smem_slow, smem_slow_dep;
+    size_t smem_fast, smem_fast_dep, smem_slow, smem_slow_dep, smem_place, smem_place_dep;
 };
 cudaError_t configure(const Args &a, int blocks_per_sm, int ring, int hist_mode, LaunchCfg *cfg);
 cudaError_t launch_inject(const Args &a, const LaunchCfg &c, int half, bool deposit,

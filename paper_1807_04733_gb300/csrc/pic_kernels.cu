@@ -32,12 +32,15 @@ cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_m
     if (e != cudaSuccess) return e;
     cfg->grid_fast = sms * o_plain;
     cfg->grid_fast_dep = sms * o_dep;
-    const size_t slow = (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.T_max * 4 +
-                        (size_t)a.jbin_max * 4 + 4 + tiles;
-    cfg->smem_slow = slow;
-    cfg->smem_slow_dep = slow + (size_t)a.nbin_max * 4;
-    if ((e = slow_cfg<false>(cfg->smem_slow, &cfg->grid_slow, sms)) != cudaSuccess) return e;
-    if ((e = slow_cfg<true>(cfg->smem_slow_dep, &cfg->grid_slow_dep, sms)) != cudaSuccess) return e;
+    const int gf_max = cfg->grid_fast > cfg->grid_fast_dep ? cfg->grid_fast : cfg->grid_fast_dep;
+    cfg->smem_slow = event_smem(a, false, 0, gf_max);
+    cfg->smem_slow_dep = event_smem(a, true, 0, gf_max);
+    if ((e = event_cfg<false>(cfg->smem_slow, &cfg->grid_slow, sms)) != cudaSuccess) return e;
+    if ((e = event_cfg<true>(cfg->smem_slow_dep, &cfg->grid_slow_dep, sms)) != cudaSuccess) return e;
+    cfg->smem_place = place_smem(a, false, 0);
+    cfg->smem_place_dep = place_smem(a, true, 0);
+    if ((e = place_cfg<false>(cfg->smem_place, &cfg->grid_place, sms)) != cudaSuccess) return e;
+    if ((e = place_cfg<true>(cfg->smem_place_dep, &cfg->grid_place_dep, sms)) != cudaSuccess) return e;
     int oc = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_compact<0>, TPB, 0)) != cudaSuccess)
         return e;
@@ -78,12 +81,16 @@ cudaError_t launch_slow(const Args &a0, const LaunchCfg &c, bool det, bool dep, 
     a.grid_fast = dep ? c.grid_fast_dep : c.grid_fast;
     const int g = dep ? c.grid_slow_dep : c.grid_slow;
     const size_t sm = dep ? c.smem_slow_dep : c.smem_slow;
+    const int gp = dep ? c.grid_place_dep : c.grid_place;
+    const size_t smp = dep ? c.smem_place_dep : c.smem_place;
+    Args ae = a;
+    ae.bump_step = 0;                    // the placement pass ends the step
     if (det) {
-        if (dep) k_slow<true, true><<<g, TPB, sm, s>>>(a);
-        else k_slow<true, false><<<g, TPB, sm, s>>>(a);
+        if (dep) { k_event<true, true><<<g, TPB, sm, s>>>(ae); k_place<true, true><<<gp, TPB, smp, s>>>(a); }
+        else { k_event<true, false><<<g, TPB, sm, s>>>(ae); k_place<true, false><<<gp, TPB, smp, s>>>(a); }
     } else {
-        if (dep) k_slow<false, true><<<g, TPB, sm, s>>>(a);
-        else k_slow<false, false><<<g, TPB, sm, s>>>(a);
+        if (dep) { k_event<false, true><<<g, TPB, sm, s>>>(ae); k_place<false, true><<<gp, TPB, smp, s>>>(a); }
+        else { k_event<false, false><<<g, TPB, sm, s>>>(ae); k_place<false, false><<<gp, TPB, smp, s>>>(a); }
     }
     return cudaGetLastError();
 }

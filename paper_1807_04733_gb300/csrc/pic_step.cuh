@@ -7,8 +7,9 @@
 //   k_fast             Transport(dt/2) -> Scattering(dt) -> Transport(dt/2)
 //                      for every carrier that neither scatters nor meets a
 //                      boundary in the step; the others are queued
-//   k_slow             the general step for the queued carriers, and the
-//                      placement of the secondaries in parent slot order
+//   k_event            the general step for the queued carriers; secondaries
+//                      staged at their parents' positions
+//   k_place            slots and ids of the secondaries, in parent slot order
 //   k_inject(half 1)   Source(dt/2), deposited at moment steps
 //   k_compact          every compact_every steps: stable removal of dead slots
 //
@@ -403,8 +404,8 @@ __device__ __forceinline__ long long chunk_lo(long long T, int j, int G)
     return T * j / G;
 }
 
-// Tiles of slow block j: the union of the chunks of the fast blocks
-// [Gf*j/Gs, Gf*(j+1)/Gs), so that it covers whole fast chunks.
+// Tiles of placement block j: the union of the chunks of the streaming
+// blocks [Gf*j/Gs, Gf*(j+1)/Gs), so that it covers whole streaming chunks.
 __device__ __forceinline__ long long slow_lo(long long T, int j, int Gs, int Gf)
 {
     return chunk_lo(T, (int)((long long)Gf * j / Gs), Gf);
@@ -413,7 +414,7 @@ __device__ __forceinline__ long long slow_lo(long long T, int j, int Gs, int Gf)
 // Exclusive prefix of the secondaries of the stack segment that starts slow
 // block b's chunk (stack tiles start at ts): walk back over the blocks whose
 // chunks end inside the same stack.  Bounded wait.
-static __device__ long long look_back_slow(const Args &a, unsigned int ep, long long T, long long ts,
+static __device__ long long look_back_place(const Args &a, unsigned int ep, long long T, long long ts,
                                     int b, int Gs, int Gf)
 {
     long long prefix = 0;
@@ -470,7 +471,7 @@ __device__ __forceinline__ long long make_tiles(const Args &a, long long *s_tpre
 // scatter and stays inside its layer for the whole step is finished here
 // (new depth, flux across the face it passed, density deposit).  Every other
 // carrier ("eventful": it scatters or meets a boundary) is copied, with its
-// position, to this block's region of the queue, in tile order, for k_slow.
+// position, to this block's region of the queue, in tile order, for k_event.
 // ---------------------------------------------------------------------------
 constexpr int FAST_WARPS = TPB / 32;             // consumer warps
 constexpr int FAST_THREADS = TPB + 32;           // + the producer warp
@@ -500,11 +501,18 @@ __device__ __forceinline__ unsigned long long consumer_sum_u64(unsigned long lon
     return t;  // valid in thread 0
 }
 
+// Resident blocks per SM the register budget must allow: four for the step
+// (56 registers, no spills: 36 warps per SM), three for the replay passes,
+// which carry the per-slot reward as well.
 #ifndef PIC_FAST_MIN_BLOCKS
-#define PIC_FAST_MIN_BLOCKS 3      // resident blocks per SM the register budget allows
+#define PIC_FAST_MIN_BLOCKS 4
+#endif
+#ifndef PIC_FAST_MIN_BLOCKS_ADJ
+#define PIC_FAST_MIN_BLOCKS_ADJ 3
 #endif
 template <bool DET, bool DEPN, bool WAGG, int ADJ = 0>
-__global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(const Args a)
+__global__ void __launch_bounds__(FAST_THREADS, ADJ ? PIC_FAST_MIN_BLOCKS_ADJ : PIC_FAST_MIN_BLOCKS)
+k_fast(const Args a)
 {
     // ring stage: z, mu, packed of a tile (+ the replay's per-slot double)
     constexpr int STG = ADJ ? 5 : 3;
@@ -770,7 +778,7 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
                 if (bin >= 0 && lane == __ffs(m) - 1) atomicAdd(&s_n[bin], (uint32_t)__popc(m));
             }
         }
-        // new depths (an eventful carrier keeps its old one here: k_slow
+        // new depths (an eventful carrier keeps its old one here: k_event
         // writes its final state); only slots below n_slots are written
         if (i0 + VEC <= nvalid) {
             *reinterpret_cast<float4 *>(gZ + i0) = make_float4(zo[0], zo[1], zo[2], zo[3]);
@@ -816,20 +824,23 @@ __global__ void __launch_bounds__(FAST_THREADS, PIC_FAST_MIN_BLOCKS) k_fast(cons
 }
 
 // ---------------------------------------------------------------------------
-// k_slow: the general step for the queued (eventful) carriers, and the
-// placement of every secondary of the step.
+// k_event: the general step for the queued (eventful) carriers.
 //
-// Slow block j works off the queues of fast blocks [Gf*j/Gs, Gf*(j+1)/Gs)
-// with all lanes busy on the event paths: interface draws against T, mirror
-// reflection, elastic and inelastic scattering, removal in the lowest bin
-// and secondary generation (Sec. III).  A secondary is staged at its
-// parent's position with one bit in a bitmap; its rank among the stack's
-// secondaries (slot order of the parents = the id order of a sequential
-// loop) is the popcount prefix of the bitmap, continued across blocks by a
-// decoupled look-back with a bounded wait.
+// The queues of all streaming blocks, concatenated in tile order, are cut
+// into equal contiguous item ranges, one per block; no block waits on
+// another.  Within its range a block takes the items of one stack at a time,
+// handed to warps 32 at a time from a shared counter (a warp that drew cheap
+// items takes more): interface draws against T, mirror reflection, elastic
+// and inelastic scattering, removal in the lowest bin and secondary
+// generation (Sec. III).  A secondary is staged at its parent's position
+// with one bit in a bitmap and counted for its parent's streaming block;
+// k_place gives it its slot.
 // ---------------------------------------------------------------------------
+#ifndef PIC_SLOW_MIN_BLOCKS
+#define PIC_SLOW_MIN_BLOCKS 2      // resident blocks per SM of the event pass
+#endif
 template <bool DET, bool DEPN, int ADJ = 0>
-__global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
+__global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     TabEnt *s_ent = reinterpret_cast<TabEnt *>(smem);
@@ -842,27 +853,62 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
     long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN && !ADJ ? a.nbin_max : 0) + 1);
     s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
     long long *s_nsl = s_tpref + a.n_stacks + 1;
+    long long *s_qpre = s_nsl + a.n_stacks;      // queue prefix over the streaming blocks
     __shared__ float s_edge[PIC_MAX_LAYERS + 1];
     __shared__ uint32_t s_p0[PIC_MAX_LAYERS];
     __shared__ DevStack s_st;
     __shared__ int s_w[TPB / 32];
     __shared__ unsigned long long s_r[TPB / 32];
-    __shared__ long long s_prefix;
-    __shared__ int s_flag, s_nspawn;
+    __shared__ unsigned long long s_next;
+    __shared__ long long s_cut;
 
-    const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
-    const int b = blockIdx.x, Gs = gridDim.x, Gf = a.grid_fast, tid = threadIdx.x;
+    const int b = blockIdx.x, G = gridDim.x, Gf = a.grid_fast, tid = threadIdx.x;
+    const int lane = tid & 31;
     const long long T = make_tiles(a, s_tpref, s_nsl);
-    const int fb0 = (int)((long long)Gf * b / Gs), fb1 = (int)((long long)Gf * (b + 1) / Gs);
-    const long long t0 = chunk_lo(T, fb0, Gf), t1 = chunk_lo(T, fb1, Gf);
     const uint32_t step = step_now(a);
     const int tj = (int)(step / (uint32_t)a.moment_every);
     const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
     const float half = a.half_dt;
     float *Z = a.z[cur], *MU = a.mu[cur];
     uint32_t *PK = a.pk[cur];
-    if (tid == 0) s_nspawn = 0;
+
+    // exclusive prefix of the queue lengths: item i of the concatenated queue
+    // is entry i - s_qpre[f] of streaming block f
+    long long run = 0;
+    for (int c0 = 0; c0 < Gf; c0 += TPB) {
+        const int f = c0 + tid;
+        const int v = f < Gf ? (int)a.qcnt[f] : 0;
+        int excl;
+        const int tot = block_scan(v, excl, s_w);
+        if (f < Gf) s_qpre[f] = run + excl;
+        run += tot;
+    }
+    if (tid == 0) s_qpre[Gf] = run;
+    __syncthreads();
+    const long long M = s_qpre[Gf];
+    const long long i0 = M * b / G, i1 = M * (b + 1) / G;
+
+    auto fast_block_of = [&](long long i) -> int {       // last f with s_qpre[f] <= i
+        int lo = 0, hi = Gf - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_qpre[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        return lo;
+    };
+    auto tile_of = [&](long long i) -> long long {
+        const int f = fast_block_of(i);
+        const long long ft0 = chunk_lo(T, f, Gf);
+        return ft0 + (long long)(__float_as_uint(a.qrec[ft0 * TILE + (i - s_qpre[f])].w) / TILE);
+    };
+    auto first_at = [&](long long lo, long long hi, long long tb) -> long long {
+        while (lo < hi) {                                 // items are in tile order
+            const long long mid = (lo + hi) >> 1;
+            if (tile_of(mid) < tb) lo = mid + 1; else hi = mid;
+        }
+        return lo;
+    };
 
     Stk S{};
     Tally ty{};
@@ -905,6 +951,204 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
         ty = Tally{};
         __syncthreads();
     };
+
+    // the general step for item i of the concatenated queue, of stack s
+    // (whose tables are loaded); f: its streaming block
+    auto item = [&](int s, long long i, int f) {
+        const DevStack &st = s_st;
+        const long long q = i - s_qpre[f];
+        const long long fpos0 = chunk_lo(T, f, Gf) * TILE;
+        const long long sbase = st.base - s_tpref[s] * TILE;     // position -> slot
+        const bool room0 = (st.cap - s_nsl[s]) <= 0;
+        const float4 rec = a.qrec[fpos0 + q];
+        float z = rec.x, mu = rec.y;
+        uint32_t pk = __float_as_uint(rec.z);
+        const long long vpos = fpos0 + __float_as_uint(rec.w);
+        const long long gslot = sbase + vpos;
+        const long long slot = vpos - s_tpref[s] * TILE;       // slot within the stack
+        const uint32_t id_lo = a.id[cur][gslot];
+        int k = (int)(pk & 0xFFu);
+        const float mu_in = mu;
+        const uint32_t pk_in = pk;
+        const int sg = (int)((pk >> 8) & 1u);
+        int layer = (int)((pk >> 9) & 0xFu);
+        const uint32_t ctr_y = (pk >> 21) | S.ctr_hi;
+        TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
+        float lo = S.edge[layer], hi = S.edge[layer + 1];
+        const int c_start = cell_of(a, S, z);
+        // adjoint: the slot's reward sum; in pass 2 the reward-to-go R
+        // that weights every decision of this step
+        const long long R = ADJ ? a.acc[cur][gslot] : 0;
+        const double Rd = ADJ == 2 ? (double)R * a.inv_q : 0.0;
+        flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
+                              step, SUB_IF, ty, Rd, s_gT);
+        const int tb = (layer * 2 + sg) * S.n_e + (k - 1);     // entry of the test
+        // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes):
+        // the slot group's test word, then the carrier's event words
+        const uint4 xg = philox_rk(make_uint4((uint32_t)(slot >> 2), S.ctr_hi, step,
+                                              SUB_TEST), a);
+        const uint32_t xs = (slot & 3) == 0 ? xg.x : (slot & 3) == 1 ? xg.y
+                          : (slot & 3) == 2 ? xg.z : xg.w;
+        bool dead = false;
+        if (ADJ == 2 && !(xs < e.P)) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * Rd);
+        if (xs < e.P) {
+            const uint4 x = philox_rk(make_uint4(id_lo, ctr_y, step, SUB_SCAT), a);
+            const bool inel = x.y < e.Q;
+            // scores of the test (scattered) and of the channel
+            if (ADJ == 2) {
+                const AdjEnt &ae = a.aent[st.ent_off + tb];
+                atomicAdd(&s_g[tb], (inel ? ae.scat_inel : ae.scat_el) * Rd);
+            }
+            if (k == 1 && (inel || (a.flags & PIC_F_LOWEST_BIN_ANY))) {
+                dead = true;
+                ++ty.absorbed;
+                ++ty.bath;
+            } else {
+                mu = mu_of(x.z);
+                if (inel) {
+                    const int kp = 1 + (int)__umulhi(x.w, (uint32_t)(k - 1));
+                    const int ks = k - kp;
+                    k = kp;
+                    e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
+                    if (a.flags & PIC_F_NO_SECONDARIES) {
+                        ty.bath += (uint32_t)ks;
+                    } else if (room0) {
+                        ++ty.spawn_drop;
+                        ty.q_drop += (uint32_t)ks;
+                        if (a.flags & PIC_F_STRICT_CAPACITY)
+                            atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
+                    } else {
+                        // secondary: same place, spin from P0, isotropic
+                        const uint4 y = philox_rk(make_uint4(id_lo, ctr_y, step, SUB_SEC), a);
+                        const uint32_t g0 = (pk >> 13) & 0xFFu;
+                        const int sgs = y.x < S.p0[layer] ? 0 : 1;
+                        const uint32_t gen = g0 < 255u ? g0 + 1u : 255u;
+                        float zs = z, mus = mu_of(y.y), los = lo, his = hi;
+                        int ls = layer;
+                        TabEnt es = S.ent[(ls * 2 + sgs) * S.n_e + (ks - 1)];
+                        Tally ts{};
+                        flight<DET>(a, S, zs, mus, ls, es, los, his, sgs, ks, half, id_lo,
+                                    ctr_y, step, SUB_SIF, ts);
+                        // the secondary's boundary events ride in the (not yet
+                        // used) id_hi bits until it is placed
+                        const uint32_t pks = (uint32_t)ks | ((uint32_t)sgs << 8) |
+                                             ((uint32_t)ls << 9) | (gen << 13) |
+                                             (ts.hits << 21) | (ts.trans << 25) |
+                                             (ts.trunc << 29);
+                        a.stage[vpos] = make_float4(zs, mus, __uint_as_float(pks), z);
+                        if (ADJ == 2) a.stage_l[vpos] = (uint32_t)layer;
+                        atomicOr(&a.spawn_bits[vpos >> 5], 1u << (vpos & 31));
+                        atomicAdd(&a.fspawn[f], 1u);
+                    }
+                }
+            }
+        }
+        long long rw = 0;        // adjoint: reward of the step
+        if (dead) {
+            pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
+            const int c_end = cell_of(a, S, z);
+            if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
+            if (ADJ) rw = flux_w(a, s, tj, sg, c_start, c_end);
+        } else {
+            flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
+                                  step, SUB_IF + 16, ty, Rd, s_gT);
+            const int c_end = cell_of(a, S, z);
+            if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
+            pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
+            if (DEPN && !ADJ) atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
+            if (ADJ) {
+                rw = flux_w(a, s, tj, sg, c_start, c_end);
+                if (DEPN) rw += dep_w(a, s, tout, sg, k, c_end);
+            }
+        }
+        if (ADJ && rw != 0) a.acc[cur][gslot] = ADJ == 1 ? R + rw : R - rw;
+        Z[gslot] = z;
+        if (__float_as_uint(mu) != __float_as_uint(mu_in) || pk != pk_in) {
+            ++ty.changed;
+            MU[gslot] = mu;
+            PK[gslot] = pk;
+        }
+        };
+
+    if (i0 < i1) {
+        const int s_first = stack_of(s_tpref, a.n_stacks, tile_of(i0));
+        const int s_last = stack_of(s_tpref, a.n_stacks, tile_of(i1 - 1));
+        long long lo = i0;
+        for (int s = s_first; s <= s_last; ++s) {
+            if (s_tpref[s + 1] == s_tpref[s]) continue;       // a stack with no tiles
+            if (tid == 0) s_cut = s == s_last ? i1 : first_at(lo, i1, s_tpref[s + 1]);
+            load_stack(a, s, S, &s_st, s_ent, s_T, s_edge, s_p0);
+            const long long hi = s_cut;
+            if (!ADJ)
+                for (int q = tid; q < 2 * (s_st.n_cells + 1); q += TPB) s_J[q] = 0;
+            if (DEPN && !ADJ)
+                for (int q = tid; q < 2 * a.n_e * s_st.n_cells; q += TPB) s_n[q] = 0u;
+            if (ADJ == 2) {
+                for (int q = tid; q < s_st.tab_n; q += TPB) s_g[q] = 0.0;
+                for (int q = tid; q < s_st.T_n; q += TPB) s_gT[q] = 0.0;
+            }
+            if (tid == 0) s_next = (unsigned long long)lo;
+            __syncthreads();
+#pragma unroll 1
+            for (;;) {
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(&s_next, 32ull);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if ((long long)base >= hi) break;
+                // the batch's first streaming block, then at most a step or two
+                // (a streaming block queues thousands of items)
+                int f = 0;
+                if (lane == 0) f = fast_block_of((long long)base);
+                f = __shfl_sync(0xffffffffu, f, 0);
+                const long long i = (long long)base + lane;
+                if (i < hi) {
+                    while (s_qpre[f + 1] <= i) ++f;
+                    item(s, i, f);
+                }
+            }
+            flush_segment(s);
+            lo = hi;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_place: slots and ids of the secondaries staged by k_event.
+//
+// Block j covers the tiles of streaming blocks [Gf j/Gp, Gf (j+1)/Gp).  The
+// secondaries of a stack take the slots after the stack's live ones in the
+// order of their parents' positions (the id order of a sequential loop over
+// the slots): a block's rank offset in a stack is the number of the stack's
+// secondaries in earlier blocks, found by a decoupled look-back with a
+// bounded wait.  Every block publishes its own count before it waits.
+// ---------------------------------------------------------------------------
+template <bool DET, bool DEPN, int ADJ = 0>
+__global__ void __launch_bounds__(TPB) k_place(const Args a)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    int32_t *s_J = reinterpret_cast<int32_t *>(smem);
+    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + (ADJ ? 0 : a.jbin_max));
+    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN && !ADJ ? a.nbin_max : 0) + 1);
+    s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
+    long long *s_nsl = s_tpref + a.n_stacks + 1;
+    __shared__ int s_w[TPB / 32];
+    __shared__ unsigned long long s_r[TPB / 32];
+    __shared__ long long s_pre[2];
+    __shared__ int s_flag;
+
+    const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
+    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
+    const int b = blockIdx.x, Gs = gridDim.x, Gf = a.grid_fast, tid = threadIdx.x;
+    const long long T = make_tiles(a, s_tpref, s_nsl);
+    const int fb0 = (int)((long long)Gf * b / Gs), fb1 = (int)((long long)Gf * (b + 1) / Gs);
+    const long long t0 = chunk_lo(T, fb0, Gf), t1 = chunk_lo(T, fb1, Gf);
+    const uint32_t step = step_now(a);
+    const int tj = (int)(step / (uint32_t)a.moment_every);
+    const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
+    const float half = a.half_dt;
+    float *Z = a.z[cur], *MU = a.mu[cur];
+    uint32_t *PK = a.pk[cur];
+    Tally ty{};
 
     // Adjoint bookkeeping of a secondary placed at slot d with id `id`, staged
     // at tile-space position pos (its parent's position).  Pass 1 records the
@@ -957,9 +1201,9 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
 
     // Place the staged secondaries of stack s in tiles [tl0, tl1) in slot
     // order, the first with rank `prefix` among the stack's secondaries of
-    // this step; clears the bitmap words it reads.  Deposits go to shared
-    // memory if `smem_hist`, else to global memory.
-    auto place = [&](int s, long long tl0, long long tl1, long long prefix, bool smem_hist) {
+    // this step; clears the bitmap words it reads; deposits into the shared
+    // histograms.  Returns the number of the segment's secondaries.
+    auto place = [&](int s, long long tl0, long long tl1, long long prefix) -> long long {
         const DevStack stg = a.stacks[s];
         const long long nsl = s_nsl[s];
         const long long room = stg.cap - nsl;
@@ -999,15 +1243,9 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
                         const int c0 = cell_of(a, tmp, r.w), c1 = cell_of(a, tmp, r.x);
                         if (ADJ) {
                             place_adj(s, stg, w * 32 + j, d, id, pk, sg, k, c0, c1, r);
-                        } else if (smem_hist) {
+                        } else {
                             if (c0 != c1) add_flux(s_J, nf, sg, c0, c1);
                             if (DEPN) atomicAdd(&s_n[(sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
-                        } else {
-                            int32_t *gJ = a.J_hist + stg.J_off + (long long)tj * 2 * nf;
-                            if (c0 != c1) add_flux(gJ, nf, sg, c0, c1);
-                            if (DEPN)
-                                atomicAdd(&a.n_hist[stg.n_off + (long long)tout * 2 * a.n_e * stg.n_cells +
-                                                    (sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
                         }
                     } else {
                         ++ty.spawn_drop;
@@ -1022,239 +1260,96 @@ __global__ void __launch_bounds__(TPB, 2) k_slow(const Args a)
         if (tid == 0 && kk) atomicAdd(&a.cnt[s].led[L_SPAWNED], kk);
         if (tid == 0 && (a.flags & PIC_F_STRICT_CAPACITY) && run > room)
             atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
+        return run - prefix;
     };
 
-    // the general step for queue entries [q_lo, q_hi) of fast block f, all of
-    // stack s (whose tables are loaded)
-    auto work = [&](int s, int f, long long q_lo, long long q_hi) {
-        const DevStack &st = s_st;
-        const long long fpos0 = chunk_lo(T, f, Gf) * TILE;
-        const long long sbase = st.base - s_tpref[s] * TILE;     // position -> slot
-        const bool room0 = (st.cap - s_nsl[s]) <= 0;
-        int nsp = 0;
-#pragma unroll 1
-        for (long long q = q_lo + tid; q < q_hi; q += TPB) {
-            const float4 rec = a.qrec[fpos0 + q];
-            float z = rec.x, mu = rec.y;
-            uint32_t pk = __float_as_uint(rec.z);
-            const long long vpos = fpos0 + __float_as_uint(rec.w);
-            const long long gslot = sbase + vpos;
-            const long long slot = vpos - s_tpref[s] * TILE;       // slot within the stack
-            const uint32_t id_lo = a.id[cur][gslot];
-            int k = (int)(pk & 0xFFu);
-            const float mu_in = mu;
-            const uint32_t pk_in = pk;
-            const int sg = (int)((pk >> 8) & 1u);
-            int layer = (int)((pk >> 9) & 0xFu);
-            const uint32_t ctr_y = (pk >> 21) | S.ctr_hi;
-            TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
-            float lo = S.edge[layer], hi = S.edge[layer + 1];
-            const int c_start = cell_of(a, S, z);
-            // adjoint: the slot's reward sum; in pass 2 the reward-to-go R
-            // that weights every decision of this step
-            const long long R = ADJ ? a.acc[cur][gslot] : 0;
-            const double Rd = ADJ == 2 ? (double)R * a.inv_q : 0.0;
-            flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
-                                  step, SUB_IF, ty, Rd, s_gT);
-            const int tb = (layer * 2 + sg) * S.n_e + (k - 1);     // entry of the test
-            // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes):
-            // the slot group's test word, then the carrier's event words
-            const uint4 xg = philox_rk(make_uint4((uint32_t)(slot >> 2), S.ctr_hi, step,
-                                                  SUB_TEST), a);
-            const uint32_t xs = (slot & 3) == 0 ? xg.x : (slot & 3) == 1 ? xg.y
-                              : (slot & 3) == 2 ? xg.z : xg.w;
-            bool dead = false;
-            if (ADJ == 2 && !(xs < e.P)) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * Rd);
-            if (xs < e.P) {
-                const uint4 x = philox_rk(make_uint4(id_lo, ctr_y, step, SUB_SCAT), a);
-                const bool inel = x.y < e.Q;
-                // scores of the test (scattered) and of the channel
-                if (ADJ == 2) {
-                    const AdjEnt &ae = a.aent[st.ent_off + tb];
-                    atomicAdd(&s_g[tb], (inel ? ae.scat_inel : ae.scat_el) * Rd);
-                }
-                if (k == 1 && (inel || (a.flags & PIC_F_LOWEST_BIN_ANY))) {
-                    dead = true;
-                    ++ty.absorbed;
-                    ++ty.bath;
-                } else {
-                    mu = mu_of(x.z);
-                    if (inel) {
-                        const int kp = 1 + (int)__umulhi(x.w, (uint32_t)(k - 1));
-                        const int ks = k - kp;
-                        k = kp;
-                        e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
-                        if (a.flags & PIC_F_NO_SECONDARIES) {
-                            ty.bath += (uint32_t)ks;
-                        } else if (room0) {
-                            ++ty.spawn_drop;
-                            ty.q_drop += (uint32_t)ks;
-                            if (a.flags & PIC_F_STRICT_CAPACITY)
-                                atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
-                        } else {
-                            // secondary: same place, spin from P0, isotropic
-                            const uint4 y = philox_rk(make_uint4(id_lo, ctr_y, step, SUB_SEC), a);
-                            const uint32_t g0 = (pk >> 13) & 0xFFu;
-                            const int sgs = y.x < S.p0[layer] ? 0 : 1;
-                            const uint32_t gen = g0 < 255u ? g0 + 1u : 255u;
-                            float zs = z, mus = mu_of(y.y), los = lo, his = hi;
-                            int ls = layer;
-                            TabEnt es = S.ent[(ls * 2 + sgs) * S.n_e + (ks - 1)];
-                            Tally ts{};
-                            flight<DET>(a, S, zs, mus, ls, es, los, his, sgs, ks, half, id_lo,
-                                        ctr_y, step, SUB_SIF, ts);
-                            // the secondary's boundary events ride in the (not yet
-                            // used) id_hi bits until it is placed
-                            const uint32_t pks = (uint32_t)ks | ((uint32_t)sgs << 8) |
-                                                 ((uint32_t)ls << 9) | (gen << 13) |
-                                                 (ts.hits << 21) | (ts.trans << 25) |
-                                                 (ts.trunc << 29);
-                            a.stage[vpos] = make_float4(zs, mus, __uint_as_float(pks), z);
-                            if (ADJ == 2) a.stage_l[vpos] = (uint32_t)layer;
-                            atomicOr(&a.spawn_bits[vpos >> 5], 1u << (vpos & 31));
-                            ++nsp;
-                        }
-                    }
-                }
-            }
-            long long rw = 0;        // adjoint: reward of the step
-            if (dead) {
-                pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
-                const int c_end = cell_of(a, S, z);
-                if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
-                if (ADJ) rw = flux_w(a, s, tj, sg, c_start, c_end);
-            } else {
-                flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
-                                      step, SUB_IF + 16, ty, Rd, s_gT);
-                const int c_end = cell_of(a, S, z);
-                if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
-                pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
-                if (DEPN && !ADJ) atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
-                if (ADJ) {
-                    rw = flux_w(a, s, tj, sg, c_start, c_end);
-                    if (DEPN) rw += dep_w(a, s, tout, sg, k, c_end);
-                }
-            }
-            if (ADJ && rw != 0) a.acc[cur][gslot] = ADJ == 1 ? R + rw : R - rw;
-            Z[gslot] = z;
-            if (__float_as_uint(mu) != __float_as_uint(mu_in) || pk != pk_in) {
-                ++ty.changed;
-                MU[gslot] = mu;
-                PK[gslot] = pk;
+    // deposits and boundary tallies of the placed secondaries of stack s
+    auto flush = [&](int s) {
+        __syncthreads();
+        const DevStack &st = a.stacks[s];
+        const int nf = st.n_cells + 1;
+        if (!ADJ) {
+            int32_t *gJ = a.J_hist + st.J_off + (long long)tj * 2 * nf;
+            for (int i = tid; i < 2 * nf; i += TPB) {
+                const int v = s_J[i];
+                if (v) atomicAdd(&gJ[i], v);
             }
         }
-        if (nsp) atomicAdd(&s_nspawn, nsp);
+        if (DEPN && !ADJ) {
+            const int nb = 2 * a.n_e * st.n_cells;
+            uint32_t *gN = a.n_hist + st.n_off + (long long)tout * nb;
+            for (int i = tid; i < nb; i += TPB) {
+                const uint32_t v = s_n[i];
+                if (v) atomicAdd(&gN[i], v);
+            }
+        }
+        unsigned long long *L = a.cnt[s].led;
+        const uint32_t vals[5] = {ty.hits, ty.trans, ty.trunc, ty.spawn_drop, ty.q_drop};
+        const int idx[5] = {L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED, L_SPAWN_DROPPED,
+                            L_Q_DROPPED};
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            const unsigned long long v = block_sum_u64(vals[q], s_r);
+            if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
+        }
+        ty = Tally{};
+        __syncthreads();
     };
 
-    // first entry of fast block f's queue (ascending by tile) with tile >=
-    // tb: the block counts the entries below tb (one pass, all threads)
-    auto lower = [&](int f, long long tb) -> long long {
-        const long long ft0 = chunk_lo(T, f, Gf), fpos0 = ft0 * TILE;
-        const long long n = a.qcnt[f];
-        unsigned long long below = 0;
-        for (long long q = tid; q < n; q += TPB)
-            below += (ft0 + __float_as_uint(a.qrec[fpos0 + q].w) / TILE < tb) ? 1u : 0u;
-        const unsigned long long tot = block_sum_u64(below, s_r);
-        if (tid == 0) s_prefix = (long long)tot;
-        __syncthreads();
-        const long long r = s_prefix;
-        __syncthreads();
-        return r;
+    // staged secondaries in tiles [tl0, tl1): the block's count (thread 0)
+    auto count_bits = [&](long long tl0, long long tl1) -> long long {
+        unsigned long long c = 0;
+        for (long long w = tl0 * (TILE / 32) + tid; w < tl1 * (TILE / 32); w += TPB)
+            c += (unsigned long long)__popc(a.spawn_bits[w]);
+        return (long long)block_sum_u64(c, s_r);
     };
 
-    int staged_stack = -1;
-    long long staged_t0 = 0, staged_t1 = 0, staged_count = 0;
-    bool have_last = false, last_staged = false;
-    int last_stack = -1;
-    long long last_t0 = 0, last_count = 0;
     if (t0 < t1) {
         const int s_first = stack_of(s_tpref, a.n_stacks, t0);
         const int s_last = stack_of(s_tpref, a.n_stacks, t1 - 1);
+        const bool inside_first = t0 > s_tpref[s_first];     // first segment starts inside its stack
+        const bool inside_last = s_first == s_last && inside_first;
+        long long c_first = 0, c_last = 0;
+        if (s_first == s_last) {
+            // one stack: the streaming blocks' counts
+            unsigned long long c = 0;
+            for (int f = fb0 + tid; f < fb1; f += TPB) c += a.fspawn[f];
+            c_last = (long long)block_sum_u64(c, s_r);
+        } else {
+            if (inside_first) c_first = count_bits(t0, s_tpref[s_first + 1]);
+            c_last = count_bits(s_tpref[s_last] > t0 ? s_tpref[s_last] : t0, t1);
+        }
+        for (int f = fb0 + tid; f < fb1; f += TPB) a.fspawn[f] = 0u;   // consumed
+        if (tid == 0) {
+            // the count of the last segment goes out before any wait
+            if (!inside_last) {
+                publish(&a.status[b], ep, FLAG_P, c_last);
+                s_pre[1] = 0;
+            } else {
+                publish(&a.status[b], ep, FLAG_A, c_last);
+                s_pre[1] = look_back_place(a, ep, T, s_tpref[s_last], b, Gs, Gf);
+                publish(&a.status[b], ep, FLAG_P, s_pre[1] + c_last);
+            }
+            s_pre[0] = (s_first < s_last && inside_first)
+                           ? look_back_place(a, ep, T, s_tpref[s_first], b, Gs, Gf) : 0;
+        }
+        __syncthreads();
+        (void)c_first;
         for (int s = s_first; s <= s_last; ++s) {
             const long long sg0 = s_tpref[s] > t0 ? s_tpref[s] : t0;
             const long long sg1 = s_tpref[s + 1] < t1 ? s_tpref[s + 1] : t1;
-            if (sg0 >= sg1) continue;               // a stack with no tiles
-            load_stack(a, s, S, &s_st, s_ent, s_T, s_edge, s_p0);
+            if (sg0 >= sg1) continue;                   // a stack with no tiles
+            const long long prefix = s == s_last ? s_pre[1] : (s == s_first ? s_pre[0] : 0);
+            const int nc = a.stacks[s].n_cells;
             if (!ADJ)
-                for (int q = tid; q < 2 * (s_st.n_cells + 1); q += TPB) s_J[q] = 0;
+                for (int q = tid; q < 2 * (nc + 1); q += TPB) s_J[q] = 0;
             if (DEPN && !ADJ)
-                for (int q = tid; q < 2 * a.n_e * s_st.n_cells; q += TPB) s_n[q] = 0u;
-            if (ADJ == 2) {
-                for (int q = tid; q < s_st.tab_n; q += TPB) s_g[q] = 0.0;
-                for (int q = tid; q < s_st.T_n; q += TPB) s_gT[q] = 0.0;
-            }
-            if (tid == 0) s_nspawn = 0;
+                for (int q = tid; q < 2 * a.n_e * nc; q += TPB) s_n[q] = 0u;
             __syncthreads();
-            for (int f = fb0; f < fb1; ++f) {
-                // the queue entries of stack s (the whole queue when the chunk
-                // lies in one stack)
-                long long q_lo = 0, q_hi = a.qcnt[f];
-                if (s_first != s_last) {
-                    q_lo = lower(f, sg0);
-                    q_hi = lower(f, sg1);
-                }
-                if (q_lo < q_hi) work(s, f, q_lo, q_hi);
-            }
-            __syncthreads();
-            const long long cnt = s_nspawn;
-            const bool inside = sg0 > s_tpref[s];   // segment starts inside its stack
-            if (s < s_last) {
-                // a segment that ends its stack inside the chunk
-                if (!inside) {
-                    if (cnt) place(s, sg0, sg1, 0, true);
-                    if (tid == 0) a.cnt[s].spawn_total = (unsigned long long)cnt;
-                } else {
-                    staged_stack = s; staged_t0 = sg0; staged_t1 = sg1; staged_count = cnt;
-                }
-                flush_segment(s);
-            } else {
-                have_last = true; last_staged = inside; last_stack = s;
-                last_t0 = sg0; last_count = cnt;
-            }
-        }
-    }
-
-    // close the last segment and publish its count of secondaries
-    if (have_last) {
-        const long long cnt = last_count;
-        const bool ends_stack = s_tpref[last_stack + 1] == t1;
-        if (!last_staged) {
-            if (tid == 0) publish(&a.status[b], ep, FLAG_P, cnt);
-            if (cnt) place(last_stack, last_t0, t1, 0, true);
-            if (ends_stack && tid == 0) a.cnt[last_stack].spawn_total = (unsigned long long)cnt;
-            flush_segment(last_stack);
-        } else {
-            if (tid == 0) {
-                publish(&a.status[b], ep, FLAG_A, cnt);
-                s_prefix = look_back_slow(a, ep, T, s_tpref[last_stack], b, Gs, Gf);
-                publish(&a.status[b], ep, FLAG_P, s_prefix + cnt);
-            }
-            __syncthreads();
-            const long long pre = s_prefix;
-            if (cnt) place(last_stack, last_t0, t1, pre, true);
-            if (ends_stack && tid == 0)
-                a.cnt[last_stack].spawn_total = (unsigned long long)(pre + cnt);
-            flush_segment(last_stack);
-        }
-        // an earlier segment (block spanning stacks) that waited for its prefix
-        if (staged_stack >= 0) {
-            __syncthreads();
-            if (tid == 0) s_prefix = look_back_slow(a, ep, T, s_tpref[staged_stack], b, Gs, Gf);
-            __syncthreads();
-            const long long pre = s_prefix;
-            if (staged_count) place(staged_stack, staged_t0, staged_t1, pre, false);
-            if (tid == 0)
-                a.cnt[staged_stack].spawn_total = (unsigned long long)(pre + staged_count);
-            unsigned long long *L = a.cnt[staged_stack].led;
-            const uint32_t vals[5] = {ty.hits, ty.trans, ty.trunc, ty.spawn_drop, ty.q_drop};
-            const int idx[5] = {L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED, L_SPAWN_DROPPED,
-                                L_Q_DROPPED};
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                const unsigned long long v = block_sum_u64(vals[q], s_r);
-                if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
-            }
-            ty = Tally{};
+            const long long n = place(s, sg0, sg1, prefix);
+            if (sg1 == s_tpref[s + 1] && tid == 0)
+                a.cnt[s].spawn_total = (unsigned long long)(prefix + n);
+            flush(s);
         }
     }
 
@@ -1554,16 +1649,46 @@ static cudaError_t pick_ring(size_t fixed, int blocks_per_sm, int ring_req, int 
 }
 
 template <bool DEPN, int ADJ = 0>
-static cudaError_t slow_cfg(size_t sm, int *grid, int sms)
+static cudaError_t event_cfg(size_t sm, int *grid, int sms)
 {
     int o1 = 0, o2 = 0;
-    cudaError_t e = occupancy(k_slow<false, DEPN, ADJ>, sm, &o1);
-    if (e == cudaSuccess) e = occupancy(k_slow<true, DEPN, ADJ>, sm, &o2);
+    cudaError_t e = occupancy(k_event<false, DEPN, ADJ>, sm, &o1);
+    if (e == cudaSuccess) e = occupancy(k_event<true, DEPN, ADJ>, sm, &o2);
     if (e != cudaSuccess) return e;
     const int o = o1 < o2 ? o1 : o2;
     if (o < 1) return cudaErrorInvalidConfiguration;
-    *grid = sms * o;
+    *grid = sms * o * 2;        // no block waits on another: more blocks than fit
     return cudaSuccess;
+}
+
+template <bool DEPN, int ADJ = 0>
+static cudaError_t place_cfg(size_t sm, int *grid, int sms)
+{
+    int o1 = 0, o2 = 0;
+    cudaError_t e = occupancy(k_place<false, DEPN, ADJ>, sm, &o1);
+    if (e == cudaSuccess) e = occupancy(k_place<true, DEPN, ADJ>, sm, &o2);
+    if (e != cudaSuccess) return e;
+    const int o = o1 < o2 ? o1 : o2;
+    if (o < 1) return cudaErrorInvalidConfiguration;
+    *grid = sms * o;            // look-back: every block resident
+    return cudaSuccess;
+}
+
+// Shared memory of the event and placement passes (ADJ: replay pass).
+inline size_t event_smem(const Args &a, bool dep, int adj, int gf_max)
+{
+    const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;
+    return (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.T_max * 4 + 8 +
+           (adj == 2 ? (size_t)(a.tab_max + a.T_max) * 8 : 0) +
+           (adj ? 0 : (size_t)a.jbin_max * 4) + (dep && !adj ? (size_t)a.nbin_max * 4 : 0) + 4 +
+           tiles + (size_t)(gf_max + 1) * 8;
+}
+
+inline size_t place_smem(const Args &a, bool dep, int adj)
+{
+    const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;
+    return (adj ? 0 : (size_t)a.jbin_max * 4) + (dep && !adj ? (size_t)a.nbin_max * 4 : 0) + 4 +
+           tiles;
 }
 
 }  // namespace pic
