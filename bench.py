@@ -103,14 +103,16 @@ def measured_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-# ncu DRAM traffic of one step-kernel launch (read + write bytes per live
-# carrier-step), valid for the kernel source whose hash is given; see
-# profiles/k_step_fe15_au300.md.  None until a capture exists.
-NCU_TRAFFIC = None   # {"bytes_per_particle_step": float, "src_sha": "..."}
+# ncu DRAM traffic of the step kernels (k_fast + k_event + k_place), bytes per
+# live carrier-step, from one steady-state capture of each on this workload
+# scaled to 1/20 (profiles/k_fast_k_event_k_place_fe15_au300_small.md); the
+# traffic grows in proportion to the carriers advanced.  Valid only for the
+# kernel source whose hash is given: reported as null once the kernels change.
+NCU_TRAFFIC = {"bytes_per_particle_step": 20.77, "src_sha": "9d2552fadbe4a4d2"}
 
 
 def kernel_sha():
-    with open(os.path.join(ROOT, "paper_1807_04733_gb300", "csrc", "pic_kernels.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_1807_04733_gb300", "csrc", "pic_step.cuh"), "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
@@ -473,19 +475,15 @@ def main():
     ps_e2e -= led1[0]["particle_steps"]
     d2h = n_host.numel() * 4 + J_host.numel() * 4 + 13 * 8
 
-    # ---- reductions over ranks ----
-    vals = torch.tensor([ms, e2e_s * 1e3], dtype=torch.float64, device="cuda")
-    cnts = torch.tensor([ps, ps_e2e], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(vals, op=dist.ReduceOp.MAX)
-        dist.all_reduce(cnts, op=dist.ReduceOp.SUM)
-    ms_max, e2e_ms = float(vals[0]), float(vals[1])
-    ps_all, ps_e2e_all = float(cnts[0]), float(cnts[1])
+    # ---- reductions over ranks: the largest time, the sum of the units ----
+    from paper_1807_04733_gb300 import shard
+    ms_max, ps_all = shard.reduce_measurement(ms, float(ps), dist, "cuda")
+    e2e_ms, ps_e2e_all = shard.reduce_measurement(e2e_s * 1e3, float(ps_e2e), dist, "cuda")
 
     peak, peak_kind = measured_peak()
-    # the step is a kernel pair: the streaming pass (k_fast) and the event
-    # pass with the placement of secondaries (k_slow); one launch of each per
-    # time step, timed together
+    # the step kernels: the streaming pass (k_fast), the event pass (k_event)
+    # and the placement of secondaries (k_place); one launch of each per time
+    # step, timed together; "per launch" = per time step
     n_k = ktimes["step"][0] + ktimes["step_moments"][0]
     k_ms = ktimes["step"][1] + ktimes["step_moments"][1] + ktimes["step_events"][1]
     alg_bytes = B_STEP * delta["particle_steps"] + B_EVENTFUL * delta["eventful"] + \
@@ -495,7 +493,7 @@ def main():
     if NCU_TRAFFIC and NCU_TRAFFIC.get("src_sha") == kernel_sha():
         traffic = NCU_TRAFFIC["bytes_per_particle_step"] * delta["particle_steps"] / n_k
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_fast+k_slow",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_fast+k_event+k_place",
                 "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg_bytes / n_k if n_k else 0,
                 "avg_launch_ms": k_ms / n_k if n_k else 0,

@@ -89,6 +89,12 @@ typedef struct {
                                memory; 0: one launch per kernel.  Results are
                                identical; kernel timing (pic_profile) always
                                uses single launches. */
+    int32_t stack_base;     /* global index of the context's first stack
+                               (0..65535 - n_stacks): stack s draws the random
+                               streams of stack stack_base + s, so that stacks
+                               split over several contexts (one per GPU or
+                               process) give the results of one context that
+                               holds them all */
 } pic_params;
 
 /* Launch configuration a context chose (pic_launch_info). */

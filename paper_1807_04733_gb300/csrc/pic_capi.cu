@@ -153,6 +153,7 @@ bool valid_params(const pic_params *p, std::string &why)
         why = "ring_stages must be 0 or 2..8"; return false;
     }
     if (p->use_graph != 0 && p->use_graph != 1) { why = "use_graph must be 0 or 1"; return false; }
+    if (p->stack_base < 0 || p->stack_base > 65535) { why = "stack_base out of range"; return false; }
     return true;
 }
 
@@ -414,6 +415,10 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         g_init_error = "n_stacks out of range or NULL stacks/tables";
         return PIC_ERR_ARG;
     }
+    if (p->stack_base + n_stacks > 65536) {
+        g_init_error = "stack_base + n_stacks must not exceed 65536";
+        return PIC_ERR_ARG;
+    }
     for (int s = 0; s < n_stacks; ++s)
         if (!valid_stack(p, &stacks[s], &tables[s], why)) {
             g_init_error = "stack " + std::to_string(s) + ": " + why;
@@ -546,6 +551,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.qrec = c->d_qrec;
     a.n_hist = c->d_nh; a.J_hist = c->d_J; a.cnt = c->d_cnt; a.ctl = c->d_ctl;
     a.seed_lo = (uint32_t)p->seed; a.seed_hi = (uint32_t)(p->seed >> 32);
+    a.stack_base = p->stack_base;
     for (int r = 0; r < 10; ++r) {      // Philox4x32-10 round keys (Weyl sequence)
         a.rk0[r] = a.seed_lo + (uint32_t)r * 0x9E3779B9u;
         a.rk1[r] = a.seed_hi + (uint32_t)r * 0xBB67AE85u;

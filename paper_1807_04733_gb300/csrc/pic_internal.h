@@ -111,6 +111,7 @@ struct Args {            // everything a kernel needs, passed by value
     DevCounters *cnt;
     DevCtl *ctl;
     uint32_t seed_lo, seed_hi;
+    int stack_base;                          // global index of stack 0 (Philox counters)
     uint32_t rk0[10], rk1[10];               // Philox round keys (key + r * Weyl)
     float half_dt, dz, inv_dz;
     int dz_pow2;

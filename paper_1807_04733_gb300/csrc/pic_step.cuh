@@ -97,7 +97,7 @@ struct Stk {
     const float *edge;
     const uint32_t *p0;
     int n_layers, n_cells, n_e;
-    uint32_t ctr_hi;     // stack << 16
+    uint32_t ctr_hi;     // (stack_base + stack) << 16
     const double2 *aT;   // adjoint: interface scores of the stack (global memory)
 };
 
@@ -338,7 +338,7 @@ __device__ __forceinline__ void load_stack(const Args &a, int s, Stk &k, DevStac
     if (threadIdx.x < st.n_layers) s_p0[threadIdx.x] = st.p0_thr[threadIdx.x];
     k.ent = s_ent; k.T = s_T; k.edge = s_edge; k.p0 = s_p0;
     k.n_layers = st.n_layers; k.n_cells = st.n_cells; k.n_e = a.n_e;
-    k.ctr_hi = (uint32_t)s << 16;
+    k.ctr_hi = (uint32_t)(a.stack_base + s) << 16;
     k.aT = a.aT ? a.aT + st.T_off : nullptr;
 }
 
@@ -684,7 +684,7 @@ k_fast(const Args a)
                 }
             }
             nc = st.n_cells;
-            ctr_hi = (uint32_t)s << 16;
+            ctr_hi = (uint32_t)(a.stack_base + s) << 16;
             seg_stack = s;
             consumer_sync();
         }
@@ -1176,13 +1176,13 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             a.acc[cur][d] = rw;
         } else {
             const long long Rc = a.tot[stg.id_off + id];
-            const uint32_t ctr_y = (ppk >> 21) | ((uint32_t)s << 16);
+            const uint32_t ctr_y = (ppk >> 21) | ((uint32_t)(a.stack_base + s) << 16);
             const uint4 y = philox_rk(make_uint4(pid_lo, ctr_y, step, SUB_SEC), a);
             Stk gs;
             gs.ent = a.ent + stg.ent_off; gs.T = a.T_thr + stg.T_off;
             gs.edge = a.stacks[s].edge; gs.p0 = nullptr;
             gs.n_layers = stg.n_layers; gs.n_cells = stg.n_cells; gs.n_e = a.n_e;
-            gs.ctr_hi = (uint32_t)s << 16; gs.aT = a.aT + stg.T_off;
+            gs.ctr_hi = (uint32_t)(a.stack_base + s) << 16; gs.aT = a.aT + stg.T_off;
             int ls = (int)a.stage_l[pos];
             TabEnt es = gs.ent[(ls * 2 + sg) * a.n_e + (k - 1)];
             float los = gs.edge[ls], his = gs.edge[ls + 1];
@@ -1408,7 +1408,7 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
         const long long j = gidx - s_pref[s];
         const DevStack &st = a.stacks[s];
         const unsigned long long id = a.cnt[s].next_id + (unsigned long long)j;
-        const uint32_t cy = (uint32_t)(id >> 32) | ((uint32_t)s << 16);
+        const uint32_t cy = (uint32_t)(id >> 32) | ((uint32_t)(a.stack_base + s) << 16);
         const uint4 r0 = philox_rk(make_uint4((uint32_t)id, cy, step, SUB_INJ + 0), a);
         const uint4 r1 = philox_rk(make_uint4((uint32_t)id, cy, step, SUB_INJ + 1), a);
         int i = 0;

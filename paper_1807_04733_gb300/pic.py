@@ -43,7 +43,8 @@ class pic_params(C.Structure):
                 ("seed", C.c_uint64), ("flags", C.c_uint32), ("compact_every", C.c_int32),
                 ("moment_every", C.c_int32), ("n_steps_max", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("hist_mode", C.c_int32),
-                ("ring_stages", C.c_int32), ("use_graph", C.c_int32)]
+                ("ring_stages", C.c_int32), ("use_graph", C.c_int32),
+                ("stack_base", C.c_int32)]
 
 
 class pic_stack_desc(C.Structure):
@@ -165,7 +166,7 @@ def _check(status, ctx=None):
 # marshalling of the workload description
 # ---------------------------------------------------------------------------
 def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hist_mode=0,
-                ring_stages=0, use_graph=0):
+                ring_stages=0, use_graph=0, stack_base=0):
     p = pic_params()
     p.n_e = wl.n_e; p.dt = wl.dt; p.dz = wl.dz
     p.seed = wl.seed if seed is None else seed
@@ -174,6 +175,7 @@ def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hi
     p.n_steps_max = wl.n_steps if n_steps_max is None else n_steps_max
     p.blocks_per_sm = blocks_per_sm; p.hist_mode = hist_mode; p.ring_stages = ring_stages
     p.use_graph = 1 if use_graph else 0
+    p.stack_base = stack_base
     return p
 
 
@@ -337,13 +339,13 @@ class Context:
 
     def __init__(self, wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0,
                  hist_mode=0, stream=None, excite=True, capacity=None, ring_stages=0,
-                 use_graph=False):
+                 use_graph=False, stack_base=0):
         import torch
         self.wl = wl
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.params = make_params(wl, n_steps_max, flags, seed, blocks_per_sm, hist_mode,
-                                  ring_stages, use_graph)
+                                  ring_stages, use_graph, stack_base)
         self._tabs = [_Tables(st) for st in wl.stacks]
         self.stacks = [make_stack(st, capacity) for st in wl.stacks]
         self.ctx = pic_init(self.params, self.stacks, [t.c for t in self._tabs],

@@ -156,3 +156,23 @@ def test_fast_build_conserves_exactly():
         t = ctx.shape(0)[2] - 1
         assert int(n[t].sum()) == int((k > 0).sum())
     ctx.close()
+
+
+def test_det_bitexact_stack_base_shard():
+    """A context holding stacks 2..4 of a batched workload with stack_base = 2
+    (one rank's shard) reproduces those stacks of the oracle, which keys its
+    random streams by the global stack index."""
+    wl = W.batched(n_stacks=5, scale=2e-3, n_steps=120, flags=DET)
+    part = wl.replace(stacks=list(wl.stacks[2:]))
+    ctx = pic.Context(part, stack_base=2)
+    ctx.step(120)
+    for j in range(3):
+        ref = OracleSim(wl, stack=2 + j)
+        assert ref.step(120) == 0
+        n, J, led = ctx.moments(j)
+        rn, rJ, rled = ref.moments()
+        assert led == rled
+        assert np.array_equal(n.cpu().numpy().view(np.uint32), rn)
+        assert np.array_equal(J.cpu().numpy(), rJ)
+        assert same_records(ctx.records(j), ref.records())
+    ctx.close()
