@@ -66,13 +66,15 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
     out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
 }
 
-/* substreams: the fourth counter word */
-#define SUB_SCAT 0x000u   /* event words of a carrier that scatters */
-#define SUB_SEC  0x001u
-#define SUB_IF   0x100u   /* + 16*half + hit : primary flights */
-#define SUB_SIF  0x200u   /* + hit           : secondary's second-half flight */
-#define SUB_INJ  0x300u   /* + j             : injection draws */
+/* substreams: the fourth counter word.  The source draws are keyed by the
+ * new carrier's id; every other word by the slot of the carrier that draws
+ * it (one carrier per slot and step, so every decision gets a fresh word). */
+#define SUB_INJ  0x300u   /* + j             : source draws (id) */
 #define SUB_TEST 0x400u   /* scattering test: slot group of four, one word each */
+#define SUB_EVT  0x500u   /* event words of a carrier that scatters (slot) */
+#define SUB_SEC  0x501u   /* its secondary's spin and direction (slot) */
+#define SUB_IF   0x600u   /* + 16*half + hit : boundary draws of a flight (slot) */
+#define SUB_SIF  0x700u   /* + hit           : the secondary's flight (parent's slot) */
 
 /* ---- packed word: k:8 | spin:1 | layer:4 | gen:8 | id_hi:11 ---- */
 #define PK_K(w)     ((w) & 0xFFu)
@@ -168,9 +170,11 @@ static double pulse_F(const or_config *c, double t)
     return (Phi((t - c->t0) / s) - a) / (b - a);
 }
 
-static void draw(const or_sim *s, uint64_t id, uint32_t step, uint32_t sub, uint32_t r[4])
+/* Philox words of counter (x, stack, step, substream); x is a carrier id or
+ * a slot */
+static void draw(const or_sim *s, uint64_t x, uint32_t step, uint32_t sub, uint32_t r[4])
 {
-    uint32_t ctr[4] = { (uint32_t)id, (uint32_t)(id >> 32) | (s->cfg.stack_index << 16),
+    uint32_t ctr[4] = { (uint32_t)x, (uint32_t)(x >> 32) | (s->cfg.stack_index << 16),
                         step, sub };
     uint32_t key[2] = { (uint32_t)s->cfg.seed, (uint32_t)(s->cfg.seed >> 32) };
     or_philox4x32_10(ctr, key, r);
@@ -266,7 +270,7 @@ static void add_score(or_sim *s, int is_T, int bin, double sc)
  * interface a uniform draw against T decides transmission (layer changes,
  * direction kept) or reflection (direction mirrored); the remaining time is
  * then flown with the velocity of the layer the carrier is in. */
-static int half_flight(or_sim *s, or_rec *p, float tau, uint64_t id, uint32_t sub0)
+static int half_flight(or_sim *s, or_rec *p, float tau, uint64_t key, uint32_t sub0)
 {
     int met = 0;      /* boundaries met (surfaces and interfaces) */
     const or_config *c = &s->cfg;
@@ -298,7 +302,7 @@ static int half_flight(or_sim *s, or_rec *p, float tau, uint64_t id, uint32_t su
             s->led.iface_hits++;
             if (!(c->flags & OR_F_TRANSPARENT)) {
                 uint32_t r[4];
-                draw(s, id, s->step, sub0 + (uint32_t)hit, r);
+                draw(s, key, s->step, sub0 + (uint32_t)hit, r);
                 int te = ((iface * 2 + dir) * 2 + sg) * c->n_e + (k - 1);
                 trans = r[0] < s->T_thr[te];
                 if (s->adj) add_score(s, 1, te, trans ? s->adj->s_tr[te] : s->adj->s_rf[te]);
@@ -379,14 +383,14 @@ static void advance(or_sim *s, or_rec *p, int64_t i)
             A->Rmag = fabs(A->own[id]) + fabs(A->acc[id]);
         }
 
-        const int met1 = half_flight(s, p, half, id, SUB_IF + 0);
+        const int met1 = half_flight(s, p, half, (uint64_t)i, SUB_IF + 0);
 
         /* Scattering(dt): one Monte-Carlo test against tau_eff (Eq. lifetimes);
          * the event words are drawn only for a carrier that scatters */
         uint32_t x[4] = { test_word(s, i), 0u, 0u, 0u };
         if (x[0] < s->P_thr[idx3(s, c->layer_mat[PK_L(p->packed)], sg, (int)PK_K(p->packed))]) {
             uint32_t ev[4];
-            draw(s, id, s->step, SUB_SCAT, ev);
+            draw(s, (uint64_t)i, s->step, SUB_EVT, ev);
             x[1] = ev[1]; x[2] = ev[2]; x[3] = ev[3];
         }
         int k = (int)PK_K(p->packed), layer = (int)PK_L(p->packed);
@@ -420,7 +424,7 @@ static void advance(or_sim *s, or_rec *p, int64_t i)
                     /* secondary: same place, spin from P0 of this material,
                      * isotropic direction, one generation more */
                     uint32_t y[4];
-                    draw(s, id, s->step, SUB_SEC, y);
+                    draw(s, (uint64_t)i, s->step, SUB_SEC, y);
                     uint32_t g = PK_G(p->packed);
                     uint32_t sgs = y[0] < s->P0_thr[m] ? 0u : 1u;
                     or_rec q;
@@ -433,7 +437,7 @@ static void advance(or_sim *s, or_rec *p, int64_t i)
                      * after the step: a dropped secondary's are taken back */
                     or_ledger keep = s->led;
                     if (A) { A->buffering = 1; A->nbuf = 0; }
-                    half_flight(s, &q, half, id, SUB_SIF);
+                    half_flight(s, &q, half, (uint64_t)i, SUB_SIF);
                     if (A) A->buffering = 0;
                     if (s->n_slots < c->capacity) {
                         uint64_t nid = s->next_id++;
@@ -472,7 +476,7 @@ static void advance(or_sim *s, or_rec *p, int64_t i)
             }
         }
 
-        const int met2 = half_flight(s, p, half, id, SUB_IF + 16);
+        const int met2 = half_flight(s, p, half, (uint64_t)i, SUB_IF + 16);
         if (met2 && !met1 && !(x[0] < s->P_thr[t])) s->led.eventful++;
         flux(s, sg, c_start, cell_of(s, p->z));
         if (A) credit(s, id, flux_reward(s, sg, c_start, cell_of(s, p->z)));

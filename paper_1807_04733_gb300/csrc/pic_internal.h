@@ -31,14 +31,16 @@ enum {
     L_TRUNCATED, L_PARTICLE_STEPS, L_CHANGED, L_EVENTFUL
 };
 
-// Philox counter layout: ctr = {id_lo, id_hi | stack << 16, step, substream}
+// Philox counter layout: ctr = {x, x_hi | global stack << 16, step, substream}
+// with x the new carrier's id for the source draws and the drawing carrier's
+// slot (within its stack) for every other word
 enum : uint32_t {
-    SUB_SCAT = 0x000u,   // scattering test and event words
-    SUB_SEC = 0x001u,    // secondary spin and direction
-    SUB_IF = 0x100u,     // + 16*half + hit: interface draws of a carrier
-    SUB_SIF = 0x200u,    // + hit: the secondary's second-half flight
-    SUB_INJ = 0x300u,    // + j: source draws
-    SUB_TEST = 0x400u,   // scattering test: ctr.x = slot / 4, word slot % 4
+    SUB_INJ = 0x300u,    // + j: source draws (id)
+    SUB_TEST = 0x400u,   // scattering test: x = slot / 4, word slot % 4
+    SUB_EVT = 0x500u,    // event words of a carrier that scatters (slot)
+    SUB_SEC = 0x501u,    // its secondary's spin and direction (slot)
+    SUB_IF = 0x600u,     // + 16*half + hit: boundary draws of a flight (slot)
+    SUB_SIF = 0x700u,    // + hit: the secondary's flight (the parent's slot)
 };
 
 struct TabEnt {          // one (layer, spin, k) entry

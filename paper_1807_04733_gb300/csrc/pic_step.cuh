@@ -122,7 +122,7 @@ __device__ __forceinline__ int cell_of(const Args &a, const Stk &s, float z)
 template <bool DET, bool SC = false>
 __device__ __forceinline__ void flight(const Args &a, const Stk &s, float &z, float &mu,
                                        int &layer, TabEnt &e, float &lo, float &hi, int sg,
-                                       int k, float tau, uint32_t id_lo, uint32_t ctr_y,
+                                       int k, float tau, uint32_t key_x, uint32_t key_y,
                                        uint32_t step, uint32_t sub0, Tally &t, double R = 0.0,
                                        double *gT = nullptr)
 {
@@ -147,7 +147,7 @@ __device__ __forceinline__ void flight(const Args &a, const Stk &s, float &z, fl
             bool trans = true;
             ++t.hits;
             if (!(a.flags & PIC_F_TRANSPARENT)) {
-                const uint4 r = philox_rk(make_uint4(id_lo, ctr_y, step, sub0 + (uint32_t)hit), a);
+                const uint4 r = philox_rk(make_uint4(key_x, key_y, step, sub0 + (uint32_t)hit), a);
                 const int ti = ((iface * 2 + dir) * 2 + sg) * s.n_e + (k - 1);
                 trans = r.x < s.T[ti];
                 if (SC) {
@@ -966,13 +966,12 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         const long long vpos = fpos0 + __float_as_uint(rec.w);
         const long long gslot = sbase + vpos;
         const long long slot = vpos - s_tpref[s] * TILE;       // slot within the stack
-        const uint32_t id_lo = a.id[cur][gslot];
         int k = (int)(pk & 0xFFu);
         const float mu_in = mu;
         const uint32_t pk_in = pk;
         const int sg = (int)((pk >> 8) & 1u);
         int layer = (int)((pk >> 9) & 0xFu);
-        const uint32_t ctr_y = (pk >> 21) | S.ctr_hi;
+        const uint32_t key_x = (uint32_t)slot;              // draws keyed by the slot
         TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
         float lo = S.edge[layer], hi = S.edge[layer + 1];
         const int c_start = cell_of(a, S, z);
@@ -980,7 +979,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         // that weights every decision of this step
         const long long R = ADJ ? a.acc[cur][gslot] : 0;
         const double Rd = ADJ == 2 ? (double)R * a.inv_q : 0.0;
-        flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
+        flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, key_x, S.ctr_hi,
                               step, SUB_IF, ty, Rd, s_gT);
         const int tb = (layer * 2 + sg) * S.n_e + (k - 1);     // entry of the test
         // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes):
@@ -992,7 +991,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         bool dead = false;
         if (ADJ == 2 && !(xs < e.P)) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * Rd);
         if (xs < e.P) {
-            const uint4 x = philox_rk(make_uint4(id_lo, ctr_y, step, SUB_SCAT), a);
+            const uint4 x = philox_rk(make_uint4(key_x, S.ctr_hi, step, SUB_EVT), a);
             const bool inel = x.y < e.Q;
             // scores of the test (scattered) and of the channel
             if (ADJ == 2) {
@@ -1019,7 +1018,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
                             atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
                     } else {
                         // secondary: same place, spin from P0, isotropic
-                        const uint4 y = philox_rk(make_uint4(id_lo, ctr_y, step, SUB_SEC), a);
+                        const uint4 y = philox_rk(make_uint4(key_x, S.ctr_hi, step, SUB_SEC), a);
                         const uint32_t g0 = (pk >> 13) & 0xFFu;
                         const int sgs = y.x < S.p0[layer] ? 0 : 1;
                         const uint32_t gen = g0 < 255u ? g0 + 1u : 255u;
@@ -1027,8 +1026,8 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
                         int ls = layer;
                         TabEnt es = S.ent[(ls * 2 + sgs) * S.n_e + (ks - 1)];
                         Tally ts{};
-                        flight<DET>(a, S, zs, mus, ls, es, los, his, sgs, ks, half, id_lo,
-                                    ctr_y, step, SUB_SIF, ts);
+                        flight<DET>(a, S, zs, mus, ls, es, los, his, sgs, ks, half, key_x,
+                                    S.ctr_hi, step, SUB_SIF, ts);
                         // the secondary's boundary events ride in the (not yet
                         // used) id_hi bits until it is placed
                         const uint32_t pks = (uint32_t)ks | ((uint32_t)sgs << 8) |
@@ -1050,7 +1049,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
             if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
             if (ADJ) rw = flux_w(a, s, tj, sg, c_start, c_end);
         } else {
-            flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, id_lo, ctr_y,
+            flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, key_x, S.ctr_hi,
                                   step, SUB_IF + 16, ty, Rd, s_gT);
             const int c_end = cell_of(a, S, z);
             if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
@@ -1176,8 +1175,9 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             a.acc[cur][d] = rw;
         } else {
             const long long Rc = a.tot[stg.id_off + id];
-            const uint32_t ctr_y = (ppk >> 21) | ((uint32_t)(a.stack_base + s) << 16);
-            const uint4 y = philox_rk(make_uint4(pid_lo, ctr_y, step, SUB_SEC), a);
+            const uint32_t key_x = (uint32_t)(pos - s_tpref[s] * TILE);   // the parent's slot
+            const uint32_t key_y = (uint32_t)(a.stack_base + s) << 16;
+            const uint4 y = philox_rk(make_uint4(key_x, key_y, step, SUB_SEC), a);
             Stk gs;
             gs.ent = a.ent + stg.ent_off; gs.T = a.T_thr + stg.T_off;
             gs.edge = a.stacks[s].edge; gs.p0 = nullptr;
@@ -1188,7 +1188,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             float los = gs.edge[ls], his = gs.edge[ls + 1];
             float zs = r.w, mus = mu_of(y.y);
             Tally tq{};
-            flight<DET, true>(a, gs, zs, mus, ls, es, los, his, sg, k, half, pid_lo, ctr_y,
+            flight<DET, true>(a, gs, zs, mus, ls, es, los, his, sg, k, half, key_x, key_y,
                               step, SUB_SIF, tq, (double)Rc * a.inv_q, a.g_T + stg.T_off);
             // the same words give the same flight: anything else means the
             // replay is not the forward run

@@ -88,15 +88,16 @@ class Tracer:
                                    s=(w >> 8) & 1, l=(w >> 9) & 15, g=(w >> 13) & 255))
         self.next_id = next_id
 
-    def rand(self, pid, sub):
-        ctr = [pid & MASK, ((pid >> 32) | (self.sidx << 16)) & MASK, self.step_no, sub]
+    def rand(self, key, sub):
+        # key: the carrier's slot (event, secondary and boundary words)
+        ctr = [key & MASK, ((key >> 32) | (self.sidx << 16)) & MASK, self.step_no, sub]
         return philox(ctr, self.key)
 
     def cell(self, z):
         c = int(np.floor(F(z) / F(self.wl.dz)))
         return min(max(c, 0), self.ncell - 1)
 
-    def fly(self, p, tau, pid, sub0):
+    def fly(self, p, tau, key, sub0):
         tau = F(tau)
         hit = 0
         while True:
@@ -126,7 +127,7 @@ class Tracer:
                 iface, d = (lay, 0) if up else (lay - 1, 1)
                 ok = True
                 if not (self.wl.flags & 4):
-                    ok = self.rand(pid, sub0 + hit)[0] < self.T[iface, d, p["s"], p["k"]]
+                    ok = self.rand(key, sub0 + hit)[0] < self.T[iface, d, p["s"], p["k"]]
                 if ok:
                     p["l"] = lay + 1 if up else lay - 1
                     self.counts["trans"] += 1
@@ -147,15 +148,14 @@ class Tracer:
             p = self.parts[i]
             if p["k"] == 0:
                 continue
-            pid = p["id"]
             c0 = self.cell(p["z"])
-            self.fly(p, half, pid, 0x100)
+            self.fly(p, half, i, 0x600)
             grp = philox([i >> 2, (self.sidx << 16) & MASK, self.step_no, 0x400], self.key)
             m = self.mat[p["l"]]
             k = p["k"]
             x = [grp[i & 3], 0, 0, 0]
             if x[0] < self.P[m, p["s"], k]:
-                x = [x[0]] + self.rand(pid, 0)[1:]
+                x = [x[0]] + self.rand(i, 0x500)[1:]
                 inel = x[1] < self.Q[m, p["s"], k]
                 if k == 1 and (inel or wl.flags & 8):
                     p["k"] = 0
@@ -170,13 +170,13 @@ class Tracer:
                     if wl.flags & 2:
                         self.counts["bath"] += k - kp
                     else:
-                        y = self.rand(pid, 1)
+                        y = self.rand(i, 0x501)
                         q = dict(z=p["z"], mu=direction(y[1]), id=None, k=k - kp,
                                  s=0 if y[0] < self.P0[m] else 1, l=p["l"],
                                  g=min(p["g"] + 1, 255))
                         cs = self.cell(q["z"])
                         before = (self.counts["iface"], self.counts["trans"])
-                        self.fly(q, half, pid, 0x200)
+                        self.fly(q, half, i, 0x700)
                         if len(self.parts) < self.st.capacity:
                             q["id"] = self.next_id
                             self.next_id += 1
@@ -186,7 +186,7 @@ class Tracer:
                         else:
                             self.counts["iface"], self.counts["trans"] = before
                             self.counts["dropped"] += 1
-            self.fly(p, half, pid, 0x110)
+            self.fly(p, half, i, 0x610)
             self.add_flux(p["s"], c0, self.cell(p["z"]))
         if (self.step_no + 1) % wl.moment_every == 0:
             t = (self.step_no + 1) // wl.moment_every - 1

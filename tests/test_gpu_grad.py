@@ -204,8 +204,9 @@ def test_fast_build_finite_differences_common_random_numbers():
     """Default build, Fe/Au bilayer with the pulse (2e5 carriers, capacity
     raised so that nothing is dropped): central differences with the same
     seed (the same Philox words) along tau_in and along T agree with the
-    adjoint's directional derivatives over 16 seeds within 2 SE."""
-    R, h = 16, 0.1
+    adjoint's directional derivatives over 32 seeds within 3 SE (a 2-SE bound
+    fails about one seed set in twenty per direction when the two agree)."""
+    R, h = 32, 0.1
     base = W.config(3, scale=0.02).replace(n_steps=300)
     st0 = base.stacks[0]
     st0.capacity = 40 * st0.n0
@@ -253,4 +254,4 @@ def test_fast_build_finite_differences_common_random_numbers():
         nif = st0.T.shape[0]
         d_T.append((vals[0] - vals[1]) / (2 * h) - (g_T[:nif] * st0.T).sum())
     for d in (np.array(d_tau), np.array(d_T)):
-        assert abs(d.mean()) <= 2 * d.std(ddof=1) / math.sqrt(R), d
+        assert abs(d.mean()) <= 3 * d.std(ddof=1) / math.sqrt(R), d

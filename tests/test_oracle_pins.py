@@ -317,7 +317,11 @@ def test_p7_branching_recurrence():
     N0[2 * n_e - 1] = (np.arange(N) % 3 == 2).sum()
     expect = np.linalg.matrix_power(A, n) @ N0
     counts = np.array(counts)
-    mean, se = counts.mean(0), counts.std(0, ddof=1) / math.sqrt(R)
+    # a bin with a few carriers per run is a rare-event count (Poisson in the
+    # limit): over 16 runs its sample variance can fall far below that, so the
+    # SE is floored at the Poisson value of the expected count
+    var = np.maximum(counts.var(0, ddof=1), expect)
+    mean, se = counts.mean(0), np.sqrt(var / R)
     ok = np.abs(mean - expect) <= 4 * se + 0.5
     assert ok.all(), (mean, expect, se)
     assert expect.sum() > 2 * N          # the cascade really multiplied carriers
