@@ -365,24 +365,43 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, uint32_t
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity)
+// One poll; a thread whose phase has not completed may be suspended, for at
+// most `hint_ns` (the instruction's suspend-time hint), so that a wait
+// bounded in polls is bounded in time too.
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, uint32_t parity,
+                                              uint32_t hint_ns)
 {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
 
-// bounded wait: false if the copy did not land within `limit` polls
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait: false if the phase did not complete within `limit` polls or
+// within PIC_WAIT_NS of the global timer, whichever comes first.
+#ifndef PIC_WAIT_NS
+#define PIC_WAIT_NS 4000000000ull
+#endif
 __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, uint32_t parity,
                                           unsigned int limit)
 {
-    for (unsigned int it = 0; it < limit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity, 20000u)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned int it = 1; it < limit; ++it) {
+        if (mbar_try_wait(bar, parity, 20000u)) return true;
+        if (global_ns() - t0 > PIC_WAIT_NS) return false;
+    }
     return false;
 }
 
