@@ -37,10 +37,10 @@ METRIC = "particle-steps/s"
 UNIT = "particle-steps/s"
 HBM_FALLBACK_GBS = 6800.0
 # algorithmic bytes: read z, mu, packed (12 B) + write z (4 B) per live
-# carrier-step; the id (4 B) of every carrier that scatters or meets a
-# boundary (it keys that carrier's event draws); 8 B (mu, packed) per carrier
-# whose record changed; 16 B per secondary placed
-B_STEP, B_EVENTFUL, B_CHANGED, B_SPAWN = 16, 4, 8, 16
+# carrier-step; nothing more for a carrier that scatters or meets a boundary
+# (its draws are keyed by its slot, its record was read once already); 8 B
+# (mu, packed) per carrier whose record changed; 16 B per secondary placed
+B_STEP, B_EVENTFUL, B_CHANGED, B_SPAWN = 16, 0, 8, 16
 
 
 def parse():
@@ -108,7 +108,7 @@ def measured_peak():
 # scaled to 1/20 (profiles/k_fast_k_event_k_place_fe15_au300_small.md); the
 # traffic grows in proportion to the carriers advanced.  Valid only for the
 # kernel source whose hash is given: reported as null once the kernels change.
-NCU_TRAFFIC = {"bytes_per_particle_step": 20.77, "src_sha": "9d2552fadbe4a4d2"}
+NCU_TRAFFIC = {"bytes_per_particle_step": 18.47, "src_sha": "c95752e5966ea27a"}
 
 
 def kernel_sha():
