@@ -520,11 +520,13 @@ __device__ __forceinline__ unsigned long long consumer_sum_u64(unsigned long lon
     return t;  // valid in thread 0
 }
 
-// Resident blocks per SM the register budget must allow: four for the step
-// (56 registers, no spills: 36 warps per SM), three for the replay passes,
-// which carry the per-slot reward as well.
+// Resident blocks per SM the register budget must allow: three for the step
+// (72 registers, no spills: 27 warps per SM; the four carriers' flights are
+// computed side by side with the Philox rounds, which four blocks at 56
+// registers cannot hold without spilling) and for the replay passes, which
+// carry the per-slot reward as well.
 #ifndef PIC_FAST_MIN_BLOCKS
-#define PIC_FAST_MIN_BLOCKS 4
+#define PIC_FAST_MIN_BLOCKS 3
 #endif
 #ifndef PIC_FAST_MIN_BLOCKS_ADJ
 #define PIC_FAST_MIN_BLOCKS_ADJ 3
@@ -746,27 +748,50 @@ k_fast(const Args a)
         const uint32_t xw[VEC] = {xg.x, xg.y, xg.z, xg.w};
         float zo[VEC] = {z4.x, z4.y, z4.z, z4.w};
         uint32_t slowbits = 0;
+        // First the two half flights and the cells of all four carriers: none
+        // of it depends on the test words, so the scheduler overlaps it with
+        // the Philox rounds.  Slots past the end or with k = 0 read entry 0.
+        float z2v[VEC];
+        uint32_t pthr[VEC];
+        int c0v[VEC], c1v[VEC];
+        uint32_t live = 0, crossm = 0;
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            const uint32_t pk = pin[j];
+            const int k = (int)(pk & 0xFFu);
+            const bool ok = (i0 + j < nvalid) && k != 0;
+            const int sg = (int)((pk >> 8) & 1u), layer = (int)((pk >> 9) & 0xFu);
+            const FastEnt e = s_ent[ok ? (layer * 2 + sg) * ne + (k - 1) : 0];
+            const float z = zin[j], mu = min_[j];
+            const float w = __fmul_rn(e.v, mu);
+            const float z1 = DET ? __fadd_rn(z, __fmul_rn(w, half)) : __fmaf_rn(w, half, z);
+            const float z2 = DET ? __fadd_rn(z1, __fmul_rn(w, half)) : __fmaf_rn(w, half, z1);
+            // the motion is monotone within the step: the end point decides
+            const bool cross = mu > 0.f ? (z2 > e.hi) : (z2 < e.lo);
+            z2v[j] = z2;
+            pthr[j] = e.P;
+            // cells floor(z / dz): 2^23 added with rounding toward -inf
+            c0v[j] = __float_as_int(__fadd_rd(__fmul_rn(z, a.inv_dz), 8388608.0f)) - 0x4B000000;
+            c1v[j] = __float_as_int(__fadd_rd(__fmul_rn(z2, a.inv_dz), 8388608.0f)) - 0x4B000000;
+            live |= (uint32_t)ok << j;
+            crossm |= (uint32_t)cross << j;
+        }
+        n_steps += __popc(live);
+        // then the scattering test, and the flux, deposit and new depth of the
+        // carriers that neither scatter nor meet a boundary
 #pragma unroll
         for (int j = 0; j < VEC; ++j) {
             int bin = -1;
-            const uint32_t pk = pin[j];
-            const int k = (int)(pk & 0xFFu);
-            if (i0 + j < nvalid && k != 0) {
-                ++n_steps;
-                const float z = zin[j], mu = min_[j];
+            if ((live >> j) & 1u) {
+                const uint32_t pk = pin[j];
+                const int k = (int)(pk & 0xFFu);
                 const int sg = (int)((pk >> 8) & 1u), layer = (int)((pk >> 9) & 0xFu);
-                const FastEnt e = s_ent[(layer * 2 + sg) * ne + (k - 1)];
-                const float w = __fmul_rn(e.v, mu);
-                const float z1 = DET ? __fadd_rn(z, __fmul_rn(w, half)) : __fmaf_rn(w, half, z);
-                const float z2 = DET ? __fadd_rn(z1, __fmul_rn(w, half)) : __fmaf_rn(w, half, z1);
-                // the motion is monotone within the step: the end point decides
-                const bool cross = mu > 0.f ? (z2 > e.hi) : (z2 < e.lo);
-                if (cross || xw[j] < e.P) {
+                (void)k; (void)layer;
+                if (((crossm >> j) & 1u) || xw[j] < pthr[j]) {
                     slowbits |= 1u << j;
                 } else {
-                    // cells floor(z / dz): 2^23 added with rounding toward -inf
-                    const int c0u = __float_as_int(__fadd_rd(__fmul_rn(z, a.inv_dz), 8388608.0f)) - 0x4B000000;
-                    const int c1u = __float_as_int(__fadd_rd(__fmul_rn(z2, a.inv_dz), 8388608.0f)) - 0x4B000000;
+                    const float z2 = z2v[j];
+                    const int c0u = c0v[j], c1u = c1v[j];
                     const int c1 = c1u < nc - 1 ? c1u : nc - 1;
                     if (!ADJ && c0u != c1u) {
                         const int c0 = c0u < nc - 1 ? c0u : nc - 1;
