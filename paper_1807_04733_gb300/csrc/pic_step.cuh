@@ -244,33 +244,63 @@ __device__ __forceinline__ void publish(unsigned long long *w, unsigned int ep,
 }
 
 // Exclusive prefix of the running count of the stack segment that starts
-// this block's chunk at tile t0 (stack tiles start at ts): walk back over the
-// blocks whose chunks end inside the same stack.  Bounded wait.
-static __device__ long long look_back(const Args &a, unsigned int ep, long long T, long long ts,
-                               int b, int G)
+// this block's chunk (the stack's tiles start at ts): walk back over the
+// blocks whose chunks end inside the same stack, 32 of them at a time (one
+// per lane of the calling warp, every lane of which must call), each with a
+// bounded wait for its status word, down to the nearest block that has
+// published an inclusive prefix.  `lo(j)` is the first tile of block j.
+template <class Lo>
+static __device__ long long look_back_warp(const Args &a, unsigned int ep, long long ts, int b,
+                                           Lo lo)
 {
+    const int lane = threadIdx.x & 31;
     long long prefix = 0;
-    for (int j = b - 1; j >= 0; --j) {
-        const long long jt0 = T * j / G, jt1 = T * (j + 1) / G;
-        if (jt1 <= ts) break;
-        if (jt0 == jt1) continue;
-        unsigned long long w = 0;
-        unsigned int it = 0;
-        for (;;) {
-            w = ld_volatile_u64(&a.status[j]);
-            if ((unsigned int)(w >> 32) == ep && ((w >> 30) & 3ull)) break;
-            if (++it > a.spin_limit) {
-                atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
-                a.ctl->timeout_where = 1u;
-                w = FLAG_P << 30;
-                break;
+    for (int j0 = b - 1; j0 >= 0; j0 -= 32) {
+        const int j = j0 - lane;
+        // 2: the walk stops before this block; 1: an inclusive prefix; 0: an
+        // aggregate, or a block without tiles
+        int kind = 0;
+        long long v = 0;
+        if (j < 0) {
+            kind = 2;
+        } else {
+            const long long jt0 = lo(j), jt1 = lo(j + 1);
+            if (jt1 <= ts) {
+                kind = 2;
+            } else if (jt0 != jt1) {
+                unsigned long long w = 0;
+                unsigned int it = 0;
+                for (;;) {
+                    w = ld_volatile_u64(&a.status[j]);
+                    if ((unsigned int)(w >> 32) == ep && ((w >> 30) & 3ull)) break;
+                    if (++it > a.spin_limit) {
+                        atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+                        a.ctl->timeout_where = 1u;
+                        w = FLAG_P << 30;
+                        break;
+                    }
+                    if (it > 64) __nanosleep(128);
+                }
+                v = (long long)(w & 0x3FFFFFFFull);
+                if (((w >> 30) & 3ull) == FLAG_P) kind = 1;
             }
-            if (it > 64) __nanosleep(128);
         }
-        prefix += (long long)(w & 0x3FFFFFFFull);
-        if (((w >> 30) & 3ull) == FLAG_P) break;
+        // the nearest block that ends the walk, and the sum up to it
+        const unsigned int term = __ballot_sync(0xffffffffu, kind != 0);
+        const int tl = term ? __ffs(term) - 1 : 32;
+        long long c = (lane < tl || (lane == tl && kind == 1)) ? v : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        prefix += c;
+        if (term) break;
     }
     return prefix;
+}
+
+__device__ __forceinline__ long long look_back(const Args &a, unsigned int ep, long long T,
+                                               long long ts, int b, int G)
+{
+    return look_back_warp(a, ep, ts, b, [&](int j) { return T * j / G; });
 }
 
 // Per-block plan shared by the streaming kernels: tiles of every stack
@@ -431,33 +461,11 @@ __device__ __forceinline__ long long slow_lo(long long T, int j, int Gs, int Gf)
 }
 
 // Exclusive prefix of the secondaries of the stack segment that starts slow
-// block b's chunk (stack tiles start at ts): walk back over the blocks whose
-// chunks end inside the same stack.  Bounded wait.
-static __device__ long long look_back_place(const Args &a, unsigned int ep, long long T, long long ts,
-                                    int b, int Gs, int Gf)
+// block b's chunk (stack tiles start at ts); warp-wide, as look_back_warp.
+__device__ __forceinline__ long long look_back_place(const Args &a, unsigned int ep, long long T,
+                                                     long long ts, int b, int Gs, int Gf)
 {
-    long long prefix = 0;
-    for (int j = b - 1; j >= 0; --j) {
-        const long long jt0 = slow_lo(T, j, Gs, Gf), jt1 = slow_lo(T, j + 1, Gs, Gf);
-        if (jt1 <= ts) break;
-        if (jt0 == jt1) continue;
-        unsigned long long w = 0;
-        unsigned int it = 0;
-        for (;;) {
-            w = ld_volatile_u64(&a.status[j]);
-            if ((unsigned int)(w >> 32) == ep && ((w >> 30) & 3ull)) break;
-            if (++it > a.spin_limit) {
-                atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
-                a.ctl->timeout_where = 1u;
-                w = FLAG_P << 30;
-                break;
-            }
-            if (it > 64) __nanosleep(128);
-        }
-        prefix += (long long)(w & 0x3FFFFFFFull);
-        if (((w >> 30) & 3ull) == FLAG_P) break;
-    }
-    return prefix;
+    return look_back_warp(a, ep, ts, b, [&](int j) { return slow_lo(T, j, Gs, Gf); });
 }
 
 // tile prefix over the stacks, in dynamic shared memory
@@ -1364,18 +1372,25 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             c_last = count_bits(s_tpref[s_last] > t0 ? s_tpref[s_last] : t0, t1);
         }
         for (int f = fb0 + tid; f < fb1; f += TPB) a.fspawn[f] = 0u;   // consumed
-        if (tid == 0) {
-            // the count of the last segment goes out before any wait
+        if (tid < 32) {
+            // the count of the last segment goes out before any wait; the
+            // look-back takes the whole warp
             if (!inside_last) {
-                publish(&a.status[b], ep, FLAG_P, c_last);
-                s_pre[1] = 0;
+                if (tid == 0) {
+                    publish(&a.status[b], ep, FLAG_P, c_last);
+                    s_pre[1] = 0;
+                }
             } else {
-                publish(&a.status[b], ep, FLAG_A, c_last);
-                s_pre[1] = look_back_place(a, ep, T, s_tpref[s_last], b, Gs, Gf);
-                publish(&a.status[b], ep, FLAG_P, s_pre[1] + c_last);
+                if (tid == 0) publish(&a.status[b], ep, FLAG_A, c_last);
+                const long long pre = look_back_place(a, ep, T, s_tpref[s_last], b, Gs, Gf);
+                if (tid == 0) {
+                    s_pre[1] = pre;
+                    publish(&a.status[b], ep, FLAG_P, pre + c_last);
+                }
             }
-            s_pre[0] = (s_first < s_last && inside_first)
-                           ? look_back_place(a, ep, T, s_tpref[s_first], b, Gs, Gf) : 0;
+            const long long pre0 = (s_first < s_last && inside_first)
+                                       ? look_back_place(a, ep, T, s_tpref[s_first], b, Gs, Gf) : 0;
+            if (tid == 0) s_pre[0] = pre0;
         }
         __syncthreads();
         (void)c_first;
@@ -1564,14 +1579,19 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
             if (s == s_last) c_last += tot;
         }
         long long pre_first = 0;
-        if (tid == 0) {
+        if (tid < 32) {
+            // the look-back takes the whole warp
             if (s_last == s_first && first_inside) {
-                publish(&a.status[b], ep, FLAG_A, c_last);
-                s_prefix = look_back(a, ep, p.T, s_tpref[s_first], b, G);
-                publish(&a.status[b], ep, FLAG_P, s_prefix + c_last);
+                if (tid == 0) publish(&a.status[b], ep, FLAG_A, c_last);
+                const long long pre = look_back(a, ep, p.T, s_tpref[s_first], b, G);
+                if (tid == 0) {
+                    s_prefix = pre;
+                    publish(&a.status[b], ep, FLAG_P, pre + c_last);
+                }
             } else {
-                publish(&a.status[b], ep, FLAG_P, c_last);
-                s_prefix = first_inside ? look_back(a, ep, p.T, s_tpref[s_first], b, G) : 0;
+                if (tid == 0) publish(&a.status[b], ep, FLAG_P, c_last);
+                const long long pre = first_inside ? look_back(a, ep, p.T, s_tpref[s_first], b, G) : 0;
+                if (tid == 0) s_prefix = pre;
             }
         }
         __syncthreads();
