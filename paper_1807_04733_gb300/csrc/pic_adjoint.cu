@@ -82,7 +82,7 @@ __global__ void k_init_acc(const Args a, int pass)
              i += (long long)gridDim.x * blockDim.x) {
             const long long slot = st.base + i;
             const unsigned long long id = (unsigned long long)a.id[0][slot] |
-                                          ((unsigned long long)(a.pk[0][slot] >> 21) << 32);
+                                          ((unsigned long long)(a.pk[0][slot * a.mp_stride] >> 21) << 32);
             long long v = 0;
             if (pass == 2) {
                 if (id < (unsigned long long)st.n_ids) v = a.tot[st.id_off + (long long)id];
@@ -104,7 +104,7 @@ __global__ void k_flush_own(const Args a)
              i += (long long)gridDim.x * blockDim.x) {
             const long long slot = st.base + i;
             const unsigned long long id = (unsigned long long)a.id[cur][slot] |
-                                          ((unsigned long long)(a.pk[cur][slot] >> 21) << 32);
+                                          ((unsigned long long)(a.pk[cur][slot * a.mp_stride] >> 21) << 32);
             if (id < (unsigned long long)st.n_ids) a.tot[st.id_off + (long long)id] = a.acc[cur][slot];
             else atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_STATE);
         }

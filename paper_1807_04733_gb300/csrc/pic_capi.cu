@@ -306,14 +306,16 @@ void free_all(pic_ctx *c)
     release(c->d_cdf_thr);
     release(c->d_cdf_cell); release(c->d_cdf_layer); release(c->d_inj);
     for (int b = 0; b < 2; ++b) {
-        release(c->d_z[b]); release(c->d_mu[b]); release(c->d_id[b]); release(c->d_pk[b]);
+        c->d_pk[b] = nullptr;                   // inside d_mu[b]
+        release(c->d_z[b]); release(c->d_mu[b]); release(c->d_id[b]);
     }
     release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh);
     release(c->d_qrec); release(c->d_qcnt); release(c->d_fspawn); release(c->d_J); release(c->d_cnt);
     release(c->d_ctl);
     Replay &r = c->rp;
     for (int b = 0; b < 2; ++b) {
-        release(r.z[b]); release(r.mu[b]); release(r.id[b]); release(r.pk[b]); release(r.acc[b]);
+        r.pk[b] = nullptr;                      // inside r.mu[b]
+        release(r.z[b]); release(r.mu[b]); release(r.id[b]); release(r.acc[b]);
     }
     release(r.stage_l); release(r.status); release(r.qcnt); release(r.fspawn); release(r.cnt); release(r.ctl); release(r.stacks);
     release(r.aent); release(r.aT); release(r.g_ent); release(r.g_T); release(r.gpot);
@@ -518,9 +520,9 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     ALLOC(c->d_inj, (size_t)n_stacks * 2 * p->n_steps_max);
     for (int b = 0; b < 2; ++b) {
         ALLOC(c->d_z[b], c->total_slots);
-        ALLOC(c->d_mu[b], c->total_slots);
+        ALLOC(c->d_mu[b], 2 * c->total_slots);     // (mu, packed) pairs
         ALLOC(c->d_id[b], c->total_slots);
-        ALLOC(c->d_pk[b], c->total_slots);
+        if (e == cudaSuccess) c->d_pk[b] = reinterpret_cast<uint32_t *>(c->d_mu[b]) + 1;
     }
     ALLOC(c->d_stage, c->total_slots);
     ALLOC(c->d_bits, c->total_slots / 32 + 1);
@@ -545,6 +547,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.inj = c->d_inj;
     for (int b = 0; b < 2; ++b) {
         a.z[b] = c->d_z[b]; a.mu[b] = c->d_mu[b]; a.id[b] = c->d_id[b]; a.pk[b] = c->d_pk[b];
+        a.mp_stride = 2;
     }
     a.stage = c->d_stage;
     a.spawn_bits = c->d_bits;
@@ -832,15 +835,18 @@ pic_status pic_records(pic_ctx *c, int stack, pic_record *out, int64_t *n)
     if (cnt == 0) return PIC_OK;
     const int b = (int)ctl.cur;
     const int64_t base = c->ds[stack].base;
-    std::vector<float> z(cnt), mu(cnt);
-    std::vector<uint32_t> id(cnt), pk(cnt);
+    std::vector<float> z(cnt);
+    std::vector<uint32_t> id(cnt), mp(2 * cnt);      // (mu, packed) pairs
     e = cudaMemcpyAsync(z.data(), c->d_z[b] + base, 4 * cnt, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(mu.data(), c->d_mu[b] + base, 4 * cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(mp.data(), c->d_mu[b] + 2 * base, 8 * cnt, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(id.data(), c->d_id[b] + base, 4 * cnt, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(pk.data(), c->d_pk[b] + base, 4 * cnt, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pic_records copy");
-    for (int64_t i = 0; i < cnt; ++i) out[i] = pic_record{z[i], mu[i], id[i], pk[i]};
+    for (int64_t i = 0; i < cnt; ++i) {
+        float mu;
+        std::memcpy(&mu, &mp[2 * i], 4);
+        out[i] = pic_record{z[i], mu, id[i], mp[2 * i + 1]};
+    }
     return PIC_OK;
 }
 
@@ -867,14 +873,18 @@ pic_status pic_set_records(pic_ctx *c, int stack, const pic_record *in, int64_t 
     if (e != cudaSuccess) return cuda_fail(c, e, "pic_set_records");
     const int b = (int)ctl.cur;
     const int64_t base = c->ds[stack].base;
-    std::vector<float> z(n), mu(n);
-    std::vector<uint32_t> id(n), pk(n);
-    for (int64_t i = 0; i < n; ++i) { z[i] = in[i].z; mu[i] = in[i].mu; id[i] = in[i].id; pk[i] = in[i].packed; }
+    std::vector<float> z(n);
+    std::vector<uint32_t> id(n), mp(2 * n);          // (mu, packed) pairs
+    for (int64_t i = 0; i < n; ++i) {
+        z[i] = in[i].z;
+        std::memcpy(&mp[2 * i], &in[i].mu, 4);
+        mp[2 * i + 1] = in[i].packed;
+        id[i] = in[i].id;
+    }
     if (n) {
         e = cudaMemcpyAsync(c->d_z[b] + base, z.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mu[b] + base, mu.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mu[b] + 2 * base, mp.data(), 8 * n, cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_id[b] + base, id.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_pk[b] + base, pk.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
     }
     const unsigned long long vals[2] = {(unsigned long long)n, (unsigned long long)next_id};
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt + stack, vals, sizeof(vals), cudaMemcpyHostToDevice, c->stream);
@@ -930,8 +940,9 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
 #define RALLOC(ptr, n) do { if (e == cudaSuccess && !(ptr)) e = dalloc(&ptr, n); } while (0)
     if (!r.ready) {
         for (int b = 0; b < 2; ++b) {
-            RALLOC(r.z[b], c->total_slots); RALLOC(r.mu[b], c->total_slots);
-            RALLOC(r.id[b], c->total_slots); RALLOC(r.pk[b], c->total_slots);
+            RALLOC(r.z[b], c->total_slots); RALLOC(r.mu[b], 2 * c->total_slots);
+            RALLOC(r.id[b], c->total_slots);
+            if (e == cudaSuccess) r.pk[b] = reinterpret_cast<uint32_t *>(r.mu[b]) + 1;
             RALLOC(r.acc[b], c->total_slots);
         }
         RALLOC(r.stage_l, c->total_slots);
@@ -1067,14 +1078,18 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
             cnt[s].next_id = c->init_next_id[s];
             const int64_t n = (int64_t)ir.size();
             if (!n) continue;
-            std::vector<float> z(n), mu(n);
-            std::vector<uint32_t> id(n), pk(n);
-            for (int64_t i = 0; i < n; ++i) { z[i] = ir[i].z; mu[i] = ir[i].mu; id[i] = ir[i].id; pk[i] = ir[i].packed; }
+            std::vector<float> z(n);
+            std::vector<uint32_t> id(n), mp(2 * n);      // (mu, packed) pairs
+            for (int64_t i = 0; i < n; ++i) {
+                z[i] = ir[i].z;
+                std::memcpy(&mp[2 * i], &ir[i].mu, 4);
+                mp[2 * i + 1] = ir[i].packed;
+                id[i] = ir[i].id;
+            }
             const int64_t base = c->ds[s].base;
             e = cudaMemcpyAsync(r.z[0] + base, z.data(), 4 * n, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r.mu[0] + base, mu.data(), 4 * n, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(r.mu[0] + 2 * base, mp.data(), 8 * n, cudaMemcpyHostToDevice, st);
             if (e == cudaSuccess) e = cudaMemcpyAsync(r.id[0] + base, id.data(), 4 * n, cudaMemcpyHostToDevice, st);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(r.pk[0] + base, pk.data(), 4 * n, cudaMemcpyHostToDevice, st);
             if (e != cudaSuccess) break;
             e = cudaStreamSynchronize(st);          // host vectors go out of scope
         }

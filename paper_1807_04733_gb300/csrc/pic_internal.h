@@ -103,9 +103,14 @@ struct Args {            // everything a kernel needs, passed by value
     const int32_t *cdf_layer;
     const long long *inj;
     float *z[2];
+    // mu and packed of slot i at mu[b][i * mp_stride] and pk[b][i * mp_stride]:
+    // a context keeps them interleaved (stride 2, pk = mu + 1), so that an
+    // event updates one 32-byte sector for both; the allocation-free
+    // compaction takes separate arrays (stride 1)
     float *mu[2];
     uint32_t *id[2];
     uint32_t *pk[2];
+    int mp_stride;
     float4 *stage;
     unsigned long long *status;      // one look-back word per block
     uint32_t *n_hist;

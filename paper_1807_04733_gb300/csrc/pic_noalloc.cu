@@ -121,6 +121,7 @@ extern "C" pic_status pic_compact_static(const float *z, const float *mu, const 
     a.mu[0] = const_cast<float *>(mu); a.mu[1] = mu_out;
     a.id[0] = const_cast<uint32_t *>(id); a.id[1] = id_out;
     a.pk[0] = const_cast<uint32_t *>(packed); a.pk[1] = packed_out;
+    a.mp_stride = 1;                      // separate mu and packed arrays
     a.status = scr->status;
     a.cnt = &scr->cnt;
     a.ctl = &scr->ctl;

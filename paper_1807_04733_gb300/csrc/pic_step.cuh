@@ -595,8 +595,7 @@ k_fast(const Args a)
     const long long ntiles = t1 - t0;
     const int nring = a.ring;
     float *Z = a.z[cur];
-    const float *MU = a.mu[cur];
-    const uint32_t *PK = a.pk[cur];
+    const float *MP = a.mu[cur];         // mu and packed, interleaved
 
     // ---------------- producer warp ----------------
     if (warp == FAST_WARPS) {
@@ -619,8 +618,7 @@ k_fast(const Args a)
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_expect_tx(&s_full[stg], STG * TILE_BYTES);
                 bulk_load(dst, Z + off, TILE_BYTES, &s_full[stg]);
-                bulk_load(dst + TILE, MU + off, TILE_BYTES, &s_full[stg]);
-                bulk_load(dst + 2 * TILE, PK + off, TILE_BYTES, &s_full[stg]);
+                bulk_load(dst + TILE, MP + 2 * off, 2 * TILE_BYTES, &s_full[stg]);
                 if (ADJ) bulk_load(dst + 3 * TILE, a.acc[cur] + off, 2 * TILE_BYTES, &s_full[stg]);
                 issued = i + 1;
                 if (++stg == nring) { stg = 0; phase ^= 1u; }
@@ -727,16 +725,17 @@ k_fast(const Args a)
             s_abort = 1;
         }
         const float *rz = ring + (size_t)stg * STG * TILE;
-        const float *rmu = rz + TILE;
-        const uint32_t *rpk = reinterpret_cast<const uint32_t *>(rz + 2 * TILE);
+        const uint4 *rmp = reinterpret_cast<const uint4 *>(rz + TILE);   // (mu, packed) pairs
         float *gZ = Z + s_st.base + tslot0;
         const int nvalid = nsl - tslot0 < TILE ? (int)(nsl - tslot0) : TILE;
         // four consecutive slots per thread; one Philox call gives the four
         // scattering-test words of the slot group
         const int i0 = VEC * tid;
         const float4 z4 = reinterpret_cast<const float4 *>(rz)[tid];
-        const float4 m4 = reinterpret_cast<const float4 *>(rmu)[tid];
-        const uint4 p4 = reinterpret_cast<const uint4 *>(rpk)[tid];
+        const uint4 q01 = rmp[2 * tid], q23 = rmp[2 * tid + 1];
+        const float4 m4 = make_float4(__uint_as_float(q01.x), __uint_as_float(q01.z),
+                                      __uint_as_float(q23.x), __uint_as_float(q23.z));
+        const uint4 p4 = make_uint4(q01.y, q01.w, q23.y, q23.w);
         long long av[VEC];
         if (ADJ) {
             const longlong2 *racc = reinterpret_cast<const longlong2 *>(rz + 3 * TILE);
@@ -922,8 +921,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
     const int tj = (int)(step / (uint32_t)a.moment_every);
     const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
     const float half = a.half_dt;
-    float *Z = a.z[cur], *MU = a.mu[cur];
-    uint32_t *PK = a.pk[cur];
+    float *Z = a.z[cur], *MU = a.mu[cur];       // MU: (mu, packed) pairs
 
     // exclusive prefix of the queue lengths: item i of the concatenated queue
     // is entry i - s_qpre[f] of streaming block f
@@ -1116,8 +1114,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         Z[gslot] = z;
         if (__float_as_uint(mu) != __float_as_uint(mu_in) || pk != pk_in) {
             ++ty.changed;
-            MU[gslot] = mu;
-            PK[gslot] = pk;
+            *reinterpret_cast<uint2 *>(MU + 2 * gslot) = make_uint2(__float_as_uint(mu), pk);
         }
         };
 
@@ -1197,8 +1194,8 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
     const int tj = (int)(step / (uint32_t)a.moment_every);
     const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
     const float half = a.half_dt;
-    float *Z = a.z[cur], *MU = a.mu[cur];
-    uint32_t *PK = a.pk[cur];
+    float *Z = a.z[cur], *MU = a.mu[cur];       // MU: (mu, packed) pairs
+    const uint32_t *PK = a.pk[cur];
     Tally ty{};
 
     // Adjoint bookkeeping of a secondary placed at slot d with id `id`, staged
@@ -1211,7 +1208,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
                          unsigned long long id, uint32_t pk, int sg, int k, int c0, int c1,
                          const float4 &r) {
         const long long pslot = stg.base + pos - s_tpref[s] * TILE;
-        const uint32_t ppk = PK[pslot], pid_lo = a.id[cur][pslot];
+        const uint32_t ppk = PK[2 * pslot], pid_lo = a.id[cur][pslot];
         const unsigned long long pid = (unsigned long long)pid_lo | ((unsigned long long)(ppk >> 21) << 32);
         if (id >= (unsigned long long)stg.n_ids || pid >= (unsigned long long)stg.n_ids) {
             atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_STATE);
@@ -1287,9 +1284,9 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
                         const unsigned long long id = nid + (unsigned long long)g;
                         const long long d = stg.base + nsl + g;
                         Z[d] = r.x;
-                        MU[d] = r.y;
+                        *reinterpret_cast<uint2 *>(MU + 2 * d) =
+                            make_uint2(__float_as_uint(r.y), pk | ((uint32_t)(id >> 32) << 21));
                         a.id[cur][d] = (uint32_t)id;
-                        PK[d] = pk | ((uint32_t)(id >> 32) << 21);
                         ++kept;
                         const int sg = (int)((pk >> 8) & 1u), k = (int)(pk & 0xFFu);
                         const int c0 = cell_of(a, tmp, r.w), c1 = cell_of(a, tmp, r.x);
@@ -1481,9 +1478,10 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
         const uint32_t layer = (uint32_t)a.cdf_layer[st.cdf_off + i];
         const long long d = st.base + (long long)a.cnt[s].n_slots + j;
         a.z[cur][d] = z;
-        a.mu[cur][d] = mu_of(r1.x);
+        *reinterpret_cast<uint2 *>(a.mu[cur] + 2 * d) = make_uint2(
+            __float_as_uint(mu_of(r1.x)),
+            k | (sg << 8) | (layer << 9) | (1u << 13) | ((uint32_t)(id >> 32) << 21));
         a.id[cur][d] = (uint32_t)id;
-        a.pk[cur][d] = k | (sg << 8) | (layer << 9) | (1u << 13) | ((uint32_t)(id >> 32) << 21);
         atomicAdd(&s_q[s], (unsigned long long)k);
         if (!ADJ && deposit) {
             Stk tmp; tmp.n_cells = st.n_cells;
@@ -1543,6 +1541,7 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
     const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur, nxt = cur ^ 1;
     const int b = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
+    const long long S = a.mp_stride;
     Plan p;
     make_plan(a, s_tpref, s_nsl, p);
 
@@ -1552,7 +1551,14 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
         const long long slot0 = (t - s_tpref[s]) * TILE + (long long)tid * VEC;
         mask = 0;
         if (slot0 < nsl) {
-            const uint4 p4 = *reinterpret_cast<const uint4 *>(a.pk[cur] + st.base + slot0);
+            uint4 p4;
+            if (a.mp_stride == 2) {
+                const uint4 *q = reinterpret_cast<const uint4 *>(a.mu[cur] + 2 * (st.base + slot0));
+                const uint4 q01 = q[0], q23 = q[1];
+                p4 = make_uint4(q01.y, q01.w, q23.y, q23.w);
+            } else {
+                p4 = *reinterpret_cast<const uint4 *>(a.pk[cur] + st.base + slot0);
+            }
             const uint32_t *pp = &p4.x;
 #pragma unroll
             for (int j = 0; j < VEC; ++j)
@@ -1620,9 +1626,14 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
                 for (int j = 0; j < VEC; ++j) {
                     if (!((m >> j) & 1u)) continue;
                     a.z[nxt][d] = a.z[cur][src + j];
-                    a.mu[nxt][d] = a.mu[cur][src + j];
+                    if (S == 2) {
+                        *reinterpret_cast<uint2 *>(a.mu[nxt] + 2 * d) =
+                            *reinterpret_cast<const uint2 *>(a.mu[cur] + 2 * (src + j));
+                    } else {
+                        a.mu[nxt][d] = a.mu[cur][src + j];
+                        a.pk[nxt][d] = a.pk[cur][src + j];
+                    }
                     a.id[nxt][d] = a.id[cur][src + j];
-                    a.pk[nxt][d] = a.pk[cur][src + j];
                     if (ADJ) a.acc[nxt][d] = a.acc[cur][src + j];
                     ++d;
                 }
@@ -1636,7 +1647,7 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
                 for (int j = 0; j < VEC; ++j) {
                     if (slot0 + j >= s_nsl[s] || ((m >> j) & 1u)) continue;
                     const unsigned long long id = (unsigned long long)a.id[cur][src + j] |
-                                                  ((unsigned long long)(a.pk[cur][src + j] >> 21) << 32);
+                                                  ((unsigned long long)(a.pk[cur][(src + j) * S] >> 21) << 32);
                     if (id < (unsigned long long)st.n_ids) a.tot[st.id_off + (long long)id] = a.acc[cur][src + j];
                     else atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_STATE);
                 }
