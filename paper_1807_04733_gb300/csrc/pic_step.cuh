@@ -849,21 +849,27 @@ k_fast(const Args a)
                     if (i0 + j < nvalid) gA[i0 + j] = av[j];
             }
         }
-        // queue the eventful carriers (record and position), in tile order
-        if (__any_sync(0xffffffffu, slowbits != 0)) {
+        // queue the eventful carriers (record and position), in tile order:
+        // the warp's exclusive prefix of the per-thread counts (0..4) from
+        // three ballots of their bits, one shared-counter reservation
+        {
+            const uint32_t cnt = (uint32_t)__popc(slowbits);
+            const unsigned int b0 = __ballot_sync(0xffffffffu, cnt & 1u);
+            const unsigned int b1 = __ballot_sync(0xffffffffu, cnt & 2u);
+            const unsigned int b2 = __ballot_sync(0xffffffffu, cnt & 4u);
+            const int tot = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
+            if (tot) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s_qn, tot);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                long long q = pos0 + base + __popc(b0 & lt_mask) + 2 * __popc(b1 & lt_mask) +
+                              4 * __popc(b2 & lt_mask);
+                n_queued += cnt;
 #pragma unroll
-            for (int j = 0; j < VEC; ++j) {
-                const bool slow = (slowbits >> j) & 1u;
-                const unsigned int m = __ballot_sync(0xffffffffu, slow);
-                if (m) {
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&s_qn, __popc(m));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (slow) {
-                        const long long q = pos0 + base + __popc(m & lt_mask);
-                        a.qrec[q] = make_float4(zin[j], min_[j], __uint_as_float(pin[j]),
-                                                __uint_as_float((uint32_t)((t - t0) * TILE + i0 + j)));
-                        ++n_queued;
+                for (int j = 0; j < VEC; ++j) {
+                    if ((slowbits >> j) & 1u) {
+                        a.qrec[q++] = make_float4(zin[j], min_[j], __uint_as_float(pin[j]),
+                                                  __uint_as_float((uint32_t)((t - t0) * TILE + i0 + j)));
                     }
                 }
             }
