@@ -1187,7 +1187,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     __shared__ int s_w[TPB / 32];
     __shared__ unsigned long long s_r[TPB / 32];
-    __shared__ long long s_pre[2];
+    __shared__ long long s_pre[2], s_cl;
     __shared__ int s_flag;
 
     const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
@@ -1272,6 +1272,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
         for (long long wb = w0; wb < w1; wb += TPB) {
             const long long w = wb + tid;
             uint32_t bits = w < w1 ? a.spawn_bits[w] : 0u;
+            if (!__syncthreads_or(bits != 0u)) continue;     // no secondary here
             int excl;
             const int tot = block_scan(__popc(bits), excl, s_w);
             if (bits) {
@@ -1393,7 +1394,10 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             }
             const long long pre0 = (s_first < s_last && inside_first)
                                        ? look_back_place(a, ep, T, s_tpref[s_first], b, Gs, Gf) : 0;
-            if (tid == 0) s_pre[0] = pre0;
+            if (tid == 0) {
+                s_pre[0] = pre0;
+                s_cl = c_last;
+            }
         }
         __syncthreads();
         (void)c_first;
@@ -1402,6 +1406,11 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             const long long sg1 = s_tpref[s + 1] < t1 ? s_tpref[s + 1] : t1;
             if (sg0 >= sg1) continue;                   // a stack with no tiles
             const long long prefix = s == s_last ? s_pre[1] : (s == s_first ? s_pre[0] : 0);
+            if (s == s_last && s_cl == 0) {
+                // no secondary staged in the segment: nothing to place or deposit
+                if (sg1 == s_tpref[s + 1] && tid == 0) a.cnt[s].spawn_total = (unsigned long long)prefix;
+                continue;
+            }
             const int nc = a.stacks[s].n_cells;
             if (!ADJ)
                 for (int q = tid; q < 2 * (nc + 1); q += TPB) s_J[q] = 0;
