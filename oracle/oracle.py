@@ -81,6 +81,7 @@ def lib():
         L.or_records.argtypes = [P, P]
         L.or_set_records.argtypes = [P, P, C.c_int64, C.c_uint64]
         L.or_moments.argtypes = [P, P, P, C.POINTER(Ledger)]
+        L.or_gen_moments.argtypes = [P, P]
         L.or_n_cells.argtypes = [P]; L.or_n_cells.restype = C.c_int32
         L.or_n_out.argtypes = [P]; L.or_n_out.restype = C.c_int32
         L.or_step_index.argtypes = [P]; L.or_step_index.restype = C.c_int32
@@ -186,6 +187,13 @@ class OracleSim:
         led = Ledger()
         lib().or_moments(self.h, n.ctypes.data, J.ctypes.data, C.byref(led))
         return n, J, led.as_dict()
+
+    def gen_moments(self) -> np.ndarray:
+        """Generation labels summed per [output time][cell] at the density
+        instants (the numerator of the mean-generation maps, Figs. 5(b), 7)."""
+        g = np.zeros((self.n_out, self.n_cells), np.uint64)
+        lib().or_gen_moments(self.h, g.ctypes.data)
+        return g
 
     def grad(self, gn, gJ, n_steps: int | None = None):
         """Score-function gradient of sum(gn * n) + sum(gJ * J) with respect to

@@ -125,6 +125,7 @@ struct or_sim {
     or_rec *recs; int64_t n_slots; uint64_t next_id; uint32_t step;
     /* moments */
     int32_t n_out; uint32_t *nh; int32_t *Jh;
+    uint64_t *gh;                 /* generation label summed per (output time, cell) */
     or_ledger led;
     int err;
 };
@@ -505,6 +506,7 @@ static void step_once(or_sim *s)
             int64_t b = ((tout * 2 + PK_S(p->packed)) * c->n_e + (k - 1)) * s->n_cells
                         + cell_of(s, p->z);
             s->nh[b] += 1;
+            s->gh[tout * s->n_cells + cell_of(s, p->z)] += PK_G(p->packed);
             if (s->adj) credit(s, (uint64_t)p->id | ((uint64_t)PK_E(p->packed) << 32), s->adj->gn[b]);
         }
     }
@@ -621,7 +623,8 @@ int or_create(const or_config *cfg, or_sim **out)
     s->n_out = (cfg->n_steps_max + cfg->moment_every - 1) / cfg->moment_every;
     s->nh = (uint32_t *)calloc((size_t)s->n_out * 2 * ne * cells + 1, sizeof(uint32_t));
     s->Jh = (int32_t *)calloc((size_t)s->n_out * 2 * (cells + 1) + 1, sizeof(int32_t));
-    if (!s->recs || !s->nh || !s->Jh) { or_destroy(s); return 4; }
+    s->gh = (uint64_t *)calloc((size_t)s->n_out * cells + 1, sizeof(uint64_t));
+    if (!s->recs || !s->nh || !s->Jh || !s->gh) { or_destroy(s); return 4; }
     *out = s;
     return 0;
 }
@@ -632,7 +635,7 @@ void or_destroy(or_sim *s)
     free(s->v); free(s->tau_in); free(s->tau_el); free(s->T); free(s->p0);
     free(s->P_thr); free(s->Q_thr); free(s->T_thr); free(s->P0_thr);
     free(s->cdf_cell); free(s->cdf_layer); free(s->cdf_thr); free(s->inj);
-    free(s->recs); free(s->nh); free(s->Jh);
+    free(s->recs); free(s->nh); free(s->Jh); free(s->gh);
     free(s);
 }
 
@@ -664,6 +667,15 @@ void or_moments(const or_sim *s, uint32_t *n_out, int32_t *J_out, or_ledger *led
     if (n_out) memcpy(n_out, s->nh, sizeof(uint32_t) * nn);
     if (J_out) memcpy(J_out, s->Jh, sizeof(int32_t) * nj);
     if (led) *led = s->led;
+}
+
+/* Mean-generation map of Figs. 5(b) and 7(b),(d) (Sec. V): the generation
+ * label of every live carrier (1 for a primary, its parent's + 1 for a
+ * secondary) summed per (output time, cell) at the same instants as the
+ * densities; divided by the summed density it gives the mean label. */
+void or_gen_moments(const or_sim *s, uint64_t *g_out)
+{
+    if (g_out) memcpy(g_out, s->gh, sizeof(uint64_t) * (size_t)s->n_out * s->n_cells);
 }
 
 void or_tables(const or_sim *s, uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_thr,

@@ -81,6 +81,8 @@ int64_t or_n_slots(const or_sim *s);
 void or_records(const or_sim *s, or_rec *out);     /* n_slots records */
 int  or_set_records(or_sim *s, const or_rec *in, int64_t n, uint64_t next_id);
 void or_moments(const or_sim *s, uint32_t *n_out, int32_t *J_out, or_ledger *led);
+/* generation label summed per [n_out][n_cells] (Figs. 5(b), 7(b),(d)) */
+void or_gen_moments(const or_sim *s, uint64_t *g_out);
 int32_t or_n_cells(const or_sim *s);
 int32_t or_n_out(const or_sim *s);
 int32_t or_step_index(const or_sim *s);

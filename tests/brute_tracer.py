@@ -78,6 +78,7 @@ class Tracer:
         self.counts = dict(absorbed=0, spawned=0, dropped=0, bath=0, iface=0, trans=0)
         self.flux = {}
         self.dens = {}
+        self.gens = {}
 
     # ---- state helpers: a particle is a dict ----
     def load(self, recs, next_id):
@@ -194,6 +195,8 @@ class Tracer:
                 if p["k"]:
                     key = (t, p["s"], p["k"], self.cell(p["z"]))
                     self.dens[key] = self.dens.get(key, 0) + 1
+                    gk = (t, self.cell(p["z"]))
+                    self.gens[gk] = self.gens.get(gk, 0) + p["g"]
         if (self.step_no + 1) % wl.compact_every == 0:
             self.parts = [p for p in self.parts if p["k"]]
         self.step_no += 1

@@ -449,8 +449,52 @@ def test_p6_brute_force_tracer(flags):
     for (t, sp, f), v in tr.flux.items():
         assert J[t, sp, f] == v
     assert np.abs(J).sum() == sum(abs(v) for v in tr.flux.values())
+    # generation map (Figs. 5(b), 7): the labels of the traced carriers
+    g = s.gen_moments()
+    for (t, c), v in tr.gens.items():
+        assert g[t, c] == v
+    assert int(g.sum()) == sum(tr.gens.values())
+    if flags & W.FLAG_NO_SECONDARIES:
+        assert np.array_equal(g, dens.sum(axis=(1, 2)).astype(np.uint64))
     assert led["absorbed"] == tr.counts["absorbed"]
     assert led["spawned"] == tr.counts["spawned"]
     assert led["iface_hits"] == tr.counts["iface"]
     if not flags & (W.FLAG_NO_SECONDARIES):
         assert led["spawned"] > 0
+
+
+# ---------------------------------------------------------------------------
+# Generation map (Figs. 5(b), 7(b),(d)): label sums against the densities
+# ---------------------------------------------------------------------------
+def test_generation_map_primaries_only_equals_density():
+    """Without secondaries every carrier is a primary (label 1): the label sum
+    of every (output time, cell) equals the carrier count there."""
+    wl = W.config(0, scale=0.05, flags=W.FLAG_NO_SECONDARIES).replace(n_steps=120)
+    s = OracleSim(wl)
+    assert s.step(wl.n_steps) == 0
+    dens, _, _ = s.moments()
+    g = s.gen_moments()
+    assert dens.sum() > 0
+    assert np.array_equal(g, dens.sum(axis=(1, 2)).astype(np.uint64))
+
+
+def test_generation_map_counts_secondaries():
+    """With the cascade on, a secondary carries its parent's label + 1, so the
+    label sum exceeds the count by at least the live secondaries, and the mean
+    label rises over time as the cascade develops (Fig. 5(b))."""
+    wl = W.config(0, scale=0.05).replace(n_steps=200)
+    s = OracleSim(wl)
+    assert s.step(wl.n_steps) == 0
+    dens, _, _ = s.moments()
+    g = s.gen_moments().astype(np.int64)
+    n = dens.sum(axis=(1, 2)).astype(np.int64)
+    recs = s.records()
+    gen = (recs["packed"] >> 13) & 0xFF
+    live = (recs["packed"] & 0xFF) > 0
+    last = wl.n_steps // wl.moment_every - 1
+    assert g[last].sum() == int(gen[live].sum())            # the final instant
+    assert np.all(g >= n)
+    assert g.sum() - n.sum() >= int(((gen >= 2) & live).sum())
+    occupied = n.sum(axis=1) > 0                             # after the pulse starts
+    mean = g.sum(axis=1)[occupied] / n.sum(axis=1)[occupied]
+    assert mean[-1] > mean[0] >= 1.0
