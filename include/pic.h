@@ -219,6 +219,16 @@ pic_status pic_step(pic_ctx *ctx, int n_steps);
 pic_status pic_moments(pic_ctx *ctx, int stack, uint32_t *n_dev, int32_t *J_dev,
                        pic_ledger *ledger_host);
 
+/* Generation map of one stack (Figs. 5(b) and 7(b),(d), Sec. V): g_dev
+ * (device, caller-owned, overwritten) receives uint64 [n_out][n_cells], the
+ * generation labels (1 for a primary, the parent's + 1 for a secondary,
+ * saturating at 255) of the live carriers in each cell summed at the same
+ * instants as the densities of pic_moments; divided by the densities summed
+ * over spin and bin it gives the mean generation of each space-time cell.
+ * Asynchronous on the context stream; PIC_ERR_ARG for a bad stack or a NULL
+ * g_dev. */
+pic_status pic_gen_moments(pic_ctx *ctx, int stack, uint64_t *g_dev);
+
 /* Score-function (likelihood-ratio) gradient of a linear functional of the
  * moments with respect to the lifetime and transmittance tables of every
  * stack.  grad_n_dev: float [n_stacks][n_out][2][n_e][n_cells_max] weights

@@ -77,6 +77,7 @@ struct pic_ctx {
     uint32_t *d_bits = nullptr, *d_qcnt = nullptr, *d_fspawn = nullptr;
     unsigned long long *d_status = nullptr;
     uint32_t *d_nh = nullptr;
+    unsigned long long *d_gh = nullptr;          // generation sums [stack][n_out][n_cells]
     int32_t *d_J = nullptr;
     DevCounters *d_cnt = nullptr;
     DevCtl *d_ctl = nullptr;
@@ -309,7 +310,7 @@ void free_all(pic_ctx *c)
         c->d_pk[b] = nullptr;                   // inside d_mu[b]
         release(c->d_z[b]); release(c->d_mu[b]); release(c->d_id[b]);
     }
-    release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh);
+    release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh); release(c->d_gh);
     release(c->d_qrec); release(c->d_qcnt); release(c->d_fspawn); release(c->d_J); release(c->d_cnt);
     release(c->d_ctl);
     Replay &r = c->rp;
@@ -528,6 +529,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     ALLOC(c->d_bits, c->total_slots / 32 + 1);
     ALLOC(c->d_qrec, c->total_slots);
     ALLOC(c->d_nh, c->nh_total);
+    ALLOC(c->d_gh, c->nh_total / (2 * p->n_e) + 1);
     ALLOC(c->d_J, c->J_total);
     ALLOC(c->d_cnt, n_stacks);
     ALLOC(c->d_ctl, 1);
@@ -553,6 +555,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.spawn_bits = c->d_bits;
     a.qrec = c->d_qrec;
     a.n_hist = c->d_nh; a.J_hist = c->d_J; a.cnt = c->d_cnt; a.ctl = c->d_ctl;
+    a.g_hist = c->d_gh;
     a.seed_lo = (uint32_t)p->seed; a.seed_hi = (uint32_t)(p->seed >> 32);
     a.stack_base = p->stack_base;
     for (int r = 0; r < 10; ++r) {      // Philox4x32-10 round keys (Weyl sequence)
@@ -566,6 +569,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.flags = p->flags; a.n_e = ne; a.moment_every = p->moment_every;
     a.step = 0;
     a.tab_max = tab_max; a.T_max = T_max; a.nbin_max = nbin_max; a.jbin_max = jbin_max;
+    a.gbin_max = nbin_max / (2 * ne);
     a.spin_limit = 1u << 24;
 
     e = configure(a, p->blocks_per_sm, p->ring_stages, p->hist_mode, &c->lc);
@@ -608,6 +612,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_fspawn, 0, sizeof(uint32_t) * gmax, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bits, 0, 4 * (size_t)(c->total_slots / 32 + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_nh, 0, 4 * (size_t)std::max<int64_t>(c->nh_total, 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gh, 0, 8 * (size_t)(c->nh_total / (2 * p->n_e) + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_J, 0, 4 * (size_t)std::max<int64_t>(c->J_total, 1), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt, cnt.data(), sizeof(DevCounters) * n_stacks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st);
@@ -818,6 +823,22 @@ pic_status pic_moments(pic_ctx *c, int stack, uint32_t *n_dev, int32_t *J_dev, p
     return st;
 }
 
+pic_status pic_gen_moments(pic_ctx *c, int stack, uint64_t *g_dev)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    if (!g_dev) return fail(c, PIC_ERR_ARG, "g_dev is NULL");
+    const HostStack &h = c->hs[stack];
+    const DevStack &d = c->ds[stack];
+    const size_t ng = (size_t)h.n_out * h.n_cells;
+    cudaError_t e = cudaSuccess;
+    if (ng)
+        e = cudaMemcpyAsync(g_dev, c->d_gh + d.n_off / (2 * c->p.n_e), 8 * ng, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_gen_moments copy");
+    return PIC_OK;
+}
+
 pic_status pic_records(pic_ctx *c, int stack, pic_record *out, int64_t *n)
 {
     if (!c || !n) return PIC_ERR_ARG;
@@ -1024,7 +1045,7 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
     }
     a.stacks = r.stacks; a.cnt = r.cnt; a.ctl = r.ctl; a.status = r.status; a.qcnt = r.qcnt;
     a.fspawn = r.fspawn;
-    a.n_hist = nullptr; a.J_hist = nullptr;
+    a.n_hist = nullptr; a.J_hist = nullptr; a.g_hist = nullptr;
     a.tot = r.tot; a.parent = r.parent; a.gen = r.gen; a.gen_max = r.gen_max;
     a.aent = r.aent; a.aT = r.aT; a.g_ent = r.g_ent; a.g_T = r.g_T;
     a.gn = grad_n ? r.qgn : nullptr; a.gpot = r.gpot; a.stage_l = r.stage_l;

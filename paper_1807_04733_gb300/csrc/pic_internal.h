@@ -114,6 +114,8 @@ struct Args {            // everything a kernel needs, passed by value
     float4 *stage;
     unsigned long long *status;      // one look-back word per block
     uint32_t *n_hist;
+    // generation labels summed per [stack][n_out][n_cells], at n_off / (2 n_e)
+    unsigned long long *g_hist;
     int32_t *J_hist;
     DevCounters *cnt;
     DevCtl *ctl;
@@ -129,6 +131,7 @@ struct Args {            // everything a kernel needs, passed by value
     const unsigned int *step_dev;            // graph replay: the step is read here
     int bump_step;                           // this kernel's last block advances *step_dev
     int tab_max, T_max, nbin_max, jbin_max;  // shared-memory sizing
+    int gbin_max;                            // cells of the widest stack (generation sums)
     unsigned int spin_limit;                 // bound of every device-side wait
     int ring;                                // tiles in k_fast's copy ring
     int grid_fast;                           // k_fast's grid (read by k_event, k_place)

@@ -18,7 +18,7 @@ cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_m
         return e;
     const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;      // tile prefix, counts
     const size_t fixed = (size_t)a.tab_max * sizeof(FastEnt) + (size_t)a.jbin_max * 4 + 4 + tiles;
-    const size_t fixed_dep = fixed + (size_t)a.nbin_max * 4;
+    const size_t fixed_dep = fixed + (size_t)(a.nbin_max + a.gbin_max) * 4;
     int o_plain = 0, o_dep = 0;
     if ((e = pick_ring<false, false>(fixed, blocks_per_sm, ring_req, &cfg->ring_fast, &o_plain,
                                      &cfg->smem_fast)) != cudaSuccess)

@@ -557,7 +557,9 @@ k_fast(const Args a)
     int32_t *s_J = reinterpret_cast<int32_t *>(s_gp + (ADJ ? a.jbin_max : 0));
     uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + (ADJ ? 0 : a.jbin_max));
     int32_t *s_gn = reinterpret_cast<int32_t *>(s_n);
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max : 0) + 1);
+    // density steps: the generation labels summed per cell, after the bins
+    uint32_t *s_gs = s_n + a.nbin_max;
+    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max + (ADJ ? 0 : a.gbin_max) : 0) + 1);
     s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     __shared__ __align__(8) unsigned long long s_full[MAX_RING], s_empty[MAX_RING];
@@ -662,6 +664,11 @@ k_fast(const Args a)
                 const uint32_t v = s_n[i];
                 if (v) atomicAdd(&gN[i], v);
             }
+            unsigned long long *gG = a.g_hist + st.n_off / (2 * a.n_e) + (long long)tout * st.n_cells;
+            for (int i = tid; i < st.n_cells; i += TPB) {
+                const uint32_t v = s_gs[i];
+                if (v) atomicAdd(&gG[i], (unsigned long long)v);
+            }
         }
         if (ADJ == 2) {
             // the no-scattering score of an entry times the sum of the
@@ -694,8 +701,10 @@ k_fast(const Args a)
             for (int q = tid; q < st.tab_n; q += TPB) s_ent[q] = a.fent[st.ent_off + q];
             if (!ADJ)
                 for (int q = tid; q < 2 * (st.n_cells + 1); q += TPB) s_J[q] = 0;
-            if (DEPN && !ADJ)
+            if (DEPN && !ADJ) {
                 for (int q = tid; q < 2 * a.n_e * st.n_cells; q += TPB) s_n[q] = 0u;
+                for (int q = tid; q < st.n_cells; q += TPB) s_gs[q] = 0u;
+            }
             if (ADJ == 2)
                 for (int q = tid; q < st.tab_n; q += TPB) s_sr[q] = 0ull;
             if (ADJ) {
@@ -808,7 +817,10 @@ k_fast(const Args a)
                         else if (c1 != c0) add_flux(s_J, nf, sg, c0, c1);
                     }
                     zo[j] = z2;
-                    if (DEPN && !ADJ) bin = (sg * ne + (k - 1)) * nc + c1;
+                    if (DEPN && !ADJ) {
+                        bin = (sg * ne + (k - 1)) * nc + c1;
+                        atomicAdd(&s_gs[c1], (pk >> 13) & 0xFFu);
+                    }
                     if (ADJ) {
                         // reward of the step: faces crossed, then the density bin
                         const int c0 = c0u < nc - 1 ? c0u : nc - 1;
@@ -907,7 +919,8 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
     double *s_gT = s_g + (ADJ == 2 ? a.tab_max : 0);
     int32_t *s_J = reinterpret_cast<int32_t *>(s_gT + (ADJ == 2 ? a.T_max : 0));
     uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + (ADJ ? 0 : a.jbin_max));
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN && !ADJ ? a.nbin_max : 0) + 1);
+    uint32_t *s_gs = s_n + a.nbin_max;       // density steps: generation labels per cell
+    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN && !ADJ ? a.nbin_max + a.gbin_max : 0) + 1);
     s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     long long *s_qpre = s_nsl + a.n_stacks;      // queue prefix over the streaming blocks
@@ -992,6 +1005,11 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
             for (int i = tid; i < nb; i += TPB) {
                 const uint32_t v = s_n[i];
                 if (v) atomicAdd(&gN[i], v);
+            }
+            unsigned long long *gG = a.g_hist + st.n_off / (2 * a.n_e) + (long long)tout * st.n_cells;
+            for (int i = tid; i < st.n_cells; i += TPB) {
+                const uint32_t v = s_gs[i];
+                if (v) atomicAdd(&gG[i], (unsigned long long)v);
             }
         }
         unsigned long long *L = a.cnt[s].led;
@@ -1110,7 +1128,10 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
             const int c_end = cell_of(a, S, z);
             if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
             pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
-            if (DEPN && !ADJ) atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
+            if (DEPN && !ADJ) {
+                atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
+                atomicAdd(&s_gs[c_end], (pk >> 13) & 0xFFu);
+            }
             if (ADJ) {
                 rw = flux_w(a, s, tj, sg, c_start, c_end);
                 if (DEPN) rw += dep_w(a, s, tout, sg, k, c_end);
@@ -1135,8 +1156,10 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
             const long long hi = s_cut;
             if (!ADJ)
                 for (int q = tid; q < 2 * (s_st.n_cells + 1); q += TPB) s_J[q] = 0;
-            if (DEPN && !ADJ)
+            if (DEPN && !ADJ) {
                 for (int q = tid; q < 2 * a.n_e * s_st.n_cells; q += TPB) s_n[q] = 0u;
+                for (int q = tid; q < s_st.n_cells; q += TPB) s_gs[q] = 0u;
+            }
             if (ADJ == 2) {
                 for (int q = tid; q < s_st.tab_n; q += TPB) s_g[q] = 0.0;
                 for (int q = tid; q < s_st.T_n; q += TPB) s_gT[q] = 0.0;
@@ -1182,7 +1205,8 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
     extern __shared__ __align__(128) unsigned char smem[];
     int32_t *s_J = reinterpret_cast<int32_t *>(smem);
     uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + (ADJ ? 0 : a.jbin_max));
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN && !ADJ ? a.nbin_max : 0) + 1);
+    uint32_t *s_gs = s_n + a.nbin_max;       // density steps: generation labels per cell
+    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN && !ADJ ? a.nbin_max + a.gbin_max : 0) + 1);
     s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     __shared__ int s_w[TPB / 32];
@@ -1301,7 +1325,10 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
                             place_adj(s, stg, w * 32 + j, d, id, pk, sg, k, c0, c1, r);
                         } else {
                             if (c0 != c1) add_flux(s_J, nf, sg, c0, c1);
-                            if (DEPN) atomicAdd(&s_n[(sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
+                            if (DEPN) {
+                                atomicAdd(&s_n[(sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
+                                atomicAdd(&s_gs[c1], (pk >> 13) & 0xFFu);
+                            }
                         }
                     } else {
                         ++ty.spawn_drop;
@@ -1337,6 +1364,11 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             for (int i = tid; i < nb; i += TPB) {
                 const uint32_t v = s_n[i];
                 if (v) atomicAdd(&gN[i], v);
+            }
+            unsigned long long *gG = a.g_hist + st.n_off / (2 * a.n_e) + (long long)tout * st.n_cells;
+            for (int i = tid; i < st.n_cells; i += TPB) {
+                const uint32_t v = s_gs[i];
+                if (v) atomicAdd(&gG[i], (unsigned long long)v);
             }
         }
         unsigned long long *L = a.cnt[s].led;
@@ -1414,8 +1446,10 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             const int nc = a.stacks[s].n_cells;
             if (!ADJ)
                 for (int q = tid; q < 2 * (nc + 1); q += TPB) s_J[q] = 0;
-            if (DEPN && !ADJ)
+            if (DEPN && !ADJ) {
                 for (int q = tid; q < 2 * a.n_e * nc; q += TPB) s_n[q] = 0u;
+                for (int q = tid; q < nc; q += TPB) s_gs[q] = 0u;
+            }
             __syncthreads();
             const long long n = place(s, sg0, sg1, prefix);
             if (sg1 == s_tpref[s + 1] && tid == 0)
@@ -1503,6 +1537,7 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
             const int c = cell_of(a, tmp, z);
             atomicAdd(&a.n_hist[st.n_off + (long long)tout * 2 * a.n_e * st.n_cells +
                                 (sg * a.n_e + (k - 1)) * st.n_cells + c], 1u);
+            atomicAdd(&a.g_hist[st.n_off / (2 * a.n_e) + (long long)tout * st.n_cells + c], 1ull);
         }
         if (ADJ) {
             // a new carrier: no parent (lineage depth 0, set when the replay
@@ -1770,15 +1805,15 @@ inline size_t event_smem(const Args &a, bool dep, int adj, int gf_max)
     const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;
     return (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.T_max * 4 + 8 +
            (adj == 2 ? (size_t)(a.tab_max + a.T_max) * 8 : 0) +
-           (adj ? 0 : (size_t)a.jbin_max * 4) + (dep && !adj ? (size_t)a.nbin_max * 4 : 0) + 4 +
-           tiles + (size_t)(gf_max + 1) * 8;
+           (adj ? 0 : (size_t)a.jbin_max * 4) + (dep && !adj ? (size_t)(a.nbin_max + a.gbin_max) * 4 : 0) +
+           4 + tiles + (size_t)(gf_max + 1) * 8;
 }
 
 inline size_t place_smem(const Args &a, bool dep, int adj)
 {
     const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;
-    return (adj ? 0 : (size_t)a.jbin_max * 4) + (dep && !adj ? (size_t)a.nbin_max * 4 : 0) + 4 +
-           tiles;
+    return (adj ? 0 : (size_t)a.jbin_max * 4) +
+           (dep && !adj ? (size_t)(a.nbin_max + a.gbin_max) * 4 : 0) + 4 + tiles;
 }
 
 }  // namespace pic

@@ -30,7 +30,8 @@ STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_ALLOC", 3: "PIC_ERR_CAPACIT
 REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u4")])
 
 # symbols declared in include/pic.h
-EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_grad", "pic_records",
+EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_gen_moments", "pic_grad",
+           "pic_records",
            "pic_set_records", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
            "pic_profile_read", "pic_compact_static", "pic_launch_config", "pic_launch_count",
            "pic_destroy", "pic_last_error", "pic_status_string", "pic_autotune")
@@ -125,6 +126,7 @@ def lib():
         L.pic_excite.argtypes = [P, C.c_int, C.POINTER(pic_pulse)]
         L.pic_step.argtypes = [P, C.c_int]
         L.pic_moments.argtypes = [P, C.c_int, P, P, C.POINTER(pic_ledger)]
+        L.pic_gen_moments.argtypes = [P, C.c_int, P]
         L.pic_grad.argtypes = [P, P, P, P, P]
         L.pic_records.argtypes = [P, C.c_int, P, C.POINTER(C.c_int64)]
         L.pic_set_records.argtypes = [P, C.c_int, P, C.c_int64, C.c_uint64]
@@ -243,6 +245,10 @@ def pic_moments(ctx, stack, n_dev_ptr, J_dev_ptr):
     _check(lib().pic_moments(ctx, stack, C.c_void_p(n_dev_ptr or 0) if n_dev_ptr else None,
                              C.c_void_p(J_dev_ptr) if J_dev_ptr else None, C.byref(led)), ctx)
     return led.as_dict()
+
+
+def pic_gen_moments(ctx, stack, g_dev_ptr):
+    _check(lib().pic_gen_moments(ctx, stack, C.c_void_p(g_dev_ptr)), ctx)
 
 
 def pic_grad(ctx, grad_n_ptr, grad_J_ptr, grad_tau_ptr, grad_T_ptr):
@@ -380,6 +386,16 @@ class Context:
         J = torch.empty((no, 2, nc + 1), dtype=torch.int32, device=dev)
         led = pic_moments(self.ctx, stack, n.data_ptr(), J.data_ptr())
         return n, J, led
+
+    def gen_moments(self, stack=0):
+        """Generation labels summed per [n_out][n_cells] (uint64 on the device,
+        returned as int64), the numerator of the mean-generation map."""
+        torch = self.torch
+        nc, no, _ = self.shape(stack)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        g = torch.empty((no, nc), dtype=torch.int64, device=dev)
+        pic_gen_moments(self.ctx, stack, g.data_ptr())
+        return g
 
     def ledger(self, stack=0):
         return pic_moments(self.ctx, stack, None, None)

@@ -1,8 +1,8 @@
 """GPU parity: the CUDA path (through the C-ABI) against the CPU oracle.
 
 Deterministic build (PIC_F_DETERMINISTIC): particle records, integer
-densities, integer fluxes and the ledger must be bit-identical to the
-oracle's on the same seeded inputs.  Sizes span many tiles, several blocks
+densities, integer fluxes, the generation map (Figs. 5(b), 7) and the ledger
+must be bit-identical to the oracle's on the same seeded inputs.  Sizes span many tiles, several blocks
 per look-back chain and ragged tails; edge cases cover empty inputs, a
 single carrier, a full buffer, strict capacity and batched stacks.
 """
@@ -46,6 +46,8 @@ def compare_run(wl, checkpoints, hist_mode=0, stacks=None, set_recs=None):
             assert led == rled, (cp, s, led, rled)
             assert np.array_equal(n.cpu().numpy().view(np.uint32), rn), (cp, s)
             assert np.array_equal(J.cpu().numpy(), rJ), (cp, s)
+            assert np.array_equal(ctx.gen_moments(s).cpu().numpy().view(np.uint64),
+                                  ref.gen_moments()), (cp, s)
             assert same_records(ctx.records(s), ref.records()), (cp, s)
     ctx.close()
     return led
@@ -155,6 +157,9 @@ def test_fast_build_conserves_exactly():
         assert led["q_injected"] == int(k.sum()) + led["q_bath"] + led["q_dropped"]
         t = ctx.shape(0)[2] - 1
         assert int(n[t].sum()) == int((k > 0).sum())
+        # the generation map at the last instant is the live carriers' labels
+        gen = unpack(r["packed"])["gen"]
+        assert int(ctx.gen_moments(0)[t].sum()) == int(gen[k > 0].sum())
     ctx.close()
 
 
@@ -174,5 +179,6 @@ def test_det_bitexact_stack_base_shard():
         assert led == rled
         assert np.array_equal(n.cpu().numpy().view(np.uint32), rn)
         assert np.array_equal(J.cpu().numpy(), rJ)
+        assert np.array_equal(ctx.gen_moments(j).cpu().numpy().view(np.uint64), ref.gen_moments())
         assert same_records(ctx.records(j), ref.records())
     ctx.close()
