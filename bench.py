@@ -108,7 +108,7 @@ def measured_peak():
 # scaled to 1/20 (profiles/k_fast_k_event_k_place_fe15_au300_small.md); the
 # traffic grows in proportion to the carriers advanced.  Valid only for the
 # kernel source whose hash is given: reported as null once the kernels change.
-NCU_TRAFFIC = {"bytes_per_particle_step": 17.16, "src_sha": "1217f03f7bbbf695"}
+NCU_TRAFFIC = {"bytes_per_particle_step": 17.10, "src_sha": "38a9d2e116d2963d"}
 
 
 def kernel_sha():
