@@ -62,6 +62,8 @@ typedef enum {
                                      scattering event (default: inelastic only) */
 #define PIC_F_STRICT_CAPACITY 16u /* overflow is PIC_ERR_CAPACITY instead of
                                      drop-and-count */
+#define PIC_F_VELOCITY_MOMENTS 32u /* also sum the carriers' velocities along z
+                                      per (time, spin, cell): pic_vel_moments */
 
 /* Global parameters of a context. */
 typedef struct {

@@ -82,6 +82,7 @@ def lib():
         L.or_set_records.argtypes = [P, P, C.c_int64, C.c_uint64]
         L.or_moments.argtypes = [P, P, P, C.POINTER(Ledger)]
         L.or_gen_moments.argtypes = [P, P]
+        L.or_vel_moments.argtypes = [P, P]
         L.or_n_cells.argtypes = [P]; L.or_n_cells.restype = C.c_int32
         L.or_n_out.argtypes = [P]; L.or_n_out.restype = C.c_int32
         L.or_step_index.argtypes = [P]; L.or_step_index.restype = C.c_int32
@@ -187,6 +188,13 @@ class OracleSim:
         led = Ledger()
         lib().or_moments(self.h, n.ctypes.data, J.ctypes.data, C.byref(led))
         return n, J, led.as_dict()
+
+    def vel_moments(self) -> np.ndarray:
+        """Velocities v*mu summed per [output time][spin][cell] in units of
+        2^-32 nm/fs (requires FLAG_VELOCITY; Eq. spincurrent)."""
+        v = np.zeros((self.n_out, 2, self.n_cells), np.int64)
+        lib().or_vel_moments(self.h, v.ctypes.data)
+        return v
 
     def gen_moments(self) -> np.ndarray:
         """Generation labels summed per [output time][cell] at the density

@@ -126,6 +126,7 @@ struct or_sim {
     /* moments */
     int32_t n_out; uint32_t *nh; int32_t *Jh;
     uint64_t *gh;                 /* generation label summed per (output time, cell) */
+    int64_t *vh;                  /* velocity v*mu summed per (output time, spin, cell) */
     or_ledger led;
     int err;
 };
@@ -507,6 +508,15 @@ static void step_once(or_sim *s)
                         + cell_of(s, p->z);
             s->nh[b] += 1;
             s->gh[tout * s->n_cells + cell_of(s, p->z)] += PK_G(p->packed);
+            if (c->flags & OR_F_VELOCITY) {
+                /* the carrier's velocity along z, v(layer material, spin, k) * mu,
+                 * in float32, kept as an integer number of 2^-32 nm/fs
+                 * (truncated) so that sums do not depend on their order */
+                const float w = s->v[idx3(s, c->layer_mat[PK_L(p->packed)], (int)PK_S(p->packed), (int)k)] *
+                                p->mu;
+                s->vh[(tout * 2 + PK_S(p->packed)) * s->n_cells + cell_of(s, p->z)] +=
+                    (int64_t)(w * 4294967296.0f);
+            }
             if (s->adj) credit(s, (uint64_t)p->id | ((uint64_t)PK_E(p->packed) << 32), s->adj->gn[b]);
         }
     }
@@ -624,7 +634,8 @@ int or_create(const or_config *cfg, or_sim **out)
     s->nh = (uint32_t *)calloc((size_t)s->n_out * 2 * ne * cells + 1, sizeof(uint32_t));
     s->Jh = (int32_t *)calloc((size_t)s->n_out * 2 * (cells + 1) + 1, sizeof(int32_t));
     s->gh = (uint64_t *)calloc((size_t)s->n_out * cells + 1, sizeof(uint64_t));
-    if (!s->recs || !s->nh || !s->Jh || !s->gh) { or_destroy(s); return 4; }
+    s->vh = (int64_t *)calloc((size_t)s->n_out * 2 * cells + 1, sizeof(int64_t));
+    if (!s->recs || !s->nh || !s->Jh || !s->gh || !s->vh) { or_destroy(s); return 4; }
     *out = s;
     return 0;
 }
@@ -635,7 +646,7 @@ void or_destroy(or_sim *s)
     free(s->v); free(s->tau_in); free(s->tau_el); free(s->T); free(s->p0);
     free(s->P_thr); free(s->Q_thr); free(s->T_thr); free(s->P0_thr);
     free(s->cdf_cell); free(s->cdf_layer); free(s->cdf_thr); free(s->inj);
-    free(s->recs); free(s->nh); free(s->Jh); free(s->gh);
+    free(s->recs); free(s->nh); free(s->Jh); free(s->gh); free(s->vh);
     free(s);
 }
 
@@ -676,6 +687,16 @@ void or_moments(const or_sim *s, uint32_t *n_out, int32_t *J_out, or_ledger *led
 void or_gen_moments(const or_sim *s, uint64_t *g_out)
 {
     if (g_out) memcpy(g_out, s->gh, sizeof(uint64_t) * (size_t)s->n_out * s->n_cells);
+}
+
+/* Velocity moment behind the spin current of Eq. spincurrent (Sec. V):
+ * with OR_F_VELOCITY, the velocities along z, v * mu, of the live carriers
+ * of each spin summed per (output time, cell) at the density instants, in
+ * units of 2^-32 nm/fs; (sum_up - sum_down) / dz is the spin-current
+ * density of the cell in carriers nm/fs per nm. */
+void or_vel_moments(const or_sim *s, int64_t *v_out)
+{
+    if (v_out) memcpy(v_out, s->vh, sizeof(int64_t) * (size_t)s->n_out * 2 * s->n_cells);
 }
 
 void or_tables(const or_sim *s, uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_thr,

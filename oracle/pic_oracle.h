@@ -31,6 +31,7 @@ extern "C" {
 #define OR_F_TRANSPARENT     4u
 #define OR_F_LOWEST_BIN_ANY  8u
 #define OR_F_STRICT_CAPACITY 16u
+#define OR_F_VELOCITY        32u  /* also sum the velocities v*mu per (time, spin, cell) */
 
 typedef struct {
     float z;          /* depth, nm */
@@ -83,6 +84,8 @@ int  or_set_records(or_sim *s, const or_rec *in, int64_t n, uint64_t next_id);
 void or_moments(const or_sim *s, uint32_t *n_out, int32_t *J_out, or_ledger *led);
 /* generation label summed per [n_out][n_cells] (Figs. 5(b), 7(b),(d)) */
 void or_gen_moments(const or_sim *s, uint64_t *g_out);
+/* velocity moment per [n_out][2][n_cells] (OR_F_VELOCITY; Eq. spincurrent) */
+void or_vel_moments(const or_sim *s, int64_t *v_out);
 int32_t or_n_cells(const or_sim *s);
 int32_t or_n_out(const or_sim *s);
 int32_t or_step_index(const or_sim *s);

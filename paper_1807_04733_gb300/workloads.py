@@ -43,6 +43,7 @@ FLAG_NO_SECONDARIES = 2     # Sec. V.A variant (3): no secondary generation
 FLAG_TRANSPARENT = 4        # Sec. V.A variant (2): T == 1 at every interface
 FLAG_LOWEST_BIN_ANY = 8     # remove a lowest-bin carrier on ANY scattering event
 FLAG_STRICT_CAPACITY = 16   # capacity overflow is an error instead of drop-and-count
+FLAG_VELOCITY = 32          # also sum the velocities v*mu per (time, spin, cell)
 
 E_UNIFORM = 0               # injected energy uniform over the N_E bins
 E_MONO = 1                  # injected energy fixed per spin (k_mono[spin])

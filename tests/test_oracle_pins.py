@@ -498,3 +498,67 @@ def test_generation_map_counts_secondaries():
     occupied = n.sum(axis=1) > 0                             # after the pulse starts
     mean = g.sum(axis=1)[occupied] / n.sum(axis=1)[occupied]
     assert mean[-1] > mean[0] >= 1.0
+
+
+# ---------------------------------------------------------------------------
+# Velocity moment behind the spin current (Eq. spincurrent, Sec. V)
+# ---------------------------------------------------------------------------
+def _ballistic_slab(n, seed):
+    """Carriers in the middle of a 2 um slab with no scattering: no wall and
+    no event within a few steps."""
+    wl = W.infinite_slab(cells=2000, capacity=n, n_steps=4, moment_every=1,
+                         flags=W.FLAG_VELOCITY, dt=0.5)
+    st = wl.stacks[0]
+    st.tau_in[:] = np.inf
+    st.tau_el[:] = np.inf
+    rng = np.random.default_rng(seed)
+    r = initial(n, 0.0, rng.integers(1, wl.n_e + 1, n), spin=rng.integers(0, 2, n), seed=seed)
+    r["z"] = rng.uniform(900.0, 1100.0, n).astype(np.float32)
+    return wl, r
+
+
+def test_velocity_moment_is_the_rate_of_the_first_moment():
+    """d/dt sum z = sum v mu for free flights: the summed velocity moment at
+    the end of step 0 times dt equals the summed displacement over step 1."""
+    wl, r = _ballistic_slab(4000, 21)
+    s = OracleSim(wl)
+    s.set_records(r, len(r))
+    assert s.step(1) == 0
+    z0 = s.records()["z"].astype(np.float64)
+    assert s.step(1) == 0
+    z1 = s.records()["z"].astype(np.float64)
+    v = s.vel_moments()
+    rate = v[0].sum() / 2.0 ** 32                        # nm/fs, both spins
+    disp = (z1 - z0).sum()
+    scale = np.abs(z1 - z0).sum()
+    assert scale > 100.0
+    assert abs(disp - wl.dt * rate) <= 1e-4 * scale
+    # each spin separately
+    spin = (s.records()["packed"] >> 8) & 1
+    for sg in (0, 1):
+        d = (z1 - z0)[spin == sg].sum()
+        assert abs(d - wl.dt * v[0, sg].sum() / 2.0 ** 32) <= 1e-4 * scale
+
+
+def test_velocity_moment_mirror_symmetry():
+    """Mirroring every direction cosine negates the velocity moment of each
+    spin exactly (summed over cells: the carriers move the other way)."""
+    wl, r = _ballistic_slab(3000, 22)
+    a = OracleSim(wl)
+    a.set_records(r, len(r))
+    assert a.step(2) == 0
+    m = r.copy()
+    m["mu"] = -m["mu"]
+    b = OracleSim(wl)
+    b.set_records(m, len(m))
+    assert b.step(2) == 0
+    va, vb = a.vel_moments(), b.vel_moments()
+    assert np.any(va[:2] != 0)
+    assert np.array_equal(va[:2].sum(axis=2), -vb[:2].sum(axis=2))
+
+
+def test_velocity_moment_off_without_the_flag():
+    wl = W.config(0, scale=0.02).replace(n_steps=40)
+    s = OracleSim(wl)
+    assert s.step(40) == 0
+    assert not s.vel_moments().any()
