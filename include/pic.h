@@ -231,6 +231,18 @@ pic_status pic_moments(pic_ctx *ctx, int stack, uint32_t *n_dev, int32_t *J_dev,
  * g_dev. */
 pic_status pic_gen_moments(pic_ctx *ctx, int stack, uint64_t *g_dev);
 
+/* Velocity moment of one stack behind the spin current of Eq. spincurrent
+ * (Sec. V), for a context made with PIC_F_VELOCITY_MOMENTS (else
+ * PIC_ERR_ARG): v_dev (device, caller-owned, overwritten) receives int64
+ * [n_out][2][n_cells], the velocities along z, v(material, spin, k) * mu,
+ * of the live carriers of each spin in each cell, summed at the same instants
+ * as the densities of pic_moments.  Each product is taken in float32 and
+ * counted as an integer number of 2^-32 nm/fs (truncated toward zero), so
+ * the sums are exact; (v[t][0][c] - v[t][1][c]) / (2^32 dz) is the
+ * spin-current density of cell c in carriers nm/fs per nm.  Asynchronous on
+ * the context stream; PIC_ERR_ARG for a bad stack or a NULL v_dev. */
+pic_status pic_vel_moments(pic_ctx *ctx, int stack, int64_t *v_dev);
+
 /* Score-function (likelihood-ratio) gradient of a linear functional of the
  * moments with respect to the lifetime and transmittance tables of every
  * stack.  grad_n_dev: float [n_stacks][n_out][2][n_e][n_cells_max] weights

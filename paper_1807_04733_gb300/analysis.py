@@ -9,6 +9,10 @@ paper plots it; nothing here is part of the time step.
   grid starts at one bin above the Fermi level).
 * ``mean_generation``: the mean generation label per (output time, cell) of
   Figs. 5(b) and 7(b),(d), the label sums divided by the carrier counts.
+* ``spin_current``: the spin-current density of Eq. spincurrent per
+  (output time, cell), (sum of v mu over up carriers - over down carriers)
+  / dz, in carriers nm/fs per nm (the paper's factor -e and its units are
+  left out), from the velocity moment of ``pic_vel_moments``.
 
 Cells without carriers are NaN (the white regions of Figs. 5 and 7).
 """
@@ -46,3 +50,10 @@ def mean_generation(g, n) -> np.ndarray:
     out = np.full(cnt.shape, np.nan)
     np.divide(g, cnt, out=out, where=cnt > 0)
     return out
+
+
+def spin_current(v, dz: float) -> np.ndarray:
+    """v: velocity sums [n_out][2][n_cells] in units of 2^-32 nm/fs; returns
+    float64 [n_out][n_cells]."""
+    v = _np(v).astype(np.float64)
+    return (v[:, 0] - v[:, 1]) / (4294967296.0 * dz)

@@ -78,6 +78,7 @@ struct pic_ctx {
     unsigned long long *d_status = nullptr;
     uint32_t *d_nh = nullptr;
     unsigned long long *d_gh = nullptr;          // generation sums [stack][n_out][n_cells]
+    long long *d_vh = nullptr;                   // velocity sums [stack][n_out][2][n_cells]
     int32_t *d_J = nullptr;
     DevCounters *d_cnt = nullptr;
     DevCtl *d_ctl = nullptr;
@@ -310,7 +311,7 @@ void free_all(pic_ctx *c)
         c->d_pk[b] = nullptr;                   // inside d_mu[b]
         release(c->d_z[b]); release(c->d_mu[b]); release(c->d_id[b]);
     }
-    release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh); release(c->d_gh);
+    release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh); release(c->d_gh); release(c->d_vh);
     release(c->d_qrec); release(c->d_qcnt); release(c->d_fspawn); release(c->d_J); release(c->d_cnt);
     release(c->d_ctl);
     Replay &r = c->rp;
@@ -530,6 +531,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     ALLOC(c->d_qrec, c->total_slots);
     ALLOC(c->d_nh, c->nh_total);
     ALLOC(c->d_gh, c->nh_total / (2 * p->n_e) + 1);
+    ALLOC(c->d_vh, c->nh_total / p->n_e + 1);
     ALLOC(c->d_J, c->J_total);
     ALLOC(c->d_cnt, n_stacks);
     ALLOC(c->d_ctl, 1);
@@ -556,6 +558,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.qrec = c->d_qrec;
     a.n_hist = c->d_nh; a.J_hist = c->d_J; a.cnt = c->d_cnt; a.ctl = c->d_ctl;
     a.g_hist = c->d_gh;
+    a.v_hist = c->d_vh;
     a.seed_lo = (uint32_t)p->seed; a.seed_hi = (uint32_t)(p->seed >> 32);
     a.stack_base = p->stack_base;
     for (int r = 0; r < 10; ++r) {      // Philox4x32-10 round keys (Weyl sequence)
@@ -613,6 +616,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bits, 0, 4 * (size_t)(c->total_slots / 32 + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_nh, 0, 4 * (size_t)std::max<int64_t>(c->nh_total, 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gh, 0, 8 * (size_t)(c->nh_total / (2 * p->n_e) + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_vh, 0, 8 * (size_t)(c->nh_total / p->n_e + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_J, 0, 4 * (size_t)std::max<int64_t>(c->J_total, 1), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt, cnt.data(), sizeof(DevCounters) * n_stacks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st);
@@ -703,6 +707,10 @@ cudaError_t enqueue_step(pic_ctx *c, const Args &a0, int s, bool inj0, bool inj1
         Args b = a;
         b.bump_step = graph;
         e = timed(c, 0, [&] { return launch_inject(b, lc, 1, dep, st); });
+        ++launches;
+    }
+    if (e == cudaSuccess && dep && (c->p.flags & PIC_F_VELOCITY_MOMENTS)) {
+        e = timed(c, 2, [&] { return launch_vmoment(a, lc, st); });
         ++launches;
     }
     if (e == cudaSuccess && ((s + 1) % c->p.compact_every) == 0) {
@@ -836,6 +844,24 @@ pic_status pic_gen_moments(pic_ctx *c, int stack, uint64_t *g_dev)
         e = cudaMemcpyAsync(g_dev, c->d_gh + d.n_off / (2 * c->p.n_e), 8 * ng, cudaMemcpyDeviceToDevice,
                             c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pic_gen_moments copy");
+    return PIC_OK;
+}
+
+pic_status pic_vel_moments(pic_ctx *c, int stack, int64_t *v_dev)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    if (!v_dev) return fail(c, PIC_ERR_ARG, "v_dev is NULL");
+    if (!(c->p.flags & PIC_F_VELOCITY_MOMENTS))
+        return fail(c, PIC_ERR_ARG, "the context was made without PIC_F_VELOCITY_MOMENTS");
+    const HostStack &h = c->hs[stack];
+    const DevStack &d = c->ds[stack];
+    const size_t nv = (size_t)h.n_out * 2 * h.n_cells;
+    cudaError_t e = cudaSuccess;
+    if (nv)
+        e = cudaMemcpyAsync(v_dev, c->d_vh + d.n_off / c->p.n_e, 8 * nv, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_vel_moments copy");
     return PIC_OK;
 }
 
@@ -1045,7 +1071,7 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
     }
     a.stacks = r.stacks; a.cnt = r.cnt; a.ctl = r.ctl; a.status = r.status; a.qcnt = r.qcnt;
     a.fspawn = r.fspawn;
-    a.n_hist = nullptr; a.J_hist = nullptr; a.g_hist = nullptr;
+    a.n_hist = nullptr; a.J_hist = nullptr; a.g_hist = nullptr; a.v_hist = nullptr;
     a.tot = r.tot; a.parent = r.parent; a.gen = r.gen; a.gen_max = r.gen_max;
     a.aent = r.aent; a.aT = r.aT; a.g_ent = r.g_ent; a.g_T = r.g_T;
     a.gn = grad_n ? r.qgn : nullptr; a.gpot = r.gpot; a.stage_l = r.stage_l;

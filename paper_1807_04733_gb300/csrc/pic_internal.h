@@ -157,6 +157,9 @@ struct Args {            // everything a kernel needs, passed by value
     uint32_t *stage_l;                       // pass 2: start layer of a staged secondary
     int n_out, ncm;                          // moment windows, cells of the widest stack
     double inv_q;                            // 2^-F: reward units to weight units
+    // velocity moment [stack][n_out][2][n_cells] at n_off / n_e, units of
+    // 2^-32 nm/fs (PIC_F_VELOCITY_MOMENTS)
+    long long *v_hist;
 };
 
 // reason of the last failure of a call without a context (pic_capi.cu);
@@ -180,6 +183,8 @@ cudaError_t launch_fast(const Args &a, const LaunchCfg &c, bool deterministic, b
 cudaError_t launch_slow(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
                         cudaStream_t s);
 cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s);
+// velocity moment of the density step just finished (pic_vmoment.cu)
+cudaError_t launch_vmoment(const Args &a, const LaunchCfg &c, cudaStream_t s);
 // set the device step counter read by graph-replayed steps
 cudaError_t launch_set_step(DevCtl *ctl, unsigned int step, cudaStream_t s);
 

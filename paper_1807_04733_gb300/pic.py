@@ -30,7 +30,8 @@ STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_ALLOC", 3: "PIC_ERR_CAPACIT
 REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u4")])
 
 # symbols declared in include/pic.h
-EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_gen_moments", "pic_grad",
+EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_gen_moments",
+           "pic_vel_moments", "pic_grad",
            "pic_records",
            "pic_set_records", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
            "pic_profile_read", "pic_compact_static", "pic_launch_config", "pic_launch_count",
@@ -127,6 +128,7 @@ def lib():
         L.pic_step.argtypes = [P, C.c_int]
         L.pic_moments.argtypes = [P, C.c_int, P, P, C.POINTER(pic_ledger)]
         L.pic_gen_moments.argtypes = [P, C.c_int, P]
+        L.pic_vel_moments.argtypes = [P, C.c_int, P]
         L.pic_grad.argtypes = [P, P, P, P, P]
         L.pic_records.argtypes = [P, C.c_int, P, C.POINTER(C.c_int64)]
         L.pic_set_records.argtypes = [P, C.c_int, P, C.c_int64, C.c_uint64]
@@ -249,6 +251,10 @@ def pic_moments(ctx, stack, n_dev_ptr, J_dev_ptr):
 
 def pic_gen_moments(ctx, stack, g_dev_ptr):
     _check(lib().pic_gen_moments(ctx, stack, C.c_void_p(g_dev_ptr)), ctx)
+
+
+def pic_vel_moments(ctx, stack, v_dev_ptr):
+    _check(lib().pic_vel_moments(ctx, stack, C.c_void_p(v_dev_ptr)), ctx)
 
 
 def pic_grad(ctx, grad_n_ptr, grad_J_ptr, grad_tau_ptr, grad_T_ptr):
@@ -396,6 +402,16 @@ class Context:
         g = torch.empty((no, nc), dtype=torch.int64, device=dev)
         pic_gen_moments(self.ctx, stack, g.data_ptr())
         return g
+
+    def vel_moments(self, stack=0):
+        """Velocities v*mu summed per [n_out][2][n_cells] in units of 2^-32
+        nm/fs (int64 on the device); needs FLAG_VELOCITY."""
+        torch = self.torch
+        nc, no, _ = self.shape(stack)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        v = torch.empty((no, 2, nc), dtype=torch.int64, device=dev)
+        pic_vel_moments(self.ctx, stack, v.data_ptr())
+        return v
 
     def ledger(self, stack=0):
         return pic_moments(self.ctx, stack, None, None)

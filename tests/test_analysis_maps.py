@@ -66,3 +66,28 @@ def test_mean_generation_is_one_without_secondaries():
     mg = analysis.mean_generation(s.gen_moments(), n)
     occ = ~np.isnan(mg)
     assert occ.any() and np.all(mg[occ] == 1.0)
+
+
+def test_spin_current_from_records():
+    """With the velocity moment on, the spin current at an output instant
+    equals (sum v mu of up carriers - of down carriers) / dz per cell,
+    counted from the records with the velocity table (float64 sums)."""
+    wl, s = _run(flags=W.FLAG_VELOCITY)
+    t = wl.n_steps // wl.moment_every - 1
+    js = analysis.spin_current(s.vel_moments(), wl.dz)
+    r = s.records()
+    k = (r["packed"] & 0xFF).astype(np.int64)
+    live = k > 0
+    spin = ((r["packed"] >> 8) & 1).astype(np.int64)
+    layer = ((r["packed"] >> 9) & 0xF).astype(np.int64)
+    st = wl.stacks[0]
+    mat = np.asarray(st.layer_mat)[layer]
+    v = st.v[mat, spin, np.maximum(k, 1) - 1].astype(np.float32)
+    w = (v * r["mu"].astype(np.float32)).astype(np.float64)
+    nc = s.n_cells
+    cell = np.minimum(np.floor(r["z"].astype(np.float32) / np.float32(wl.dz)).astype(np.int64), nc - 1)
+    sign = np.where(spin == 0, 1.0, -1.0)
+    ref = np.bincount(cell[live], weights=(sign * w)[live], minlength=nc) / wl.dz
+    # each carrier's term was truncated to 2^-32 nm/fs
+    assert np.abs(js[t] - ref).max() <= live.sum() * 2.0 ** -32 / wl.dz + 1e-12
+    assert np.abs(ref).max() > 1e-3
