@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -125,7 +126,8 @@ class Clocks:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%s.csv" % gpu_index)
+        # the samples are read back at the end of the timed region
+        self.path = os.path.join(tempfile.gettempdir(), "pic_bench_clocks_%d_%s.csv" % (os.getpid(), gpu_index))
 
     def start(self):
         try:
