@@ -306,11 +306,11 @@ pic_status pic_profile_read(pic_ctx *ctx, pic_kernel_times *out);
  *   n_alive (host, written): number of live slots.
  *   cuda_stream: cudaStream_t the work is ordered on; the call synchronises it.
  * n must be below 2^30 (the look-back words carry 30-bit counts); larger n,
- * NULL pointers or a misaligned packed array return PIC_ERR_ARG.  The first
- * call on a device looks up the array's device address (with that device
- * current).  Calls share the array: each call resets the part that must
- * start from zero, and calls whose kernels overlap on one GPU (different
- * streams or host threads) race on it. */
+ * NULL pointers or a misaligned packed array return PIC_ERR_ARG.  Every
+ * call looks up the array's device address on the current device (so a
+ * device reset between calls is harmless).  Calls share the array: each call
+ * resets the part that must start from zero, and calls whose kernels overlap
+ * on one GPU (different streams or host threads) race on it. */
 pic_status pic_compact_static(const float *z, const float *mu, const uint32_t *id,
                               const uint32_t *packed, int64_t n, float *z_out, float *mu_out,
                               uint32_t *id_out, uint32_t *packed_out, int64_t *n_alive,

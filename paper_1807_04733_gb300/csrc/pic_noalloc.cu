@@ -77,18 +77,20 @@ extern "C" pic_status pic_compact_static(const float *z, const float *mu, const 
     int grid = 0;
     unsigned int epoch = 0;
     {
-        // one-time set-up per device, with that device current: the device
-        // address of the static array (its host-side name is only a stand-in)
+        // set-up, with the device current: the device address of the static
+        // array (its host-side name is only a stand-in).  It is looked up on
+        // every call, not cached: after a cudaDeviceReset the module is loaded
+        // again and the array may sit at another address.
         std::lock_guard<std::mutex> lock(g_mu);
         DeviceSetup &d = g_dev[dev];
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_compact_scratch);
+        if (e != cudaSuccess) return cuda_error(e, "pic_compact_static: scratch address");
+        d.addr = static_cast<Scratch *>(p);
         if (!d.ready) {
-            void *p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_compact_scratch);
-            if (e != cudaSuccess) return cuda_error(e, "pic_compact_static: scratch address");
             int sms = 0;
             e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return cuda_error(e, "pic_compact_static: SM count");
-            d.addr = static_cast<Scratch *>(p);
             d.grid = sms * (2048 / TPB);
             if (d.grid > kMaxBlocks) d.grid = kMaxBlocks;
             d.ready = true;

@@ -68,6 +68,19 @@ def test_det_bitexact_variants(flags):
     compare_run(wl, [50, 200])
 
 
+def test_det_bitexact_excitation_variant():
+    """The excitation of Sec. III / Sec. V.A: homogeneous over the excited
+    layers (abs_len = 0, both Fe layers of the spin valve), fixed energy per
+    spin (e_mode = 1: majority 1.5 eV, minority 1.0 eV)."""
+    wl = W.spin_valve(False, n0=20_000, capacity=90_000, n_steps=300, flags=DET)
+    st = wl.stacks[0]
+    st.abs_len = 0.0
+    st.e_mode = W.E_MONO
+    st.k_mono = (30, 20)
+    st.excite_mask = 0b101
+    compare_run(wl, [60, 150, 300])
+
+
 @pytest.mark.parametrize("ap", [False, True])
 def test_det_bitexact_spin_valve(ap):
     wl = W.spin_valve(ap, n0=20_000, capacity=90_000, n_steps=400, flags=DET,

@@ -562,3 +562,61 @@ def test_velocity_moment_off_without_the_flag():
     s = OracleSim(wl)
     assert s.step(40) == 0
     assert not s.vel_moments().any()
+
+
+# ---------------------------------------------------------------------------
+# Excitation variant of Sec. III ("Number of Particles") and Sec. V.A: carriers
+# created homogeneously over the excited layers, at a fixed energy per spin
+# (majority 1.5 eV, minority 1.0 eV above E_F)
+# ---------------------------------------------------------------------------
+def _mono_homogeneous_run(excite_mask, k_mono, n0=120_000):
+    wl = W.spin_valve(False, fe_nm=10, au_nm=20, n0=n0, capacity=n0, n_steps=1)
+    st = wl.stacks[0]
+    st.t0 = 0.25; st.fwhm = 0.1          # the whole pulse inside the first 0.5 fs step
+    st.tau_in[:] = INF; st.tau_el[:] = INF
+    st.v[:] = np.float32(1e-9)           # carriers stay where they are born
+    st.abs_len = 0.0                     # homogeneous in the excited layers
+    st.e_mode = W.E_MONO
+    st.k_mono = k_mono
+    st.excite_mask = excite_mask
+    s = OracleSim(wl)
+    assert s.step(1) == 0
+    return wl, s.records()
+
+
+def test_excitation_homogeneous_fixed_energy_per_spin():
+    # distinct bins per spin, so that a swapped index cannot pass: 1.5 eV
+    # (k = 30) for the majority and 1.0 eV (k = 20) for the minority channel
+    wl, r = _mono_homogeneous_run(0b101, (30, 20))
+    st = wl.stacks[0]
+    u = unpack(r["packed"])
+    N = len(r)
+    assert N == st.n0 and np.all(u["gen"] == 1)
+    assert np.all(u["k"][u["spin"] == 0] == 30) and np.all(u["k"][u["spin"] == 1] == 20)
+    up = int((u["spin"] == 0).sum())
+    assert abs(up - N * 2 / 3) <= 4 * math.sqrt(N * 2 / 9)
+    # births only in the two excited Fe layers (cells 0..9 and 30..39), each
+    # cell equally likely; none in the Au spacer
+    z = r["z"]
+    assert np.all((z < 10.0) | (z >= 30.0)) and z.min() >= 0.0 and z.max() <= 40.0
+    assert np.array_equal(u["layer"], np.where(z < 10.0, 0, 2).astype(np.uint32))
+    cnt, _ = np.histogram(z, np.arange(41.0))
+    assert np.all(cnt[10:30] == 0)
+    exc = np.concatenate([cnt[:10], cnt[30:]])
+    assert stats.chisquare(exc).pvalue > 1e-4
+    # an exp(-z/15 nm) profile over the same cells would be rejected outright
+    lam = 15.0
+    zc = np.concatenate([np.arange(10.0), np.arange(30.0, 40.0)])
+    m = np.exp(-zc / lam) - np.exp(-(zc + 1) / lam)
+    assert stats.chisquare(exc, N * m / m.sum()).pvalue < 1e-12
+    # the position inside a cell is uniform
+    assert stats.kstest(z - np.floor(z), "uniform").pvalue > 1e-4
+
+
+def test_excitation_variant_single_layer_and_equal_bins():
+    # one excited layer (the collector only) and the same bin for both spins
+    wl, r = _mono_homogeneous_run(0b100, (7, 7), n0=30_000)
+    u = unpack(r["packed"])
+    assert np.all(u["k"] == 7) and np.all(u["layer"] == 2)
+    cnt, _ = np.histogram(r["z"], np.arange(30.0, 41.0))
+    assert cnt.sum() == len(r) and stats.chisquare(cnt).pvalue > 1e-4
