@@ -75,7 +75,7 @@ typedef struct {
     uint32_t flags;         /* PIC_F_* */
     int32_t compact_every;  /* stable removal of dead slots every N steps (>= 1) */
     int32_t moment_every;   /* density snapshot every N steps (>= 1); the flux
-                               is accumulated over the same windows */
+                               is taken over the same windows */
     int32_t n_steps_max;    /* steps this context may run; sizes the moment
                                buffers: n_out = ceil(n_steps_max/moment_every) */
     int32_t blocks_per_sm;  /* persistent blocks per SM for the step kernel;
@@ -97,6 +97,10 @@ typedef struct {
                                split over several contexts (one per GPU or
                                process) give the results of one context that
                                holds them all */
+    int32_t consumer_warps; /* warps of the streaming pass that work on the
+                               carriers, 4 or 8 (each thread then takes 8 or 4
+                               consecutive slots of a 1024-slot tile); 0 = 8.
+                               Results do not depend on it. */
 } pic_params;
 
 /* Launch configuration a context chose (pic_launch_info). */
@@ -106,6 +110,7 @@ typedef struct {
     int32_t grid_compact, grid_inject;
     int32_t ring_step, ring_step_moments;   /* bulk-copy ring depth (tiles) */
     int64_t smem_step, smem_step_moments;   /* dynamic shared memory, bytes */
+    int32_t warps_step, warps_step_moments; /* consumer warps per block */
     /* pic_grad's replay passes 1 and 2 (zero before the first pic_grad):
      * streaming pass with density weights, its ring depth and shared memory */
     int32_t grid_adj_step[2], ring_adj_step[2];
@@ -170,8 +175,9 @@ typedef struct {
  * (streaming pass), 2 = step with density deposit (streaming pass),
  * 3 = compaction, 4 = step (event pass and placement of secondaries);
  * pic_grad's replays: 5 = streaming pass, 6 = event pass, 7 = the rest
- * (source, compaction, flux potential, flush, lineage totals). */
-#define PIC_KERNEL_KINDS 8
+ * (source, compaction, flux potential, flush, lineage totals);
+ * 8 = the fluxes derived by pic_moments. */
+#define PIC_KERNEL_KINDS 9
 typedef struct {
     int64_t launches[PIC_KERNEL_KINDS];
     double ms[PIC_KERNEL_KINDS];
@@ -216,8 +222,13 @@ pic_status pic_step(pic_ctx *ctx, int n_steps);
  * the end of each moment window.  J_dev (device, may be NULL): int32
  * [n_out][2][n_cells+1] net number of carriers of each spin that crossed
  * each cell face towards +z during the window (the time-integrated spin
- * flux; face f sits at z = f*dz).  ledger_host (host, may be NULL).
- * Synchronises the context stream; returns any pending device status. */
+ * flux; face f sits at z = f*dz); the window still running holds the
+ * crossings so far.  The library does not count crossings one by one: it
+ * derives these integers, exactly, from the densities at the ends of the
+ * windows and the cells where carriers were created and removed (a kernel
+ * pass on the device per call; one over the current state when a window is
+ * running).  ledger_host (host, may be NULL).  Synchronises the context
+ * stream; returns any pending device status. */
 pic_status pic_moments(pic_ctx *ctx, int stack, uint32_t *n_dev, int32_t *J_dev,
                        pic_ledger *ledger_host);
 
@@ -261,7 +272,12 @@ pic_status pic_grad(pic_ctx *ctx, const float *grad_n_dev, const float *grad_J_d
 pic_status pic_records(pic_ctx *ctx, int stack, pic_record *host_out, int64_t *n);
 
 /* Replace the particle slots of one stack (test set-up and resume from a
- * saved state).  next_id is the id given to the next created carrier. */
+ * saved state).  next_id is the id given to the next created carrier.
+ * Every record must have k in 0..n_e, a layer of the stack, a finite
+ * non-zero mu in [-1, 1] and z inside its layer (edges included); otherwise
+ * PIC_ERR_ARG and nothing changes.  For the fluxes of the running window the
+ * replaced carriers count as removed and the loaded ones as created where
+ * they are (no crossing is counted for either). */
 pic_status pic_set_records(pic_ctx *ctx, int stack, const pic_record *host_in,
                            int64_t n, uint64_t next_id);
 
@@ -326,6 +342,8 @@ typedef struct {
     int32_t hist_mode;      /* density deposit: 0 shared atomics, 1 warp-aggregated */
     int32_t chosen;         /* 1 for the configuration the context keeps */
     double ns_per_particle_step;  /* device time of the trial / carriers advanced */
+    int32_t consumer_warps; /* warps of the streaming pass on the carriers (4 or 8),
+                               i.e. 8 or 4 consecutive slots per thread */
 } pic_tune_entry;
 
 /* Time candidate launch configurations of the step kernels on the running
@@ -333,11 +351,12 @@ typedef struct {
  * trial_steps ordinary steps (results do not depend on the launch
  * configuration: the slot order and every random word are fixed by the
  * run), timed with CUDA events on the context stream and divided by the
- * carriers advanced.  Candidates: 1 to 4 resident blocks per SM, ring
- * depth 2, 3, 4, 6 or 8 where it fits, and both deposit modes when the
- * trial contains density steps.  entries (host, may be NULL): up to
+ * carriers advanced.  Candidates: 8 or 4 consumer warps per block of the
+ * streaming pass (4 or 8 slots per thread), 1 to 6 (8 with four warps)
+ * resident blocks per SM, ring depth 2, 3, 4, 6 or 8 where it fits, and both
+ * deposit modes when the trial contains density steps.  entries (host, may be NULL): up to
  * max_entries results in the order tried; *n_entries (may be NULL): their
- * number.  Needs steps left: up to 40 * trial_steps.  Synchronises. */
+ * number.  Needs steps left: up to 140 * trial_steps.  Synchronises. */
 pic_status pic_autotune(pic_ctx *ctx, int trial_steps, pic_tune_entry *entries,
                         int max_entries, int *n_entries);
 

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpic.so")
-SOURCES = ["pic_kernels.cu", "pic_adjoint.cu", "pic_capi.cu", "pic_noalloc.cu", "pic_vmoment.cu"]
+SOURCES = ["pic_kernels.cu", "pic_adjoint.cu", "pic_capi.cu", "pic_noalloc.cu"]
 HEADERS = [os.path.join(CSRC, "pic_internal.h"), os.path.join(CSRC, "pic_step.cuh"),
            os.path.join(ROOT, "include", "pic.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

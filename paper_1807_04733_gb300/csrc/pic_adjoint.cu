@@ -133,7 +133,7 @@ cudaError_t configure_pass(const Args &a, LaunchCfg *cfg)
     const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;
     // tables, pass 2's sums of R, the flux potential slice and (with the
     // density deposit) the density-weight slice
-    const size_t fixed = (size_t)a.tab_max * sizeof(FastEnt) +
+    const size_t fixed = (size_t)a.ftab_max * sizeof(FastEnt) +
                          (ADJ == 2 ? (size_t)a.tab_max * 8 : 0) + (size_t)a.jbin_max * 8 + 4 +
                          tiles;
     const size_t fixed_dep = fixed + (size_t)a.nbin_max * 4;

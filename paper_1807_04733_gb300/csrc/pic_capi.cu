@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -80,6 +81,10 @@ struct pic_ctx {
     unsigned long long *d_gh = nullptr;          // generation sums [stack][n_out][n_cells]
     long long *d_vh = nullptr;                   // velocity sums [stack][n_out][2][n_cells]
     int32_t *d_J = nullptr;
+    int32_t *d_bd = nullptr;                     // births minus removals, J layout
+    int32_t *d_hnow = nullptr;                   // live carriers per [stack][2][ncm+1]
+    int ncm = 1;                                 // cells of the widest stack
+    int flux_final = 0;                          // windows whose fluxes are final
     DevCounters *d_cnt = nullptr;
     DevCtl *d_ctl = nullptr;
     int64_t total_slots = 0, nh_total = 0, J_total = 0;
@@ -155,6 +160,9 @@ bool valid_params(const pic_params *p, std::string &why)
         why = "ring_stages must be 0 or 2..8"; return false;
     }
     if (p->use_graph != 0 && p->use_graph != 1) { why = "use_graph must be 0 or 1"; return false; }
+    if (p->consumer_warps != 0 && p->consumer_warps != 4 && p->consumer_warps != 8) {
+        why = "consumer_warps must be 0, 4 or 8"; return false;
+    }
     if (p->stack_base < 0 || p->stack_base > 65535) { why = "stack_base out of range"; return false; }
     return true;
 }
@@ -313,6 +321,7 @@ void free_all(pic_ctx *c)
     }
     release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh); release(c->d_gh); release(c->d_vh);
     release(c->d_qrec); release(c->d_qcnt); release(c->d_fspawn); release(c->d_J); release(c->d_cnt);
+    release(c->d_bd); release(c->d_hnow);
     release(c->d_ctl);
     Replay &r = c->rp;
     for (int b = 0; b < 2; ++b) {
@@ -436,7 +445,14 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     c->hs.resize(n_stacks);
     c->ds.resize(n_stacks);
     const int ne = p->n_e;
-    int tab_max = 1, T_max = 1, nbin_max = 1, jbin_max = 1;
+    // the streaming pass's table: 2^kb entries per (layer, spin), kb the
+    // smallest power of two above n_e, so that the packed word indexes it
+    int kb = 0;
+    while ((1 << kb) < ne + 1) ++kb;
+    const int KP = 1 << kb;
+    const float inf = std::numeric_limits<float>::infinity();
+    const FastEnt inert{0.f, 0u, -inf, inf};
+    int tab_max = 1, T_max = 1, nbin_max = 1, jbin_max = 1, ftab_max = 1;
     std::vector<TabEnt> ent;
     std::vector<FastEnt> fent;
     std::vector<uint32_t> Tall;
@@ -467,13 +483,18 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         // layer-indexed {v, P, Q} entries
         d.tab_n = h.d.n_layers * 2 * ne;
         d.ent_off = (int64_t)ent.size();
+        d.ftab_n = h.d.n_layers * 2 * KP;
+        d.fent_off = (int64_t)fent.size();
         for (int l = 0; l < h.d.n_layers; ++l)
-            for (int sp = 0; sp < 2; ++sp)
+            for (int sp = 0; sp < 2; ++sp) {
+                fent.push_back(inert);                       // k = 0: a removed carrier
                 for (int k = 0; k < ne; ++k) {
                     const size_t i = ((size_t)h.d.layer_mat[l] * 2 + sp) * ne + k;
                     ent.push_back(TabEnt{h.v[i], h.P_thr[i], h.Q_thr[i], 0u});
                     fent.push_back(FastEnt{h.v[i], h.P_thr[i], d.edge[l], d.edge[l + 1]});
                 }
+                for (int k = ne + 1; k < KP; ++k) fent.push_back(inert);
+            }
         d.T_n = (h.d.n_layers - 1) * 4 * ne;
         d.T_off = (int64_t)Tall.size();
         Tall.insert(Tall.end(), h.T_thr.begin(), h.T_thr.end());
@@ -489,6 +510,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         d.n_cdf = 0;
         d.inj_off = (int64_t)s * 2 * p->n_steps_max;
         tab_max = std::max(tab_max, d.tab_n);
+        ftab_max = std::max(ftab_max, d.ftab_n);
         T_max = std::max(T_max, d.T_n);
         nbin_max = std::max(nbin_max, 2 * ne * cells);
         jbin_max = std::max(jbin_max, 2 * (cells + 1));
@@ -508,6 +530,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     for (int s = 0; s < n_stacks; ++s) {
         c->ds[s].cdf_off = total_cells;
         total_cells += c->hs[s].n_cells;
+        c->ncm = std::max(c->ncm, c->hs[s].n_cells);
     }
 
     cudaError_t e = cudaSuccess;
@@ -533,6 +556,8 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     ALLOC(c->d_gh, c->nh_total / (2 * p->n_e) + 1);
     ALLOC(c->d_vh, c->nh_total / p->n_e + 1);
     ALLOC(c->d_J, c->J_total);
+    ALLOC(c->d_bd, c->J_total);
+    ALLOC(c->d_hnow, (size_t)n_stacks * 2 * (c->ncm + 1));
     ALLOC(c->d_cnt, n_stacks);
     ALLOC(c->d_ctl, 1);
 #undef ALLOC
@@ -557,6 +582,11 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.spawn_bits = c->d_bits;
     a.qrec = c->d_qrec;
     a.n_hist = c->d_nh; a.J_hist = c->d_J; a.cnt = c->d_cnt; a.ctl = c->d_ctl;
+    a.bd_hist = c->d_bd;
+    a.kb = kb;
+    a.kshr = 8 - kb;
+    a.kmask = (uint32_t)KP - 1u;
+    a.hmask = 0x1Fu << kb;
     a.g_hist = c->d_gh;
     a.v_hist = c->d_vh;
     a.seed_lo = (uint32_t)p->seed; a.seed_hi = (uint32_t)(p->seed >> 32);
@@ -572,10 +602,11 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.flags = p->flags; a.n_e = ne; a.moment_every = p->moment_every;
     a.step = 0;
     a.tab_max = tab_max; a.T_max = T_max; a.nbin_max = nbin_max; a.jbin_max = jbin_max;
+    a.ftab_max = ftab_max;
     a.gbin_max = nbin_max / (2 * ne);
     a.spin_limit = 1u << 24;
 
-    e = configure(a, p->blocks_per_sm, p->ring_stages, p->hist_mode, &c->lc);
+    e = configure(a, p->blocks_per_sm, p->ring_stages, p->hist_mode, p->consumer_warps, &c->lc);
     if (e != cudaSuccess) {
         g_init_error = std::string("kernel configuration (moment grid too large for shared "
                                    "memory, or no device): ") + cudaGetErrorString(e);
@@ -584,9 +615,14 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
         cudaGetLastError();
         return PIC_ERR_ARG;   // moment grid too large for shared memory, or no device
     }
+    // look-back words and per-block counts for the largest grid any launch
+    // configuration (pic_autotune's included) can give
+    int sms_now = 0, dev_now = 0;
+    cudaGetDevice(&dev_now);
+    cudaDeviceGetAttribute(&sms_now, cudaDevAttrMultiProcessorCount, dev_now);
     const int gmax = std::max({c->lc.grid_fast, c->lc.grid_fast_dep, c->lc.grid_slow,
                                c->lc.grid_slow_dep, c->lc.grid_place, c->lc.grid_place_dep,
-                               c->lc.grid_compact});
+                               c->lc.grid_compact, 16 * sms_now});
     c->n_status = gmax;
     if (dalloc(&c->d_status, (size_t)gmax) != cudaSuccess ||
         dalloc(&c->d_qcnt, (size_t)gmax) != cudaSuccess ||
@@ -618,6 +654,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_gh, 0, 8 * (size_t)(c->nh_total / (2 * p->n_e) + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_vh, 0, 8 * (size_t)(c->nh_total / p->n_e + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_J, 0, 4 * (size_t)std::max<int64_t>(c->J_total, 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bd, 0, 4 * (size_t)std::max<int64_t>(c->J_total, 1), st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt, cnt.data(), sizeof(DevCounters) * n_stacks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -709,10 +746,6 @@ cudaError_t enqueue_step(pic_ctx *c, const Args &a0, int s, bool inj0, bool inj1
         e = timed(c, 0, [&] { return launch_inject(b, lc, 1, dep, st); });
         ++launches;
     }
-    if (e == cudaSuccess && dep && (c->p.flags & PIC_F_VELOCITY_MOMENTS)) {
-        e = timed(c, 2, [&] { return launch_vmoment(a, lc, st); });
-        ++launches;
-    }
     if (e == cudaSuccess && ((s + 1) % c->p.compact_every) == 0) {
         e = timed(c, 3, [&] { return launch_compact(a, lc, st); });
         ++launches;
@@ -754,6 +787,30 @@ cudaError_t capture_period(pic_ctx *c, int which)
 }
 
 int gcd_int(int x, int y) { return y ? gcd_int(y, x % y) : x; }
+
+// The fluxes of every window reached so far, from the densities and the
+// births-minus-removals histograms (k_flux): windows that have ended are
+// computed once; the running window (if any) is computed from a count of the
+// current state each time it is asked for.
+cudaError_t derive_fluxes(pic_ctx *c)
+{
+    const int me = c->p.moment_every, n_out = c->hs[0].n_out;
+    const int ended = std::min(c->step / me, n_out);
+    cudaError_t e = cudaSuccess;
+    if (c->flux_final < ended) {
+        e = timed(c, 8, [&] { return launch_flux(c->args, c->flux_final, ended, -1, nullptr, c->ncm, c->stream); });
+        if (e != cudaSuccess) return e;
+        c->flux_final = ended;
+    }
+    if (c->step % me != 0 && ended < n_out) {
+        e = cudaMemsetAsync(c->d_hnow, 0, sizeof(int32_t) * (size_t)c->n_stacks * 2 * (c->ncm + 1), c->stream);
+        if (e == cudaSuccess)
+            e = timed(c, 8, [&] { return launch_state_hist(c->args, 0, c->n_stacks, 1, 0, 1, c->d_hnow, c->ncm, c->stream); });
+        if (e == cudaSuccess)
+            e = timed(c, 8, [&] { return launch_flux(c->args, ended, ended + 1, ended, c->d_hnow, c->ncm, c->stream); });
+    }
+    return e;
+}
 
 }  // namespace
 
@@ -815,7 +872,8 @@ pic_status pic_moments(pic_ctx *c, int stack, uint32_t *n_dev, int32_t *J_dev, p
     if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
     const HostStack &h = c->hs[stack];
     const DevStack &d = c->ds[stack];
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = J_dev ? derive_fluxes(c) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_moments fluxes");
     const size_t nn = (size_t)h.n_out * 2 * c->p.n_e * h.n_cells;
     const size_t nj = (size_t)h.n_out * 2 * (h.n_cells + 1);
     if (n_dev && nn) e = cudaMemcpyAsync(n_dev, c->d_nh + d.n_off, 4 * nn, cudaMemcpyDeviceToDevice, c->stream);
@@ -913,9 +971,19 @@ pic_status pic_set_records(pic_ctx *c, int stack, const pic_record *in, int64_t 
         if (k > (uint32_t)c->p.n_e || (int)layer >= hs.d.n_layers || !(in[i].z >= 0.f) ||
             !(in[i].z <= L) || !(in[i].mu >= -1.f && in[i].mu <= 1.f) || in[i].mu == 0.f)
             return fail(c, PIC_ERR_ARG, "record " + std::to_string(i) + " is out of range");
+        // a carrier sits inside the layer its state names (edges included)
+        if (!(in[i].z >= c->ds[stack].edge[layer] && in[i].z <= c->ds[stack].edge[layer + 1]))
+            return fail(c, PIC_ERR_ARG, "record " + std::to_string(i) + " lies outside its layer");
     }
+    // the carriers the stack holds now leave it, in the current window, and
+    // the loaded ones enter it (births and removals at their cells: the
+    // fluxes count only crossings)
+    const int win = c->step / c->p.moment_every;
+    const bool in_run = win < hs.n_out;
+    cudaError_t e = cudaSuccess;
+    if (in_run) e = launch_state_hist(c->args, stack, stack + 1, 0, win, -1, nullptr, c->ncm, c->stream);
     DevCtl ctl{};
-    cudaError_t e = cudaMemcpyAsync(&ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pic_set_records");
     const int b = (int)ctl.cur;
@@ -934,7 +1002,13 @@ pic_status pic_set_records(pic_ctx *c, int stack, const pic_record *in, int64_t 
         if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_id[b] + base, id.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
     }
     const unsigned long long vals[2] = {(unsigned long long)n, (unsigned long long)next_id};
+    unsigned long long live = 0;
+    for (int64_t i = 0; i < n; ++i) live += (in[i].packed & 0xFFu) != 0u;
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt + stack, vals, sizeof(vals), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&c->d_cnt[stack].live, &live, sizeof(live), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && in_run)
+        e = launch_state_hist(c->args, stack, stack + 1, 0, win, 1, nullptr, c->ncm, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pic_set_records copy");
     // the adjoint replays from records loaded before the first step, whose
@@ -1123,6 +1197,7 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
             const std::vector<pic_record> &ir = c->init_recs[s];
             cnt[s].n_slots = ir.size();
             cnt[s].next_id = c->init_next_id[s];
+            for (const pic_record &q : ir) cnt[s].live += (q.packed & 0xFFu) != 0u;
             const int64_t n = (int64_t)ir.size();
             if (!n) continue;
             std::vector<float> z(n);
@@ -1250,6 +1325,8 @@ pic_status pic_launch_config(const pic_ctx *c, pic_launch_info *out)
     out->ring_step_moments = c->lc.ring_fast_dep;
     out->smem_step = (int64_t)c->lc.smem_fast;
     out->smem_step_moments = (int64_t)c->lc.smem_fast_dep;
+    out->warps_step = c->lc.nw_fast;
+    out->warps_step_moments = c->lc.nw_fast_dep;
     for (int i = 0; i < 2; ++i) {
         const bool r = c->rp.ready;
         out->grid_adj_step[i] = r ? c->rp.lc[i].grid_fast_dep : 0;
@@ -1265,12 +1342,13 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
     if (!c) return PIC_ERR_ARG;
     if (trial_steps < 1) return fail(c, PIC_ERR_ARG, "pic_autotune: trial_steps < 1");
     if (c->profiling) return fail(c, PIC_ERR_STATE, "pic_autotune: profiling is on");
-    struct Cand { int bps, ring, hm; };
+    struct Cand { int bps, ring, hm, nw; };
     std::vector<Cand> cands;
     const bool dep_in_trial = trial_steps >= c->p.moment_every;
     for (int hm = 0; hm <= (dep_in_trial ? 1 : 0); ++hm)
-        for (int bps = 1; bps <= 4; ++bps)
-            for (int ring : {2, 3, 4, 6, 8}) cands.push_back({bps, ring, hm});
+        for (int nw : {8, 4})
+            for (int bps = 1; bps <= (nw == 4 ? 8 : 6); ++bps)
+                for (int ring : {2, 3, 4, 6, 8}) cands.push_back({bps, ring, hm, nw});
     if ((int64_t)c->step + (int64_t)trial_steps * (int64_t)cands.size() > c->p.n_steps_max)
         return fail(c, PIC_ERR_ARG, "pic_autotune: not enough steps left for the trials");
     const int use_graph = c->p.use_graph;
@@ -1294,12 +1372,12 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
     const pic_params keep_p = c->p;
     double best = 0.0;
     LaunchCfg best_lc = keep;
-    Cand best_c{keep_p.blocks_per_sm, keep_p.ring_stages, keep_p.hist_mode};
+    Cand best_c{keep_p.blocks_per_sm, keep_p.ring_stages, keep_p.hist_mode, keep_p.consumer_warps};
     std::vector<pic_tune_entry> res;
     for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
         const Cand &k = cands[i];
         LaunchCfg lc{};
-        if (configure(c->args, k.bps, k.ring, k.hm, &lc) != cudaSuccess) {
+        if (configure(c->args, k.bps, k.ring, k.hm, k.nw, &lc) != cudaSuccess) {
             cudaGetLastError();               // does not fit: not a candidate
             continue;
         }
@@ -1325,7 +1403,7 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
         if (e != cudaSuccess) break;
         const double ns = ps1 > ps0 ? 1e6 * (double)ms / (double)(ps1 - ps0) : 1e30;
-        res.push_back(pic_tune_entry{k.bps, k.ring, k.hm, 0, ns});
+        res.push_back(pic_tune_entry{k.bps, k.ring, k.hm, 0, ns, k.nw});
         if (res.size() == 1 || ns < best) {
             best = ns;
             best_lc = lc;
@@ -1344,6 +1422,7 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
     c->p.blocks_per_sm = best_c.bps;
     c->p.ring_stages = best_c.ring;
     c->p.hist_mode = best_c.hm;
+    c->p.consumer_warps = best_c.nw;
     // graphs captured with the old configuration are stale
     for (cudaGraphExec_t &g : c->period_graph) {
         if (g) cudaGraphExecDestroy(g);
@@ -1351,7 +1430,7 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
     }
     for (pic_tune_entry &r : res)
         r.chosen = (r.blocks_per_sm == best_c.bps && r.ring_stages == best_c.ring &&
-                    r.hist_mode == best_c.hm) ? 1 : 0;
+                    r.hist_mode == best_c.hm && r.consumer_warps == best_c.nw) ? 1 : 0;
     if (entries)
         for (int i = 0; i < (int)res.size() && i < max_entries; ++i) entries[i] = res[i];
     if (n_entries) *n_entries = (int)res.size();

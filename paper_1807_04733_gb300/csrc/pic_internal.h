@@ -10,8 +10,12 @@
 //               secondary of the carrier at that position, before its final
 //               place is known, flagged by one bit per slot in spawn_bits.
 //   tables    : per stack, per layer: {v, P_thr, Q_thr} (16 B) for
-//               [layer][spin][k], the interface thresholds, P0 per layer.
-//   moments   : uint32 densities and int32 fluxes per output window.
+//               [layer][spin][k], the interface thresholds, P0 per layer;
+//               the streaming pass's {v, P_thr, lo, hi} padded to 2^kb bins
+//               per (layer, spin) so that the packed word indexes it directly.
+//   moments   : uint32 densities and int32 fluxes per output window; the
+//               births minus removals of carriers per window and cell, from
+//               which the fluxes are derived (see k_flux in pic_kernels.cu).
 #pragma once
 #include <cstdint>
 
@@ -55,6 +59,12 @@ struct FastEnt {         // the common path's (layer, spin, k) entry
     uint32_t P;          // scatter iff test word < P
     float lo, hi;        // edges of the layer, nm
 };
+// The streaming pass's table holds 2^kb entries per (layer, spin), kb the
+// smallest power of two above n_e: entry ((layer * 2 + spin) << kb) + k, read
+// with the index (pk & kmask) | ((pk >> (8 - kb)) & hmask) of the packed word
+// pk = k:8 | spin:1 | layer:4 | ....  Entries k = 0 (a removed carrier) and
+// k > n_e hold the inert entry {v = 0, P = 0, lo = -inf, hi = +inf}: such a
+// slot never moves, scatters or meets a boundary.
 
 struct AdjEnt {          // d log P / d tau_in of the outcomes of one (layer, spin, k) entry
     double noscat;       // no scattering in the step
@@ -70,6 +80,7 @@ struct DevStack {        // immutable per-stack description (device copy)
     int64_t base, cap;                  // slot range
     int64_t n_off, J_off;               // offsets in the moment arrays
     int64_t ent_off, T_off;             // offsets in the table arrays
+    int64_t fent_off; int32_t ftab_n;   // padded streaming-pass table
     int64_t cdf_off; int32_t n_cdf;     // source profile
     uint32_t up_thr;
     int32_t e_mode, k_mono0, k_mono1;
@@ -80,6 +91,7 @@ struct DevStack {        // immutable per-stack description (device copy)
 struct DevCounters {     // mutable per stack
     unsigned long long n_slots, next_id, spawn_total, alive_total;
     unsigned long long led[LEDGER_N];
+    unsigned long long live;   // live carriers (k > 0) among the slots
 };
 
 struct DevCtl {
@@ -96,7 +108,9 @@ struct Args {            // everything a kernel needs, passed by value
     const DevStack *stacks;
     int n_stacks;
     const TabEnt *ent;
-    const FastEnt *fent;                     // same indexing as ent
+    const FastEnt *fent;                     // padded: see FastEnt
+    uint32_t kmask, hmask;                   // fast-table index of a packed word:
+    int kshr, kb;                            //   (pk & kmask) | ((pk >> kshr) & hmask)
     const uint32_t *T_thr;
     const uint32_t *cdf_thr;
     const int32_t *cdf_cell;
@@ -117,6 +131,10 @@ struct Args {            // everything a kernel needs, passed by value
     // generation labels summed per [stack][n_out][n_cells], at n_off / (2 n_e)
     unsigned long long *g_hist;
     int32_t *J_hist;
+    // births minus removals of carriers per [stack][n_out][2][n_cells+1]
+    // (J layout, last entry unused): the fluxes are derived from these and
+    // the densities
+    int32_t *bd_hist;
     DevCounters *cnt;
     DevCtl *ctl;
     uint32_t seed_lo, seed_hi;
@@ -131,6 +149,7 @@ struct Args {            // everything a kernel needs, passed by value
     const unsigned int *step_dev;            // graph replay: the step is read here
     int bump_step;                           // this kernel's last block advances *step_dev
     int tab_max, T_max, nbin_max, jbin_max;  // shared-memory sizing
+    int ftab_max;                            // entries of the padded fast table
     int gbin_max;                            // cells of the widest stack (generation sums)
     unsigned int spin_limit;                 // bound of every device-side wait
     int ring;                                // tiles in k_fast's copy ring
@@ -168,14 +187,17 @@ void pic_set_static_error(const char *msg);
 
 // host-side launchers (pic_kernels.cu)
 struct LaunchCfg {
-    int grid_fast, grid_fast_dep;          // k_fast (without / with density deposit)
+    int grid_fast, grid_fast_dep;          // streaming pass (without / with density deposit)
+    int nw_fast, nw_fast_dep;              // its consumer warps per block (4 or 8)
     int grid_slow, grid_slow_dep;          // k_event
     int grid_place, grid_place_dep;        // k_place
     int grid_compact, grid_inject;
     int ring_fast, ring_fast_dep;
     size_t smem_fast, smem_fast_dep, smem_slow, smem_slow_dep, smem_place, smem_place_dep;
 };
-cudaError_t configure(const Args &a, int blocks_per_sm, int ring, int hist_mode, LaunchCfg *cfg);
+// blocks_per_sm, ring, nw: 0 = chosen from the occupancy
+cudaError_t configure(const Args &a, int blocks_per_sm, int ring, int hist_mode, int nw,
+                      LaunchCfg *cfg);
 cudaError_t launch_inject(const Args &a, const LaunchCfg &c, int half, bool deposit,
                           cudaStream_t s);
 cudaError_t launch_fast(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
@@ -183,8 +205,17 @@ cudaError_t launch_fast(const Args &a, const LaunchCfg &c, bool deterministic, b
 cudaError_t launch_slow(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
                         cudaStream_t s);
 cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s);
-// velocity moment of the density step just finished (pic_vmoment.cu)
-cudaError_t launch_vmoment(const Args &a, const LaunchCfg &c, cudaStream_t s);
+// live carriers of stacks [s0, s1) counted per (spin, cell) into out (int32,
+// per stack at out + stack_off(s) ...): mode 0 = the windows' births-minus-
+// removals histogram of window `win` (sign +1 or -1), mode 1 = a scratch
+// [stack][2][ncm+1]
+cudaError_t launch_state_hist(const Args &a, int s0, int s1, int mode, int win, int sign,
+                              int32_t *scratch, int ncm, cudaStream_t st);
+// fluxes of windows [w0, w1) of every stack from the densities and the
+// births-minus-removals histograms; window w_now (unfinished) takes its end
+// counts from `now` [stack][2][ncm+1] (the current state) instead
+cudaError_t launch_flux(const Args &a, int w0, int w1, int w_now, const int32_t *now, int ncm,
+                        cudaStream_t st);
 // set the device step counter read by graph-replayed steps
 cudaError_t launch_set_step(DevCtl *ctl, unsigned int step, cudaStream_t s);
 

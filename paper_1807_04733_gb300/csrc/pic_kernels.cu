@@ -1,5 +1,7 @@
 // Forward step of the hot-electron PIC method: launch configuration and
-// launchers of the kernels in pic_step.cuh.
+// launchers of the kernels in pic_step.cuh, and the two small kernels that
+// turn the densities and the births and removals of carriers into the
+// fluxes through the cell faces.
 #include <cuda_runtime.h>
 
 #include "pic_step.cuh"
@@ -7,29 +9,150 @@
 namespace pic {
 
 // ---------------------------------------------------------------------------
+// Fluxes from counts.  The spin flux of a moment window through face f (the
+// net number of carriers of one spin that crossed it towards +z, reading of
+// Eq. spincurrent) is, carrier by carrier, [cell at the end >= f] - [cell at
+// the start >= f], the ends being the window's ends or the carrier's birth
+// and removal.  Summed over carriers:
+//
+//   J_w[f] = sum_{c >= f} ( N_w[c] - N_{w-1}[c] - B_w[c] )
+//
+// with N_w the live carriers per cell at the end of window w (the densities
+// summed over energy; N_{-1} = 0), and B_w the births minus removals per cell
+// in window w (source, secondaries, removals, replaced records).  The result
+// is the same integer as counting every crossing step by step.
+// ---------------------------------------------------------------------------
+
+// One block per (stack, window, spin) row: J of window w from the densities
+// of windows w and w - 1 (or `now` for an unfinished window w == w_now).
+__global__ void __launch_bounds__(TPB) k_flux(const Args a, int w0, int w1, int w_now,
+                                              const int32_t *now, int ncm)
+{
+    __shared__ int s_w[TPB / 32];
+    const int nw = w1 - w0;
+    const int row = blockIdx.x;
+    const int s = row / (2 * nw), rem = row % (2 * nw), w = w0 + rem / 2, sg = rem % 2;
+    const DevStack &st = a.stacks[s];
+    const int nc = st.n_cells, nf = nc + 1, ne = a.n_e;
+    const long long nbins = 2LL * ne * nc;
+    const uint32_t *Ne = a.n_hist + st.n_off + (long long)w * nbins + (long long)sg * ne * nc;
+    const uint32_t *Ns = w > 0 ? Ne - nbins : nullptr;
+    const int32_t *B = a.bd_hist + st.J_off + ((long long)w * 2 + sg) * nf;
+    const int32_t *Nn = (w == w_now && now) ? now + ((long long)s * 2 + sg) * (ncm + 1) : nullptr;
+    int32_t *J = a.J_hist + st.J_off + ((long long)w * 2 + sg) * nf;
+    // suffix sums over cells, in chunks of TPB cells from the top
+    int carry = 0;
+    for (int c1 = nc; c1 > 0; c1 -= TPB) {
+        const int c = c1 - 1 - threadIdx.x;          // descending cell of this thread
+        int d = 0;
+        if (c >= 0) {
+            long long ne_c = 0, ns_c = 0;
+            if (Nn) {
+                ne_c = Nn[c];
+            } else {
+                for (int k = 0; k < ne; ++k) ne_c += Ne[(long long)k * nc + c];
+            }
+            if (Ns)
+                for (int k = 0; k < ne; ++k) ns_c += Ns[(long long)k * nc + c];
+            d = (int)(ne_c - ns_c) - B[c];
+        }
+        int excl;
+        const int tot = block_scan(d, excl, s_w);
+        if (c >= 0) J[c] = carry + excl + d;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) J[nc] = 0;
+}
+
+// Live carriers of stacks [s0, s1) per (spin, cell): mode 0 adds `sign` per
+// carrier to the births-minus-removals histogram of window `win`; mode 1
+// counts into out[stack][2][ncm + 1] (zeroed by the caller).
+__global__ void __launch_bounds__(TPB) k_state_hist(const Args a, int s0, int s1, int mode,
+                                                    int win, int sign, int32_t *out, int ncm)
+{
+    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
+    for (int s = s0; s < s1; ++s) {
+        const DevStack &st = a.stacks[s];
+        const long long n = (long long)a.cnt[s].n_slots;
+        Stk tmp;
+        tmp.n_cells = st.n_cells;
+        int32_t *h = mode == 0 ? a.bd_hist + st.J_off + (long long)win * 2 * (st.n_cells + 1)
+                               : out + (long long)s * 2 * (ncm + 1);
+        const int nf = mode == 0 ? st.n_cells + 1 : ncm + 1;
+        for (long long i = (long long)blockIdx.x * TPB + threadIdx.x; i < n;
+             i += (long long)gridDim.x * TPB) {
+            const long long g = st.base + i;
+            const uint32_t pk = a.pk[cur][g * a.mp_stride];
+            if ((pk & 0xFFu) == 0u) continue;
+            const int sg = (int)((pk >> 8) & 1u);
+            atomicAdd(&h[sg * nf + cell_of(a, tmp, a.z[cur][g])], sign);
+        }
+    }
+}
+
+cudaError_t launch_flux(const Args &a, int w0, int w1, int w_now, const int32_t *now, int ncm,
+                        cudaStream_t st)
+{
+    if (w1 <= w0) return cudaSuccess;
+    k_flux<<<a.n_stacks * 2 * (w1 - w0), TPB, 0, st>>>(a, w0, w1, w_now, now, ncm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_hist(const Args &a, int s0, int s1, int mode, int win, int sign,
+                              int32_t *scratch, int ncm, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    k_state_hist<<<sms * 4, TPB, 0, st>>>(a, s0, s1, mode, win, sign, scratch, ncm);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
-cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_mode, LaunchCfg *cfg)
+namespace {
+
+// k_stream's configuration for one deposit variant and consumer-warp count
+template <bool DEPN, bool WAGG>
+cudaError_t stream_cfg(size_t fixed, int blocks_per_sm, int ring_req, int nw, int *ring,
+                       int *blocks, size_t *smem)
+{
+    return nw == 4 ? pick_stream_ring<DEPN, WAGG, 4>(fixed, blocks_per_sm, ring_req, ring, blocks, smem)
+                   : pick_stream_ring<DEPN, WAGG, 8>(fixed, blocks_per_sm, ring_req, ring, blocks, smem);
+}
+
+}  // namespace
+
+cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_mode, int nw,
+                      LaunchCfg *cfg)
 {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
+    if (nw != 0 && nw != 4 && nw != 8) return cudaErrorInvalidValue;
     const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;      // tile prefix, counts
-    const size_t fixed = (size_t)a.tab_max * sizeof(FastEnt) + (size_t)a.jbin_max * 4 + 4 + tiles;
-    const size_t fixed_dep = fixed + (size_t)(a.nbin_max + a.gbin_max) * 4;
+    const size_t fixed = (size_t)a.ftab_max * sizeof(FastEnt) + tiles;
+    const size_t fixed_dep = fixed + (size_t)(a.nbin_max + a.gbin_max) * 4 + (size_t)a.gbin_max * 16 + 8;
+    // consumer warps: eight unless four were asked for (the density-step
+    // variant, which holds large histograms, always takes eight)
+    const int nw_plain = nw == 4 ? 4 : 8;
     int o_plain = 0, o_dep = 0;
-    if ((e = pick_ring<false, false>(fixed, blocks_per_sm, ring_req, &cfg->ring_fast, &o_plain,
-                                     &cfg->smem_fast)) != cudaSuccess)
+    if ((e = stream_cfg<false, false>(fixed, blocks_per_sm, ring_req, nw_plain, &cfg->ring_fast,
+                                      &o_plain, &cfg->smem_fast)) != cudaSuccess)
         return e;
     if (hist_mode == 1)
-        e = pick_ring<true, true>(fixed_dep, blocks_per_sm, 0, &cfg->ring_fast_dep, &o_dep,
-                                  &cfg->smem_fast_dep);
-    else
-        e = pick_ring<true, false>(fixed_dep, blocks_per_sm, 0, &cfg->ring_fast_dep, &o_dep,
+        e = stream_cfg<true, true>(fixed_dep, blocks_per_sm, 0, 8, &cfg->ring_fast_dep, &o_dep,
                                    &cfg->smem_fast_dep);
+    else
+        e = stream_cfg<true, false>(fixed_dep, blocks_per_sm, 0, 8, &cfg->ring_fast_dep, &o_dep,
+                                    &cfg->smem_fast_dep);
     if (e != cudaSuccess) return e;
+    cfg->nw_fast = nw_plain;
+    cfg->nw_fast_dep = 8;
     cfg->grid_fast = sms * o_plain;
     cfg->grid_fast_dep = sms * o_dep;
     const int gf_max = cfg->grid_fast > cfg->grid_fast_dep ? cfg->grid_fast : cfg->grid_fast_dep;
@@ -49,27 +172,39 @@ cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_m
     return cudaSuccess;
 }
 
+namespace {
+
+template <bool DET, bool DEPN, bool WAGG>
+void stream_launch(const Args &a, int g, int nw, size_t sm, cudaStream_t s)
+{
+    if (nw == 4) k_stream<DET, DEPN, WAGG, 4><<<g, stream_threads<4>(), sm, s>>>(a);
+    else k_stream<DET, DEPN, WAGG, 8><<<g, stream_threads<8>(), sm, s>>>(a);
+}
+
+}  // namespace
+
 cudaError_t launch_fast(const Args &a0, const LaunchCfg &c, bool det, bool dep, int hist_mode,
                         cudaStream_t s)
 {
     Args a = a0;
     a.ring = dep ? c.ring_fast_dep : c.ring_fast;
     const int g = dep ? c.grid_fast_dep : c.grid_fast;
+    const int nw = dep ? c.nw_fast_dep : c.nw_fast;
     const size_t sm = dep ? c.smem_fast_dep : c.smem_fast;
     const bool w = hist_mode == 1;
     if (det) {
         if (dep) {
-            if (w) k_fast<true, true, true><<<g, FAST_THREADS, sm, s>>>(a);
-            else k_fast<true, true, false><<<g, FAST_THREADS, sm, s>>>(a);
+            if (w) stream_launch<true, true, true>(a, g, nw, sm, s);
+            else stream_launch<true, true, false>(a, g, nw, sm, s);
         } else {
-            k_fast<true, false, false><<<g, FAST_THREADS, sm, s>>>(a);
+            stream_launch<true, false, false>(a, g, nw, sm, s);
         }
     } else {
         if (dep) {
-            if (w) k_fast<false, true, true><<<g, FAST_THREADS, sm, s>>>(a);
-            else k_fast<false, true, false><<<g, FAST_THREADS, sm, s>>>(a);
+            if (w) stream_launch<false, true, true>(a, g, nw, sm, s);
+            else stream_launch<false, true, false>(a, g, nw, sm, s);
         } else {
-            k_fast<false, false, false><<<g, FAST_THREADS, sm, s>>>(a);
+            stream_launch<false, false, false>(a, g, nw, sm, s);
         }
     }
     return cudaGetLastError();

@@ -486,8 +486,9 @@ __device__ __forceinline__ long long make_tiles(const Args &a, long long *s_tpre
 }
 
 // ---------------------------------------------------------------------------
-// k_fast: the common case of Transport(dt/2) -> Scattering(dt) ->
-// Transport(dt/2), streamed.
+// k_fast: the streaming pass of the adjoint replay (ADJ = 1, 2; the forward
+// step runs k_stream below): the common case of Transport(dt/2) ->
+// Scattering(dt) -> Transport(dt/2), streamed, with the per-slot reward.
 //
 // Warp-specialised pipeline: one producer warp issues the bulk copies of the
 // z, mu and packed arrays of each tile into a ring of a.ring shared-memory
@@ -500,6 +501,19 @@ __device__ __forceinline__ long long make_tiles(const Args &a, long long *s_tpre
 // carrier ("eventful": it scatters or meets a boundary) is copied, with its
 // position, to this block's region of the queue, in tile order, for k_event.
 // ---------------------------------------------------------------------------
+// index of a carrier's entry in the padded streaming-pass table
+__device__ __forceinline__ int fast_index(const Args &a, uint32_t pk)
+{
+    return (int)((pk & a.kmask) | ((pk >> a.kshr) & a.hmask));
+}
+
+// the velocity along z in fixed point: float32 product, 2^-32 nm/fs units,
+// truncated toward zero (exact sums, independent of their order)
+__device__ __forceinline__ long long vel_q(float w)
+{
+    return __float2ll_rz(__fmul_rn(w, 4294967296.0f));
+}
+
 constexpr int FAST_WARPS = TPB / 32;             // consumer warps
 constexpr int FAST_THREADS = TPB + 32;           // + the producer warp
 
@@ -550,7 +564,7 @@ k_fast(const Args a)
     FastEnt *s_ent = reinterpret_cast<FastEnt *>(ring + (size_t)a.ring * STG * TILE);
     // pass 2: sum of the reward-to-go of the carriers that passed the
     // scattering test, per entry (fixed point, two's complement)
-    unsigned long long *s_sr = reinterpret_cast<unsigned long long *>(s_ent + a.tab_max);
+    unsigned long long *s_sr = reinterpret_cast<unsigned long long *>(s_ent + a.ftab_max);
     // replay: the window's flux potential [2][n_cells] and density weights
     // [2][n_e][n_cells] of the stack, in place of the histograms
     long long *s_gp = reinterpret_cast<long long *>(s_sr + (ADJ == 2 ? a.tab_max : 0));
@@ -698,7 +712,7 @@ k_fast(const Args a)
             if (tid == 0) s_st = a.stacks[s];
             consumer_sync();
             const DevStack &st = s_st;
-            for (int q = tid; q < st.tab_n; q += TPB) s_ent[q] = a.fent[st.ent_off + q];
+            for (int q = tid; q < st.ftab_n; q += TPB) s_ent[q] = a.fent[st.fent_off + q];
             if (!ADJ)
                 for (int q = tid; q < 2 * (st.n_cells + 1); q += TPB) s_J[q] = 0;
             if (DEPN && !ADJ) {
@@ -777,7 +791,7 @@ k_fast(const Args a)
             const int k = (int)(pk & 0xFFu);
             const bool ok = (i0 + j < nvalid) && k != 0;
             const int sg = (int)((pk >> 8) & 1u), layer = (int)((pk >> 9) & 0xFu);
-            const FastEnt e = s_ent[ok ? (layer * 2 + sg) * ne + (k - 1) : 0];
+            const FastEnt e = s_ent[ok ? fast_index(a, pk) : 0];
             const float z = zin[j], mu = min_[j];
             const float w = __fmul_rn(e.v, mu);
             const float z1 = DET ? __fadd_rn(z, __fmul_rn(w, half)) : __fmaf_rn(w, half, z);
@@ -893,6 +907,342 @@ k_fast(const Args a)
 }
 
 // ---------------------------------------------------------------------------
+// k_stream: the forward streaming pass (Transport(dt/2) -> Scattering(dt) ->
+// Transport(dt/2) for every carrier that neither scatters nor meets a
+// boundary in the step; the others are queued for k_event).
+//
+// Warp-specialised as k_fast: one producer warp issues the bulk copies of a
+// tile's z and (mu, packed) pairs into a ring of shared-memory stages with
+// full/empty mbarriers; NW consumer warps each take G = TILE / (32 NW)
+// consecutive slots per thread (4 or 8: one Philox call per four slots).
+// What a carrier costs on an ordinary step: one index of the padded table
+// straight from its packed word, the two half flights, two compares against
+// the layer edges and one against the scattering threshold, and its new
+// depth written back with the others of the thread.  Nothing else is
+// counted per carrier: the flux through the cell faces follows from the
+// densities at the ends of the moment windows and the births and removals
+// in between (k_flux), and the carriers advanced in the step are the live
+// count kept by the kernels that create and remove carriers.  On a density
+// step the carriers finished here are also deposited (density, generation
+// label and, with PIC_F_VELOCITY_MOMENTS, velocity) into shared-memory
+// histograms flushed once per block and stack segment.
+// ---------------------------------------------------------------------------
+// resident blocks per SM the register budget must allow: four of 288
+// threads (eight consumer warps, 56 registers) or five of 160 (four consumer
+// warps with eight slots per thread, 80 registers)
+template <int NW>
+constexpr int stream_min_blocks() { return NW == 8 ? 4 : 5; }
+
+template <int NW>
+__device__ __forceinline__ void stream_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * NW) : "memory");
+}
+
+template <int NW>
+__device__ __forceinline__ unsigned long long stream_sum_u64(unsigned long long v,
+                                                             unsigned long long *s_r)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = v;
+    stream_sync<NW>();
+    unsigned long long t = 0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < NW; ++i) t += s_r[i];
+    stream_sync<NW>();
+    return t;  // valid in thread 0
+}
+
+template <int NW>
+constexpr int stream_threads() { return 32 * NW + 32; }
+
+template <bool DET, bool DEPN, bool WAGG, int NW>
+__global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW>()) k_stream(const Args a)
+{
+    constexpr int NT = 32 * NW;              // consumer threads
+    constexpr int G = TILE / NT;             // slots per consumer thread and tile
+    constexpr int NC = G / 4;                // Philox calls (and float4s) per thread
+    static_assert(G % 4 == 0 && G <= 8, "4 or 8 slots per thread");
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *ring = reinterpret_cast<float *>(smem);                      // a.ring x 3 x TILE
+    FastEnt *s_ent = reinterpret_cast<FastEnt *>(ring + (size_t)a.ring * 3 * TILE);
+    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_ent + a.ftab_max);   // density steps
+    uint32_t *s_gs = s_n + (DEPN ? a.nbin_max : 0);                     // generation sums
+    unsigned long long *s_v = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(s_gs + (DEPN ? a.gbin_max : 0)) + 7) & ~uintptr_t(7));
+    long long *s_tpref = reinterpret_cast<long long *>(s_v + (DEPN ? 2 * a.gbin_max : 0));
+    long long *s_nsl = s_tpref + a.n_stacks + 1;
+    __shared__ __align__(8) unsigned long long s_full[MAX_RING], s_empty[MAX_RING];
+    __shared__ DevStack s_st;
+    __shared__ unsigned long long s_r[NW];
+    __shared__ int s_qn, s_abort;
+
+    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
+    const int b = blockIdx.x, G_ = gridDim.x, tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const unsigned int lt_mask = (1u << lane) - 1u;
+    for (int i = tid; i < a.n_stacks; i += NT + 32) {
+        s_nsl[i] = (long long)a.cnt[i].n_slots;
+        // the carriers advanced in this step: every live one (the counts
+        // change only in the source, event and placement kernels)
+        if (b == 0) a.cnt[i].led[L_PARTICLE_STEPS] += a.cnt[i].live;
+    }
+    if (tid == 0) {
+        for (int i = 0; i < a.ring; ++i) {
+            mbar_init(&s_full[i], 1);
+            mbar_init(&s_empty[i], NW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_qn = 0;
+        s_abort = 0;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long acc = 0;
+        for (int i = 0; i < a.n_stacks; ++i) {
+            s_tpref[i] = acc;
+            acc += (s_nsl[i] + TILE - 1) / TILE;
+        }
+        s_tpref[a.n_stacks] = acc;
+    }
+    __syncthreads();
+    const long long T = s_tpref[a.n_stacks];
+    const long long t0 = chunk_lo(T, b, G_), t1 = chunk_lo(T, b + 1, G_);
+    const long long ntiles = t1 - t0;
+    const int nring = a.ring;
+    float *Z = a.z[cur];
+    const float *MP = a.mu[cur];         // mu and packed, interleaved
+
+    // ---------------- producer warp ----------------
+    if (warp == NW) {
+        if (lane == 0) {
+            long long issued = 0;
+            int stg = 0;
+            uint32_t phase = 0;          // completions of stage stg so far, mod 2
+            for (long long i = 0; i < ntiles; ++i) {
+                if (i >= nring &&
+                    !mbar_wait(&s_empty[stg], phase ^ 1u, a.spin_limit)) {
+                    atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+                    a.ctl->timeout_where = 4u;
+                    s_abort = 1;
+                }
+                if (*(volatile int *)&s_abort) break;
+                const long long t = t0 + i;
+                const int s = stack_of(s_tpref, a.n_stacks, t);
+                const long long off = a.stacks[s].base + (t - s_tpref[s]) * TILE;
+                float *dst = ring + (size_t)stg * 3 * TILE;
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&s_full[stg], 3 * TILE_BYTES);
+                bulk_load(dst, Z + off, TILE_BYTES, &s_full[stg]);
+                bulk_load(dst + TILE, MP + 2 * off, 2 * TILE_BYTES, &s_full[stg]);
+                issued = i + 1;
+                if (++stg == nring) { stg = 0; phase ^= 1u; }
+            }
+            if (*(volatile int *)&s_abort) {
+                // wait (bounded) for the copies that may still be in flight,
+                // so that none lands in shared memory after the block exits
+                for (long long i = issued > nring ? issued - nring : 0; i < issued; ++i)
+                    mbar_wait(&s_full[(int)(i % nring)], (uint32_t)((i / nring) & 1), a.spin_limit);
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
+    const uint32_t step = step_now(a);
+    const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
+    const float half = a.half_dt;
+    const long long pos0 = t0 * TILE;                // queue region of this block
+    const bool vmom = DEPN && (a.flags & PIC_F_VELOCITY_MOMENTS);
+    const int i0 = G * tid;                          // the thread's first slot in a tile
+    int seg_stack = -1, nc = 1, ne = a.n_e;
+    long long seg_t0 = 0, seg_t1 = -1;               // tiles of the current stack
+    int nsl = 0;
+    float *gZs = Z;
+    uint32_t ctr_hi = 0;
+    uint32_t n_queued = 0;
+
+    auto flush = [&](int s) {
+        stream_sync<NW>();
+        const DevStack &st = s_st;
+        if (DEPN) {
+            const int nbins = 2 * a.n_e * st.n_cells;
+            uint32_t *gN = a.n_hist + st.n_off + (long long)tout * nbins;
+            for (int i = tid; i < nbins; i += NT) {
+                const uint32_t v = s_n[i];
+                if (v) atomicAdd(&gN[i], v);
+            }
+            unsigned long long *gG = a.g_hist + st.n_off / (2 * a.n_e) + (long long)tout * st.n_cells;
+            for (int i = tid; i < st.n_cells; i += NT) {
+                const uint32_t v = s_gs[i];
+                if (v) atomicAdd(&gG[i], (unsigned long long)v);
+            }
+            if (vmom) {
+                unsigned long long *gV = reinterpret_cast<unsigned long long *>(a.v_hist) +
+                                         st.n_off / a.n_e + (long long)tout * 2 * st.n_cells;
+                for (int i = tid; i < 2 * st.n_cells; i += NT) {
+                    const unsigned long long v = s_v[i];
+                    if (v) atomicAdd(&gV[i], v);
+                }
+            }
+        }
+        const unsigned long long v1 = stream_sum_u64<NW>(n_queued, s_r);
+        if (tid == 0 && v1) atomicAdd(&a.cnt[s].led[L_EVENTFUL], v1);
+        n_queued = 0;
+        stream_sync<NW>();
+    };
+
+    int stg = 0;
+    uint32_t phase = 0;                  // completions of full[stg] consumed, mod 2
+    for (long long i = 0; i < ntiles; ++i) {
+        const long long t = t0 + i;
+        if (t >= seg_t1) {
+            // a new stack segment: its tables, histograms and constants
+            const int s = stack_of(s_tpref, a.n_stacks, t);
+            if (seg_stack >= 0) flush(seg_stack);
+            stream_sync<NW>();
+            if (tid == 0) s_st = a.stacks[s];
+            stream_sync<NW>();
+            const DevStack &st = s_st;
+            for (int q = tid; q < st.ftab_n; q += NT) s_ent[q] = a.fent[st.fent_off + q];
+            if (DEPN) {
+                for (int q = tid; q < 2 * a.n_e * st.n_cells; q += NT) s_n[q] = 0u;
+                for (int q = tid; q < st.n_cells; q += NT) s_gs[q] = 0u;
+                if (vmom)
+                    for (int q = tid; q < 2 * st.n_cells; q += NT) s_v[q] = 0ull;
+            }
+            nc = st.n_cells;
+            ctr_hi = (uint32_t)(a.stack_base + s) << 16;
+            seg_stack = s;
+            seg_t0 = s_tpref[s];
+            seg_t1 = s_tpref[s + 1];
+            nsl = (int)s_nsl[s];
+            gZs = Z + st.base;
+            stream_sync<NW>();
+        }
+        const int slot0 = (int)(t - seg_t0) * TILE;  // first slot of the tile in its stack
+        const int nvalid = nsl - slot0;              // valid slots of the tile (>= 1)
+        // after a failed wait every later wait is skipped: the warps run the
+        // same control flow to the end (results are invalid, the status says so)
+        if (!*(volatile int *)&s_abort && !mbar_wait(&s_full[stg], phase, a.spin_limit)) {
+            atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+            a.ctl->timeout_where = 3u;
+            s_abort = 1;
+        }
+        const float *rz = ring + (size_t)stg * 3 * TILE;
+        const uint4 *rmp = reinterpret_cast<const uint4 *>(rz + TILE);   // (mu, packed) pairs
+        float zin[G], min_[G];
+        uint32_t pin[G];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const float4 z4 = reinterpret_cast<const float4 *>(rz)[NC * tid + c];
+            const uint4 q01 = rmp[2 * (NC * tid + c)], q23 = rmp[2 * (NC * tid + c) + 1];
+            zin[4 * c] = z4.x; zin[4 * c + 1] = z4.y; zin[4 * c + 2] = z4.z; zin[4 * c + 3] = z4.w;
+            min_[4 * c] = __uint_as_float(q01.x); min_[4 * c + 1] = __uint_as_float(q01.z);
+            min_[4 * c + 2] = __uint_as_float(q23.x); min_[4 * c + 3] = __uint_as_float(q23.z);
+            pin[4 * c] = q01.y; pin[4 * c + 1] = q01.w; pin[4 * c + 2] = q23.y; pin[4 * c + 3] = q23.w;
+        }
+        // the stage is no longer needed by this warp
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_empty[stg]);
+        if (++stg == nring) { stg = 0; phase ^= 1u; }
+        // slots past the stack's end read the inert entry
+        if (nvalid < TILE) {
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                if (i0 + j >= nvalid) pin[j] = 0u;
+        }
+        // scattering-test words: word (slot mod 4) of the call for slot / 4
+        uint32_t xw[G];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            const uint4 x = philox_rk(make_uint4((uint32_t)(slot0 >> 2) + (uint32_t)(NC * tid + c),
+                                                 ctr_hi, step, SUB_TEST), a);
+            xw[4 * c] = x.x; xw[4 * c + 1] = x.y; xw[4 * c + 2] = x.z; xw[4 * c + 3] = x.w;
+        }
+        float zo[G];
+        uint32_t slowbits = 0;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const uint32_t pk = pin[j];
+            const FastEnt e = s_ent[fast_index(a, pk)];
+            const float w = __fmul_rn(e.v, min_[j]);
+            const float z1 = DET ? __fadd_rn(zin[j], __fmul_rn(w, half)) : __fmaf_rn(w, half, zin[j]);
+            const float z2 = DET ? __fadd_rn(z1, __fmul_rn(w, half)) : __fmaf_rn(w, half, z1);
+            // the motion is monotone within the step and the carrier starts
+            // inside its layer: the end point decides whether it meets a boundary
+            const bool slow = (z2 > e.hi) | (z2 < e.lo) | (xw[j] < e.P);
+            zo[j] = z2;          // an eventful carrier's final depth is written by k_event
+            slowbits |= (uint32_t)slow << j;
+            if (DEPN) {
+                int bin = -1;
+                const uint32_t k = pk & 0xFFu;
+                if (!slow && k != 0u) {
+                    const int sg = (int)((pk >> 8) & 1u);
+                    const int cu = __float_as_int(__fmaf_rd(z2, a.inv_dz, 8388608.0f)) - 0x4B000000;
+                    const int c1 = cu < nc - 1 ? cu : nc - 1;
+                    bin = (sg * ne + (int)k - 1) * nc + c1;
+                    atomicAdd(&s_gs[c1], (pk >> 13) & 0xFFu);
+                    if (vmom) atomicAdd(&s_v[sg * nc + c1], (unsigned long long)vel_q(w));
+                }
+                if (!WAGG && bin >= 0) atomicAdd(&s_n[bin], 1u);
+                if (WAGG) {
+                    const unsigned int m = __match_any_sync(0xffffffffu, bin);
+                    if (bin >= 0 && lane == __ffs(m) - 1) atomicAdd(&s_n[bin], (uint32_t)__popc(m));
+                }
+            }
+        }
+        // new depths (only slots below n_slots are written)
+        float *gZ = gZs + slot0 + i0;
+        if (i0 + G <= nvalid) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                reinterpret_cast<float4 *>(gZ)[c] =
+                    make_float4(zo[4 * c], zo[4 * c + 1], zo[4 * c + 2], zo[4 * c + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < G; ++j)
+                if (i0 + j < nvalid) gZ[j] = zo[j];
+        }
+        // queue the eventful carriers (record and position), in tile order:
+        // the warp's exclusive prefix of the per-thread counts (0..G) from
+        // ballots of their bits, one shared-counter reservation per warp
+        {
+            const uint32_t cnt = (uint32_t)__popc(slowbits);
+            constexpr int NB = G == 4 ? 3 : 4;       // bits of a count 0..G
+            unsigned int bal[NB];
+            int tot = 0;
+#pragma unroll
+            for (int q = 0; q < NB; ++q) {
+                bal[q] = __ballot_sync(0xffffffffu, (cnt >> q) & 1u);
+                tot += __popc(bal[q]) << q;
+            }
+            if (tot) {
+                int base = 0;
+                if (lane == 0) base = atomicAdd(&s_qn, tot);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                long long q = pos0 + base;
+#pragma unroll
+                for (int r = 0; r < NB; ++r) q += (long long)(__popc(bal[r] & lt_mask) << r);
+                n_queued += cnt;
+                const uint32_t rel = (uint32_t)((t - t0) * TILE) + (uint32_t)i0;
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    if ((slowbits >> j) & 1u) {
+                        a.qrec[q++] = make_float4(zin[j], min_[j], __uint_as_float(pin[j]),
+                                                  __uint_as_float(rel + (uint32_t)j));
+                    }
+                }
+            }
+        }
+    }
+    if (seg_stack >= 0) flush(seg_stack);
+    stream_sync<NW>();
+    if (tid == 0) a.qcnt[b] = (uint32_t)s_qn;
+}
+
+// ---------------------------------------------------------------------------
 // k_event: the general step for the queued (eventful) carriers.
 //
 // The queues of all streaming blocks, concatenated in tile order, are cut
@@ -917,11 +1267,15 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
     // pass 2: gradient bins of the lifetime and transmittance entries
     double *s_g = reinterpret_cast<double *>((reinterpret_cast<uintptr_t>(s_T + a.T_max) + 7) & ~uintptr_t(7));
     double *s_gT = s_g + (ADJ == 2 ? a.tab_max : 0);
+    // removals per (spin, cell) of this step (the births-minus-removals
+    // histogram the fluxes are derived from)
     int32_t *s_J = reinterpret_cast<int32_t *>(s_gT + (ADJ == 2 ? a.T_max : 0));
     uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + (ADJ ? 0 : a.jbin_max));
     uint32_t *s_gs = s_n + a.nbin_max;       // density steps: generation labels per cell
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN && !ADJ ? a.nbin_max + a.gbin_max : 0) + 1);
-    s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
+    // density steps: velocity sums per (spin, cell)
+    unsigned long long *s_v = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(s_n + (DEPN && !ADJ ? a.nbin_max + a.gbin_max : 0)) + 7) & ~uintptr_t(7));
+    long long *s_tpref = reinterpret_cast<long long *>(s_v + (DEPN && !ADJ ? 2 * a.gbin_max : 0)) + 1;
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     long long *s_qpre = s_nsl + a.n_stacks;      // queue prefix over the streaming blocks
     __shared__ float s_edge[PIC_MAX_LAYERS + 1];
@@ -935,6 +1289,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
     const int b = blockIdx.x, G = gridDim.x, Gf = a.grid_fast, tid = threadIdx.x;
     const int lane = tid & 31;
+    const bool vmom = DEPN && !ADJ && (a.flags & PIC_F_VELOCITY_MOMENTS);
     const long long T = make_tiles(a, s_tpref, s_nsl);
     const uint32_t step = step_now(a);
     const int tj = (int)(step / (uint32_t)a.moment_every);
@@ -987,10 +1342,10 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         const DevStack &st = s_st;
         const int nf = st.n_cells + 1;
         if (!ADJ) {
-            int32_t *gJ = a.J_hist + st.J_off + (long long)tj * 2 * nf;
+            int32_t *gB = a.bd_hist + st.J_off + (long long)tj * 2 * nf;
             for (int i = tid; i < 2 * nf; i += TPB) {
                 const int v = s_J[i];
-                if (v) atomicAdd(&gJ[i], v);
+                if (v) atomicAdd(&gB[i], v);
             }
         }
         if (ADJ == 2) {
@@ -1011,6 +1366,14 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
                 const uint32_t v = s_gs[i];
                 if (v) atomicAdd(&gG[i], (unsigned long long)v);
             }
+            if (vmom) {
+                unsigned long long *gV = reinterpret_cast<unsigned long long *>(a.v_hist) +
+                                         st.n_off / a.n_e + (long long)tout * 2 * st.n_cells;
+                for (int i = tid; i < 2 * st.n_cells; i += TPB) {
+                    const unsigned long long v = s_v[i];
+                    if (v) atomicAdd(&gV[i], v);
+                }
+            }
         }
         unsigned long long *L = a.cnt[s].led;
         const uint32_t vals[8] = {ty.absorbed, ty.bath, ty.hits, ty.trans, ty.trunc,
@@ -1021,6 +1384,8 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         for (int q = 0; q < 8; ++q) {
             const unsigned long long v = block_sum_u64(vals[q], s_r);
             if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
+            // removed carriers leave the live count
+            if (q == 0 && tid == 0 && v) atomicAdd(&a.cnt[s].live, 0ull - v);
         }
         ty = Tally{};
         __syncthreads();
@@ -1048,7 +1413,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         const uint32_t key_x = (uint32_t)slot;              // draws keyed by the slot
         TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
         float lo = S.edge[layer], hi = S.edge[layer + 1];
-        const int c_start = cell_of(a, S, z);
+        const int c_start = ADJ ? cell_of(a, S, z) : 0;     // the replay's flux reward
         // adjoint: the slot's reward sum; in pass 2 the reward-to-go R
         // that weights every decision of this step
         const long long R = ADJ ? a.acc[cur][gslot] : 0;
@@ -1120,17 +1485,19 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         if (dead) {
             pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
             const int c_end = cell_of(a, S, z);
-            if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
+            // a removal, where the carrier stopped
+            if (!ADJ) atomicAdd(&s_J[sg * (S.n_cells + 1) + c_end], -1);
             if (ADJ) rw = flux_w(a, s, tj, sg, c_start, c_end);
         } else {
             flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, key_x, S.ctr_hi,
                                   step, SUB_IF + 16, ty, Rd, s_gT);
             const int c_end = cell_of(a, S, z);
-            if (!ADJ && c_end != c_start) add_flux(s_J, S.n_cells + 1, sg, c_start, c_end);
             pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
             if (DEPN && !ADJ) {
                 atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
                 atomicAdd(&s_gs[c_end], (pk >> 13) & 0xFFu);
+                if (vmom)
+                    atomicAdd(&s_v[sg * S.n_cells + c_end], (unsigned long long)vel_q(__fmul_rn(e.v, mu)));
             }
             if (ADJ) {
                 rw = flux_w(a, s, tj, sg, c_start, c_end);
@@ -1159,6 +1526,8 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
             if (DEPN && !ADJ) {
                 for (int q = tid; q < 2 * a.n_e * s_st.n_cells; q += TPB) s_n[q] = 0u;
                 for (int q = tid; q < s_st.n_cells; q += TPB) s_gs[q] = 0u;
+                if (vmom)
+                    for (int q = tid; q < 2 * s_st.n_cells; q += TPB) s_v[q] = 0ull;
             }
             if (ADJ == 2) {
                 for (int q = tid; q < s_st.tab_n; q += TPB) s_g[q] = 0.0;
@@ -1203,11 +1572,15 @@ template <bool DET, bool DEPN, int ADJ = 0>
 __global__ void __launch_bounds__(TPB) k_place(const Args a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    // births per (spin, cell) of this step (the births-minus-removals
+    // histogram the fluxes are derived from)
     int32_t *s_J = reinterpret_cast<int32_t *>(smem);
     uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + (ADJ ? 0 : a.jbin_max));
     uint32_t *s_gs = s_n + a.nbin_max;       // density steps: generation labels per cell
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN && !ADJ ? a.nbin_max + a.gbin_max : 0) + 1);
-    s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
+    // density steps: velocity sums per (spin, cell)
+    unsigned long long *s_v = reinterpret_cast<unsigned long long *>(
+        (reinterpret_cast<uintptr_t>(s_n + (DEPN && !ADJ ? a.nbin_max + a.gbin_max : 0)) + 7) & ~uintptr_t(7));
+    long long *s_tpref = reinterpret_cast<long long *>(s_v + (DEPN && !ADJ ? 2 * a.gbin_max : 0)) + 1;
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     __shared__ int s_w[TPB / 32];
     __shared__ unsigned long long s_r[TPB / 32];
@@ -1217,6 +1590,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
     const unsigned int ep = *(volatile unsigned int *)&a.ctl->epoch;
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
     const int b = blockIdx.x, Gs = gridDim.x, Gf = a.grid_fast, tid = threadIdx.x;
+    const bool vmom = DEPN && !ADJ && (a.flags & PIC_F_VELOCITY_MOMENTS);
     const long long T = make_tiles(a, s_tpref, s_nsl);
     const int fb0 = (int)((long long)Gf * b / Gs), fb1 = (int)((long long)Gf * (b + 1) / Gs);
     const long long t0 = chunk_lo(T, fb0, Gf), t1 = chunk_lo(T, fb1, Gf);
@@ -1324,10 +1698,17 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
                         if (ADJ) {
                             place_adj(s, stg, w * 32 + j, d, id, pk, sg, k, c0, c1, r);
                         } else {
-                            if (c0 != c1) add_flux(s_J, nf, sg, c0, c1);
+                            // a birth, where the parent created it
+                            atomicAdd(&s_J[sg * nf + c0], 1);
                             if (DEPN) {
                                 atomicAdd(&s_n[(sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
                                 atomicAdd(&s_gs[c1], (pk >> 13) & 0xFFu);
+                                if (vmom) {
+                                    const int ls = (int)((pk >> 9) & 0xFu);
+                                    const float v = a.ent[stg.ent_off + (ls * 2 + sg) * a.n_e + (k - 1)].v;
+                                    atomicAdd(&s_v[sg * stg.n_cells + c1],
+                                              (unsigned long long)vel_q(__fmul_rn(v, r.y)));
+                                }
                             }
                         }
                     } else {
@@ -1352,10 +1733,10 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
         const DevStack &st = a.stacks[s];
         const int nf = st.n_cells + 1;
         if (!ADJ) {
-            int32_t *gJ = a.J_hist + st.J_off + (long long)tj * 2 * nf;
+            int32_t *gB = a.bd_hist + st.J_off + (long long)tj * 2 * nf;
             for (int i = tid; i < 2 * nf; i += TPB) {
                 const int v = s_J[i];
-                if (v) atomicAdd(&gJ[i], v);
+                if (v) atomicAdd(&gB[i], v);
             }
         }
         if (DEPN && !ADJ) {
@@ -1369,6 +1750,14 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             for (int i = tid; i < st.n_cells; i += TPB) {
                 const uint32_t v = s_gs[i];
                 if (v) atomicAdd(&gG[i], (unsigned long long)v);
+            }
+            if (vmom) {
+                unsigned long long *gV = reinterpret_cast<unsigned long long *>(a.v_hist) +
+                                         st.n_off / a.n_e + (long long)tout * 2 * st.n_cells;
+                for (int i = tid; i < 2 * st.n_cells; i += TPB) {
+                    const unsigned long long v = s_v[i];
+                    if (v) atomicAdd(&gV[i], v);
+                }
             }
         }
         unsigned long long *L = a.cnt[s].led;
@@ -1449,6 +1838,8 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             if (DEPN && !ADJ) {
                 for (int q = tid; q < 2 * a.n_e * nc; q += TPB) s_n[q] = 0u;
                 for (int q = tid; q < nc; q += TPB) s_gs[q] = 0u;
+                if (vmom)
+                    for (int q = tid; q < 2 * nc; q += TPB) s_v[q] = 0ull;
             }
             __syncthreads();
             const long long n = place(s, sg0, sg1, prefix);
@@ -1467,6 +1858,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             const long long kept = tot < room ? tot : (room > 0 ? room : 0);
             c.n_slots += (unsigned long long)kept;
             c.next_id += (unsigned long long)kept;
+            c.live += (unsigned long long)kept;
             c.spawn_total = 0;
         }
         if (tid == 0) {
@@ -1506,7 +1898,9 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
     }
     __syncthreads();
     const long long total = s_pref[a.n_stacks];
+    const int tj = (int)(step / (uint32_t)a.moment_every);
     const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
+    const bool vmom = !ADJ && deposit && (a.flags & PIC_F_VELOCITY_MOMENTS);
     for (long long gidx = (long long)blockIdx.x * TPB + tid; gidx < total;
          gidx += (long long)gridDim.x * TPB) {
         const int s = stack_of(s_pref, a.n_stacks, gidx);
@@ -1532,12 +1926,25 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
             k | (sg << 8) | (layer << 9) | (1u << 13) | ((uint32_t)(id >> 32) << 21));
         a.id[cur][d] = (uint32_t)id;
         atomicAdd(&s_q[s], (unsigned long long)k);
-        if (!ADJ && deposit) {
+        if (!ADJ) {
             Stk tmp; tmp.n_cells = st.n_cells;
             const int c = cell_of(a, tmp, z);
-            atomicAdd(&a.n_hist[st.n_off + (long long)tout * 2 * a.n_e * st.n_cells +
-                                (sg * a.n_e + (k - 1)) * st.n_cells + c], 1u);
-            atomicAdd(&a.g_hist[st.n_off / (2 * a.n_e) + (long long)tout * st.n_cells + c], 1ull);
+            // a birth (the births-minus-removals histogram of the window);
+            // the warp's carriers born in the same bin are added at once
+            const long long bi = st.J_off + ((long long)tj * 2 + sg) * (st.n_cells + 1) + c;
+            const unsigned int grp = __match_any_sync(__activemask(), (unsigned long long)bi);
+            if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&a.bd_hist[bi], __popc(grp));
+            if (deposit) {
+                atomicAdd(&a.n_hist[st.n_off + (long long)tout * 2 * a.n_e * st.n_cells +
+                                    (sg * a.n_e + (k - 1)) * st.n_cells + c], 1u);
+                atomicAdd(&a.g_hist[st.n_off / (2 * a.n_e) + (long long)tout * st.n_cells + c], 1ull);
+                if (vmom) {
+                    const float v = a.ent[st.ent_off + (layer * 2 + sg) * a.n_e + (k - 1)].v;
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.v_hist) + st.n_off / a.n_e +
+                                  ((long long)tout * 2 + sg) * st.n_cells + c,
+                              (unsigned long long)vel_q(__fmul_rn(v, mu_of(r1.x))));
+                }
+            }
         }
         if (ADJ) {
             // a new carrier: no parent (lineage depth 0, set when the replay
@@ -1565,6 +1972,7 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
             const long long kept = s_n[s];
             c.n_slots += (unsigned long long)kept;
             c.next_id += (unsigned long long)kept;
+            c.live += (unsigned long long)kept;
             c.led[L_INJECTED] += (unsigned long long)kept;
             c.led[L_INJECT_DROPPED] += (unsigned long long)(n - kept);
             if (n > kept && (a.flags & PIC_F_STRICT_CAPACITY))
@@ -1773,6 +2181,31 @@ static cudaError_t pick_ring(size_t fixed, int blocks_per_sm, int ring_req, int 
     return best < 0 ? cudaErrorInvalidConfiguration : cudaSuccess;
 }
 
+// Ring depth and resident blocks of k_stream for one variant, both builds
+// (with and without fused multiply-add) fitting: the most resident blocks per
+// SM such that at least three tiles per SM are in flight, then the deepest
+// ring (blocks_per_sm, ring_req: 0 = free).
+template <bool DEPN, bool WAGG, int NW>
+static cudaError_t pick_stream_ring(size_t fixed, int blocks_per_sm, int ring_req, int *ring,
+                                    int *blocks, size_t *smem)
+{
+    int best = -1;
+    for (int r = 2; r <= MAX_RING; ++r) {
+        if (ring_req > 0 && r != ring_req) continue;
+        const size_t sm = fixed + (size_t)r * 3 * TILE_BYTES;
+        int o1 = 0, o2 = 0;
+        cudaError_t e = occupancy(k_stream<false, DEPN, WAGG, NW>, sm, &o1, stream_threads<NW>());
+        if (e == cudaSuccess) e = occupancy(k_stream<true, DEPN, WAGG, NW>, sm, &o2, stream_threads<NW>());
+        if (e != cudaSuccess) return e;
+        int o = o1 < o2 ? o1 : o2;
+        if (blocks_per_sm > 0 && o > blocks_per_sm) o = blocks_per_sm;
+        if (o < 1) continue;
+        const int enough = o * (r - 1) >= 3 ? 1 : 0;
+        const int score = enough * 10000 + o * 100 + r;
+        if (score > best) { best = score; *ring = r; *blocks = o; *smem = sm; }
+    }
+    return best < 0 ? cudaErrorInvalidConfiguration : cudaSuccess;
+}
 template <bool DEPN, int ADJ = 0>
 static cudaError_t event_cfg(size_t sm, int *grid, int sms)
 {
@@ -1806,14 +2239,15 @@ inline size_t event_smem(const Args &a, bool dep, int adj, int gf_max)
     return (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.T_max * 4 + 8 +
            (adj == 2 ? (size_t)(a.tab_max + a.T_max) * 8 : 0) +
            (adj ? 0 : (size_t)a.jbin_max * 4) + (dep && !adj ? (size_t)(a.nbin_max + a.gbin_max) * 4 : 0) +
-           4 + tiles + (size_t)(gf_max + 1) * 8;
+           (dep && !adj ? (size_t)a.gbin_max * 16 : 0) + 16 + tiles + (size_t)(gf_max + 1) * 8;
 }
 
 inline size_t place_smem(const Args &a, bool dep, int adj)
 {
     const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;
     return (adj ? 0 : (size_t)a.jbin_max * 4) +
-           (dep && !adj ? (size_t)(a.nbin_max + a.gbin_max) * 4 : 0) + 4 + tiles;
+           (dep && !adj ? (size_t)(a.nbin_max + a.gbin_max) * 4 + (size_t)a.gbin_max * 16 : 0) + 16 +
+           tiles;
 }
 
 }  // namespace pic

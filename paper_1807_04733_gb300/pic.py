@@ -37,7 +37,7 @@ EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_gen_moments
            "pic_profile_read", "pic_compact_static", "pic_launch_config", "pic_launch_count",
            "pic_destroy", "pic_last_error", "pic_status_string", "pic_autotune")
 KERNEL_KINDS = ("inject", "step", "step_moments", "compact", "step_events", "adjoint_step",
-                "adjoint_events", "adjoint_other")
+                "adjoint_events", "adjoint_other", "flux")
 
 
 class pic_params(C.Structure):
@@ -46,7 +46,7 @@ class pic_params(C.Structure):
                 ("moment_every", C.c_int32), ("n_steps_max", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("hist_mode", C.c_int32),
                 ("ring_stages", C.c_int32), ("use_graph", C.c_int32),
-                ("stack_base", C.c_int32)]
+                ("stack_base", C.c_int32), ("consumer_warps", C.c_int32)]
 
 
 class pic_stack_desc(C.Structure):
@@ -79,6 +79,7 @@ class pic_launch_info(C.Structure):
                 ("grid_compact", C.c_int32), ("grid_inject", C.c_int32),
                 ("ring_step", C.c_int32), ("ring_step_moments", C.c_int32),
                 ("smem_step", C.c_int64), ("smem_step_moments", C.c_int64),
+                ("warps_step", C.c_int32), ("warps_step_moments", C.c_int32),
                 ("grid_adj_step", C.c_int32 * 2), ("ring_adj_step", C.c_int32 * 2),
                 ("smem_adj_step", C.c_int64 * 2)]
 
@@ -93,7 +94,7 @@ class pic_launch_info(C.Structure):
 class pic_tune_entry(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int32), ("ring_stages", C.c_int32),
                 ("hist_mode", C.c_int32), ("chosen", C.c_int32),
-                ("ns_per_particle_step", C.c_double)]
+                ("ns_per_particle_step", C.c_double), ("consumer_warps", C.c_int32)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if n.startswith("ns") else int(getattr(self, n)))
@@ -170,7 +171,7 @@ def _check(status, ctx=None):
 # marshalling of the workload description
 # ---------------------------------------------------------------------------
 def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hist_mode=0,
-                ring_stages=0, use_graph=0, stack_base=0):
+                ring_stages=0, use_graph=0, stack_base=0, consumer_warps=0):
     p = pic_params()
     p.n_e = wl.n_e; p.dt = wl.dt; p.dz = wl.dz
     p.seed = wl.seed if seed is None else seed
@@ -180,6 +181,7 @@ def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hi
     p.blocks_per_sm = blocks_per_sm; p.hist_mode = hist_mode; p.ring_stages = ring_stages
     p.use_graph = 1 if use_graph else 0
     p.stack_base = stack_base
+    p.consumer_warps = consumer_warps
     return p
 
 
@@ -351,13 +353,13 @@ class Context:
 
     def __init__(self, wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0,
                  hist_mode=0, stream=None, excite=True, capacity=None, ring_stages=0,
-                 use_graph=False, stack_base=0):
+                 use_graph=False, stack_base=0, consumer_warps=0):
         import torch
         self.wl = wl
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.params = make_params(wl, n_steps_max, flags, seed, blocks_per_sm, hist_mode,
-                                  ring_stages, use_graph, stack_base)
+                                  ring_stages, use_graph, stack_base, consumer_warps)
         self._tabs = [_Tables(st) for st in wl.stacks]
         self.stacks = [make_stack(st, capacity) for st in wl.stacks]
         self.ctx = pic_init(self.params, self.stacks, [t.c for t in self._tabs],

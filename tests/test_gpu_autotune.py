@@ -24,14 +24,19 @@ def test_autotune_keeps_results_and_picks_fastest():
     trials = tuned.autotune(6)
     assert len(trials) >= 4
     assert sum(t["chosen"] for t in trials) == 1
+    # both shapes of the streaming pass were timed: 8 consumer warps with 4
+    # slots per thread and 4 with 8
+    assert {t["consumer_warps"] for t in trials} == {4, 8}
     best = min(trials, key=lambda t: t["ns_per_particle_step"])
     assert best["chosen"] == 1
     info = tuned.launch_config()
     assert info["ring_step"] == best["ring_stages"]
+    assert info["warps_step"] == best["consumer_warps"]
     done = tuned.shape(0)[2]
+    end = max(900, done)
     plain.step(done - 100)
-    plain.step(900 - done)
-    tuned.step(900 - done)
+    plain.step(end - done)
+    tuned.step(end - done)
     n1, J1, l1 = plain.moments(0)
     n2, J2, l2 = tuned.moments(0)
     assert l1 == l2
