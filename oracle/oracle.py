@@ -53,6 +53,7 @@ class _Config(C.Structure):
         ("n0", C.c_int64), ("fwhm", C.c_double), ("t0", C.c_double),
         ("abs_len", C.c_double), ("excite_mask", C.c_uint32), ("up_frac", C.c_double),
         ("e_mode", C.c_int32), ("k_mono", C.c_int32 * 2),
+        ("cell_bias", C.POINTER(C.c_double)), ("e_bias", C.POINTER(C.c_double)),
     ]
 
 
@@ -83,6 +84,9 @@ def lib():
         L.or_moments.argtypes = [P, P, P, C.POINTER(Ledger)]
         L.or_gen_moments.argtypes = [P, P]
         L.or_vel_moments.argtypes = [P, P]
+        L.or_weighted_moments.argtypes = [P, P, P, P]
+        L.or_weights.argtypes = [P, P]
+        L.or_set_weights.argtypes = [P, P, C.c_int64]
         L.or_n_cells.argtypes = [P]; L.or_n_cells.restype = C.c_int32
         L.or_n_out.argtypes = [P]; L.or_n_out.restype = C.c_int32
         L.or_step_index.argtypes = [P]; L.or_step_index.restype = C.c_int32
@@ -142,6 +146,16 @@ class OracleSim:
         cfg.n0 = st.n0; cfg.fwhm = st.fwhm; cfg.t0 = st.t0; cfg.abs_len = st.abs_len
         cfg.excite_mask = st.excite_mask; cfg.up_frac = st.up_frac
         cfg.e_mode = st.e_mode; cfg.k_mono[0] = st.k_mono[0]; cfg.k_mono[1] = st.k_mono[1]
+        if getattr(st, "cell_bias", None) is not None:
+            cb = np.ascontiguousarray(st.cell_bias, np.float64)
+            assert cb.shape == (st.n_cells,)
+            self._keep.append(cb)
+            cfg.cell_bias = _ptr(cb, C.c_double)
+        if getattr(st, "e_bias", None) is not None:
+            eb = np.ascontiguousarray(st.e_bias, np.float64)
+            assert eb.shape == (wl.n_e,)
+            self._keep.append(eb)
+            cfg.e_bias = _ptr(eb, C.c_double)
         self.cfg = cfg
         h = C.c_void_p()
         rc = lib().or_create(C.byref(cfg), C.byref(h))
@@ -195,6 +209,29 @@ class OracleSim:
         v = np.zeros((self.n_out, 2, self.n_cells), np.int64)
         lib().or_vel_moments(self.h, v.ctypes.data)
         return v
+
+    def weighted_moments(self):
+        """Superparticle weights (FLAG_WEIGHTS; Eq. PIC): the densities
+        [n_out][2][n_e][n_cells] (uint64) and fluxes [n_out][2][n_cells+1]
+        (int64) with every carrier counted with its weight, in units of
+        2^-20, and the summed weight of the carriers the source created."""
+        nw = np.zeros((self.n_out, 2, self.wl.n_e, self.n_cells), np.uint64)
+        Jw = np.zeros((self.n_out, 2, self.n_cells + 1), np.int64)
+        wi = np.zeros(1, np.uint64)
+        lib().or_weighted_moments(self.h, nw.ctypes.data, Jw.ctypes.data, wi.ctypes.data)
+        return nw, Jw, int(wi[0])
+
+    def weights(self) -> np.ndarray:
+        n = lib().or_n_slots(self.h)
+        w = np.zeros(n, np.uint32)
+        if n:
+            lib().or_weights(self.h, w.ctypes.data)
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, np.uint32)
+        if lib().or_set_weights(self.h, w.ctypes.data, len(w)):
+            raise ValueError("set_weights: one weight per slot, each > 0")
 
     def gen_moments(self) -> np.ndarray:
         """Generation labels summed per [output time][cell] at the density

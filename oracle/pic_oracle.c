@@ -123,6 +123,11 @@ struct or_sim {
     int64_t *inj;                 /* per half step */
     /* particles */
     or_rec *recs; int64_t n_slots; uint64_t next_id; uint32_t step;
+    /* superparticle weights (OR_F_WEIGHTS), units of 2^-20 per slot, and
+     * the importance-sampling ratios p/q of the source: per entry of the
+     * birth-cell table and per bin */
+    uint32_t *wq; double *wcell, *wbin; uint32_t *kthr; int has_ebias;
+    uint64_t *nhw; int64_t *Jhw; uint64_t w_injected;
     /* moments */
     int32_t n_out; uint32_t *nh; int32_t *Jh;
     uint64_t *gh;                 /* generation label summed per (output time, cell) */
@@ -204,12 +209,15 @@ static int32_t cell_of(const or_sim *s, float z)
 
 static int idx3(const or_sim *s, int m, int sg, int k) { return (m * 2 + sg) * s->cfg.n_e + (k - 1); }
 
-/* net flux through the cell faces between the start cell a and end cell b */
-static void flux(or_sim *s, int sg, int a, int b)
+/* net flux through the cell faces between the start cell a and end cell b
+ * of a carrier of weight w (2^-20 units; the weighted flux counts it w times) */
+static void flux(or_sim *s, int sg, int a, int b, uint32_t w)
 {
-    int32_t *J = s->Jh + ((int64_t)(s->step / s->cfg.moment_every) * 2 + sg) * (s->n_cells + 1);
-    if (b > a) for (int f = a + 1; f <= b; ++f) J[f] += 1;
-    else       for (int f = b + 1; f <= a; ++f) J[f] -= 1;
+    int64_t row = ((int64_t)(s->step / s->cfg.moment_every) * 2 + sg) * (s->n_cells + 1);
+    int32_t *J = s->Jh + row;
+    int64_t *Jw = s->Jhw + row;
+    if (b > a) for (int f = a + 1; f <= b; ++f) { J[f] += 1; Jw[f] += w; }
+    else       for (int f = b + 1; f <= a; ++f) { J[f] -= 1; Jw[f] -= w; }
 }
 
 /* ---- adjoint bookkeeping (used only when s->adj is set) ---- */
@@ -317,9 +325,10 @@ static int half_flight(or_sim *s, or_rec *p, float tau, uint64_t key, uint32_t s
     return met;
 }
 
-static int append(or_sim *s, or_rec r)
+static int append(or_sim *s, or_rec r, uint32_t w)
 {
     if (s->n_slots >= s->cfg.capacity) return 0;
+    s->wq[s->n_slots] = w;
     s->recs[s->n_slots++] = r;
     return 1;
 }
@@ -345,13 +354,26 @@ static void inject(or_sim *s, int half)
         while (i < s->n_cdf - 1 && !(a[0] < s->cdf_thr[i])) ++i;
         float z = ((float)s->cdf_cell[i] + unit_from(a[1])) * c->dz;
         uint32_t sg = a[2] < s->up_thr ? 0u : 1u;
-        uint32_t k = c->e_mode == 1 ? (uint32_t)c->k_mono[sg] : 1u + below(a[3], (uint32_t)c->n_e);
+        uint32_t k;
+        if (c->e_mode == 1) {
+            k = (uint32_t)c->k_mono[sg];
+        } else if (s->has_ebias) {
+            /* the bin from the biased sampling distribution q */
+            k = 1u;
+            while ((int)k < c->n_e && !(a[3] < s->kthr[k - 1])) ++k;
+        } else {
+            k = 1u + below(a[3], (uint32_t)c->n_e);
+        }
+        /* weight p/q of the carrier's birth cell and bin (Eq. PIC) */
+        double wr = s->wcell[i] * s->wbin[k - 1] * 1048576.0;
+        uint32_t w = wr < 1.0 ? 1u : wr > 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)nearbyint(wr);
         or_rec r;
         r.z = z;
         r.mu = mu_from(b[0]);
         r.id = (uint32_t)id;
         r.packed = pk(k, sg, (uint32_t)s->cdf_layer[i], 1u, (uint32_t)(id >> 32));
-        append(s, r);
+        append(s, r, w);
+        s->w_injected += w;
         s->led.injected++;
         s->led.q_injected += k;
     }
@@ -366,7 +388,7 @@ static void absorb(or_sim *s, or_rec *p)
 
 /* Transport(dt/2) -> Scattering(dt) -> Transport(dt/2) of the live carrier
  * p that sits in slot i; a secondary is appended to the slots. */
-static void advance(or_sim *s, or_rec *p, int64_t i)
+static void advance(or_sim *s, or_rec *p, int64_t i, uint32_t w)
 {
     const or_config *c = &s->cfg;
     const float half = c->dt * 0.5f;
@@ -410,7 +432,7 @@ static void advance(or_sim *s, or_rec *p, int64_t i)
             int inel = x[1] < s->Q_thr[t];
             if (k == 1 && (inel || (c->flags & OR_F_LOWEST_BIN_ANY))) {
                 absorb(s, p);
-                flux(s, sg, c_start, cell_of(s, p->z));
+                flux(s, sg, c_start, cell_of(s, p->z), w);
                 if (A) credit(s, id, flux_reward(s, sg, c_start, cell_of(s, p->z)));
                 s->led.changed++;
                 return;
@@ -445,9 +467,10 @@ static void advance(or_sim *s, or_rec *p, int64_t i)
                         uint64_t nid = s->next_id++;
                         q.id = (uint32_t)nid;
                         q.packed |= (uint32_t)(nid >> 32) << 21;
-                        append(s, q);
+                        /* the secondary carries its parent's weight */
+                        append(s, q, w);
                         s->led.spawned++;
-                        flux(s, (int)sgs, cs, cell_of(s, q.z));
+                        flux(s, (int)sgs, cs, cell_of(s, q.z), w);
                         if (A) {
                             adj_grow(s, s->next_id);
                             if (A->pass == 1) {
@@ -480,7 +503,7 @@ static void advance(or_sim *s, or_rec *p, int64_t i)
 
         const int met2 = half_flight(s, p, half, (uint64_t)i, SUB_IF + 16);
         if (met2 && !met1 && !(x[0] < s->P_thr[t])) s->led.eventful++;
-        flux(s, sg, c_start, cell_of(s, p->z));
+        flux(s, sg, c_start, cell_of(s, p->z), w);
         if (A) credit(s, id, flux_reward(s, sg, c_start, cell_of(s, p->z)));
         if (p->mu != mu_in || p->packed != pk_in) s->led.changed++;
     }
@@ -494,7 +517,7 @@ static void step_once(or_sim *s)
     for (int64_t i = 0; i < n_start; ++i) {
         or_rec *p = &s->recs[i];
         if (PK_K(p->packed) == 0) continue;
-        advance(s, p, i);
+        advance(s, p, i, s->wq[i]);
     }
     inject(s, 1);
 
@@ -507,6 +530,7 @@ static void step_once(or_sim *s)
             int64_t b = ((tout * 2 + PK_S(p->packed)) * c->n_e + (k - 1)) * s->n_cells
                         + cell_of(s, p->z);
             s->nh[b] += 1;
+            s->nhw[b] += s->wq[i];
             s->gh[tout * s->n_cells + cell_of(s, p->z)] += PK_G(p->packed);
             if (c->flags & OR_F_VELOCITY) {
                 /* the carrier's velocity along z, v(layer material, spin, k) * mu,
@@ -523,7 +547,10 @@ static void step_once(or_sim *s)
     if ((s->step + 1) % (uint32_t)c->compact_every == 0) {
         int64_t j = 0;
         for (int64_t i = 0; i < s->n_slots; ++i)
-            if (PK_K(s->recs[i].packed) != 0) s->recs[j++] = s->recs[i];
+            if (PK_K(s->recs[i].packed) != 0) {
+                s->wq[j] = s->wq[i];
+                s->recs[j++] = s->recs[i];
+            }
         s->n_slots = j;
     }
     s->step++;
@@ -575,11 +602,38 @@ static void derive(or_sim *s)
     }
     s->n_cdf = n;
     double cum = 0.0;
-    for (int i = 0; i < n; ++i) {
-        cum += mass[i];
-        s->cdf_thr[i] = (i == n - 1) ? 0xFFFFFFFFu : to_thr(cum / total);
+    if (c->cell_bias && (c->flags & OR_F_WEIGHTS)) {
+        /* importance sampling of the birth cell: q_i proportional to
+         * mass_i * bias_i, weight p_i / q_i = (sum mass*bias / sum mass) / bias_i */
+        double total_b = 0.0;
+        for (int i = 0; i < n; ++i) total_b += mass[i] * c->cell_bias[s->cdf_cell[i]];
+        for (int i = 0; i < n; ++i) {
+            cum += mass[i] * c->cell_bias[s->cdf_cell[i]];
+            s->cdf_thr[i] = (i == n - 1) ? 0xFFFFFFFFu : to_thr(cum / total_b);
+            s->wcell[i] = (total_b / total) / c->cell_bias[s->cdf_cell[i]];
+        }
+    } else {
+        for (int i = 0; i < n; ++i) {
+            cum += mass[i];
+            s->cdf_thr[i] = (i == n - 1) ? 0xFFFFFFFFu : to_thr(cum / total);
+            s->wcell[i] = 1.0;
+        }
     }
     free(mass);
+    /* importance sampling of the birth bin (e_mode 0): q_k proportional to
+     * bias_k, weight p_k / q_k = (sum bias / n_e) / bias_k */
+    s->has_ebias = c->e_bias && (c->flags & OR_F_WEIGHTS) && c->e_mode == 0;
+    if (s->has_ebias) {
+        double tb = 0.0, cb = 0.0;
+        for (int k = 0; k < ne; ++k) tb += c->e_bias[k];
+        for (int k = 0; k < ne; ++k) {
+            cb += c->e_bias[k];
+            s->kthr[k] = (k == ne - 1) ? 0xFFFFFFFFu : to_thr(cb / tb);
+            s->wbin[k] = (tb / (double)ne) / c->e_bias[k];
+        }
+    } else {
+        for (int k = 0; k < ne; ++k) s->wbin[k] = 1.0;
+    }
 
     /* injected carriers per half step: floor(N0 F(t_{h+1})) - floor(N0 F(t_h)) */
     int64_t nh = 2 * (int64_t)c->n_steps_max;
@@ -627,15 +681,24 @@ int or_create(const or_config *cfg, or_sim **out)
     s->cdf_layer = (int32_t *)malloc(sizeof(int32_t) * cells);
     s->cdf_thr = (uint32_t *)malloc(sizeof(uint32_t) * cells);
     s->inj = (int64_t *)calloc((size_t)(2 * (int64_t)cfg->n_steps_max + 1), sizeof(int64_t));
+    s->wcell = (double *)malloc(sizeof(double) * (size_t)(cells > 0 ? cells : 1));
+    s->wbin = (double *)malloc(sizeof(double) * (size_t)ne);
+    s->kthr = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)ne);
     derive(s);
 
     s->recs = (or_rec *)malloc(sizeof(or_rec) * (size_t)(cfg->capacity > 0 ? cfg->capacity : 1));
+    s->wq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(cfg->capacity > 0 ? cfg->capacity : 1));
     s->n_out = (cfg->n_steps_max + cfg->moment_every - 1) / cfg->moment_every;
     s->nh = (uint32_t *)calloc((size_t)s->n_out * 2 * ne * cells + 1, sizeof(uint32_t));
     s->Jh = (int32_t *)calloc((size_t)s->n_out * 2 * (cells + 1) + 1, sizeof(int32_t));
     s->gh = (uint64_t *)calloc((size_t)s->n_out * cells + 1, sizeof(uint64_t));
     s->vh = (int64_t *)calloc((size_t)s->n_out * 2 * cells + 1, sizeof(int64_t));
-    if (!s->recs || !s->nh || !s->Jh || !s->gh || !s->vh) { or_destroy(s); return 4; }
+    s->nhw = (uint64_t *)calloc((size_t)s->n_out * 2 * ne * cells + 1, sizeof(uint64_t));
+    s->Jhw = (int64_t *)calloc((size_t)s->n_out * 2 * (cells + 1) + 1, sizeof(int64_t));
+    if (!s->recs || !s->wq || !s->nh || !s->Jh || !s->gh || !s->vh || !s->nhw || !s->Jhw) {
+        or_destroy(s);
+        return 4;
+    }
     *out = s;
     return 0;
 }
@@ -647,6 +710,7 @@ void or_destroy(or_sim *s)
     free(s->P_thr); free(s->Q_thr); free(s->T_thr); free(s->P0_thr);
     free(s->cdf_cell); free(s->cdf_layer); free(s->cdf_thr); free(s->inj);
     free(s->recs); free(s->nh); free(s->Jh); free(s->gh); free(s->vh);
+    free(s->wq); free(s->wcell); free(s->wbin); free(s->kthr); free(s->nhw); free(s->Jhw);
     free(s);
 }
 
@@ -666,6 +730,7 @@ int or_set_records(or_sim *s, const or_rec *in, int64_t n, uint64_t next_id)
 {
     if (n < 0 || n > s->cfg.capacity) return 1;
     memcpy(s->recs, in, sizeof(or_rec) * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) s->wq[i] = 1u << 20;     /* unit weight */
     s->n_slots = n;
     s->next_id = next_id;
     return 0;
@@ -697,6 +762,26 @@ void or_gen_moments(const or_sim *s, uint64_t *g_out)
 void or_vel_moments(const or_sim *s, int64_t *v_out)
 {
     if (v_out) memcpy(v_out, s->vh, sizeof(int64_t) * (size_t)s->n_out * 2 * s->n_cells);
+}
+
+void or_weighted_moments(const or_sim *s, uint64_t *nw_out, int64_t *Jw_out, uint64_t *w_injected)
+{
+    if (nw_out) memcpy(nw_out, s->nhw, sizeof(uint64_t) * (size_t)s->n_out * 2 * s->cfg.n_e * s->n_cells);
+    if (Jw_out) memcpy(Jw_out, s->Jhw, sizeof(int64_t) * (size_t)s->n_out * 2 * (s->n_cells + 1));
+    if (w_injected) *w_injected = s->w_injected;
+}
+
+void or_weights(const or_sim *s, uint32_t *w_out)
+{
+    memcpy(w_out, s->wq, sizeof(uint32_t) * (size_t)s->n_slots);
+}
+
+int or_set_weights(or_sim *s, const uint32_t *w, int64_t n)
+{
+    if (n != s->n_slots) return 1;
+    for (int64_t i = 0; i < n; ++i) if (w[i] == 0u) return 1;
+    memcpy(s->wq, w, sizeof(uint32_t) * (size_t)n);
+    return 0;
 }
 
 void or_tables(const or_sim *s, uint32_t *P_thr, uint32_t *Q_thr, uint32_t *T_thr,
@@ -818,7 +903,7 @@ int or_advance_one(or_sim *s, const or_rec *in, int64_t slot, int room, or_rec *
     s->cfg.capacity = room ? 1 : 0;
     int made = 0;
     if (PK_K(p.packed) != 0) {
-        advance(s, &p, slot);
+        advance(s, &p, slot, 1u << 20);
         made = s->n_slots == 1;
         if (made && sec) *sec = s->recs[0];
     }

@@ -32,6 +32,7 @@ extern "C" {
 #define OR_F_LOWEST_BIN_ANY  8u
 #define OR_F_STRICT_CAPACITY 16u
 #define OR_F_VELOCITY        32u  /* also sum the velocities v*mu per (time, spin, cell) */
+#define OR_F_WEIGHTS         64u  /* superparticle weights w_i of Eq. PIC (Sec. III.A) */
 
 typedef struct {
     float z;          /* depth, nm */
@@ -63,6 +64,11 @@ typedef struct {
     double up_frac;
     int32_t e_mode;
     int32_t k_mono[2];
+    /* importance sampling of the source (OR_F_WEIGHTS): relative sampling
+     * densities of the birth cell ([n_cells] of the stack; only excited
+     * cells matter) and of the birth bin ([n_e], e_mode 0); NULL = none */
+    const double *cell_bias;
+    const double *e_bias;
 } or_config;
 
 typedef struct {
@@ -86,6 +92,13 @@ void or_moments(const or_sim *s, uint32_t *n_out, int32_t *J_out, or_ledger *led
 void or_gen_moments(const or_sim *s, uint64_t *g_out);
 /* velocity moment per [n_out][2][n_cells] (OR_F_VELOCITY; Eq. spincurrent) */
 void or_vel_moments(const or_sim *s, int64_t *v_out);
+/* Superparticle weights (OR_F_WEIGHTS; Eq. PIC, Sec. III.A), in units of
+ * 2^-20: the weighted densities [n_out][2][n_e][n_cells] and fluxes
+ * [n_out][2][n_cells+1] (the counts with every carrier counted w times),
+ * and the summed weight of the carriers the source created. */
+void or_weighted_moments(const or_sim *s, uint64_t *nw_out, int64_t *Jw_out, uint64_t *w_injected);
+void or_weights(const or_sim *s, uint32_t *w_out);                 /* n_slots weights */
+int  or_set_weights(or_sim *s, const uint32_t *w, int64_t n);     /* after or_set_records */
 int32_t or_n_cells(const or_sim *s);
 int32_t or_n_out(const or_sim *s);
 int32_t or_step_index(const or_sim *s);

@@ -930,8 +930,14 @@ k_fast(const Args a)
 // resident blocks per SM the register budget must allow: four of 288
 // threads (eight consumer warps, 56 registers) or five of 160 (four consumer
 // warps with eight slots per thread, 80 registers)
+#ifndef PIC_STREAM_MIN_BLOCKS_8
+#define PIC_STREAM_MIN_BLOCKS_8 4
+#endif
+#ifndef PIC_STREAM_MIN_BLOCKS_4
+#define PIC_STREAM_MIN_BLOCKS_4 5
+#endif
 template <int NW>
-constexpr int stream_min_blocks() { return NW == 8 ? 4 : 5; }
+constexpr int stream_min_blocks() { return NW == 8 ? PIC_STREAM_MIN_BLOCKS_8 : PIC_STREAM_MIN_BLOCKS_4; }
 
 template <int NW>
 __device__ __forceinline__ void stream_sync()

@@ -44,6 +44,7 @@ FLAG_TRANSPARENT = 4        # Sec. V.A variant (2): T == 1 at every interface
 FLAG_LOWEST_BIN_ANY = 8     # remove a lowest-bin carrier on ANY scattering event
 FLAG_STRICT_CAPACITY = 16   # capacity overflow is an error instead of drop-and-count
 FLAG_VELOCITY = 32          # also sum the velocities v*mu per (time, spin, cell)
+FLAG_WEIGHTS = 64           # superparticle weights w_i (importance-sampled source)
 
 E_UNIFORM = 0               # injected energy uniform over the N_E bins
 E_MONO = 1                  # injected energy fixed per spin (k_mono[spin])
@@ -76,6 +77,11 @@ class Stack:
     up_frac: float = 2.0 / 3.0  # fraction of injected carriers with spin up
     e_mode: int = E_UNIFORM
     k_mono: tuple = (1, 1)      # bins for E_MONO (spin up, spin down)
+    # importance sampling of the source (FLAG_WEIGHTS): relative sampling
+    # densities of the birth cell (float64 [n_cells]) and of the birth bin
+    # (float64 [n_e], E_UNIFORM only); None = sample the physical profile
+    cell_bias: np.ndarray = None
+    e_bias: np.ndarray = None
 
     @property
     def n_cells(self) -> int:
