@@ -64,6 +64,12 @@ typedef enum {
                                      drop-and-count */
 #define PIC_F_VELOCITY_MOMENTS 32u /* also sum the carriers' velocities along z
                                       per (time, spin, cell): pic_vel_moments */
+#define PIC_F_WEIGHTS         64u /* superparticle weights w_i of Eq. PIC
+                                     (Sec. III.A): every carrier carries a
+                                     weight, set at birth by importance
+                                     sampling of the source (pic_pulse
+                                     cell_bias, e_bias) and inherited by its
+                                     secondaries; pic_weighted_moments */
 
 /* Global parameters of a context. */
 typedef struct {
@@ -154,6 +160,15 @@ typedef struct {
     double up_frac;         /* probability that a created carrier is spin up */
     int32_t e_mode;         /* 0: k uniform on 1..n_e; 1: k = k_mono[spin] */
     int32_t k_mono[2];      /* bins for e_mode 1 */
+    /* Importance sampling of the births (PIC_F_WEIGHTS only; host, copied,
+     * may be NULL): relative sampling densities of the birth cell
+     * (cell_bias[n_cells] of the stack, > 0 on excited cells) and of the
+     * birth bin (e_bias[n_e], > 0, e_mode 0).  A carrier is drawn from
+     * q proportional to p * bias instead of the physical profile p and
+     * carries the weight p/q (Eq. PIC: "adjusted to improve the
+     * representation of less likely events"); NULL = q = p, weight 1. */
+    const double *cell_bias;
+    const double *e_bias;
 } pic_pulse;
 
 /* Device-resident bookkeeping, per stack (exact integer counts). */
@@ -176,8 +191,9 @@ typedef struct {
  * 3 = compaction, 4 = step (event pass and placement of secondaries);
  * pic_grad's replays: 5 = streaming pass, 6 = event pass, 7 = the rest
  * (source, compaction, flux potential, flush, lineage totals);
- * 8 = the fluxes derived by pic_moments. */
-#define PIC_KERNEL_KINDS 9
+ * 8 = the fluxes derived by pic_moments and pic_weighted_moments;
+ * 9 = the weighted densities (PIC_F_WEIGHTS). */
+#define PIC_KERNEL_KINDS 10
 typedef struct {
     int64_t launches[PIC_KERNEL_KINDS];
     double ms[PIC_KERNEL_KINDS];
@@ -253,6 +269,28 @@ pic_status pic_gen_moments(pic_ctx *ctx, int stack, uint64_t *g_dev);
  * spin-current density of cell c in carriers nm/fs per nm.  Asynchronous on
  * the context stream; PIC_ERR_ARG for a bad stack or a NULL v_dev. */
 pic_status pic_vel_moments(pic_ctx *ctx, int stack, int64_t *v_dev);
+
+/* Weighted moments of one stack (PIC_F_WEIGHTS; Eq. PIC, Sec. III.A): the
+ * densities and fluxes of pic_moments with every carrier counted with its
+ * weight w_i, in units of 2^-20 (weights are kept as integers of that unit,
+ * so the sums are exact).  nw_dev (device, may be NULL): uint64
+ * [n_out][2][n_e][n_cells]; Jw_dev (device, may be NULL): int64
+ * [n_out][2][n_cells+1]; w_injected_host (host, may be NULL): the summed
+ * weight of the carriers the source has created, the denominator of the
+ * normalisation C = rho_exc / sum w_i.  Synchronises; PIC_ERR_ARG for a
+ * context made without PIC_F_WEIGHTS or a bad stack. */
+pic_status pic_weighted_moments(pic_ctx *ctx, int stack, uint64_t *nw_dev, int64_t *Jw_dev,
+                                uint64_t *w_injected_host);
+
+/* The weights (2^-20 units) of one stack's slots, in slot order (PIC_F_WEIGHTS).
+ * host_out NULL: only the count is written to *n.  Synchronises. */
+pic_status pic_weights(pic_ctx *ctx, int stack, uint32_t *host_out, int64_t *n);
+
+/* Replace the weights of one stack's slots (PIC_F_WEIGHTS), n = the slot
+ * count, every weight > 0; pic_set_records gives loaded carriers weight 1
+ * (2^20).  For the weighted fluxes of the running window the carriers count
+ * as removed with their old weights and created with the new ones. */
+pic_status pic_set_weights(pic_ctx *ctx, int stack, const uint32_t *host_in, int64_t n);
 
 /* Score-function (likelihood-ratio) gradient of a linear functional of the
  * moments with respect to the lifetime and transmittance tables of every

@@ -127,6 +127,7 @@ struct or_sim {
      * the importance-sampling ratios p/q of the source: per entry of the
      * birth-cell table and per bin */
     uint32_t *wq; double *wcell, *wbin; uint32_t *kthr; int has_ebias;
+    uint64_t *lkey;               /* OR_F_LINEAGE_KEYS: the random-stream key per slot */
     uint64_t *nhw; int64_t *Jhw; uint64_t w_injected;
     /* moments */
     int32_t n_out; uint32_t *nh; int32_t *Jh;
@@ -185,6 +186,34 @@ static void draw(const or_sim *s, uint64_t x, uint32_t step, uint32_t sub, uint3
                         step, sub };
     uint32_t key[2] = { (uint32_t)s->cfg.seed, (uint32_t)(s->cfg.seed >> 32) };
     or_philox4x32_10(ctr, key, r);
+}
+
+/* Philox words of counter (key low, key high, step, substream): the draws
+ * of a carrier with lineage key `key` (OR_F_LINEAGE_KEYS) */
+static void draw_lineage(const or_sim *s, uint64_t key, uint32_t step, uint32_t sub, uint32_t r[4])
+{
+    uint32_t ctr[4] = { (uint32_t)key, (uint32_t)(key >> 32), step, sub };
+    uint32_t k2[2] = { (uint32_t)s->cfg.seed, (uint32_t)(s->cfg.seed >> 32) };
+    or_philox4x32_10(ctr, k2, r);
+}
+
+/* the draws of the carrier whose draw key is dk: its slot, or with
+ * OR_F_LINEAGE_KEYS its lineage key */
+static void draw_x(const or_sim *s, uint64_t dk, uint32_t step, uint32_t sub, uint32_t r[4])
+{
+    if (s->cfg.flags & OR_F_LINEAGE_KEYS) draw_lineage(s, dk, step, sub, r);
+    else draw(s, dk, step, sub, r);
+}
+
+/* the lineage key of a secondary created at `step` by the carrier with
+ * key `parent`: a Philox hash of both (the top two bits are the tags of
+ * primaries and loaded carriers) */
+static uint64_t child_key(uint64_t parent, uint32_t step)
+{
+    uint32_t ctr[4] = { (uint32_t)parent, (uint32_t)(parent >> 32), step, 0xC0DEu };
+    uint32_t k2[2] = { 0x2545F491u, 0x4F6CDD1Du }, r[4];
+    or_philox4x32_10(ctr, k2, r);
+    return (((uint64_t)r[1] << 32) | r[0]) & ~(3ull << 62);
 }
 
 /* word of the scattering test of the carrier in slot i at this step: word
@@ -312,7 +341,7 @@ static int half_flight(or_sim *s, or_rec *p, float tau, uint64_t key, uint32_t s
             s->led.iface_hits++;
             if (!(c->flags & OR_F_TRANSPARENT)) {
                 uint32_t r[4];
-                draw(s, key, s->step, sub0 + (uint32_t)hit, r);
+                draw_x(s, key, s->step, sub0 + (uint32_t)hit, r);
                 int te = ((iface * 2 + dir) * 2 + sg) * c->n_e + (k - 1);
                 trans = r[0] < s->T_thr[te];
                 if (s->adj) add_score(s, 1, te, trans ? s->adj->s_tr[te] : s->adj->s_rf[te]);
@@ -325,10 +354,11 @@ static int half_flight(or_sim *s, or_rec *p, float tau, uint64_t key, uint32_t s
     return met;
 }
 
-static int append(or_sim *s, or_rec r, uint32_t w)
+static int append(or_sim *s, or_rec r, uint32_t w, uint64_t lk)
 {
     if (s->n_slots >= s->cfg.capacity) return 0;
     s->wq[s->n_slots] = w;
+    s->lkey[s->n_slots] = lk;
     s->recs[s->n_slots++] = r;
     return 1;
 }
@@ -348,8 +378,15 @@ static void inject(or_sim *s, int half)
         uint64_t id = s->next_id++;
         if (s->adj) adj_grow(s, s->next_id);
         uint32_t a[4], b[4];
-        draw(s, id, s->step, SUB_INJ + 0, a);
-        draw(s, id, s->step, SUB_INJ + 1, b);
+        /* lineage key of a primary: its birth half step and index */
+        const uint64_t lk = (1ull << 63) | ((uint64_t)h << 32) | (uint64_t)j;
+        if (c->flags & OR_F_LINEAGE_KEYS) {
+            draw_lineage(s, lk, s->step, SUB_INJ + 0, a);
+            draw_lineage(s, lk, s->step, SUB_INJ + 1, b);
+        } else {
+            draw(s, id, s->step, SUB_INJ + 0, a);
+            draw(s, id, s->step, SUB_INJ + 1, b);
+        }
         int i = 0;
         while (i < s->n_cdf - 1 && !(a[0] < s->cdf_thr[i])) ++i;
         float z = ((float)s->cdf_cell[i] + unit_from(a[1])) * c->dz;
@@ -372,7 +409,7 @@ static void inject(or_sim *s, int half)
         r.mu = mu_from(b[0]);
         r.id = (uint32_t)id;
         r.packed = pk(k, sg, (uint32_t)s->cdf_layer[i], 1u, (uint32_t)(id >> 32));
-        append(s, r, w);
+        append(s, r, w, lk);
         s->w_injected += w;
         s->led.injected++;
         s->led.q_injected += k;
@@ -388,7 +425,7 @@ static void absorb(or_sim *s, or_rec *p)
 
 /* Transport(dt/2) -> Scattering(dt) -> Transport(dt/2) of the live carrier
  * p that sits in slot i; a secondary is appended to the slots. */
-static void advance(or_sim *s, or_rec *p, int64_t i, uint32_t w)
+static void advance(or_sim *s, or_rec *p, int64_t i, uint32_t w, uint64_t dk)
 {
     const or_config *c = &s->cfg;
     const float half = c->dt * 0.5f;
@@ -407,14 +444,21 @@ static void advance(or_sim *s, or_rec *p, int64_t i, uint32_t w)
             A->Rmag = fabs(A->own[id]) + fabs(A->acc[id]);
         }
 
-        const int met1 = half_flight(s, p, half, (uint64_t)i, SUB_IF + 0);
+        const int met1 = half_flight(s, p, half, dk, SUB_IF + 0);
 
         /* Scattering(dt): one Monte-Carlo test against tau_eff (Eq. lifetimes);
          * the event words are drawn only for a carrier that scatters */
-        uint32_t x[4] = { test_word(s, i), 0u, 0u, 0u };
+        uint32_t x[4] = { 0u, 0u, 0u, 0u };
+        if (c->flags & OR_F_LINEAGE_KEYS) {
+            uint32_t tw[4];
+            draw_lineage(s, dk, s->step, SUB_TEST, tw);
+            x[0] = tw[0];
+        } else {
+            x[0] = test_word(s, i);
+        }
         if (x[0] < s->P_thr[idx3(s, c->layer_mat[PK_L(p->packed)], sg, (int)PK_K(p->packed))]) {
             uint32_t ev[4];
-            draw(s, (uint64_t)i, s->step, SUB_EVT, ev);
+            draw_x(s, dk, s->step, SUB_EVT, ev);
             x[1] = ev[1]; x[2] = ev[2]; x[3] = ev[3];
         }
         int k = (int)PK_K(p->packed), layer = (int)PK_L(p->packed);
@@ -448,7 +492,7 @@ static void advance(or_sim *s, or_rec *p, int64_t i, uint32_t w)
                     /* secondary: same place, spin from P0 of this material,
                      * isotropic direction, one generation more */
                     uint32_t y[4];
-                    draw(s, (uint64_t)i, s->step, SUB_SEC, y);
+                    draw_x(s, dk, s->step, SUB_SEC, y);
                     uint32_t g = PK_G(p->packed);
                     uint32_t sgs = y[0] < s->P0_thr[m] ? 0u : 1u;
                     or_rec q;
@@ -461,14 +505,14 @@ static void advance(or_sim *s, or_rec *p, int64_t i, uint32_t w)
                      * after the step: a dropped secondary's are taken back */
                     or_ledger keep = s->led;
                     if (A) { A->buffering = 1; A->nbuf = 0; }
-                    half_flight(s, &q, half, (uint64_t)i, SUB_SIF);
+                    half_flight(s, &q, half, dk, SUB_SIF);
                     if (A) A->buffering = 0;
                     if (s->n_slots < c->capacity) {
                         uint64_t nid = s->next_id++;
                         q.id = (uint32_t)nid;
                         q.packed |= (uint32_t)(nid >> 32) << 21;
                         /* the secondary carries its parent's weight */
-                        append(s, q, w);
+                        append(s, q, w, child_key(dk, s->step));
                         s->led.spawned++;
                         flux(s, (int)sgs, cs, cell_of(s, q.z), w);
                         if (A) {
@@ -501,7 +545,7 @@ static void advance(or_sim *s, or_rec *p, int64_t i, uint32_t w)
             }
         }
 
-        const int met2 = half_flight(s, p, half, (uint64_t)i, SUB_IF + 16);
+        const int met2 = half_flight(s, p, half, dk, SUB_IF + 16);
         if (met2 && !met1 && !(x[0] < s->P_thr[t])) s->led.eventful++;
         flux(s, sg, c_start, cell_of(s, p->z), w);
         if (A) credit(s, id, flux_reward(s, sg, c_start, cell_of(s, p->z)));
@@ -517,7 +561,7 @@ static void step_once(or_sim *s)
     for (int64_t i = 0; i < n_start; ++i) {
         or_rec *p = &s->recs[i];
         if (PK_K(p->packed) == 0) continue;
-        advance(s, p, i, s->wq[i]);
+        advance(s, p, i, s->wq[i], (c->flags & OR_F_LINEAGE_KEYS) ? s->lkey[i] : (uint64_t)i);
     }
     inject(s, 1);
 
@@ -549,6 +593,7 @@ static void step_once(or_sim *s)
         for (int64_t i = 0; i < s->n_slots; ++i)
             if (PK_K(s->recs[i].packed) != 0) {
                 s->wq[j] = s->wq[i];
+                s->lkey[j] = s->lkey[i];
                 s->recs[j++] = s->recs[i];
             }
         s->n_slots = j;
@@ -688,6 +733,7 @@ int or_create(const or_config *cfg, or_sim **out)
 
     s->recs = (or_rec *)malloc(sizeof(or_rec) * (size_t)(cfg->capacity > 0 ? cfg->capacity : 1));
     s->wq = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(cfg->capacity > 0 ? cfg->capacity : 1));
+    s->lkey = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(cfg->capacity > 0 ? cfg->capacity : 1));
     s->n_out = (cfg->n_steps_max + cfg->moment_every - 1) / cfg->moment_every;
     s->nh = (uint32_t *)calloc((size_t)s->n_out * 2 * ne * cells + 1, sizeof(uint32_t));
     s->Jh = (int32_t *)calloc((size_t)s->n_out * 2 * (cells + 1) + 1, sizeof(int32_t));
@@ -695,7 +741,7 @@ int or_create(const or_config *cfg, or_sim **out)
     s->vh = (int64_t *)calloc((size_t)s->n_out * 2 * cells + 1, sizeof(int64_t));
     s->nhw = (uint64_t *)calloc((size_t)s->n_out * 2 * ne * cells + 1, sizeof(uint64_t));
     s->Jhw = (int64_t *)calloc((size_t)s->n_out * 2 * (cells + 1) + 1, sizeof(int64_t));
-    if (!s->recs || !s->wq || !s->nh || !s->Jh || !s->gh || !s->vh || !s->nhw || !s->Jhw) {
+    if (!s->recs || !s->wq || !s->lkey || !s->nh || !s->Jh || !s->gh || !s->vh || !s->nhw || !s->Jhw) {
         or_destroy(s);
         return 4;
     }
@@ -710,7 +756,7 @@ void or_destroy(or_sim *s)
     free(s->P_thr); free(s->Q_thr); free(s->T_thr); free(s->P0_thr);
     free(s->cdf_cell); free(s->cdf_layer); free(s->cdf_thr); free(s->inj);
     free(s->recs); free(s->nh); free(s->Jh); free(s->gh); free(s->vh);
-    free(s->wq); free(s->wcell); free(s->wbin); free(s->kthr); free(s->nhw); free(s->Jhw);
+    free(s->wq); free(s->lkey); free(s->wcell); free(s->wbin); free(s->kthr); free(s->nhw); free(s->Jhw);
     free(s);
 }
 
@@ -730,7 +776,10 @@ int or_set_records(or_sim *s, const or_rec *in, int64_t n, uint64_t next_id)
 {
     if (n < 0 || n > s->cfg.capacity) return 1;
     memcpy(s->recs, in, sizeof(or_rec) * (size_t)n);
-    for (int64_t i = 0; i < n; ++i) s->wq[i] = 1u << 20;     /* unit weight */
+    for (int64_t i = 0; i < n; ++i) {
+        s->wq[i] = 1u << 20;                               /* unit weight */
+        s->lkey[i] = (1ull << 62) | (uint64_t)i;           /* lineage key of a loaded carrier */
+    }
     s->n_slots = n;
     s->next_id = next_id;
     return 0;
@@ -903,7 +952,7 @@ int or_advance_one(or_sim *s, const or_rec *in, int64_t slot, int room, or_rec *
     s->cfg.capacity = room ? 1 : 0;
     int made = 0;
     if (PK_K(p.packed) != 0) {
-        advance(s, &p, slot, 1u << 20);
+        advance(s, &p, slot, 1u << 20, (uint64_t)slot);
         made = s->n_slots == 1;
         if (made && sec) *sec = s->recs[0];
     }

@@ -33,6 +33,14 @@ extern "C" {
 #define OR_F_STRICT_CAPACITY 16u
 #define OR_F_VELOCITY        32u  /* also sum the velocities v*mu per (time, spin, cell) */
 #define OR_F_WEIGHTS         64u  /* superparticle weights w_i of Eq. PIC (Sec. III.A) */
+/* Oracle-only: every random word of a carrier is keyed by its lineage (a
+ * primary by its birth half step and index, a secondary by a hash of its
+ * parent's key and its birth step) instead of by its slot, so that a
+ * decision that flips in a perturbed run changes only that carrier's line:
+ * common random numbers for central finite differences.  The trajectories
+ * have the same law as with slot keys (every decision still draws a fresh
+ * word); the library keys by slot. */
+#define OR_F_LINEAGE_KEYS   128u
 
 typedef struct {
     float z;          /* depth, nm */

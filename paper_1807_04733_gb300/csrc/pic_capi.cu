@@ -82,6 +82,14 @@ struct pic_ctx {
     long long *d_vh = nullptr;                   // velocity sums [stack][n_out][2][n_cells]
     int32_t *d_J = nullptr;
     int32_t *d_bd = nullptr;                     // births minus removals, J layout
+    // superparticle weights (PIC_F_WEIGHTS)
+    uint32_t *d_w[2] = {nullptr, nullptr};       // per slot, 2^-20 units
+    double *d_wcell = nullptr, *d_wbin = nullptr;
+    uint32_t *d_kthr = nullptr;
+    unsigned long long *d_nhw = nullptr;         // weighted densities, d_nh layout
+    long long *d_bdw = nullptr, *d_Jw = nullptr; // weighted births-minus-removals, fluxes
+    long long *d_hnow_w = nullptr;
+    int flux_final_w = 0;
     int32_t *d_hnow = nullptr;                   // live carriers per [stack][2][ncm+1]
     int ncm = 1;                                 // cells of the widest stack
     int flux_final = 0;                          // windows whose fluxes are final
@@ -239,10 +247,14 @@ double pulse_fraction(const pic_pulse &u, double t)
     return (std_normal_cdf((t - u.t0) / sd) - lo) / (hi - lo);
 }
 
-// Source schedule and depth profile of one stack.
+// Source schedule and depth profile of one stack.  With PIC_F_WEIGHTS and a
+// cell bias the birth cell is drawn from q proportional to mass * bias and
+// wcell[i] = p_i / q_i = (sum mass*bias / sum mass) / bias_i; otherwise
+// wcell = 1 (Eq. PIC weights).
 void source_tables(const pic_params &p, const pic_stack_desc &s, const pic_pulse &u,
                    std::vector<uint32_t> &thr, std::vector<int32_t> &cell,
-                   std::vector<int32_t> &layer, std::vector<long long> &inj)
+                   std::vector<int32_t> &layer, std::vector<long long> &inj,
+                   std::vector<double> *wcell = nullptr)
 {
     thr.clear(); cell.clear(); layer.clear();
     std::vector<double> mass;
@@ -259,9 +271,21 @@ void source_tables(const pic_params &p, const pic_stack_desc &s, const pic_pulse
             total += m;
         }
     double run = 0.0;
-    for (size_t i = 0; i < mass.size(); ++i) {
-        run += mass[i];
-        thr.push_back(i + 1 == mass.size() ? 0xFFFFFFFFu : threshold_of(run / total));
+    const bool tilt = (p.flags & PIC_F_WEIGHTS) && u.cell_bias;
+    if (wcell) wcell->assign(mass.size(), 1.0);
+    if (tilt) {
+        double total_b = 0.0;
+        for (size_t i = 0; i < mass.size(); ++i) total_b += mass[i] * u.cell_bias[cell[i]];
+        for (size_t i = 0; i < mass.size(); ++i) {
+            run += mass[i] * u.cell_bias[cell[i]];
+            thr.push_back(i + 1 == mass.size() ? 0xFFFFFFFFu : threshold_of(run / total_b));
+            if (wcell) (*wcell)[i] = (total_b / total) / u.cell_bias[cell[i]];
+        }
+    } else {
+        for (size_t i = 0; i < mass.size(); ++i) {
+            run += mass[i];
+            thr.push_back(i + 1 == mass.size() ? 0xFFFFFFFFu : threshold_of(run / total));
+        }
     }
     const int64_t nh = 2 * (int64_t)p.n_steps_max;
     inj.assign((size_t)nh, 0);
@@ -274,9 +298,22 @@ void source_tables(const pic_params &p, const pic_stack_desc &s, const pic_pulse
     }
 }
 
-bool valid_pulse(const pic_pulse *u, int n_layers, int n_e, std::string &why)
+bool valid_pulse(const pic_pulse *u, int n_layers, int n_e, std::string &why,
+                 int n_cells = 0, uint32_t flags = 0)
 {
     if (!u) { why = "pulse is NULL"; return false; }
+    if (flags & PIC_F_WEIGHTS) {
+        if (u->cell_bias)
+            for (int i = 0; i < n_cells; ++i)
+                if (!(u->cell_bias[i] > 0.0) || !std::isfinite(u->cell_bias[i])) {
+                    why = "cell_bias must be finite and > 0"; return false;
+                }
+        if (u->e_bias)
+            for (int k = 0; k < n_e; ++k)
+                if (!(u->e_bias[k] > 0.0) || !std::isfinite(u->e_bias[k])) {
+                    why = "e_bias must be finite and > 0"; return false;
+                }
+    }
     if (u->n0 < 0) { why = "n0 < 0"; return false; }
     if (u->n0 > 0 && !(u->fwhm > 0.0 && u->t0 > 0.0)) { why = "fwhm and t0 must be > 0"; return false; }
     if (!(u->abs_len >= 0.0)) { why = "abs_len < 0"; return false; }
@@ -322,6 +359,8 @@ void free_all(pic_ctx *c)
     release(c->d_stage); release(c->d_bits); release(c->d_status); release(c->d_nh); release(c->d_gh); release(c->d_vh);
     release(c->d_qrec); release(c->d_qcnt); release(c->d_fspawn); release(c->d_J); release(c->d_cnt);
     release(c->d_bd); release(c->d_hnow);
+    release(c->d_w[0]); release(c->d_w[1]); release(c->d_wcell); release(c->d_wbin);
+    release(c->d_kthr); release(c->d_nhw); release(c->d_bdw); release(c->d_Jw); release(c->d_hnow_w);
     release(c->d_ctl);
     Replay &r = c->rp;
     for (int b = 0; b < 2; ++b) {
@@ -557,6 +596,17 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     ALLOC(c->d_vh, c->nh_total / p->n_e + 1);
     ALLOC(c->d_J, c->J_total);
     ALLOC(c->d_bd, c->J_total);
+    if (p->flags & PIC_F_WEIGHTS) {
+        ALLOC(c->d_w[0], c->total_slots);
+        ALLOC(c->d_w[1], c->total_slots);
+        ALLOC(c->d_wcell, total_cells);
+        ALLOC(c->d_wbin, (size_t)n_stacks * ne);
+        ALLOC(c->d_kthr, (size_t)n_stacks * ne);
+        ALLOC(c->d_nhw, c->nh_total);
+        ALLOC(c->d_bdw, c->J_total);
+        ALLOC(c->d_Jw, c->J_total);
+        ALLOC(c->d_hnow_w, (size_t)n_stacks * 2 * (c->ncm + 1));
+    }
     ALLOC(c->d_hnow, (size_t)n_stacks * 2 * (c->ncm + 1));
     ALLOC(c->d_cnt, n_stacks);
     ALLOC(c->d_ctl, 1);
@@ -583,6 +633,9 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.qrec = c->d_qrec;
     a.n_hist = c->d_nh; a.J_hist = c->d_J; a.cnt = c->d_cnt; a.ctl = c->d_ctl;
     a.bd_hist = c->d_bd;
+    a.w[0] = c->d_w[0]; a.w[1] = c->d_w[1];
+    a.wcell = c->d_wcell; a.wbin = c->d_wbin; a.kthr = c->d_kthr;
+    a.nhw = c->d_nhw; a.bdw = c->d_bdw; a.Jw = c->d_Jw;
     a.kb = kb;
     a.kshr = 8 - kb;
     a.kmask = (uint32_t)KP - 1u;
@@ -655,6 +708,14 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_vh, 0, 8 * (size_t)(c->nh_total / p->n_e + 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_J, 0, 4 * (size_t)std::max<int64_t>(c->J_total, 1), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bd, 0, 4 * (size_t)std::max<int64_t>(c->J_total, 1), st);
+    std::vector<double> ones((size_t)std::max<int64_t>(total_cells, (int64_t)n_stacks * ne), 1.0);
+    if (p->flags & PIC_F_WEIGHTS) {
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_nhw, 0, 8 * (size_t)std::max<int64_t>(c->nh_total, 1), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bdw, 0, 8 * (size_t)std::max<int64_t>(c->J_total, 1), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->d_Jw, 0, 8 * (size_t)std::max<int64_t>(c->J_total, 1), st);
+        if (e == cudaSuccess && total_cells) e = cudaMemcpyAsync(c->d_wcell, ones.data(), 8 * (size_t)total_cells, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_wbin, ones.data(), 8 * (size_t)n_stacks * ne, cudaMemcpyHostToDevice, st);
+    }
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt, cnt.data(), sizeof(DevCounters) * n_stacks, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -676,7 +737,8 @@ pic_status pic_excite(pic_ctx *c, int stack, const pic_pulse *u)
     const int s0 = stack < 0 ? 0 : stack, s1 = stack < 0 ? c->n_stacks : stack + 1;
     std::string why;
     for (int s = s0; s < s1; ++s)
-        if (!valid_pulse(u, c->hs[s].d.n_layers, c->p.n_e, why)) return fail(c, PIC_ERR_ARG, why);
+        if (!valid_pulse(u, c->hs[s].d.n_layers, c->p.n_e, why, c->hs[s].n_cells, c->p.flags))
+            return fail(c, PIC_ERR_ARG, why);
     if (c->step > 0) {
         c->replayable = false;
         c->replay_why = "pic_grad: the source changed after step 0";
@@ -685,8 +747,11 @@ pic_status pic_excite(pic_ctx *c, int stack, const pic_pulse *u)
         HostStack &h = c->hs[s];
         DevStack &d = c->ds[s];
         std::vector<uint32_t> thr; std::vector<int32_t> cell, layer;
-        source_tables(c->p, h.d, *u, thr, cell, layer, h.inj);
+        std::vector<double> wcell;
+        source_tables(c->p, h.d, *u, thr, cell, layer, h.inj, &wcell);
         h.pulse = *u;
+        h.pulse.cell_bias = nullptr;      // not kept: the tables are
+        h.pulse.e_bias = nullptr;
         h.excited = true;
         d.n_cdf = (int32_t)thr.size();
         d.up_thr = threshold_of(u->up_frac);
@@ -701,6 +766,29 @@ pic_status pic_excite(pic_ctx *c, int stack, const pic_pulse *u)
         }
         if (e == cudaSuccess && !h.inj.empty())
             e = cudaMemcpyAsync(c->d_inj + d.inj_off, h.inj.data(), sizeof(long long) * h.inj.size(), cudaMemcpyHostToDevice, c->stream);
+        // importance sampling of the birth bin: q_k proportional to bias_k,
+        // weight p_k / q_k = (sum bias / n_e) / bias_k (e_mode 0)
+        const int ne = c->p.n_e;
+        std::vector<uint32_t> kthr(ne, 0u);
+        std::vector<double> wbin(ne, 1.0);
+        d.has_ebias = ((c->p.flags & PIC_F_WEIGHTS) && u->e_bias && u->e_mode == 0) ? 1 : 0;
+        if (d.has_ebias) {
+            double tb = 0.0, cb = 0.0;
+            for (int k = 0; k < ne; ++k) tb += u->e_bias[k];
+            for (int k = 0; k < ne; ++k) {
+                cb += u->e_bias[k];
+                kthr[k] = k == ne - 1 ? 0xFFFFFFFFu : threshold_of(cb / tb);
+                wbin[k] = (tb / (double)ne) / u->e_bias[k];
+            }
+        }
+        if (e == cudaSuccess && (c->p.flags & PIC_F_WEIGHTS)) {
+            if (!wcell.empty())
+                e = cudaMemcpyAsync(c->d_wcell + d.cdf_off, wcell.data(), 8 * wcell.size(), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->d_wbin + (size_t)s * ne, wbin.data(), 8 * (size_t)ne, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->d_kthr + (size_t)s * ne, kthr.data(), 4 * (size_t)ne, cudaMemcpyHostToDevice, c->stream);
+        }
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(c->d_stacks + s, &d, sizeof(DevStack), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -744,6 +832,10 @@ cudaError_t enqueue_step(pic_ctx *c, const Args &a0, int s, bool inj0, bool inj1
         Args b = a;
         b.bump_step = graph;
         e = timed(c, 0, [&] { return launch_inject(b, lc, 1, dep, st); });
+        ++launches;
+    }
+    if (e == cudaSuccess && dep && (c->p.flags & PIC_F_WEIGHTS)) {
+        e = timed(c, 9, [&] { return launch_wdep(a, lc, st); });
         ++launches;
     }
     if (e == cudaSuccess && ((s + 1) % c->p.compact_every) == 0) {
@@ -808,6 +900,28 @@ cudaError_t derive_fluxes(pic_ctx *c)
             e = timed(c, 8, [&] { return launch_state_hist(c->args, 0, c->n_stacks, 1, 0, 1, c->d_hnow, c->ncm, c->stream); });
         if (e == cudaSuccess)
             e = timed(c, 8, [&] { return launch_flux(c->args, ended, ended + 1, ended, c->d_hnow, c->ncm, c->stream); });
+    }
+    return e;
+}
+
+// The weighted fluxes, as derive_fluxes, from the weighted densities and
+// the weighted births minus removals.
+cudaError_t derive_fluxes_w(pic_ctx *c)
+{
+    const int me = c->p.moment_every, n_out = c->hs[0].n_out;
+    const int ended = std::min(c->step / me, n_out);
+    cudaError_t e = cudaSuccess;
+    if (c->flux_final_w < ended) {
+        e = timed(c, 8, [&] { return launch_flux_w(c->args, c->flux_final_w, ended, -1, nullptr, c->ncm, c->stream); });
+        if (e != cudaSuccess) return e;
+        c->flux_final_w = ended;
+    }
+    if (c->step % me != 0 && ended < n_out) {
+        e = cudaMemsetAsync(c->d_hnow_w, 0, sizeof(long long) * (size_t)c->n_stacks * 2 * (c->ncm + 1), c->stream);
+        if (e == cudaSuccess)
+            e = timed(c, 8, [&] { return launch_state_hist_w(c->args, 0, c->n_stacks, 1, 0, 1, c->d_hnow_w, c->ncm, c->stream); });
+        if (e == cudaSuccess)
+            e = timed(c, 8, [&] { return launch_flux_w(c->args, ended, ended + 1, ended, c->d_hnow_w, c->ncm, c->stream); });
     }
     return e;
 }
@@ -887,6 +1001,79 @@ pic_status pic_moments(pic_ctx *c, int stack, uint32_t *n_dev, int32_t *J_dev, p
         std::memcpy(led, hc.led, sizeof(pic_ledger));
     }
     return st;
+}
+
+pic_status pic_weighted_moments(pic_ctx *c, int stack, uint64_t *nw_dev, int64_t *Jw_dev,
+                                uint64_t *w_injected_host)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    if (!(c->p.flags & PIC_F_WEIGHTS))
+        return fail(c, PIC_ERR_ARG, "the context was made without PIC_F_WEIGHTS");
+    const HostStack &h = c->hs[stack];
+    const DevStack &d = c->ds[stack];
+    cudaError_t e = Jw_dev ? derive_fluxes_w(c) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_weighted_moments fluxes");
+    const size_t nn = (size_t)h.n_out * 2 * c->p.n_e * h.n_cells;
+    const size_t nj = (size_t)h.n_out * 2 * (h.n_cells + 1);
+    if (nw_dev && nn) e = cudaMemcpyAsync(nw_dev, c->d_nhw + d.n_off, 8 * nn, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess && Jw_dev && nj) e = cudaMemcpyAsync(Jw_dev, c->d_Jw + d.J_off, 8 * nj, cudaMemcpyDeviceToDevice, c->stream);
+    DevCounters hc{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, c->d_cnt + stack, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_weighted_moments copy");
+    const pic_status st = device_status(c);
+    if (w_injected_host) *w_injected_host = hc.w_injected;
+    return st;
+}
+
+pic_status pic_weights(pic_ctx *c, int stack, uint32_t *out, int64_t *n)
+{
+    if (!c || !n) return PIC_ERR_ARG;
+    if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    if (!(c->p.flags & PIC_F_WEIGHTS))
+        return fail(c, PIC_ERR_ARG, "the context was made without PIC_F_WEIGHTS");
+    DevCounters hc{};
+    DevCtl ctl{};
+    cudaError_t e = cudaMemcpyAsync(&hc, c->d_cnt + stack, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_weights");
+    const int64_t cnt = (int64_t)hc.n_slots;
+    if (!out) { *n = cnt; return PIC_OK; }
+    if (*n < cnt) { *n = cnt; return fail(c, PIC_ERR_ARG, "output buffer too small"); }
+    *n = cnt;
+    if (cnt) e = cudaMemcpyAsync(out, c->d_w[ctl.cur] + c->ds[stack].base, 4 * (size_t)cnt, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_weights copy");
+    return PIC_OK;
+}
+
+pic_status pic_set_weights(pic_ctx *c, int stack, const uint32_t *in, int64_t n)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    if (!(c->p.flags & PIC_F_WEIGHTS))
+        return fail(c, PIC_ERR_ARG, "the context was made without PIC_F_WEIGHTS");
+    DevCounters hc{};
+    DevCtl ctl{};
+    cudaError_t e = cudaMemcpyAsync(&hc, c->d_cnt + stack, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_set_weights");
+    if (n != (int64_t)hc.n_slots || (n > 0 && !in)) return fail(c, PIC_ERR_ARG, "one weight per slot");
+    for (int64_t i = 0; i < n; ++i)
+        if (in[i] == 0u) return fail(c, PIC_ERR_ARG, "weights must be > 0");
+    // the carriers leave with their old weights and come back with the new
+    const int win = c->step / c->p.moment_every;
+    const bool in_run = win < c->hs[stack].n_out;
+    if (in_run) e = launch_state_hist_w(c->args, stack, stack + 1, 0, win, -1, nullptr, c->ncm, c->stream);
+    if (e == cudaSuccess && n)
+        e = cudaMemcpyAsync(c->d_w[ctl.cur] + c->ds[stack].base, in, 4 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && in_run)
+        e = launch_state_hist_w(c->args, stack, stack + 1, 0, win, 1, nullptr, c->ncm, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_set_weights copy");
+    return PIC_OK;
 }
 
 pic_status pic_gen_moments(pic_ctx *c, int stack, uint64_t *g_dev)
@@ -981,7 +1168,10 @@ pic_status pic_set_records(pic_ctx *c, int stack, const pic_record *in, int64_t 
     const int win = c->step / c->p.moment_every;
     const bool in_run = win < hs.n_out;
     cudaError_t e = cudaSuccess;
+    const bool wts = (c->p.flags & PIC_F_WEIGHTS) != 0;
     if (in_run) e = launch_state_hist(c->args, stack, stack + 1, 0, win, -1, nullptr, c->ncm, c->stream);
+    if (e == cudaSuccess && in_run && wts)
+        e = launch_state_hist_w(c->args, stack, stack + 1, 0, win, -1, nullptr, c->ncm, c->stream);
     DevCtl ctl{};
     if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -1007,8 +1197,13 @@ pic_status pic_set_records(pic_ctx *c, int stack, const pic_record *in, int64_t 
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt + stack, vals, sizeof(vals), cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(&c->d_cnt[stack].live, &live, sizeof(live), cudaMemcpyHostToDevice, c->stream);
+    std::vector<uint32_t> unit(wts ? (size_t)n : 0, 1u << 20);      // loaded carriers weigh 1
+    if (e == cudaSuccess && wts && n)
+        e = cudaMemcpyAsync(c->d_w[b] + base, unit.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && in_run)
         e = launch_state_hist(c->args, stack, stack + 1, 0, win, 1, nullptr, c->ncm, c->stream);
+    if (e == cudaSuccess && in_run && wts)
+        e = launch_state_hist_w(c->args, stack, stack + 1, 0, win, 1, nullptr, c->ncm, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "pic_set_records copy");
     // the adjoint replays from records loaded before the first step, whose
@@ -1146,6 +1341,9 @@ pic_status pic_grad(pic_ctx *c, const float *grad_n, const float *grad_J, double
     a.stacks = r.stacks; a.cnt = r.cnt; a.ctl = r.ctl; a.status = r.status; a.qcnt = r.qcnt;
     a.fspawn = r.fspawn;
     a.n_hist = nullptr; a.J_hist = nullptr; a.g_hist = nullptr; a.v_hist = nullptr;
+    a.bd_hist = nullptr;
+    a.w[0] = a.w[1] = nullptr;                // the replay carries no weights
+    a.nhw = nullptr; a.bdw = nullptr; a.Jw = nullptr;
     a.tot = r.tot; a.parent = r.parent; a.gen = r.gen; a.gen_max = r.gen_max;
     a.aent = r.aent; a.aT = r.aT; a.g_ent = r.g_ent; a.g_T = r.g_T;
     a.gn = grad_n ? r.qgn : nullptr; a.gpot = r.gpot; a.stage_l = r.stage_l;

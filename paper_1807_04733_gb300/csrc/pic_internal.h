@@ -84,6 +84,7 @@ struct DevStack {        // immutable per-stack description (device copy)
     int64_t cdf_off; int32_t n_cdf;     // source profile
     uint32_t up_thr;
     int32_t e_mode, k_mono0, k_mono1;
+    int32_t has_ebias;                  // weights: births drawn from the biased bin CDF
     int64_t inj_off;                    // source schedule, 2*n_steps_max
     int64_t id_off, n_ids;              // adjoint: range of the id-indexed arrays
 };
@@ -92,6 +93,7 @@ struct DevCounters {     // mutable per stack
     unsigned long long n_slots, next_id, spawn_total, alive_total;
     unsigned long long led[LEDGER_N];
     unsigned long long live;   // live carriers (k > 0) among the slots
+    unsigned long long w_injected;   // weights (2^-20 units) of the carriers created
 };
 
 struct DevCtl {
@@ -155,6 +157,16 @@ struct Args {            // everything a kernel needs, passed by value
     int ring;                                // tiles in k_fast's copy ring
     int grid_fast;                           // k_fast's grid (read by k_event, k_place)
     uint32_t *spawn_bits;                    // one bit per position: secondary staged
+    // superparticle weights (PIC_F_WEIGHTS; null otherwise): per slot in
+    // 2^-20 units, both buffers; the source's importance ratios p/q per
+    // birth-cell entry (cdf_off indexing) and per bin ([stack][n_e]), with
+    // the biased bin thresholds; the weighted densities (n_hist layout),
+    // births minus removals and fluxes (J layout)
+    uint32_t *w[2];
+    const double *wcell, *wbin;
+    const uint32_t *kthr;
+    unsigned long long *nhw;
+    long long *bdw, *Jw;
     float4 *qrec;                            // eventful carriers: z, mu, packed, position
     uint32_t *qcnt;                          // queue length per fast block
     uint32_t *fspawn;                        // secondaries staged per fast block
@@ -211,11 +223,20 @@ cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s);
 // [stack][2][ncm+1]
 cudaError_t launch_state_hist(const Args &a, int s0, int s1, int mode, int win, int sign,
                               int32_t *scratch, int ncm, cudaStream_t st);
+// the same, each carrier counted with its weight (births-minus-removals
+// histogram bdw, or a scratch [stack][2][ncm+1] of int64)
+cudaError_t launch_state_hist_w(const Args &a, int s0, int s1, int mode, int win, int sign,
+                                long long *scratch, int ncm, cudaStream_t st);
+// weighted densities of the density step just finished (PIC_F_WEIGHTS)
+cudaError_t launch_wdep(const Args &a, const LaunchCfg &c, cudaStream_t st);
 // fluxes of windows [w0, w1) of every stack from the densities and the
 // births-minus-removals histograms; window w_now (unfinished) takes its end
 // counts from `now` [stack][2][ncm+1] (the current state) instead
 cudaError_t launch_flux(const Args &a, int w0, int w1, int w_now, const int32_t *now, int ncm,
                         cudaStream_t st);
+// the weighted fluxes Jw from nhw, bdw (and `now` [stack][2][ncm+1] int64)
+cudaError_t launch_flux_w(const Args &a, int w0, int w1, int w_now, const long long *now, int ncm,
+                          cudaStream_t st);
 // set the device step counter read by graph-replayed steps
 cudaError_t launch_set_step(DevCtl *ctl, unsigned int step, cudaStream_t s);
 

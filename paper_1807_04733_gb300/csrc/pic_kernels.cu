@@ -90,6 +90,194 @@ __global__ void __launch_bounds__(TPB) k_state_hist(const Args a, int s0, int s1
     }
 }
 
+// The weighted fluxes (PIC_F_WEIGHTS): the same sums over the weighted
+// densities (2^-20 units) and the weighted births minus removals.
+__global__ void __launch_bounds__(TPB) k_flux_w(const Args a, int w0, int w1, int w_now,
+                                                const long long *now, int ncm)
+{
+    __shared__ long long s_w[TPB / 32];
+    __shared__ long long s_tot;
+    const int nw = w1 - w0;
+    const int row = blockIdx.x;
+    const int s = row / (2 * nw), rem = row % (2 * nw), w = w0 + rem / 2, sg = rem % 2;
+    const DevStack &st = a.stacks[s];
+    const int nc = st.n_cells, nf = nc + 1, ne = a.n_e;
+    const long long nbins = 2LL * ne * nc;
+    const unsigned long long *Ne = a.nhw + st.n_off + (long long)w * nbins + (long long)sg * ne * nc;
+    const unsigned long long *Ns = w > 0 ? Ne - nbins : nullptr;
+    const long long *B = a.bdw + st.J_off + ((long long)w * 2 + sg) * nf;
+    const long long *Nn = (w == w_now && now) ? now + ((long long)s * 2 + sg) * (ncm + 1) : nullptr;
+    long long *J = a.Jw + st.J_off + ((long long)w * 2 + sg) * nf;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long carry = 0;
+    for (int c1 = nc; c1 > 0; c1 -= TPB) {
+        const int c = c1 - 1 - threadIdx.x;          // descending cell of this thread
+        long long d = 0;
+        if (c >= 0) {
+            long long ne_c = 0, ns_c = 0;
+            if (Nn) {
+                ne_c = Nn[c];
+            } else {
+                for (int k = 0; k < ne; ++k) ne_c += (long long)Ne[(long long)k * nc + c];
+            }
+            if (Ns)
+                for (int k = 0; k < ne; ++k) ns_c += (long long)Ns[(long long)k * nc + c];
+            d = ne_c - ns_c - B[c];
+        }
+        // block-wide inclusive scan of d in thread order (descending cells)
+        long long x = d;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[wid] = x;
+        __syncthreads();
+        long long before = 0;
+        for (int q = 0; q < wid; ++q) before += s_w[q];
+        if (threadIdx.x == TPB - 1) s_tot = before + x;
+        if (c >= 0) J[c] = carry + before + x;
+        __syncthreads();
+        carry += s_tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) J[nc] = 0;
+}
+
+// Weighted live carriers of stacks [s0, s1) per (spin, cell), as
+// k_state_hist: mode 0 adds sign * w to the weighted births-minus-removals
+// histogram of window `win`; mode 1 sums into out[stack][2][ncm + 1].
+__global__ void __launch_bounds__(TPB) k_state_hist_w(const Args a, int s0, int s1, int mode,
+                                                      int win, int sign, long long *out, int ncm)
+{
+    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
+    for (int s = s0; s < s1; ++s) {
+        const DevStack &st = a.stacks[s];
+        const long long n = (long long)a.cnt[s].n_slots;
+        Stk tmp;
+        tmp.n_cells = st.n_cells;
+        long long *h = mode == 0 ? a.bdw + st.J_off + (long long)win * 2 * (st.n_cells + 1)
+                                 : out + (long long)s * 2 * (ncm + 1);
+        const int nf = mode == 0 ? st.n_cells + 1 : ncm + 1;
+        for (long long i = (long long)blockIdx.x * TPB + threadIdx.x; i < n;
+             i += (long long)gridDim.x * TPB) {
+            const long long g = st.base + i;
+            const uint32_t pk = a.pk[cur][g * a.mp_stride];
+            if ((pk & 0xFFu) == 0u) continue;
+            const int sg = (int)((pk >> 8) & 1u);
+            const long long v = (long long)a.w[cur][g] * sign;
+            atomicAdd(reinterpret_cast<unsigned long long *>(&h[sg * nf + cell_of(a, tmp, a.z[cur][g])]),
+                      (unsigned long long)v);
+        }
+    }
+}
+
+// Weighted densities at the end of a density step: every live carrier adds
+// its weight to its (spin, bin, cell) entry.  One block owns a contiguous
+// chunk of tiles; with SM the stack's histogram is privatised in shared
+// memory and flushed once per stack segment, otherwise added in global
+// memory.  Launched after the step's last kernel: in a graph replay that
+// kernel has already advanced the device step counter.
+template <bool SM>
+__global__ void __launch_bounds__(TPB) k_wdep(const Args a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned long long *s_h = reinterpret_cast<unsigned long long *>(smem);
+    __shared__ long long s_tpref[PIC_MAX_STACKS + 1];
+    __shared__ long long s_nsl[PIC_MAX_STACKS];
+    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
+    const int tid = threadIdx.x;
+    const uint32_t step = a.step_dev ? __ldcg(a.step_dev) - 1u : a.step;
+    const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
+    Plan p;
+    make_plan(a, s_tpref, s_nsl, p);
+    const uint2 *MP = reinterpret_cast<const uint2 *>(a.mu[cur]);   // (mu, packed) pairs
+    auto hist = [&](int s) {
+        const DevStack &st = a.stacks[s];
+        return a.nhw + st.n_off + (long long)tout * 2 * a.n_e * st.n_cells;
+    };
+    auto flush = [&](int s) {
+        __syncthreads();
+        const int nb = 2 * a.n_e * a.stacks[s].n_cells;
+        unsigned long long *gh = hist(s);
+        for (int i = tid; i < nb; i += TPB)
+            if (s_h[i]) atomicAdd(&gh[i], s_h[i]);
+        __syncthreads();
+    };
+    int seg = -1;
+    unsigned long long *gh = nullptr;
+    for (long long t = p.t0; t < p.t1; ++t) {
+        const int s = stack_of(s_tpref, a.n_stacks, t);
+        if (s != seg) {
+            if (SM) {
+                if (seg >= 0) flush(seg);
+                for (int i = tid; i < 2 * a.n_e * a.stacks[s].n_cells; i += TPB) s_h[i] = 0ull;
+                __syncthreads();
+            }
+            gh = hist(s);
+            seg = s;
+        }
+        const DevStack &st = a.stacks[s];
+        Stk tmp;
+        tmp.n_cells = st.n_cells;
+        const long long slot0 = (t - s_tpref[s]) * TILE + (long long)tid * VEC;
+        const long long nsl = s_nsl[s];
+#pragma unroll
+        for (int j = 0; j < VEC; ++j) {
+            const long long slot = slot0 + j;
+            if (slot >= nsl) break;
+            const long long g = st.base + slot;
+            const uint32_t pk = MP[g].y;
+            const int k = (int)(pk & 0xFFu);
+            if (k == 0) continue;
+            const int sg = (int)((pk >> 8) & 1u);
+            const int b = (sg * a.n_e + (k - 1)) * st.n_cells + cell_of(a, tmp, a.z[cur][g]);
+            const unsigned long long w = a.w[cur][g];
+            if (SM) atomicAdd(&s_h[b], w);
+            else atomicAdd(&gh[b], w);
+        }
+    }
+    if (SM && seg >= 0) flush(seg);
+}
+
+cudaError_t launch_flux_w(const Args &a, int w0, int w1, int w_now, const long long *now, int ncm,
+                          cudaStream_t st)
+{
+    if (w1 <= w0) return cudaSuccess;
+    k_flux_w<<<a.n_stacks * 2 * (w1 - w0), TPB, 0, st>>>(a, w0, w1, w_now, now, ncm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_hist_w(const Args &a, int s0, int s1, int mode, int win, int sign,
+                                long long *scratch, int ncm, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    k_state_hist_w<<<sms * 4, TPB, 0, st>>>(a, s0, s1, mode, win, sign, scratch, ncm);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wdep(const Args &a, const LaunchCfg &c, cudaStream_t st)
+{
+    // privatised in shared memory when the widest stack's histogram fits
+    const size_t sm = (size_t)a.nbin_max * sizeof(unsigned long long);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    const size_t static_sm = (size_t)(2 * PIC_MAX_STACKS + 1) * 8;
+    if (sm + static_sm <= (size_t)optin) {
+        e = cudaFuncSetAttribute(k_wdep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        k_wdep<true><<<c.grid_compact, TPB, sm, st>>>(a);
+    } else {
+        k_wdep<false><<<c.grid_compact, TPB, 0, st>>>(a);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_flux(const Args &a, int w0, int w1, int w_now, const int32_t *now, int ncm,
                         cudaStream_t st)
 {

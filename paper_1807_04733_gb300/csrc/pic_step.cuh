@@ -1491,8 +1491,14 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         if (dead) {
             pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
             const int c_end = cell_of(a, S, z);
-            // a removal, where the carrier stopped
-            if (!ADJ) atomicAdd(&s_J[sg * (S.n_cells + 1) + c_end], -1);
+            // a removal, where the carrier stopped (with its weight)
+            if (!ADJ) {
+                atomicAdd(&s_J[sg * (S.n_cells + 1) + c_end], -1);
+                if (a.w[0])
+                    atomicAdd(reinterpret_cast<unsigned long long *>(a.bdw) + st.J_off +
+                                  ((long long)tj * 2 + sg) * (S.n_cells + 1) + c_end,
+                              0ull - (unsigned long long)a.w[cur][gslot]);
+            }
             if (ADJ) rw = flux_w(a, s, tj, sg, c_start, c_end);
         } else {
             flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, key_x, S.ctr_hi,
@@ -1704,8 +1710,17 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
                         if (ADJ) {
                             place_adj(s, stg, w * 32 + j, d, id, pk, sg, k, c0, c1, r);
                         } else {
-                            // a birth, where the parent created it
+                            // a birth, where the parent created it; the
+                            // secondary carries its parent's weight
                             atomicAdd(&s_J[sg * nf + c0], 1);
+                            if (a.w[0]) {
+                                const long long pos = w * 32 + j;
+                                const uint32_t wp = a.w[cur][stg.base + pos - s_tpref[s] * TILE];
+                                a.w[cur][d] = wp;
+                                atomicAdd(reinterpret_cast<unsigned long long *>(a.bdw) + stg.J_off +
+                                              ((long long)tj * 2 + sg) * nf + c0,
+                                          (unsigned long long)wp);
+                            }
                             if (DEPN) {
                                 atomicAdd(&s_n[(sg * a.n_e + (k - 1)) * stg.n_cells + c1], 1u);
                                 atomicAdd(&s_gs[c1], (pk >> 13) & 0xFFu);
@@ -1884,6 +1899,7 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
     __shared__ long long s_pref[PIC_MAX_STACKS + 1];
     __shared__ long long s_n[PIC_MAX_STACKS];
     __shared__ unsigned long long s_q[PIC_MAX_STACKS];
+    __shared__ unsigned long long s_wsum[PIC_MAX_STACKS];   // weights created
     __shared__ int s_flag;
     const int tid = threadIdx.x;
     const uint32_t step = step_now(a);
@@ -1895,6 +1911,7 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
         const long long room = st.cap - (long long)a.cnt[s].n_slots;
         s_n[s] = n < room ? n : (room > 0 ? room : 0);
         s_q[s] = 0;
+        s_wsum[s] = 0;
     }
     __syncthreads();
     if (tid == 0) {
@@ -1922,8 +1939,17 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
         const int cell = a.cdf_cell[st.cdf_off + i];
         const float z = __fmul_rn(__fadd_rn((float)cell, unit_of(r0.y)), a.dz);
         const uint32_t sg = r0.z < st.up_thr ? 0u : 1u;
-        const uint32_t k = st.e_mode == 1 ? (uint32_t)(sg ? st.k_mono1 : st.k_mono0)
-                                          : 1u + __umulhi(r0.w, (uint32_t)a.n_e);
+        uint32_t k;
+        if (st.e_mode == 1) {
+            k = (uint32_t)(sg ? st.k_mono1 : st.k_mono0);
+        } else if (st.has_ebias) {
+            // the bin from the biased sampling distribution (weights)
+            const uint32_t *kt = a.kthr + (long long)s * a.n_e;
+            k = 1u;
+            while ((int)k < a.n_e && !(r0.w < kt[k - 1])) ++k;
+        } else {
+            k = 1u + __umulhi(r0.w, (uint32_t)a.n_e);
+        }
         const uint32_t layer = (uint32_t)a.cdf_layer[st.cdf_off + i];
         const long long d = st.base + (long long)a.cnt[s].n_slots + j;
         a.z[cur][d] = z;
@@ -1932,6 +1958,15 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
             k | (sg << 8) | (layer << 9) | (1u << 13) | ((uint32_t)(id >> 32) << 21));
         a.id[cur][d] = (uint32_t)id;
         atomicAdd(&s_q[s], (unsigned long long)k);
+        uint32_t wq = 1u << 20;
+        if (!ADJ && a.w[0]) {
+            // weight p/q of the birth cell and bin (Eq. PIC), 2^-20 units
+            const double wr = __dmul_rn(__dmul_rn(a.wcell[st.cdf_off + i],
+                                                  a.wbin[(long long)s * a.n_e + k - 1]), 1048576.0);
+            wq = wr < 1.0 ? 1u : (wr > 4294967295.0 ? 0xFFFFFFFFu : __double2uint_rn(wr));
+            a.w[cur][d] = wq;
+            atomicAdd(&s_wsum[s], (unsigned long long)wq);
+        }
         if (!ADJ) {
             Stk tmp; tmp.n_cells = st.n_cells;
             const int c = cell_of(a, tmp, z);
@@ -1940,6 +1975,7 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
             const long long bi = st.J_off + ((long long)tj * 2 + sg) * (st.n_cells + 1) + c;
             const unsigned int grp = __match_any_sync(__activemask(), (unsigned long long)bi);
             if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicAdd(&a.bd_hist[bi], __popc(grp));
+            if (a.w[0]) atomicAdd(reinterpret_cast<unsigned long long *>(a.bdw) + bi, (unsigned long long)wq);
             if (deposit) {
                 atomicAdd(&a.n_hist[st.n_off + (long long)tout * 2 * a.n_e * st.n_cells +
                                     (sg * a.n_e + (k - 1)) * st.n_cells + c], 1u);
@@ -1968,8 +2004,10 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
         }
     }
     __syncthreads();
-    for (int s = tid; s < a.n_stacks; s += TPB)
+    for (int s = tid; s < a.n_stacks; s += TPB) {
         if (s_q[s]) atomicAdd(&a.cnt[s].led[L_Q_INJECTED], s_q[s]);
+        if (s_wsum[s]) atomicAdd(&a.cnt[s].w_injected, s_wsum[s]);
+    }
     if (last_block(a, &s_flag)) {
         for (int s = tid; s < a.n_stacks; s += TPB) {
             const DevStack &st = a.stacks[s];
@@ -2098,6 +2136,7 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
                         a.pk[nxt][d] = a.pk[cur][src + j];
                     }
                     a.id[nxt][d] = a.id[cur][src + j];
+                    if (!ADJ && a.w[0]) a.w[nxt][d] = a.w[cur][src + j];
                     if (ADJ) a.acc[nxt][d] = a.acc[cur][src + j];
                     ++d;
                 }

@@ -31,13 +31,13 @@ REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u
 
 # symbols declared in include/pic.h
 EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_gen_moments",
-           "pic_vel_moments", "pic_grad",
+           "pic_vel_moments", "pic_weighted_moments", "pic_weights", "pic_set_weights", "pic_grad",
            "pic_records",
            "pic_set_records", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
            "pic_profile_read", "pic_compact_static", "pic_launch_config", "pic_launch_count",
            "pic_destroy", "pic_last_error", "pic_status_string", "pic_autotune")
 KERNEL_KINDS = ("inject", "step", "step_moments", "compact", "step_events", "adjoint_step",
-                "adjoint_events", "adjoint_other", "flux")
+                "adjoint_events", "adjoint_other", "flux", "weights")
 
 
 class pic_params(C.Structure):
@@ -63,7 +63,8 @@ class pic_tables(C.Structure):
 class pic_pulse(C.Structure):
     _fields_ = [("n0", C.c_int64), ("fwhm", C.c_double), ("t0", C.c_double),
                 ("abs_len", C.c_double), ("excite_mask", C.c_uint32), ("up_frac", C.c_double),
-                ("e_mode", C.c_int32), ("k_mono", C.c_int32 * 2)]
+                ("e_mode", C.c_int32), ("k_mono", C.c_int32 * 2),
+                ("cell_bias", C.POINTER(C.c_double)), ("e_bias", C.POINTER(C.c_double))]
 
 
 class pic_ledger(C.Structure):
@@ -130,6 +131,9 @@ def lib():
         L.pic_moments.argtypes = [P, C.c_int, P, P, C.POINTER(pic_ledger)]
         L.pic_gen_moments.argtypes = [P, C.c_int, P]
         L.pic_vel_moments.argtypes = [P, C.c_int, P]
+        L.pic_weighted_moments.argtypes = [P, C.c_int, P, P, C.POINTER(C.c_uint64)]
+        L.pic_weights.argtypes = [P, C.c_int, P, C.POINTER(C.c_int64)]
+        L.pic_set_weights.argtypes = [P, C.c_int, P, C.c_int64]
         L.pic_grad.argtypes = [P, P, P, P, P]
         L.pic_records.argtypes = [P, C.c_int, P, C.POINTER(C.c_int64)]
         L.pic_set_records.argtypes = [P, C.c_int, P, C.c_int64, C.c_uint64]
@@ -215,10 +219,22 @@ class _Tables:
 
 
 def make_pulse(st):
+    """The pulse of a stack; the bias arrays (if any) are kept on the returned
+    structure (attribute _keep) while it is alive."""
     u = pic_pulse()
     u.n0 = st.n0; u.fwhm = st.fwhm; u.t0 = st.t0; u.abs_len = st.abs_len
     u.excite_mask = st.excite_mask; u.up_frac = st.up_frac; u.e_mode = st.e_mode
     u.k_mono[0] = st.k_mono[0]; u.k_mono[1] = st.k_mono[1]
+    keep = []
+    if getattr(st, "cell_bias", None) is not None:
+        cb = np.ascontiguousarray(st.cell_bias, np.float64)
+        keep.append(cb)
+        u.cell_bias = cb.ctypes.data_as(C.POINTER(C.c_double))
+    if getattr(st, "e_bias", None) is not None:
+        eb = np.ascontiguousarray(st.e_bias, np.float64)
+        keep.append(eb)
+        u.e_bias = eb.ctypes.data_as(C.POINTER(C.c_double))
+    u._keep = keep
     return u
 
 
@@ -249,6 +265,28 @@ def pic_moments(ctx, stack, n_dev_ptr, J_dev_ptr):
     _check(lib().pic_moments(ctx, stack, C.c_void_p(n_dev_ptr or 0) if n_dev_ptr else None,
                              C.c_void_p(J_dev_ptr) if J_dev_ptr else None, C.byref(led)), ctx)
     return led.as_dict()
+
+
+def pic_weighted_moments(ctx, stack, nw_dev_ptr, Jw_dev_ptr):
+    wi = C.c_uint64(0)
+    _check(lib().pic_weighted_moments(ctx, stack, C.c_void_p(nw_dev_ptr) if nw_dev_ptr else None,
+                                      C.c_void_p(Jw_dev_ptr) if Jw_dev_ptr else None,
+                                      C.byref(wi)), ctx)
+    return wi.value
+
+
+def pic_weights(ctx, stack):
+    n = C.c_int64(0)
+    _check(lib().pic_weights(ctx, stack, None, C.byref(n)), ctx)
+    out = np.zeros(n.value, np.uint32)
+    if n.value:
+        _check(lib().pic_weights(ctx, stack, out.ctypes.data, C.byref(n)), ctx)
+    return out
+
+
+def pic_set_weights(ctx, stack, w):
+    w = np.ascontiguousarray(w, np.uint32)
+    _check(lib().pic_set_weights(ctx, stack, w.ctypes.data if len(w) else None, len(w)), ctx)
 
 
 def pic_gen_moments(ctx, stack, g_dev_ptr):
@@ -414,6 +452,25 @@ class Context:
         v = torch.empty((no, 2, nc), dtype=torch.int64, device=dev)
         pic_vel_moments(self.ctx, stack, v.data_ptr())
         return v
+
+    def weighted_moments(self, stack=0):
+        """Densities [n_out][2][n_e][n_cells] (uint64 as int64 on the device)
+        and fluxes [n_out][2][n_cells+1] (int64) with every carrier counted
+        with its weight (2^-20 units), and the summed weight the source
+        created (PIC_F_WEIGHTS; Eq. PIC)."""
+        torch = self.torch
+        nc, no, _ = self.shape(stack)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        nw = torch.empty((no, 2, self.wl.n_e, nc), dtype=torch.int64, device=dev)
+        Jw = torch.empty((no, 2, nc + 1), dtype=torch.int64, device=dev)
+        wi = pic_weighted_moments(self.ctx, stack, nw.data_ptr(), Jw.data_ptr())
+        return nw, Jw, wi
+
+    def weights(self, stack=0):
+        return pic_weights(self.ctx, stack)
+
+    def set_weights(self, w, stack=0):
+        pic_set_weights(self.ctx, stack, w)
 
     def ledger(self, stack=0):
         return pic_moments(self.ctx, stack, None, None)

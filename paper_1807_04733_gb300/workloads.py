@@ -45,6 +45,9 @@ FLAG_LOWEST_BIN_ANY = 8     # remove a lowest-bin carrier on ANY scattering even
 FLAG_STRICT_CAPACITY = 16   # capacity overflow is an error instead of drop-and-count
 FLAG_VELOCITY = 32          # also sum the velocities v*mu per (time, spin, cell)
 FLAG_WEIGHTS = 64           # superparticle weights w_i (importance-sampled source)
+# oracle only: random words keyed by lineage instead of slot (common random
+# numbers for finite differences); the library keys by slot
+FLAG_LINEAGE_KEYS = 128
 
 E_UNIFORM = 0               # injected energy uniform over the N_E bins
 E_MONO = 1                  # injected energy fixed per spin (k_mono[spin])
