@@ -319,6 +319,27 @@ pic_status pic_records(pic_ctx *ctx, int stack, pic_record *host_out, int64_t *n
 pic_status pic_set_records(pic_ctx *ctx, int stack, const pic_record *host_in,
                            int64_t n, uint64_t next_id);
 
+/* Checkpoint of a context's evolving state into a caller-owned host buffer:
+ * the step index, every stack's slots (records and, with PIC_F_WEIGHTS,
+ * weights), counters and ledger, the moment windows (densities, births and
+ * removals, generation and velocity sums, weighted sums) and the initial
+ * records pic_grad replays from, behind a header with a fingerprint of the
+ * parameters that define the run (launch-configuration fields excluded),
+ * the stacks, their tables and their excitation.  Storage of the superparticle
+ * state between runs is the paper's restart of the PIC dynamics; the format
+ * is this library's own.  buf NULL: *bytes receives the size needed.
+ * *bytes smaller than that: PIC_ERR_ARG (and *bytes = the size).
+ * Synchronises; returns any pending device status first. */
+pic_status pic_save(pic_ctx *ctx, void *buf, size_t *bytes);
+
+/* Restore a checkpoint of pic_save into a context created with the same
+ * parameters, stacks and tables and given the same excitation (pic_excite)
+ * as the saved one; a different fingerprint, size or a corrupt header is
+ * PIC_ERR_ARG and changes nothing.  Stepping on from the restored state
+ * gives the results of the uninterrupted run bit for bit (the random
+ * streams are keyed by step and slot). */
+pic_status pic_load(pic_ctx *ctx, const void *buf, size_t bytes);
+
 /* Wait for the context stream and return the pending device status. */
 pic_status pic_sync(pic_ctx *ctx);
 

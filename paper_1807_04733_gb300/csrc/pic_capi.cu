@@ -29,6 +29,7 @@ struct HostStack {
     std::vector<long long> inj;     // per half step
     pic_pulse pulse{};
     bool excited = false;
+    uint64_t bias_hash = 0;         // of the importance-sampling inputs of pic_excite
 };
 
 // Buffers of the adjoint replay, allocated by the first pic_grad: a second
@@ -130,6 +131,14 @@ thread_local std::string g_init_error;   // reason of the last failed pic_init
 
 const char *kStatusNames[] = {"PIC_OK", "PIC_ERR_ARG", "PIC_ERR_ALLOC", "PIC_ERR_CAPACITY",
                               "PIC_ERR_TIMEOUT", "PIC_ERR_CUDA", "PIC_ERR_STATE"};
+
+// 64-bit FNV-1a over bytes (the fingerprint of a checkpoint)
+uint64_t fnv1a(const void *data, size_t n, uint64_t h = 0xcbf29ce484222325ull)
+{
+    const unsigned char *b = static_cast<const unsigned char *>(data);
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 0x100000001b3ull; }
+    return h;
+}
 
 // floor(p * 2^32) saturated to [0, 2^32-1]: "x < threshold" with a uniform
 // 32-bit word x happens with probability threshold / 2^32.
@@ -752,6 +761,8 @@ pic_status pic_excite(pic_ctx *c, int stack, const pic_pulse *u)
         h.pulse = *u;
         h.pulse.cell_bias = nullptr;      // not kept: the tables are
         h.pulse.e_bias = nullptr;
+        h.bias_hash = fnv1a(u->cell_bias, u->cell_bias ? 8 * (size_t)h.n_cells : 0,
+                            fnv1a(u->e_bias, u->e_bias ? 8 * (size_t)c->p.n_e : 0));
         h.excited = true;
         d.n_cdf = (int32_t)thr.size();
         d.up_thr = threshold_of(u->up_frac);
@@ -971,6 +982,206 @@ pic_status pic_step(pic_ctx *c, int n_steps)
         c->step = s + 1;
         --left;
     }
+    return PIC_OK;
+}
+
+namespace {
+
+// What a checkpoint must match: the parameters that define the run (not the
+// launch configuration), the stacks, their tables and their excitation.
+uint64_t fingerprint(const pic_ctx *c)
+{
+    pic_params p = c->p;
+    p.blocks_per_sm = 0; p.hist_mode = 0; p.ring_stages = 0; p.use_graph = 0; p.consumer_warps = 0;
+    uint64_t h = fnv1a(&p, sizeof(p));
+    h = fnv1a(&c->n_stacks, sizeof(c->n_stacks), h);
+    for (const HostStack &s : c->hs) {
+        h = fnv1a(&s.d, sizeof(s.d), h);
+        h = fnv1a(s.v.data(), 4 * s.v.size(), h);
+        h = fnv1a(s.tau_in.data(), 8 * s.tau_in.size(), h);
+        h = fnv1a(s.tau_el.data(), 8 * s.tau_el.size(), h);
+        h = fnv1a(s.T.data(), 8 * s.T.size(), h);
+        h = fnv1a(s.p0.data(), 8 * s.p0.size(), h);
+        h = fnv1a(s.inj.data(), 8 * s.inj.size(), h);
+        pic_pulse u = s.pulse;
+        u.cell_bias = nullptr; u.e_bias = nullptr;
+        h = fnv1a(&u, sizeof(u), h);
+        h = fnv1a(&s.bias_hash, 8, h);
+    }
+    return h;
+}
+
+constexpr uint64_t kSaveMagic = 0x3130455641534950ull;   // "PISAVE01"
+
+struct SaveHeader {
+    uint64_t magic, fingerprint, bytes;
+    int32_t step, n_stacks, replayable, pad;
+};
+
+// The device arrays a checkpoint holds besides the particle slots, as
+// (pointer, bytes) pairs, in a fixed order.
+std::vector<std::pair<void *, size_t>> moment_arrays(pic_ctx *c)
+{
+    std::vector<std::pair<void *, size_t>> v;
+    const size_t ng = (size_t)(c->nh_total / (2 * c->p.n_e) + 1);
+    v.push_back({c->d_nh, 4 * (size_t)c->nh_total});
+    v.push_back({c->d_bd, 4 * (size_t)c->J_total});
+    v.push_back({c->d_gh, 8 * ng});
+    if (c->p.flags & PIC_F_VELOCITY_MOMENTS) v.push_back({c->d_vh, 8 * (size_t)(c->nh_total / c->p.n_e + 1)});
+    if (c->p.flags & PIC_F_WEIGHTS) {
+        v.push_back({c->d_nhw, 8 * (size_t)c->nh_total});
+        v.push_back({c->d_bdw, 8 * (size_t)c->J_total});
+    }
+    return v;
+}
+
+}  // namespace
+
+pic_status pic_save(pic_ctx *c, void *buf, size_t *bytes)
+{
+    if (!c || !bytes) return PIC_ERR_ARG;
+    const pic_status st0 = device_status(c);
+    if (st0 != PIC_OK) return st0;
+    const int S = c->n_stacks;
+    const bool wts = (c->p.flags & PIC_F_WEIGHTS) != 0;
+    std::vector<DevCounters> cnt(S);
+    DevCtl ctl{};
+    cudaError_t e = cudaMemcpyAsync(cnt.data(), c->d_cnt, sizeof(DevCounters) * S, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&ctl, c->d_ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_save");
+    const auto arrays = moment_arrays(c);
+    size_t need = sizeof(SaveHeader) + sizeof(DevCounters) * S;
+    for (int s = 0; s < S; ++s) {
+        need += (size_t)cnt[s].n_slots * (sizeof(pic_record) + (wts ? 4 : 0));
+        need += 16 + c->init_recs[s].size() * sizeof(pic_record);
+    }
+    for (const auto &x : arrays) need += x.second;
+    if (!buf) { *bytes = need; return PIC_OK; }
+    if (*bytes < need) { *bytes = need; return fail(c, PIC_ERR_ARG, "pic_save: buffer too small"); }
+    unsigned char *o = static_cast<unsigned char *>(buf);
+    SaveHeader hd{kSaveMagic, fingerprint(c), need, c->step, S, c->replayable ? 1 : 0, 0};
+    std::memcpy(o, &hd, sizeof(hd)); o += sizeof(hd);
+    std::memcpy(o, cnt.data(), sizeof(DevCounters) * S); o += sizeof(DevCounters) * S;
+    for (int s = 0; s < S && e == cudaSuccess; ++s) {
+        const int64_t n = (int64_t)cnt[s].n_slots, base = c->ds[s].base;
+        std::vector<float> z(n);
+        std::vector<uint32_t> id(n), mp(2 * n);
+        if (n) {
+            e = cudaMemcpyAsync(z.data(), c->d_z[ctl.cur] + base, 4 * n, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(mp.data(), c->d_mu[ctl.cur] + 2 * base, 8 * n, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(id.data(), c->d_id[ctl.cur] + base, 4 * n, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess && wts)
+                e = cudaMemcpyAsync(o + n * sizeof(pic_record), c->d_w[ctl.cur] + base, 4 * n, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            pic_record r;
+            r.z = z[i];
+            std::memcpy(&r.mu, &mp[2 * i], 4);
+            r.packed = mp[2 * i + 1];
+            r.id = id[i];
+            std::memcpy(o + i * sizeof(pic_record), &r, sizeof(r));
+        }
+        o += n * (sizeof(pic_record) + (wts ? 4 : 0));
+        const uint64_t ni = c->init_recs[s].size(), nid = c->init_next_id[s];
+        std::memcpy(o, &ni, 8); std::memcpy(o + 8, &nid, 8); o += 16;
+        if (ni) std::memcpy(o, c->init_recs[s].data(), ni * sizeof(pic_record));
+        o += ni * sizeof(pic_record);
+    }
+    for (const auto &x : arrays) {
+        if (e == cudaSuccess && x.second) e = cudaMemcpyAsync(o, x.first, x.second, cudaMemcpyDeviceToHost, c->stream);
+        o += x.second;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_save copy");
+    *bytes = need;
+    return PIC_OK;
+}
+
+pic_status pic_load(pic_ctx *c, const void *buf, size_t bytes)
+{
+    if (!c || !buf) return PIC_ERR_ARG;
+    const int S = c->n_stacks;
+    const bool wts = (c->p.flags & PIC_F_WEIGHTS) != 0;
+    SaveHeader hd{};
+    if (bytes < sizeof(hd)) return fail(c, PIC_ERR_ARG, "pic_load: not a checkpoint");
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != kSaveMagic || hd.bytes != bytes || hd.n_stacks != S)
+        return fail(c, PIC_ERR_ARG, "pic_load: not a checkpoint of this size");
+    if (hd.fingerprint != fingerprint(c))
+        return fail(c, PIC_ERR_ARG, "pic_load: the checkpoint belongs to other parameters, stacks, tables or excitation");
+    if (hd.step < 0 || hd.step > c->p.n_steps_max) return fail(c, PIC_ERR_ARG, "pic_load: step out of range");
+    const unsigned char *o = static_cast<const unsigned char *>(buf) + sizeof(hd);
+    std::vector<DevCounters> cnt(S);
+    std::memcpy(cnt.data(), o, sizeof(DevCounters) * S); o += sizeof(DevCounters) * S;
+    const auto arrays = moment_arrays(c);
+    size_t need = sizeof(SaveHeader) + sizeof(DevCounters) * S;
+    {
+        const unsigned char *q = o;
+        for (int s = 0; s < S; ++s) {
+            if (cnt[s].n_slots > (unsigned long long)c->hs[s].d.capacity)
+                return fail(c, PIC_ERR_ARG, "pic_load: more slots than the capacity");
+            const size_t rb = (size_t)cnt[s].n_slots * (sizeof(pic_record) + (wts ? 4 : 0));
+            need += rb + 16;
+            if (need > bytes) return fail(c, PIC_ERR_ARG, "pic_load: truncated checkpoint");
+            q += rb;
+            uint64_t ni = 0;
+            std::memcpy(&ni, q, 8);
+            if (ni > (uint64_t)c->hs[s].d.capacity) return fail(c, PIC_ERR_ARG, "pic_load: bad initial records");
+            need += ni * sizeof(pic_record);
+            q += 16 + ni * sizeof(pic_record);
+        }
+        for (const auto &x : arrays) need += x.second;
+        if (need != bytes) return fail(c, PIC_ERR_ARG, "pic_load: checkpoint size does not match");
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    DevCtl ctl{};
+    ctl.epoch = 1u;                       // fresh look-back words, particle buffer 0
+    for (int s = 0; s < S && e == cudaSuccess; ++s) {
+        const int64_t n = (int64_t)cnt[s].n_slots, base = c->ds[s].base;
+        std::vector<float> z(n);
+        std::vector<uint32_t> id(n), mp(2 * n);
+        for (int64_t i = 0; i < n; ++i) {
+            pic_record r;
+            std::memcpy(&r, o + i * sizeof(pic_record), sizeof(r));
+            z[i] = r.z;
+            std::memcpy(&mp[2 * i], &r.mu, 4);
+            mp[2 * i + 1] = r.packed;
+            id[i] = r.id;
+        }
+        if (n) {
+            e = cudaMemcpyAsync(c->d_z[0] + base, z.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mu[0] + 2 * base, mp.data(), 8 * n, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_id[0] + base, id.data(), 4 * n, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess && wts)
+                e = cudaMemcpyAsync(c->d_w[0] + base, o + n * sizeof(pic_record), 4 * n, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);      // host vectors go out of scope
+        }
+        o += n * (sizeof(pic_record) + (wts ? 4 : 0));
+        uint64_t ni = 0, nid = 0;
+        std::memcpy(&ni, o, 8); std::memcpy(&nid, o + 8, 8); o += 16;
+        c->init_recs[s].resize(ni);
+        if (ni) std::memcpy(c->init_recs[s].data(), o, ni * sizeof(pic_record));
+        c->init_next_id[s] = nid;
+        o += ni * sizeof(pic_record);
+    }
+    for (const auto &x : arrays) {
+        if (e == cudaSuccess && x.second) e = cudaMemcpyAsync(x.first, o, x.second, cudaMemcpyHostToDevice, c->stream);
+        o += x.second;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_cnt, cnt.data(), sizeof(DevCounters) * S, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_ctl, &ctl, sizeof(DevCtl), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned long long) * c->n_status, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_fspawn, 0, sizeof(uint32_t) * c->n_status, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_load copy");
+    c->step = hd.step;
+    c->flux_final = 0;                    // the fluxes are derived again from the counts
+    c->flux_final_w = 0;
+    c->dev_step_valid = false;
+    c->replayable = hd.replayable != 0;
+    c->replay_why = c->replayable ? "" : "pic_grad: the saved run could not be replayed";
     return PIC_OK;
 }
 

@@ -33,7 +33,7 @@ REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u
 EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_gen_moments",
            "pic_vel_moments", "pic_weighted_moments", "pic_weights", "pic_set_weights", "pic_grad",
            "pic_records",
-           "pic_set_records", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
+           "pic_set_records", "pic_save", "pic_load", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
            "pic_profile_read", "pic_compact_static", "pic_launch_config", "pic_launch_count",
            "pic_destroy", "pic_last_error", "pic_status_string", "pic_autotune")
 KERNEL_KINDS = ("inject", "step", "step_moments", "compact", "step_events", "adjoint_step",
@@ -134,6 +134,8 @@ def lib():
         L.pic_weighted_moments.argtypes = [P, C.c_int, P, P, C.POINTER(C.c_uint64)]
         L.pic_weights.argtypes = [P, C.c_int, P, C.POINTER(C.c_int64)]
         L.pic_set_weights.argtypes = [P, C.c_int, P, C.c_int64]
+        L.pic_save.argtypes = [P, P, C.POINTER(C.c_size_t)]
+        L.pic_load.argtypes = [P, P, C.c_size_t]
         L.pic_grad.argtypes = [P, P, P, P, P]
         L.pic_records.argtypes = [P, C.c_int, P, C.POINTER(C.c_int64)]
         L.pic_set_records.argtypes = [P, C.c_int, P, C.c_int64, C.c_uint64]
@@ -287,6 +289,20 @@ def pic_weights(ctx, stack):
 def pic_set_weights(ctx, stack, w):
     w = np.ascontiguousarray(w, np.uint32)
     _check(lib().pic_set_weights(ctx, stack, w.ctypes.data if len(w) else None, len(w)), ctx)
+
+
+def pic_save(ctx):
+    """The context's checkpoint as bytes."""
+    n = C.c_size_t(0)
+    _check(lib().pic_save(ctx, None, C.byref(n)), ctx)
+    buf = (C.c_ubyte * n.value)()
+    _check(lib().pic_save(ctx, buf, C.byref(n)), ctx)
+    return bytes(buf)
+
+
+def pic_load(ctx, data):
+    buf = (C.c_ubyte * len(data)).from_buffer_copy(data)
+    _check(lib().pic_load(ctx, buf, len(data)), ctx)
 
 
 def pic_gen_moments(ctx, stack, g_dev_ptr):
@@ -465,6 +481,14 @@ class Context:
         Jw = torch.empty((no, 2, nc + 1), dtype=torch.int64, device=dev)
         wi = pic_weighted_moments(self.ctx, stack, nw.data_ptr(), Jw.data_ptr())
         return nw, Jw, wi
+
+    def save(self):
+        """Checkpoint of the evolving state (pic_save), as bytes."""
+        return pic_save(self.ctx)
+
+    def load(self, data):
+        """Restore a checkpoint of a context with the same workload (pic_load)."""
+        pic_load(self.ctx, data)
 
     def weights(self, stack=0):
         return pic_weights(self.ctx, stack)
