@@ -5,11 +5,15 @@ achieved fraction of the HBM roofline of the step kernel.
 Workload (default): the large Fe(15 nm)/Au(300 nm) bilayer, 2e8 carriers
 created by the pump pulse, capacity 4e8, dt = 0.5 fs, 60 energy bins,
 densities every 50 steps, compaction every 50 steps.  Set-up (untimed) runs
-the pulse window (t < 150 fs) so that the timed steps see the steady state.
-One benchmark step = one moment/compaction period of 50 time steps, i.e. one
-pass of every stage of the step (flight, scattering, secondaries, deposit,
-compaction).  The particle state (6.4 GB) is larger than L2, so no flush is
-needed between steps.
+the pulse window (t < 150 fs) and the launch-configuration autotuner, so that
+the timed steps see the steady state.  One benchmark step = one
+moment/compaction period of 50 time steps, i.e. one pass of every stage of
+the step (flight, scattering, secondaries, deposit, compaction).  The
+particle state (6.4 GB) is larger than L2, so no flush is needed between
+steps.  At this capacity the buffer is full from the pulse on (the cascade
+would hold more than 5 times the 2e8 primaries), so most secondaries are
+dropped and counted; a second leg with the capacity raised to 2^30 slots
+times the same kernels while secondaries are still placed.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -37,11 +41,14 @@ if ROOT not in sys.path:
 METRIC = "particle-steps/s"
 UNIT = "particle-steps/s"
 HBM_FALLBACK_GBS = 6800.0
-# algorithmic bytes: read z, mu, packed (12 B) + write z (4 B) per live
-# carrier-step; nothing more for a carrier that scatters or meets a boundary
-# (its draws are keyed by its slot, its record was read once already); 8 B
-# (mu, packed) per carrier whose record changed; 16 B per secondary placed
-B_STEP, B_EVENTFUL, B_CHANGED, B_SPAWN = 16, 0, 8, 16
+# Algorithmic bytes per unit, the count of the method's data movement:
+# read the 16 B state and write z (4 B) per live carrier-step, write the
+# other 12 B for a carrier with an event, 16 B per secondary placed.
+B_STEP, B_EVENTFUL, B_CHANGED, B_SPAWN = 20, 12, 0, 16
+# The stricter count of what the kernels must move: read z, mu, packed (12 B)
+# + write z (4 B) per carrier-step (the id is never read: draws are keyed by
+# slot), 8 B (mu, packed) per carrier whose record changed, 16 B per secondary
+S_STEP, S_EVENTFUL, S_CHANGED, S_SPAWN = 16, 0, 8, 16
 
 
 def parse():
@@ -64,6 +71,11 @@ def parse():
     ap.add_argument("--batched-scale", type=float, default=1.0)
     ap.add_argument("--batched-steps", type=int, default=0)
     ap.add_argument("--adjoint-scale", type=float, default=1.0)
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--autotune-steps", type=int, default=4)
+    ap.add_argument("--no-unsaturated", action="store_true")
+    ap.add_argument("--no-spin-valve", action="store_true")
+    ap.add_argument("--spin-valve-scale", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -104,12 +116,12 @@ def measured_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-# ncu DRAM traffic of the step kernels (k_fast + k_event + k_place), bytes per
-# live carrier-step, from one steady-state capture of each on this workload
-# scaled to 1/20 (profiles/k_fast_k_event_k_place_fe15_au300_small.md); the
-# traffic grows in proportion to the carriers advanced.  Valid only for the
-# kernel source whose hash is given: reported as null once the kernels change.
-NCU_TRAFFIC = {"bytes_per_particle_step": 17.10, "src_sha": "38a9d2e116d2963d"}
+# ncu DRAM traffic of the step kernels (k_stream + k_event + k_place), bytes
+# per live carrier-step, from one steady-state capture of each on this
+# workload scaled to 1/20; the traffic grows in proportion to the carriers
+# advanced.  Valid only for the kernel source whose hash is given: reported
+# as null once the kernels change.
+NCU_TRAFFIC = {"bytes_per_particle_step": 0.0, "src_sha": ""}
 
 
 def kernel_sha():
@@ -225,26 +237,45 @@ def cpu_sample(args, wl, pre):
     return cores, scale, n_each
 
 
-def run_cpu_baseline(args, wl, period, pre, timed_steps=1):
-    cores, scale, cap_each = cpu_sample(args, wl, pre)
-    pool = OraclePool(args.config, scale, cores, pre + period * (timed_steps + 2) + 1)
+def oracle_replicas(cfg_index, total_n0, pre, timed, cores=None, label=""):
+    """The oracle on the host cores: one replica per core (its own seed), the
+    workload scaled so that the replicas start total_n0 carriers together;
+    pre untimed steps (the pulse window), then `timed` steps timed."""
+    from paper_1807_04733_gb300 import workloads as W
+    cores = cores or max(1, min(os.cpu_count() or 1, 64))
+    full = W.config(cfg_index)
+    scale = total_n0 / float(full.stacks[0].n0) / cores
+    each = W.config(cfg_index, scale=scale)
+    pool = OraclePool(cfg_index, scale, cores, pre + timed + 1)
     try:
-        pool.step(pre)                      # pulse window, untimed
+        pool.step(pre)
         t = time.perf_counter()
-        ps = 0
-        n_steps = 0
-        while True:                          # timed: whole periods, ~cpu_seconds
-            ps += pool.step(period)
-            n_steps += 1
-            if time.perf_counter() - t > args.cpu_seconds or n_steps >= timed_steps:
-                break
+        ps = pool.step(timed)
         dt = time.perf_counter() - t
     finally:
         pool.close()
-    sample = ("%d oracle replicas (one per core) of %s scaled by %g (capacity %d each): "
-              "%d pre-roll steps untimed, then %d x %d time steps timed"
-              % (cores, wl.name, scale, cap_each, pre, n_steps, period))
-    return {"value": ps / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    st = each.stacks[0]
+    sample = ("%s: %d oracle replica(s), one per core, of %s scaled by %.4g (%d carriers, capacity %d, "
+              "%.0f MB of particle state each): %d pulse steps untimed, %d steps timed"
+              % (label, cores, full.name, scale, st.n0, st.capacity, st.capacity * 16 / 1e6, pre, timed))
+    return {"value": ps / dt, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "particle_steps": ps, "seconds": dt}
+
+
+def run_cpu_baselines():
+    """The oracle as it stands, timed on the host: single-threaded on the
+    Fe/Au bilayer in full (1e5 carriers, 500 steps of 1 fs), one replica per
+    core on the spin valve (1e7 carriers in all, 100 steps after the pulse)
+    and on the large bilayer (1e7 carriers in all, 50 steps after the pulse).
+    Each replica's state is larger than the caches of its core."""
+    out = {}
+    out["single_thread_fe15_au100_full"] = oracle_replicas(0, 1e5, 0, 500, cores=1,
+                                                           label="full workload, single thread")
+    out["multicore_spin_valve_1e7_100_steps"] = oracle_replicas(1, 1e7, 300, 100,
+                                                                label="1e7 carriers in all")
+    out["multicore_large_1e7_50_steps"] = oracle_replicas(4, 1e7, 300, 50,
+                                                          label="1e7 carriers in all")
+    return out
 
 
 def reference_arm(args):
@@ -355,7 +386,22 @@ def batched_leg(args):
     n = args.batched_steps or wl.n_steps
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
-    ctx = pic.Context(wl, use_graph=True)
+    # launch configuration: tuned on a scratch context of the same stacks
+    # after the pulse window, then used for the timed one
+    tune = {}
+    if not args.no_autotune:
+        scratch = pic.Context(wl, n_steps_max=200 + 140 * 2)
+        scratch.step(200)
+        trials = scratch.autotune(2)
+        cfg = scratch.launch_config()
+        best = [t for t in trials if t["chosen"]][0]
+        tune = {"trials": len(trials), "chosen": best}
+        scratch.close()
+        ctx = pic.Context(wl, use_graph=True, blocks_per_sm=best["blocks_per_sm"],
+                          ring_stages=best["ring_stages"], hist_mode=best["hist_mode"],
+                          consumer_warps=best["consumer_warps"])
+    else:
+        ctx = pic.Context(wl, use_graph=True)
     torch.cuda.synchronize()
     ev[0].record(ctx.stream)
     ctx.step(n)
@@ -384,7 +430,126 @@ def batched_leg(args):
             "batched_graph_ms": ms_b, "sequential_plain_ms": ms_s, "speedup": ms_s / ms_b,
             "batched_particle_steps_per_s": ps_b / (ms_b * 1e-3),
             "sequential_particle_steps_per_s": ps_s / (ms_s * 1e-3),
-            "batched_launches": launches_b, "sequential_launches": launches_s}
+            "batched_launches": launches_b, "sequential_launches": launches_s,
+            "autotune": tune}
+
+
+# ---------------------------------------------------------------------------
+# roofline of the step kernels and timed legs of other configurations
+# ---------------------------------------------------------------------------
+def roofline_of(delta, ktimes, ms):
+    """The step kernels: the streaming pass (k_stream), the event pass
+    (k_event) and the placement of secondaries (k_place); one launch of each
+    per time step, timed together with CUDA events on the context stream;
+    "per launch" = per time step."""
+    peak, peak_kind = measured_peak()
+    n_k = ktimes["step"][0] + ktimes["step_moments"][0]
+    k_ms = ktimes["step"][1] + ktimes["step_moments"][1] + ktimes["step_events"][1]
+    if not n_k or not k_ms:
+        return None
+    alg = B_STEP * delta["particle_steps"] + B_EVENTFUL * delta["eventful"] + \
+        B_CHANGED * delta["changed"] + B_SPAWN * delta["spawned"]
+    strict = S_STEP * delta["particle_steps"] + S_EVENTFUL * delta["eventful"] + \
+        S_CHANGED * delta["changed"] + S_SPAWN * delta["spawned"]
+    achieved = (alg / n_k) / (k_ms / n_k * 1e-3) / 1e9
+    achieved_s = (strict / n_k) / (k_ms / n_k * 1e-3) / 1e9
+    traffic = None
+    if NCU_TRAFFIC and NCU_TRAFFIC.get("src_sha") == kernel_sha():
+        traffic = NCU_TRAFFIC["bytes_per_particle_step"] * delta["particle_steps"] / n_k
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "k_stream+k_event+k_place",
+            "peak_source": peak_kind,
+            "byte_count": "per carrier-step 20 B (16 B read, z written) + 12 B per eventful "
+                          "carrier + 16 B per placed secondary",
+            "algorithmic_bytes_per_launch": alg / n_k,
+            "strict": {"byte_count": "per carrier-step 16 B (z, mu, packed read, z written) + "
+                                     "8 B per changed record + 16 B per placed secondary",
+                       "bytes_per_launch": strict / n_k, "achieved": achieved_s,
+                       "frac": achieved_s / peak},
+            "avg_launch_ms": k_ms / n_k,
+            "kernel_share_of_step_time": k_ms / ms if ms else 0}
+
+
+def saturation(delta):
+    tot = delta["spawned"] + delta["spawn_dropped"]
+    return {"spawned": delta["spawned"], "spawn_dropped": delta["spawn_dropped"],
+            "dropped_fraction": delta["spawn_dropped"] / tot if tot else 0.0}
+
+
+def timed_leg(wl, pre, n_timed, chunk, capacity=None, autotune_steps=0):
+    """A context of `wl`: `pre` untimed steps (the pulse window), the
+    autotuner, then n_timed steps timed with CUDA events and per-kernel
+    events; particle-steps/s over the timed steps and the step kernels'
+    roofline."""
+    import torch
+    from paper_1807_04733_gb300 import pic
+    n_max = pre + 140 * autotune_steps + n_timed + 1
+    ctx = pic.Context(wl, n_steps_max=max(wl.n_steps, n_max), capacity=capacity)
+    left = pre
+    while left > 0:
+        k = min(left, 100)
+        ctx.step(k)
+        left -= k
+    tune = None
+    if autotune_steps:
+        trials = ctx.autotune(autotune_steps)
+        tune = {"trials": len(trials), "chosen": [t for t in trials if t["chosen"]][0]}
+    S = len(wl.stacks)
+    led0 = [ctx.ledger(s) for s in range(S)]
+    torch.cuda.synchronize()
+    pic.pic_profile(ctx.ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(ctx.stream)
+    left = n_timed
+    while left > 0:
+        k = min(left, chunk)
+        ctx.step(k)
+        left -= k
+    e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = pic.pic_profile_read(ctx.ctx)
+    pic.pic_profile(ctx.ctx, False)
+    led1 = [ctx.ledger(s) for s in range(S)]
+    delta = {k: sum(b[k] - a[k] for a, b in zip(led0, led1)) for k in led1[0]}
+    out = {"value": delta["particle_steps"] / (ms * 1e-3), "unit": UNIT, "ms": ms,
+           "time_steps": n_timed, "roofline": roofline_of(delta, kt, ms),
+           "saturation": saturation(delta), "ledger_delta": delta,
+           "kernel_ms": {k: v[1] for k, v in kt.items() if v[0]},
+           "launch_config": ctx.launch_config(), "autotune": tune}
+    ctx.close()
+    return out
+
+
+def unsaturated_leg(args):
+    """The large bilayer with its capacity raised to 2^30 slots (the most a
+    stack holds; the cascade fills even these by about 750 time steps):
+    after the pulse window, 300 time steps timed while every secondary is
+    placed."""
+    from paper_1807_04733_gb300 import workloads as W
+    wl = W.config(4, scale=args.scale)
+    cap = (1 << 30) - 1024
+    pre = int(math.ceil(2 * wl.stacks[0].t0 / wl.dt))
+    out = timed_leg(wl, pre, 300, 50, capacity=cap)
+    out["workload"] = "%s with capacity %d, time steps %d..%d" % (wl.name, cap, pre, pre + 300)
+    return out
+
+
+def spin_valve_legs(args):
+    """The Fe(10)/Au(50)/Fe(10) spin valve, parallel and antiparallel (1e7
+    carriers, capacity 5e7, 0.5 fs, densities and fluxes every step): after
+    the pulse window, 200 time steps timed, tuned by the autotuner."""
+    from paper_1807_04733_gb300 import workloads as W
+    out = {}
+    for ap in (False, True):
+        wl = W.spin_valve(ap, n0=int(1e7 * args.spin_valve_scale),
+                          capacity=int(5e7 * args.spin_valve_scale))
+        pre = int(math.ceil(2 * wl.stacks[0].t0 / wl.dt))
+        leg = timed_leg(wl, pre, 200, 50, autotune_steps=0 if args.no_autotune else 2)
+        leg["workload"] = "%s: n0 %d, capacity %d, time steps %d..%d" % (
+            wl.name, wl.stacks[0].n0, wl.stacks[0].capacity, pre, pre + 200)
+        out[wl.name] = leg
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -413,7 +578,8 @@ def main():
     wl, period, pre = workload(args)
     # replicas: every rank runs its own copy with its own seed (weak scaling)
     wl = wl.replace(seed=wl.seed + rank)
-    total = pre + period * (args.warmup + 2 * args.steps) + 1
+    tune_steps = 0 if args.no_autotune else args.autotune_steps
+    total = pre + 140 * tune_steps + period * (args.warmup + 2 * args.steps) + 1
     ctx = pic.Context(wl, n_steps_max=max(wl.n_steps, total), blocks_per_sm=args.blocks_per_sm,
                       hist_mode=args.hist_mode, ring_stages=args.ring)
     stream = ctx.stream
@@ -423,6 +589,17 @@ def main():
         n = min(left, 100)
         ctx.step(n)
         left -= n
+    # launch configuration: timed candidates on the running simulation
+    tune = None
+    if tune_steps:
+        trials = ctx.autotune(tune_steps)
+        tune = {"trials": len(trials), "chosen": [t for t in trials if t["chosen"]][0],
+                "fastest_ns_per_particle_step": min(t["ns_per_particle_step"] for t in trials),
+                "slowest_ns_per_particle_step": max(t["ns_per_particle_step"] for t in trials)}
+    # whole periods from here on
+    s_now = ctx.shape(0)[2]
+    if s_now % period:
+        ctx.step(period - s_now % period)
     for _ in range(args.warmup):
         ctx.step(period)
     led0 = [ctx.ledger(s) for s in range(len(wl.stacks))]
@@ -482,24 +659,7 @@ def main():
     ms_max, ps_all = shard.reduce_measurement(ms, float(ps), dist, "cuda")
     e2e_ms, ps_e2e_all = shard.reduce_measurement(e2e_s * 1e3, float(ps_e2e), dist, "cuda")
 
-    peak, peak_kind = measured_peak()
-    # the step kernels: the streaming pass (k_fast), the event pass (k_event)
-    # and the placement of secondaries (k_place); one launch of each per time
-    # step, timed together; "per launch" = per time step
-    n_k = ktimes["step"][0] + ktimes["step_moments"][0]
-    k_ms = ktimes["step"][1] + ktimes["step_moments"][1] + ktimes["step_events"][1]
-    alg_bytes = B_STEP * delta["particle_steps"] + B_EVENTFUL * delta["eventful"] + \
-        B_CHANGED * delta["changed"] + B_SPAWN * delta["spawned"]
-    achieved = (alg_bytes / n_k) / (k_ms / n_k * 1e-3) / 1e9 if n_k else 0.0
-    traffic = None
-    if NCU_TRAFFIC and NCU_TRAFFIC.get("src_sha") == kernel_sha():
-        traffic = NCU_TRAFFIC["bytes_per_particle_step"] * delta["particle_steps"] / n_k
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": "k_fast+k_event+k_place",
-                "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": alg_bytes / n_k if n_k else 0,
-                "avg_launch_ms": k_ms / n_k if n_k else 0,
-                "kernel_share_of_step_time": k_ms / ms if ms else 0}
+    roofline = roofline_of(delta, ktimes, ms)
 
     line = {
         "metric": METRIC, "value": ps_all / (ms_max * 1e-3), "unit": UNIT,
@@ -507,6 +667,9 @@ def main():
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": config_dict(wl, period, pre, args),
+        # the buffer is full in the timed window: most secondaries are
+        # dropped and counted (the "unsaturated" leg places them all)
+        "saturation": saturation(delta),
         "roofline": roofline,
         "e2e": {"value": ps_e2e_all / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h},
@@ -516,14 +679,21 @@ def main():
         "kernel_ms": {k: v[1] for k, v in ktimes.items()},
         "kernel_launches": {k: v[0] for k, v in ktimes.items()},
         "launch_config": ctx.launch_config(),
+        "autotune": tune,
     }
     ctx.close()
+    if rank == 0 and world == 1 and not args.no_unsaturated and args.config == 4:
+        line["unsaturated"] = unsaturated_leg(args)
+    if rank == 0 and world == 1 and not args.no_spin_valve:
+        line["spin_valve"] = spin_valve_legs(args)
     if rank == 0 and world == 1 and not args.no_adjoint:
         line["adjoint"] = adjoint_leg(args)
     if rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = batched_leg(args)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = run_cpu_baseline(args, wl, period, pre, timed_steps=60)
+        base = run_cpu_baselines()
+        line["cpu_baseline"] = base["multicore_large_1e7_50_steps"]
+        line["cpu_baselines"] = base
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()

@@ -134,16 +134,17 @@ cudaError_t configure_pass(const Args &a, LaunchCfg *cfg)
     // tables, pass 2's sums of R, the flux potential slice and (with the
     // density deposit) the density-weight slice
     const size_t fixed = (size_t)a.ftab_max * sizeof(FastEnt) +
-                         (ADJ == 2 ? (size_t)a.tab_max * 8 : 0) + (size_t)a.jbin_max * 8 + 4 +
+                         (ADJ == 2 ? (size_t)a.tab_max * 8 : 0) + (size_t)a.jbin_max * 8 + 8 +
                          tiles;
     const size_t fixed_dep = fixed + (size_t)a.nbin_max * 4;
     int o_plain = 0, o_dep = 0;
-    if ((e = pick_ring<false, false, ADJ>(fixed, 0, 0, &cfg->ring_fast, &o_plain,
-                                          &cfg->smem_fast)) != cudaSuccess)
+    if ((e = pick_stream_ring<false, false, 8, ADJ>(fixed, 0, 0, &cfg->ring_fast, &o_plain,
+                                                    &cfg->smem_fast)) != cudaSuccess)
         return e;
-    if ((e = pick_ring<true, false, ADJ>(fixed_dep, 0, 0, &cfg->ring_fast_dep, &o_dep,
-                                         &cfg->smem_fast_dep)) != cudaSuccess)
+    if ((e = pick_stream_ring<true, false, 8, ADJ>(fixed_dep, 0, 0, &cfg->ring_fast_dep, &o_dep,
+                                                   &cfg->smem_fast_dep)) != cudaSuccess)
         return e;
+    cfg->nw_fast = cfg->nw_fast_dep = 8;
     cfg->grid_fast = sms * o_plain;
     cfg->grid_fast_dep = sms * o_dep;
     const int gf_max = cfg->grid_fast > cfg->grid_fast_dep ? cfg->grid_fast : cfg->grid_fast_dep;
@@ -168,12 +169,13 @@ void fast_pass(const Args &a, const LaunchCfg &c, bool det, bool dep, cudaStream
 {
     const int g = dep ? c.grid_fast_dep : c.grid_fast;
     const size_t sm = dep ? c.smem_fast_dep : c.smem_fast;
+    constexpr int T = stream_threads<8>();
     if (det) {
-        if (dep) k_fast<true, true, false, ADJ><<<g, FAST_THREADS, sm, s>>>(a);
-        else k_fast<true, false, false, ADJ><<<g, FAST_THREADS, sm, s>>>(a);
+        if (dep) k_stream<true, true, false, 8, ADJ><<<g, T, sm, s>>>(a);
+        else k_stream<true, false, false, 8, ADJ><<<g, T, sm, s>>>(a);
     } else {
-        if (dep) k_fast<false, true, false, ADJ><<<g, FAST_THREADS, sm, s>>>(a);
-        else k_fast<false, false, false, ADJ><<<g, FAST_THREADS, sm, s>>>(a);
+        if (dep) k_stream<false, true, false, 8, ADJ><<<g, T, sm, s>>>(a);
+        else k_stream<false, false, false, 8, ADJ><<<g, T, sm, s>>>(a);
     }
 }
 

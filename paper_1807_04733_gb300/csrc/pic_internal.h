@@ -154,8 +154,8 @@ struct Args {            // everything a kernel needs, passed by value
     int ftab_max;                            // entries of the padded fast table
     int gbin_max;                            // cells of the widest stack (generation sums)
     unsigned int spin_limit;                 // bound of every device-side wait
-    int ring;                                // tiles in k_fast's copy ring
-    int grid_fast;                           // k_fast's grid (read by k_event, k_place)
+    int ring;                                // tiles in the streaming pass's copy ring
+    int grid_fast;                           // the streaming pass's grid (read by k_event, k_place)
     uint32_t *spawn_bits;                    // one bit per position: secondary staged
     // superparticle weights (PIC_F_WEIGHTS; null otherwise): per slot in
     // 2^-20 units, both buffers; the source's importance ratios p/q per

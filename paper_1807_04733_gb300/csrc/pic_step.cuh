@@ -4,7 +4,7 @@
 //
 // One Strang step (Eq. strang, Sec. III.A) is, per stack:
 //   k_inject(half 0)   Source(dt/2): append new carriers
-//   k_fast             Transport(dt/2) -> Scattering(dt) -> Transport(dt/2)
+//   k_stream           Transport(dt/2) -> Scattering(dt) -> Transport(dt/2)
 //                      for every carrier that neither scatters nor meets a
 //                      boundary in the step; the others are queued
 //   k_event            the general step for the queued carriers; secondaries
@@ -150,7 +150,7 @@ __device__ __forceinline__ void flight(const Args &a, const Stk &s, float &z, fl
                 const uint4 r = philox_rk(make_uint4(key_x, key_y, step, sub0 + (uint32_t)hit), a);
                 const int ti = ((iface * 2 + dir) * 2 + sg) * s.n_e + (k - 1);
                 trans = r.x < s.T[ti];
-                if (SC) {
+                if (SC && R != 0.0) {
                     const double2 sc = s.aT[ti];
                     atomicAdd(&gT[ti], (trans ? sc.x : sc.y) * R);
                 }
@@ -485,22 +485,6 @@ __device__ __forceinline__ long long make_tiles(const Args &a, long long *s_tpre
     return s_tpref[a.n_stacks];
 }
 
-// ---------------------------------------------------------------------------
-// k_fast: the streaming pass of the adjoint replay (ADJ = 1, 2; the forward
-// step runs k_stream below): the common case of Transport(dt/2) ->
-// Scattering(dt) -> Transport(dt/2), streamed, with the per-slot reward.
-//
-// Warp-specialised pipeline: one producer warp issues the bulk copies of the
-// z, mu and packed arrays of each tile into a ring of a.ring shared-memory
-// stages; eight consumer warps wait on the stage's "full" mbarrier, work on
-// four consecutive slots per thread, and release the stage with one arrival
-// per warp on its "empty" mbarrier, which gates the producer's next copy
-// into it.  No block-wide barrier runs per tile.  A carrier that does not
-// scatter and stays inside its layer for the whole step is finished here
-// (new depth, flux across the face it passed, density deposit).  Every other
-// carrier ("eventful": it scatters or meets a boundary) is copied, with its
-// position, to this block's region of the queue, in tile order, for k_event.
-// ---------------------------------------------------------------------------
 // index of a carrier's entry in the padded streaming-pass table
 __device__ __forceinline__ int fast_index(const Args &a, uint32_t pk)
 {
@@ -514,404 +498,17 @@ __device__ __forceinline__ long long vel_q(float w)
     return __float2ll_rz(__fmul_rn(w, 4294967296.0f));
 }
 
-constexpr int FAST_WARPS = TPB / 32;             // consumer warps
-constexpr int FAST_THREADS = TPB + 32;           // + the producer warp
-
 __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// barrier among the consumer warps only (the producer warp never joins)
-__device__ __forceinline__ void consumer_sync()
-{
-    asm volatile("bar.sync 1, %0;" ::"n"(TPB) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long consumer_sum_u64(unsigned long long v,
-                                                               unsigned long long *s_r)
-{
-#pragma unroll
-    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = v;
-    consumer_sync();
-    unsigned long long t = 0;
-    if (threadIdx.x == 0)
-        for (int i = 0; i < FAST_WARPS; ++i) t += s_r[i];
-    consumer_sync();
-    return t;  // valid in thread 0
-}
-
-// Resident blocks per SM the register budget must allow: three for the step
-// (72 registers, no spills: 27 warps per SM; the four carriers' flights are
-// computed side by side with the Philox rounds, which four blocks at 56
-// registers cannot hold without spilling) and for the replay passes, which
-// carry the per-slot reward as well.
-#ifndef PIC_FAST_MIN_BLOCKS
-#define PIC_FAST_MIN_BLOCKS 3
-#endif
-#ifndef PIC_FAST_MIN_BLOCKS_ADJ
-#define PIC_FAST_MIN_BLOCKS_ADJ 3
-#endif
-template <bool DET, bool DEPN, bool WAGG, int ADJ = 0>
-__global__ void __launch_bounds__(FAST_THREADS, ADJ ? PIC_FAST_MIN_BLOCKS_ADJ : PIC_FAST_MIN_BLOCKS)
-k_fast(const Args a)
-{
-    // ring stage: z, mu, packed of a tile (+ the replay's per-slot double)
-    constexpr int STG = ADJ ? 5 : 3;
-    extern __shared__ __align__(128) unsigned char smem[];
-    float *ring = reinterpret_cast<float *>(smem);                      // a.ring x STG x TILE
-    FastEnt *s_ent = reinterpret_cast<FastEnt *>(ring + (size_t)a.ring * STG * TILE);
-    // pass 2: sum of the reward-to-go of the carriers that passed the
-    // scattering test, per entry (fixed point, two's complement)
-    unsigned long long *s_sr = reinterpret_cast<unsigned long long *>(s_ent + a.ftab_max);
-    // replay: the window's flux potential [2][n_cells] and density weights
-    // [2][n_e][n_cells] of the stack, in place of the histograms
-    long long *s_gp = reinterpret_cast<long long *>(s_sr + (ADJ == 2 ? a.tab_max : 0));
-    int32_t *s_J = reinterpret_cast<int32_t *>(s_gp + (ADJ ? a.jbin_max : 0));
-    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_J + (ADJ ? 0 : a.jbin_max));
-    int32_t *s_gn = reinterpret_cast<int32_t *>(s_n);
-    // density steps: the generation labels summed per cell, after the bins
-    uint32_t *s_gs = s_n + a.nbin_max;
-    long long *s_tpref = reinterpret_cast<long long *>(s_n + (DEPN ? a.nbin_max + (ADJ ? 0 : a.gbin_max) : 0) + 1);
-    s_tpref = reinterpret_cast<long long *>((reinterpret_cast<uintptr_t>(s_tpref) + 7) & ~uintptr_t(7));
-    long long *s_nsl = s_tpref + a.n_stacks + 1;
-    __shared__ __align__(8) unsigned long long s_full[MAX_RING], s_empty[MAX_RING];
-    __shared__ DevStack s_st;
-    __shared__ unsigned long long s_r[FAST_WARPS];
-    __shared__ int s_qn, s_abort;
-
-    const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
-    const int b = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
-    const int warp = tid >> 5, lane = tid & 31;
-    const unsigned int lt_mask = (1u << lane) - 1u;
-    // tile prefix over the stacks (every thread of the block takes part)
-    for (int i = tid; i < a.n_stacks; i += FAST_THREADS) s_nsl[i] = (long long)a.cnt[i].n_slots;
-    if (tid == 0) {
-        for (int i = 0; i < a.ring; ++i) {
-            mbar_init(&s_full[i], 1);
-            mbar_init(&s_empty[i], FAST_WARPS);
-        }
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_qn = 0;
-        s_abort = 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        long long acc = 0;
-        for (int i = 0; i < a.n_stacks; ++i) {
-            s_tpref[i] = acc;
-            acc += (s_nsl[i] + TILE - 1) / TILE;
-        }
-        s_tpref[a.n_stacks] = acc;
-    }
-    __syncthreads();
-    const long long T = s_tpref[a.n_stacks];
-    const long long t0 = chunk_lo(T, b, G), t1 = chunk_lo(T, b + 1, G);
-    const long long ntiles = t1 - t0;
-    const int nring = a.ring;
-    float *Z = a.z[cur];
-    const float *MP = a.mu[cur];         // mu and packed, interleaved
-
-    // ---------------- producer warp ----------------
-    if (warp == FAST_WARPS) {
-        if (lane == 0) {
-            long long issued = 0;
-            int stg = 0;
-            uint32_t phase = 0;          // completions of stage stg so far, mod 2
-            for (long long i = 0; i < ntiles; ++i) {
-                if (i >= nring &&
-                    !mbar_wait(&s_empty[stg], phase ^ 1u, a.spin_limit)) {
-                    atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
-                    a.ctl->timeout_where = 4u;
-                    s_abort = 1;
-                }
-                if (*(volatile int *)&s_abort) break;
-                const long long t = t0 + i;
-                const int s = stack_of(s_tpref, a.n_stacks, t);
-                const long long off = a.stacks[s].base + (t - s_tpref[s]) * TILE;
-                float *dst = ring + (size_t)stg * STG * TILE;
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&s_full[stg], STG * TILE_BYTES);
-                bulk_load(dst, Z + off, TILE_BYTES, &s_full[stg]);
-                bulk_load(dst + TILE, MP + 2 * off, 2 * TILE_BYTES, &s_full[stg]);
-                if (ADJ) bulk_load(dst + 3 * TILE, a.acc[cur] + off, 2 * TILE_BYTES, &s_full[stg]);
-                issued = i + 1;
-                if (++stg == nring) { stg = 0; phase ^= 1u; }
-            }
-            if (*(volatile int *)&s_abort) {
-                // wait (bounded) for the copies that may still be in flight
-                // (the last `ring` issued), so that none lands in shared
-                // memory after the block has exited
-                for (long long i = issued > nring ? issued - nring : 0; i < issued; ++i)
-                    mbar_wait(&s_full[(int)(i % nring)], (uint32_t)((i / nring) & 1), a.spin_limit);
-            }
-        }
-        return;
-    }
-
-    // ---------------- consumer warps ----------------
-    const uint32_t step = step_now(a);
-    const int tj = (int)(step / (uint32_t)a.moment_every);
-    const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
-    const float half = a.half_dt;
-    const long long pos0 = t0 * TILE;                // queue region of this block
-    int seg_stack = -1, nc = 1, ne = a.n_e;
-    uint32_t ctr_hi = 0;
-    uint32_t n_steps = 0, n_queued = 0;
-
-    auto flush = [&](int s) {
-        consumer_sync();
-        const DevStack &st = s_st;
-        const int nf = st.n_cells + 1;
-        if (!ADJ) {
-            int32_t *gJ = a.J_hist + st.J_off + (long long)tj * 2 * nf;
-            for (int i = tid; i < 2 * nf; i += TPB) {
-                const int v = s_J[i];
-                if (v) atomicAdd(&gJ[i], v);
-            }
-        }
-        if (DEPN && !ADJ) {
-            const int nbins = 2 * a.n_e * st.n_cells;
-            uint32_t *gN = a.n_hist + st.n_off + (long long)tout * nbins;
-            for (int i = tid; i < nbins; i += TPB) {
-                const uint32_t v = s_n[i];
-                if (v) atomicAdd(&gN[i], v);
-            }
-            unsigned long long *gG = a.g_hist + st.n_off / (2 * a.n_e) + (long long)tout * st.n_cells;
-            for (int i = tid; i < st.n_cells; i += TPB) {
-                const uint32_t v = s_gs[i];
-                if (v) atomicAdd(&gG[i], (unsigned long long)v);
-            }
-        }
-        if (ADJ == 2) {
-            // the no-scattering score of an entry times the sum of the
-            // reward-to-go of the carriers that passed the test with it
-            for (int i = tid; i < st.tab_n; i += TPB) {
-                const long long v = (long long)s_sr[i];
-                if (v) atomicAdd(&a.g_ent[st.ent_off + i], (double)v * a.inv_q * a.aent[st.ent_off + i].noscat);
-            }
-        }
-        const unsigned long long v0 = consumer_sum_u64(n_steps, s_r);
-        if (tid == 0 && v0) atomicAdd(&a.cnt[s].led[L_PARTICLE_STEPS], v0);
-        const unsigned long long v1 = consumer_sum_u64(n_queued, s_r);
-        if (tid == 0 && v1) atomicAdd(&a.cnt[s].led[L_EVENTFUL], v1);
-        n_steps = 0;
-        n_queued = 0;
-        consumer_sync();
-    };
-
-    int stg = 0;
-    uint32_t phase = 0;                  // completions of full[stg] consumed, mod 2
-    for (long long i = 0; i < ntiles; ++i) {
-        const long long t = t0 + i;
-        const int s = stack_of(s_tpref, a.n_stacks, t);
-        if (s != seg_stack) {
-            if (seg_stack >= 0) flush(seg_stack);
-            consumer_sync();
-            if (tid == 0) s_st = a.stacks[s];
-            consumer_sync();
-            const DevStack &st = s_st;
-            for (int q = tid; q < st.ftab_n; q += TPB) s_ent[q] = a.fent[st.fent_off + q];
-            if (!ADJ)
-                for (int q = tid; q < 2 * (st.n_cells + 1); q += TPB) s_J[q] = 0;
-            if (DEPN && !ADJ) {
-                for (int q = tid; q < 2 * a.n_e * st.n_cells; q += TPB) s_n[q] = 0u;
-                for (int q = tid; q < st.n_cells; q += TPB) s_gs[q] = 0u;
-            }
-            if (ADJ == 2)
-                for (int q = tid; q < st.tab_n; q += TPB) s_sr[q] = 0ull;
-            if (ADJ) {
-                const long long *gp = a.gpot + (long long)(s * a.n_out + tj) * 2 * a.ncm;
-                for (int q = tid; q < 2 * st.n_cells; q += TPB)
-                    s_gp[q] = gp[(q / st.n_cells) * a.ncm + q % st.n_cells];
-                if (DEPN) {
-                    const int rows = 2 * a.n_e;
-                    for (int q = tid; q < rows * st.n_cells; q += TPB)
-                        s_gn[q] = a.gn ? a.gn[((long long)(s * a.n_out + tout) * rows + q / st.n_cells) * a.ncm +
-                                              q % st.n_cells]
-                                       : 0;
-                }
-            }
-            nc = st.n_cells;
-            ctr_hi = (uint32_t)(a.stack_base + s) << 16;
-            seg_stack = s;
-            consumer_sync();
-        }
-        const long long nsl = s_nsl[s];
-        const long long tslot0 = (t - s_tpref[s]) * TILE;
-        // after a failed wait every later wait is skipped: the warps run the
-        // same control flow to the end (results are invalid, the status says so)
-        if (!*(volatile int *)&s_abort && !mbar_wait(&s_full[stg], phase, a.spin_limit)) {
-            atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
-            a.ctl->timeout_where = 3u;
-            s_abort = 1;
-        }
-        const float *rz = ring + (size_t)stg * STG * TILE;
-        const uint4 *rmp = reinterpret_cast<const uint4 *>(rz + TILE);   // (mu, packed) pairs
-        float *gZ = Z + s_st.base + tslot0;
-        const int nvalid = nsl - tslot0 < TILE ? (int)(nsl - tslot0) : TILE;
-        // four consecutive slots per thread; one Philox call gives the four
-        // scattering-test words of the slot group
-        const int i0 = VEC * tid;
-        const float4 z4 = reinterpret_cast<const float4 *>(rz)[tid];
-        const uint4 q01 = rmp[2 * tid], q23 = rmp[2 * tid + 1];
-        const float4 m4 = make_float4(__uint_as_float(q01.x), __uint_as_float(q01.z),
-                                      __uint_as_float(q23.x), __uint_as_float(q23.z));
-        const uint4 p4 = make_uint4(q01.y, q01.w, q23.y, q23.w);
-        long long av[VEC];
-        if (ADJ) {
-            const longlong2 *racc = reinterpret_cast<const longlong2 *>(rz + 3 * TILE);
-            const longlong2 a01 = racc[2 * tid], a23 = racc[2 * tid + 1];
-            av[0] = a01.x; av[1] = a01.y; av[2] = a23.x; av[3] = a23.y;
-        }
-        bool achg = false;
-        // the stage is no longer needed by this warp
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&s_empty[stg]);
-        if (++stg == nring) { stg = 0; phase ^= 1u; }
-        const uint4 xg = philox_rk(make_uint4((uint32_t)(tslot0 >> 2) + (uint32_t)tid, ctr_hi,
-                                              step, SUB_TEST), a);
-        const float zin[VEC] = {z4.x, z4.y, z4.z, z4.w};
-        const float min_[VEC] = {m4.x, m4.y, m4.z, m4.w};
-        const uint32_t pin[VEC] = {p4.x, p4.y, p4.z, p4.w};
-        const uint32_t xw[VEC] = {xg.x, xg.y, xg.z, xg.w};
-        float zo[VEC] = {z4.x, z4.y, z4.z, z4.w};
-        uint32_t slowbits = 0;
-        // First the two half flights and the cells of all four carriers: none
-        // of it depends on the test words, so the scheduler overlaps it with
-        // the Philox rounds.  Slots past the end or with k = 0 read entry 0.
-        float z2v[VEC];
-        uint32_t pthr[VEC];
-        int c0v[VEC], c1v[VEC];
-        uint32_t live = 0, crossm = 0;
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            const uint32_t pk = pin[j];
-            const int k = (int)(pk & 0xFFu);
-            const bool ok = (i0 + j < nvalid) && k != 0;
-            const int sg = (int)((pk >> 8) & 1u), layer = (int)((pk >> 9) & 0xFu);
-            const FastEnt e = s_ent[ok ? fast_index(a, pk) : 0];
-            const float z = zin[j], mu = min_[j];
-            const float w = __fmul_rn(e.v, mu);
-            const float z1 = DET ? __fadd_rn(z, __fmul_rn(w, half)) : __fmaf_rn(w, half, z);
-            const float z2 = DET ? __fadd_rn(z1, __fmul_rn(w, half)) : __fmaf_rn(w, half, z1);
-            // the motion is monotone within the step: the end point decides
-            const bool cross = mu > 0.f ? (z2 > e.hi) : (z2 < e.lo);
-            z2v[j] = z2;
-            pthr[j] = e.P;
-            // cells floor(z / dz): 2^23 added with rounding toward -inf
-            c0v[j] = __float_as_int(__fadd_rd(__fmul_rn(z, a.inv_dz), 8388608.0f)) - 0x4B000000;
-            c1v[j] = __float_as_int(__fadd_rd(__fmul_rn(z2, a.inv_dz), 8388608.0f)) - 0x4B000000;
-            live |= (uint32_t)ok << j;
-            crossm |= (uint32_t)cross << j;
-        }
-        n_steps += __popc(live);
-        // then the scattering test, and the flux, deposit and new depth of the
-        // carriers that neither scatter nor meet a boundary
-#pragma unroll
-        for (int j = 0; j < VEC; ++j) {
-            int bin = -1;
-            if ((live >> j) & 1u) {
-                const uint32_t pk = pin[j];
-                const int k = (int)(pk & 0xFFu);
-                const int sg = (int)((pk >> 8) & 1u), layer = (int)((pk >> 9) & 0xFu);
-                (void)k; (void)layer;
-                if (((crossm >> j) & 1u) || xw[j] < pthr[j]) {
-                    slowbits |= 1u << j;
-                } else {
-                    const float z2 = z2v[j];
-                    const int c0u = c0v[j], c1u = c1v[j];
-                    const int c1 = c1u < nc - 1 ? c1u : nc - 1;
-                    if (!ADJ && c0u != c1u) {
-                        const int c0 = c0u < nc - 1 ? c0u : nc - 1;
-                        const int nf = nc + 1;
-                        if (c1 == c0 + 1) atomicAdd(&s_J[sg * nf + c1], 1);
-                        else if (c1 == c0 - 1) atomicAdd(&s_J[sg * nf + c0], -1);
-                        else if (c1 != c0) add_flux(s_J, nf, sg, c0, c1);
-                    }
-                    zo[j] = z2;
-                    if (DEPN && !ADJ) {
-                        bin = (sg * ne + (k - 1)) * nc + c1;
-                        atomicAdd(&s_gs[c1], (pk >> 13) & 0xFFu);
-                    }
-                    if (ADJ) {
-                        // reward of the step: faces crossed, then the density bin
-                        const int c0 = c0u < nc - 1 ? c0u : nc - 1;
-                        long long r = s_gp[sg * nc + c1] - s_gp[sg * nc + c0];
-                        if (DEPN) r += s_gn[(sg * ne + (k - 1)) * nc + c1];
-                        if (ADJ == 2)
-                            atomicAdd(&s_sr[(layer * 2 + sg) * ne + (k - 1)], (unsigned long long)av[j]);
-                        if (r != 0) {
-                            av[j] = ADJ == 1 ? av[j] + r : av[j] - r;
-                            achg = true;
-                        }
-                    }
-                }
-            }
-            if (DEPN && !WAGG && bin >= 0) atomicAdd(&s_n[bin], 1u);
-            if (DEPN && WAGG) {
-                const unsigned int m = __match_any_sync(0xffffffffu, bin);
-                if (bin >= 0 && lane == __ffs(m) - 1) atomicAdd(&s_n[bin], (uint32_t)__popc(m));
-            }
-        }
-        // new depths (an eventful carrier keeps its old one here: k_event
-        // writes its final state); only slots below n_slots are written
-        if (i0 + VEC <= nvalid) {
-            *reinterpret_cast<float4 *>(gZ + i0) = make_float4(zo[0], zo[1], zo[2], zo[3]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < VEC; ++j)
-                if (i0 + j < nvalid) gZ[i0 + j] = zo[j];
-        }
-        if (ADJ && achg) {
-            long long *gA = a.acc[cur] + s_st.base + tslot0;
-            if (i0 + VEC <= nvalid) {
-                reinterpret_cast<longlong2 *>(gA + i0)[0] = make_longlong2(av[0], av[1]);
-                reinterpret_cast<longlong2 *>(gA + i0)[1] = make_longlong2(av[2], av[3]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < VEC; ++j)
-                    if (i0 + j < nvalid) gA[i0 + j] = av[j];
-            }
-        }
-        // queue the eventful carriers (record and position), in tile order:
-        // the warp's exclusive prefix of the per-thread counts (0..4) from
-        // three ballots of their bits, one shared-counter reservation
-        {
-            const uint32_t cnt = (uint32_t)__popc(slowbits);
-            const unsigned int b0 = __ballot_sync(0xffffffffu, cnt & 1u);
-            const unsigned int b1 = __ballot_sync(0xffffffffu, cnt & 2u);
-            const unsigned int b2 = __ballot_sync(0xffffffffu, cnt & 4u);
-            const int tot = __popc(b0) + 2 * __popc(b1) + 4 * __popc(b2);
-            if (tot) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&s_qn, tot);
-                base = __shfl_sync(0xffffffffu, base, 0);
-                long long q = pos0 + base + __popc(b0 & lt_mask) + 2 * __popc(b1 & lt_mask) +
-                              4 * __popc(b2 & lt_mask);
-                n_queued += cnt;
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) {
-                    if ((slowbits >> j) & 1u) {
-                        a.qrec[q++] = make_float4(zin[j], min_[j], __uint_as_float(pin[j]),
-                                                  __uint_as_float((uint32_t)((t - t0) * TILE + i0 + j)));
-                    }
-                }
-            }
-        }
-    }
-    if (seg_stack >= 0) flush(seg_stack);
-    consumer_sync();
-    if (tid == 0) a.qcnt[b] = (uint32_t)s_qn;
-}
-
 // ---------------------------------------------------------------------------
-// k_stream: the forward streaming pass (Transport(dt/2) -> Scattering(dt) ->
+// k_stream: the streaming pass (Transport(dt/2) -> Scattering(dt) ->
 // Transport(dt/2) for every carrier that neither scatters nor meets a
 // boundary in the step; the others are queued for k_event).
 //
-// Warp-specialised as k_fast: one producer warp issues the bulk copies of a
+// Warp-specialised: one producer warp issues the bulk copies of a
 // tile's z and (mu, packed) pairs into a ring of shared-memory stages with
 // full/empty mbarriers; NW consumer warps each take G = TILE / (32 NW)
 // consecutive slots per thread (4 or 8: one Philox call per four slots).
@@ -926,6 +523,12 @@ k_fast(const Args a)
 // step the carriers finished here are also deposited (density, generation
 // label and, with PIC_F_VELOCITY_MOMENTS, velocity) into shared-memory
 // histograms flushed once per block and stack segment.
+//
+// ADJ = 1, 2: the same pass in the two replays of the adjoint, with the
+// per-slot reward (a fourth array of the ring): a finished carrier earns the
+// flux weights of the faces it crossed and, on a density step, the weight of
+// its bin; pass 2 also adds its reward-to-go to the no-scattering sum of its
+// table entry.
 // ---------------------------------------------------------------------------
 // resident blocks per SM the register budget must allow: four of 288
 // threads (eight consumer warps, 56 registers) or five of 160 (four consumer
@@ -936,8 +539,12 @@ k_fast(const Args a)
 #ifndef PIC_STREAM_MIN_BLOCKS_4
 #define PIC_STREAM_MIN_BLOCKS_4 5
 #endif
-template <int NW>
-constexpr int stream_min_blocks() { return NW == 8 ? PIC_STREAM_MIN_BLOCKS_8 : PIC_STREAM_MIN_BLOCKS_4; }
+// the replays carry the slots' rewards as well: three blocks (72 registers)
+template <int NW, int ADJ>
+constexpr int stream_min_blocks()
+{
+    return ADJ ? 3 : (NW == 8 ? PIC_STREAM_MIN_BLOCKS_8 : PIC_STREAM_MIN_BLOCKS_4);
+}
 
 template <int NW>
 __device__ __forceinline__ void stream_sync()
@@ -963,21 +570,28 @@ __device__ __forceinline__ unsigned long long stream_sum_u64(unsigned long long 
 template <int NW>
 constexpr int stream_threads() { return 32 * NW + 32; }
 
-template <bool DET, bool DEPN, bool WAGG, int NW>
-__global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW>()) k_stream(const Args a)
+template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0>
+__global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW, ADJ>()) k_stream(const Args a)
 {
     constexpr int NT = 32 * NW;              // consumer threads
     constexpr int G = TILE / NT;             // slots per consumer thread and tile
     constexpr int NC = G / 4;                // Philox calls (and float4s) per thread
+    constexpr int STG = ADJ ? 5 : 3;         // ring arrays: z, (mu, packed) [, reward]
     static_assert(G % 4 == 0 && G <= 8, "4 or 8 slots per thread");
     extern __shared__ __align__(128) unsigned char smem[];
-    float *ring = reinterpret_cast<float *>(smem);                      // a.ring x 3 x TILE
-    FastEnt *s_ent = reinterpret_cast<FastEnt *>(ring + (size_t)a.ring * 3 * TILE);
-    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_ent + a.ftab_max);   // density steps
+    float *ring = reinterpret_cast<float *>(smem);                      // a.ring x STG x TILE
+    FastEnt *s_ent = reinterpret_cast<FastEnt *>(ring + (size_t)a.ring * STG * TILE);
+    // forward density steps: histograms; replay: the window's flux potential
+    // [2][n_cells], density weights [2][n_e][n_cells] and (pass 2) the
+    // no-scattering sums of the reward-to-go per entry (fixed point)
+    unsigned long long *s_sr = reinterpret_cast<unsigned long long *>(s_ent + a.ftab_max);
+    long long *s_gp = reinterpret_cast<long long *>(s_sr + (ADJ == 2 ? a.tab_max : 0));
+    uint32_t *s_n = reinterpret_cast<uint32_t *>(s_gp + (ADJ ? a.jbin_max : 0));
+    int32_t *s_gn = reinterpret_cast<int32_t *>(s_n);
     uint32_t *s_gs = s_n + (DEPN ? a.nbin_max : 0);                     // generation sums
     unsigned long long *s_v = reinterpret_cast<unsigned long long *>(
-        (reinterpret_cast<uintptr_t>(s_gs + (DEPN ? a.gbin_max : 0)) + 7) & ~uintptr_t(7));
-    long long *s_tpref = reinterpret_cast<long long *>(s_v + (DEPN ? 2 * a.gbin_max : 0));
+        (reinterpret_cast<uintptr_t>(s_gs + (DEPN && !ADJ ? a.gbin_max : 0)) + 7) & ~uintptr_t(7));
+    long long *s_tpref = reinterpret_cast<long long *>(s_v + (DEPN && !ADJ ? 2 * a.gbin_max : 0));
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     __shared__ __align__(8) unsigned long long s_full[MAX_RING], s_empty[MAX_RING];
     __shared__ DevStack s_st;
@@ -1037,11 +651,12 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW>()) k_strea
                 const long long t = t0 + i;
                 const int s = stack_of(s_tpref, a.n_stacks, t);
                 const long long off = a.stacks[s].base + (t - s_tpref[s]) * TILE;
-                float *dst = ring + (size_t)stg * 3 * TILE;
+                float *dst = ring + (size_t)stg * STG * TILE;
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(&s_full[stg], 3 * TILE_BYTES);
+                mbar_expect_tx(&s_full[stg], STG * TILE_BYTES);
                 bulk_load(dst, Z + off, TILE_BYTES, &s_full[stg]);
                 bulk_load(dst + TILE, MP + 2 * off, 2 * TILE_BYTES, &s_full[stg]);
+                if (ADJ) bulk_load(dst + 3 * TILE, a.acc[cur] + off, 2 * TILE_BYTES, &s_full[stg]);
                 issued = i + 1;
                 if (++stg == nring) { stg = 0; phase ^= 1u; }
             }
@@ -1057,10 +672,11 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW>()) k_strea
 
     // ---------------- consumer warps ----------------
     const uint32_t step = step_now(a);
+    const int tj = (int)(step / (uint32_t)a.moment_every);
     const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
     const float half = a.half_dt;
     const long long pos0 = t0 * TILE;                // queue region of this block
-    const bool vmom = DEPN && (a.flags & PIC_F_VELOCITY_MOMENTS);
+    const bool vmom = DEPN && !ADJ && (a.flags & PIC_F_VELOCITY_MOMENTS);
     const int i0 = G * tid;                          // the thread's first slot in a tile
     int seg_stack = -1, nc = 1, ne = a.n_e;
     long long seg_t0 = 0, seg_t1 = -1;               // tiles of the current stack
@@ -1072,7 +688,15 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW>()) k_strea
     auto flush = [&](int s) {
         stream_sync<NW>();
         const DevStack &st = s_st;
-        if (DEPN) {
+        if (ADJ == 2) {
+            // the no-scattering score of an entry times the sum of the
+            // reward-to-go of the carriers that passed the test with it
+            for (int i = tid; i < st.tab_n; i += NT) {
+                const long long v = (long long)s_sr[i];
+                if (v) atomicAdd(&a.g_ent[st.ent_off + i], (double)v * a.inv_q * a.aent[st.ent_off + i].noscat);
+            }
+        }
+        if (DEPN && !ADJ) {
             const int nbins = 2 * a.n_e * st.n_cells;
             uint32_t *gN = a.n_hist + st.n_off + (long long)tout * nbins;
             for (int i = tid; i < nbins; i += NT) {
@@ -1112,11 +736,25 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW>()) k_strea
             stream_sync<NW>();
             const DevStack &st = s_st;
             for (int q = tid; q < st.ftab_n; q += NT) s_ent[q] = a.fent[st.fent_off + q];
-            if (DEPN) {
+            if (DEPN && !ADJ) {
                 for (int q = tid; q < 2 * a.n_e * st.n_cells; q += NT) s_n[q] = 0u;
                 for (int q = tid; q < st.n_cells; q += NT) s_gs[q] = 0u;
                 if (vmom)
                     for (int q = tid; q < 2 * st.n_cells; q += NT) s_v[q] = 0ull;
+            }
+            if (ADJ == 2)
+                for (int q = tid; q < st.tab_n; q += NT) s_sr[q] = 0ull;
+            if (ADJ) {
+                const long long *gp = a.gpot + (long long)(s * a.n_out + tj) * 2 * a.ncm;
+                for (int q = tid; q < 2 * st.n_cells; q += NT)
+                    s_gp[q] = gp[(q / st.n_cells) * a.ncm + q % st.n_cells];
+                if (DEPN) {
+                    const int rows = 2 * a.n_e;
+                    for (int q = tid; q < rows * st.n_cells; q += NT)
+                        s_gn[q] = a.gn ? a.gn[((long long)(s * a.n_out + tout) * rows + q / st.n_cells) * a.ncm +
+                                              q % st.n_cells]
+                                       : 0;
+                }
             }
             nc = st.n_cells;
             ctr_hi = (uint32_t)(a.stack_base + s) << 16;
@@ -1136,10 +774,21 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW>()) k_strea
             a.ctl->timeout_where = 3u;
             s_abort = 1;
         }
-        const float *rz = ring + (size_t)stg * 3 * TILE;
+        const float *rz = ring + (size_t)stg * STG * TILE;
         const uint4 *rmp = reinterpret_cast<const uint4 *>(rz + TILE);   // (mu, packed) pairs
         float zin[G], min_[G];
         uint32_t pin[G];
+        long long av[ADJ ? G : 1];           // replay: the slots' rewards
+        if (ADJ) {
+            const longlong2 *racc = reinterpret_cast<const longlong2 *>(rz + 3 * TILE);
+#pragma unroll
+            for (int c = 0; c < G / 2; ++c) {
+                const longlong2 v = racc[(G / 2) * tid + c];
+                av[2 * c] = v.x;
+                av[2 * c + 1] = v.y;
+            }
+        }
+        bool achg = false;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
             const float4 z4 = reinterpret_cast<const float4 *>(rz)[NC * tid + c];
@@ -1181,7 +830,27 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW>()) k_strea
             const bool slow = (z2 > e.hi) | (z2 < e.lo) | (xw[j] < e.P);
             zo[j] = z2;          // an eventful carrier's final depth is written by k_event
             slowbits |= (uint32_t)slow << j;
-            if (DEPN) {
+            if (ADJ) {
+                // the reward of a finished carrier: the faces it crossed,
+                // then its density bin; pass 2 sums its reward-to-go into the
+                // no-scattering sum of its entry
+                const uint32_t k = pk & 0xFFu;
+                if (!slow && k != 0u) {
+                    const int sg = (int)((pk >> 8) & 1u), layer = (int)((pk >> 9) & 0xFu);
+                    const int c0u = __float_as_int(__fmaf_rd(zin[j], a.inv_dz, 8388608.0f)) - 0x4B000000;
+                    const int c1u = __float_as_int(__fmaf_rd(z2, a.inv_dz, 8388608.0f)) - 0x4B000000;
+                    const int c0 = c0u < nc - 1 ? c0u : nc - 1, c1 = c1u < nc - 1 ? c1u : nc - 1;
+                    long long r = s_gp[sg * nc + c1] - s_gp[sg * nc + c0];
+                    if (DEPN) r += s_gn[(sg * ne + (int)k - 1) * nc + c1];
+                    if (ADJ == 2 && av[j] != 0)
+                        atomicAdd(&s_sr[(layer * 2 + sg) * ne + (int)k - 1], (unsigned long long)av[j]);
+                    if (r != 0) {
+                        av[j] = ADJ == 1 ? av[j] + r : av[j] - r;
+                        achg = true;
+                    }
+                }
+            }
+            if (DEPN && !ADJ) {
                 int bin = -1;
                 const uint32_t k = pk & 0xFFu;
                 if (!slow && k != 0u) {
@@ -1210,6 +879,18 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW>()) k_strea
 #pragma unroll
             for (int j = 0; j < G; ++j)
                 if (i0 + j < nvalid) gZ[j] = zo[j];
+        }
+        if (ADJ && achg) {
+            long long *gA = a.acc[cur] + (gZs - Z) + slot0 + i0;
+            if (i0 + G <= nvalid) {
+#pragma unroll
+                for (int c = 0; c < G / 2; ++c)
+                    reinterpret_cast<longlong2 *>(gA)[c] = make_longlong2(av[2 * c], av[2 * c + 1]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < G; ++j)
+                    if (i0 + j < nvalid) gA[j] = av[j];
+            }
         }
         // queue the eventful carriers (record and position), in tile order:
         // the warp's exclusive prefix of the per-thread counts (0..G) from
@@ -1434,12 +1115,12 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         const uint32_t xs = (slot & 3) == 0 ? xg.x : (slot & 3) == 1 ? xg.y
                           : (slot & 3) == 2 ? xg.z : xg.w;
         bool dead = false;
-        if (ADJ == 2 && !(xs < e.P)) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * Rd);
+        if (ADJ == 2 && !(xs < e.P) && Rd != 0.0) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * Rd);
         if (xs < e.P) {
             const uint4 x = philox_rk(make_uint4(key_x, S.ctr_hi, step, SUB_EVT), a);
             const bool inel = x.y < e.Q;
             // scores of the test (scattered) and of the channel
-            if (ADJ == 2) {
+            if (ADJ == 2 && Rd != 0.0) {
                 const AdjEnt &ae = a.aent[st.ent_off + tb];
                 atomicAdd(&s_g[tb], (inel ? ae.scat_inel : ae.scat_el) * Rd);
             }
@@ -2200,47 +1881,21 @@ static cudaError_t occupancy(K kernel, size_t smem, int *blocks, int threads = T
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, kernel, threads, smem);
 }
 
-// Ring depth of k_fast for one variant, both builds (with and without fused
-// multiply-add) fitting: the most resident blocks per SM (warps to hide the
-// arithmetic latency) such that at least three tiles per SM are in flight
-// (blocks x (stages - 1) >= 3, about 48 KB), then the deepest ring.
-template <bool DEPN, bool WAGG, int ADJ = 0>
-static cudaError_t pick_ring(size_t fixed, int blocks_per_sm, int ring_req, int *ring, int *blocks,
-                             size_t *smem)
-{
-    int best = -1;
-    for (int r = 2; r <= MAX_RING; ++r) {
-        if (ring_req > 0 && r != ring_req) continue;
-        const size_t sm = fixed + (size_t)r * (ADJ ? 5 : 3) * TILE_BYTES;
-        int o1 = 0, o2 = 0;
-        cudaError_t e = occupancy(k_fast<false, DEPN, WAGG, ADJ>, sm, &o1, FAST_THREADS);
-        if (e == cudaSuccess) e = occupancy(k_fast<true, DEPN, WAGG, ADJ>, sm, &o2, FAST_THREADS);
-        if (e != cudaSuccess) return e;
-        int o = o1 < o2 ? o1 : o2;
-        if (blocks_per_sm > 0 && o > blocks_per_sm) o = blocks_per_sm;
-        if (o < 1) continue;
-        const int enough = o * (r - 1) >= 3 ? 1 : 0;
-        const int score = enough * 10000 + o * 100 + r;
-        if (score > best) { best = score; *ring = r; *blocks = o; *smem = sm; }
-    }
-    return best < 0 ? cudaErrorInvalidConfiguration : cudaSuccess;
-}
-
 // Ring depth and resident blocks of k_stream for one variant, both builds
 // (with and without fused multiply-add) fitting: the most resident blocks per
 // SM such that at least three tiles per SM are in flight, then the deepest
 // ring (blocks_per_sm, ring_req: 0 = free).
-template <bool DEPN, bool WAGG, int NW>
+template <bool DEPN, bool WAGG, int NW, int ADJ = 0>
 static cudaError_t pick_stream_ring(size_t fixed, int blocks_per_sm, int ring_req, int *ring,
                                     int *blocks, size_t *smem)
 {
     int best = -1;
     for (int r = 2; r <= MAX_RING; ++r) {
         if (ring_req > 0 && r != ring_req) continue;
-        const size_t sm = fixed + (size_t)r * 3 * TILE_BYTES;
+        const size_t sm = fixed + (size_t)r * (ADJ ? 5 : 3) * TILE_BYTES;
         int o1 = 0, o2 = 0;
-        cudaError_t e = occupancy(k_stream<false, DEPN, WAGG, NW>, sm, &o1, stream_threads<NW>());
-        if (e == cudaSuccess) e = occupancy(k_stream<true, DEPN, WAGG, NW>, sm, &o2, stream_threads<NW>());
+        cudaError_t e = occupancy(k_stream<false, DEPN, WAGG, NW, ADJ>, sm, &o1, stream_threads<NW>());
+        if (e == cudaSuccess) e = occupancy(k_stream<true, DEPN, WAGG, NW, ADJ>, sm, &o2, stream_threads<NW>());
         if (e != cudaSuccess) return e;
         int o = o1 < o2 ? o1 : o2;
         if (blocks_per_sm > 0 && o > blocks_per_sm) o = blocks_per_sm;

@@ -201,35 +201,25 @@ def test_autograd_function_backward_matches_grad():
 
 
 def test_fast_build_finite_differences_common_random_numbers():
-    """Default build, Fe/Au bilayer with the pulse (2e5 carriers, capacity
-    raised so that nothing is dropped, no compaction): central differences
-    with the same seed along tau_in and along T agree with the adjoint's
-    directional derivatives over 32 seeds within 3 SE (a 2-SE bound fails
-    about one seed set in twenty per direction when the two agree).  The
-    random words are keyed by slot, and compaction shifts every slot behind a
-    removed carrier: without it the perturbed runs keep their slots, and so
-    their common random numbers."""
-    R, h = 32, 0.1
-    base = W.config(3, scale=0.02).replace(n_steps=300, compact_every=1000)
+    """Default (fused multiply-add) build, Fe/Au bilayer with the pulse (2e5
+    carriers, capacity raised so that nothing is dropped, compaction every 50
+    steps): central differences with the same seed agree with the adjoint's
+    directional derivatives within 2 SE over 16 seeds, along tau_in and along
+    T, each entry moved by h = 0.1 of itself with the sign of the gradient of
+    an independent pilot run (a wrong sign would sit >= 4 SE away).  The
+    library keys the random words by slot: a flipped decision that creates or
+    removes a carrier renumbers the later slots, so the perturbed runs share
+    few words and the estimate's spread is close to that of independent runs,
+    sqrt(2) sd(O) / 2h; at h = 1e-3 that spread is some 200 times the
+    gradient, which is why the step of 1e-3 is tested on the oracle with
+    lineage-keyed words (test_oracle_grad.py), against the adjoint this one
+    reproduces."""
+    R, h = 16, 0.1
+    base = W.config(3, scale=0.02).replace(n_steps=300, compact_every=50)
     st0 = base.stacks[0]
     st0.capacity = 40 * st0.n0
 
-    def O(wl, seed, ctx=None):
-        own = ctx is None
-        if own:
-            ctx = pic.Context(wl, seed=seed)
-            ctx.step(wl.n_steps)
-        n, J = ctx.moments_all()
-        val = float(n[0, :, 0, :, 90:100].sum() - n[0, :, 1, :, 90:100].sum()
-                    + J[0, :, 0, 15].sum() - J[0, :, 1, 15].sum())
-        if own:
-            ctx.close()
-        return val
-
-    d_tau, d_T = [], []
-    for rep in range(R):
-        ctx = pic.Context(base, seed=rep)
-        ctx.step(base.n_steps)
+    def weights(ctx):
         n, J = ctx.moments_all()
         gn = torch.zeros_like(n)
         gJ = torch.zeros_like(J)
@@ -237,24 +227,48 @@ def test_fast_build_finite_differences_common_random_numbers():
         gn[0, :, 1, :, 90:100] = -1.0
         gJ[0, :, 0, 15] = 1.0
         gJ[0, :, 1, 15] = -1.0
-        g_tau, g_T = ctx.grad(gn, gJ)
+        return n, J, gn, gJ
+
+    def O(wl, seed):
+        ctx = pic.Context(wl, seed=seed)
+        ctx.step(wl.n_steps)
+        n, J, gn, gJ = weights(ctx)
+        val = float((n.double() * gn.double()).sum() + (J.double() * gJ.double()).sum())
+        ctx.close()
+        return val
+
+    pilot = pic.Context(base, seed=1000)
+    pilot.step(base.n_steps)
+    _, _, gn, gJ = weights(pilot)
+    pt, pT = (g.cpu().numpy()[0] for g in pilot.grad(gn, gJ))
+    pilot.close()
+    nm, nif = st0.tau_in.shape[0], st0.T.shape[0]
+    d_tau = np.sign(pt[:nm]) * st0.tau_in
+    d_T = np.sign(pT[:nif]) * st0.T
+
+    rows = []
+    for rep in range(R):
+        ctx = pic.Context(base, seed=rep)
+        ctx.step(base.n_steps)
+        _, _, gn, gJ = weights(ctx)
+        g_tau, g_T = (g.cpu().numpy()[0] for g in ctx.grad(gn, gJ))
         _, _, led = ctx.moments(0)
         assert led["spawn_dropped"] == 0
         ctx.close()
-        g_tau, g_T = g_tau.cpu().numpy()[0], g_T.cpu().numpy()[0]
-        vals = []
-        for f in (1 + h, 1 - h):
-            wl = copy.deepcopy(base)
-            wl.stacks[0].tau_in = st0.tau_in * f
-            vals.append(O(wl, rep))
-        nm = st0.tau_in.shape[0]
-        d_tau.append((vals[0] - vals[1]) / (2 * h) - (g_tau[:nm] * st0.tau_in).sum())
-        vals = []
-        for f in (1 + h, 1 - h):
-            wl = copy.deepcopy(base)
-            wl.stacks[0].T = np.clip(st0.T * f, 0.0, 1.0)
-            vals.append(O(wl, rep))
-        nif = st0.T.shape[0]
-        d_T.append((vals[0] - vals[1]) / (2 * h) - (g_T[:nif] * st0.T).sum())
-    for d in (np.array(d_tau), np.array(d_T)):
-        assert abs(d.mean()) <= 3 * d.std(ddof=1) / math.sqrt(R), d
+        row = []
+        for d, field, g in ((d_tau, "tau_in", g_tau[:nm]), (d_T, "T", g_T[:nif])):
+            vals = []
+            for f in (h, -h):
+                wl = copy.deepcopy(base)
+                setattr(wl.stacks[0], field, np.clip(getattr(st0, field) + f * d, 0.0, None)
+                        if field == "tau_in" else np.clip(st0.T + f * d, 0.0, 1.0))
+                vals.append(O(wl, rep))
+            row.append(((vals[0] - vals[1]) / (2 * h), float((g * d).sum())))
+        rows.append(row)
+    for j in range(2):
+        fd = np.array([r[j][0] for r in rows])
+        ad = np.array([r[j][1] for r in rows])
+        d = fd - ad
+        se = d.std(ddof=1) / math.sqrt(R)
+        assert abs(d.mean()) <= 2 * se, (j, d.mean(), se)
+        assert ad.mean() >= 2 * se, (j, ad.mean(), se)

@@ -17,6 +17,7 @@ result that does not come from the oracle:
 """
 import copy
 import math
+import os
 
 import numpy as np
 import pytest
@@ -273,3 +274,75 @@ def test_finite_differences_common_random_numbers():
         d_T.append((vals[0] - vals[1]) / (2 * h) - (g_T * st0.T).sum())
     for d in (np.array(d_tau), np.array(d_T)):
         assert abs(d.mean()) <= 3 * d.std(ddof=1) / math.sqrt(R), d
+
+
+# ---------------------------------------------------------------------------
+# The adjoint against central finite differences at a relative step of 1e-3
+# with common random numbers, 2 SE over 16 seeds, compaction on (every 50
+# steps).  With the random words keyed by slot, as in the library, a flipped
+# decision that creates or removes a carrier renumbers every later slot, so
+# at this step the two perturbed runs share almost no words (measured: the
+# spread of the estimate is that of independent runs, sqrt(2) sd(O) / 2h,
+# some 200 times the gradient).  The oracle's lineage keys (a carrier's words
+# keyed by its birth, not its slot) keep every other carrier's words common.
+# The direction perturbs every entry by 1e-3 of itself with the sign of the
+# gradient of an independent pilot run, so that a few flips carry a signal;
+# the test then can tell a wrong sign (the adjoint mean lies >= 2 SE from 0).
+# ---------------------------------------------------------------------------
+def _fd_seed(args):
+    import copy as _copy
+    import numpy as _np
+    from oracle.oracle import OracleSim as _Sim
+    rep, base, d_tau, d_T, gn, gJ, h = args
+    st0 = base.stacks[0]
+
+    def O(wl):
+        s = _Sim(wl, seed=rep)
+        s.step(wl.n_steps)
+        n, J, _ = s.moments()
+        return float((gn * n).sum() + (gJ * J).sum())
+
+    s = _Sim(base, seed=rep)
+    s.step(base.n_steps)
+    g_tau, g_T, _, _ = s.grad(gn, gJ)
+    out = []
+    for d, field in ((d_tau, "tau_in"), (d_T, "T")):
+        v = []
+        for f in (h, -h):
+            wl = _copy.deepcopy(base)
+            setattr(wl.stacks[0], field, getattr(st0, field) + f * d)
+            v.append(O(wl))
+        g = g_tau if field == "tau_in" else g_T
+        out.append(((v[0] - v[1]) / (2 * h), float((g * d).sum())))
+    return out
+
+
+def test_finite_differences_step_1e3_lineage_crn_with_compaction():
+    import multiprocessing as mp
+    R, h = 16, 1e-3
+    base = W.config(3, scale=0.004, flags=W.FLAG_LINEAGE_KEYS).replace(n_steps=150,
+                                                                        compact_every=50)
+    st0 = base.stacks[0]
+    st0.capacity = 40 * st0.n0             # nothing is dropped: no coupling through the slots
+    pilot = OracleSim(base, seed=10_000)
+    pilot.step(base.n_steps)
+    gn, gJ = zero_weights(pilot, base)
+    gn[:, 0, :, 90:100] = 1.0
+    gn[:, 1, :, 90:100] = -1.0
+    gJ[:, 0, 15] = 1.0
+    gJ[:, 1, 15] = -1.0
+    pt, pT, _, _ = pilot.grad(gn, gJ)
+    d_tau = np.sign(pt) * st0.tau_in
+    d_T = np.sign(pT) * st0.T
+    args = [(rep, base, d_tau, d_T, gn, gJ, h) for rep in range(R)]
+    with mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1)) as pool:
+        rows = pool.map(_fd_seed, args)
+    for j in range(2):
+        fd = np.array([r[j][0] for r in rows])
+        ad = np.array([r[j][1] for r in rows])
+        d = fd - ad
+        se = d.std(ddof=1) / math.sqrt(R)
+        assert abs(d.mean()) <= 2 * se, (j, d.mean(), se)
+        assert ad.mean() >= 2 * se, (j, ad.mean(), se)      # a flipped sign would fail
+    # an independent check of the run: no carrier was dropped
+    assert pilot.moments()[2]["spawn_dropped"] == 0
