@@ -412,6 +412,19 @@ def batched_leg(args):
     ps_b = sum(ctx.ledger(s)["particle_steps"] for s in range(len(wl.stacks)))
     ctx.close()
 
+    # the same stacks, each 50-step period one persistent cooperative launch
+    # (replayed from a graph)
+    pctx = pic.Context(wl, use_graph=2)
+    torch.cuda.synchronize()
+    ev[0].record(pctx.stream)
+    pctx.step(n)
+    ev[1].record(pctx.stream)
+    torch.cuda.synchronize()
+    ms_p = ev[0].elapsed_time(ev[1])
+    launches_p = pctx.launches
+    ps_p = sum(pctx.ledger(s)["particle_steps"] for s in range(len(wl.stacks)))
+    pctx.close()
+
     singles = [pic.Context(wl.replace(stacks=[st])) for st in wl.stacks]
     torch.cuda.synchronize()
     ev[0].record(singles[0].stream)
@@ -431,6 +444,9 @@ def batched_leg(args):
             "batched_particle_steps_per_s": ps_b / (ms_b * 1e-3),
             "sequential_particle_steps_per_s": ps_s / (ms_s * 1e-3),
             "batched_launches": launches_b, "sequential_launches": launches_s,
+            "persistent_ms": ms_p, "persistent_speedup": ms_s / ms_p,
+            "persistent_particle_steps_per_s": ps_p / (ms_p * 1e-3),
+            "persistent_launches": launches_p,
             "autotune": tune}
 
 

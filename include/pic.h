@@ -94,7 +94,11 @@ typedef struct {
                                common multiple of moment_every and
                                compact_every) from CUDA graphs captured once,
                                the kernels reading the step index from device
-                               memory; 0: one launch per kernel.  Results are
+                               memory; 2: each whole period is one persistent
+                               cooperative launch (every block resident, the
+                               passes of every step separated by grid barriers
+                               with bounded waits), captured in a CUDA graph;
+                               0: one launch per kernel.  Results are
                                identical; kernel timing (pic_profile) always
                                uses single launches. */
     int32_t stack_base;     /* global index of the context's first stack

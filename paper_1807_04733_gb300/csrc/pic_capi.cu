@@ -118,6 +118,11 @@ struct pic_ctx {
     int64_t period_launches[2] = {0, 0};
     int period = 0;
     bool dev_step_valid = false;     // d_ctl->step == step
+    // the persistent kernel (use_graph 2): its configuration and the graph of
+    // one launch covering a period
+    PersistCfg pcfg;
+    cudaGraphExec_t persist_graph = nullptr;
+    bool persist_direct = false;     // the launch could not be captured: launched directly
     // kernel timing (pic_profile)
     bool profiling = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -176,7 +181,7 @@ bool valid_params(const pic_params *p, std::string &why)
     if (p->ring_stages != 0 && (p->ring_stages < 2 || p->ring_stages > 8)) {
         why = "ring_stages must be 0 or 2..8"; return false;
     }
-    if (p->use_graph != 0 && p->use_graph != 1) { why = "use_graph must be 0 or 1"; return false; }
+    if (p->use_graph < 0 || p->use_graph > 2) { why = "use_graph must be 0, 1 or 2"; return false; }
     if (p->consumer_warps != 0 && p->consumer_warps != 4 && p->consumer_warps != 8) {
         why = "consumer_warps must be 0, 4 or 8"; return false;
     }
@@ -356,6 +361,8 @@ void free_all(pic_ctx *c)
         if (g) cudaGraphExecDestroy(g);
         g = nullptr;
     }
+    if (c->persist_graph) cudaGraphExecDestroy(c->persist_graph);
+    c->persist_graph = nullptr;
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     c->cap_stream = nullptr;
     release(c->d_stacks); release(c->d_ent); release(c->d_fent); release(c->d_T);
@@ -662,6 +669,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.dz_pow2 = 1;
     a.inv_dz = 1.0f / p->dz;      // exact: dz is a power of two
     a.flags = p->flags; a.n_e = ne; a.moment_every = p->moment_every;
+    a.compact_every = p->compact_every;
     a.step = 0;
     a.tab_max = tab_max; a.T_max = T_max; a.nbin_max = nbin_max; a.jbin_max = jbin_max;
     a.ftab_max = ftab_max;
@@ -946,7 +954,8 @@ pic_status pic_step(pic_ctx *c, int n_steps)
     if ((int64_t)c->step + n_steps > c->p.n_steps_max)
         return fail(c, PIC_ERR_ARG, "steps would exceed n_steps_max");
     c->launches = 0;
-    const bool graphs = c->p.use_graph == 1 && !c->profiling;
+    const bool persist = c->p.use_graph == 2 && !c->profiling;
+    const bool graphs = (c->p.use_graph == 1 || persist) && !c->profiling;
     if (graphs && c->period == 0) {
         const int me = c->p.moment_every, ce = c->p.compact_every;
         const long long l = (long long)me / gcd_int(me, ce) * ce;
@@ -956,7 +965,48 @@ pic_status pic_step(pic_ctx *c, int n_steps)
     while (left > 0) {
         const int s = c->step;
         cudaError_t e = cudaSuccess;
-        if (graphs && c->period > 0 && s % c->period == 0 && left >= c->period) {
+        if (persist && c->period > 0 && s % c->period == 0 && left >= c->period) {
+            // one cooperative launch runs the whole period (captured in a
+            // graph once; the kernel reads and advances the device step)
+            if (!c->pcfg.ok) {
+                e = configure_persistent(c->args, (c->p.flags & PIC_F_DETERMINISTIC) != 0, &c->pcfg);
+                if (e != cudaSuccess) return cuda_fail(c, e, "pic_step persistent configuration");
+                if (c->pcfg.grid > c->n_status)
+                    return fail(c, PIC_ERR_CUDA, "pic_step: persistent grid larger than the look-back words");
+            }
+            Args a = c->args;
+            a.step_dev = &c->d_ctl->step;
+            const bool det = (c->p.flags & PIC_F_DETERMINISTIC) != 0;
+            if (!c->persist_graph && !c->persist_direct) {
+                if (!c->cap_stream) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+                cudaGraph_t g = nullptr;
+                if (e == cudaSuccess) e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+                if (e == cudaSuccess) {
+                    cudaError_t e1 = launch_persistent(a, c->pcfg, det, c->period, c->cap_stream);
+                    cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &g);
+                    if (e1 == cudaSuccess && e2 == cudaSuccess)
+                        e1 = cudaGraphInstantiate(&c->persist_graph, g, 0);
+                    if (g) cudaGraphDestroy(g);
+                    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+                        cudaGetLastError();               // not capturable here: launch directly
+                        c->persist_graph = nullptr;
+                        c->persist_direct = true;
+                    }
+                }
+                if (e != cudaSuccess) return cuda_fail(c, e, "pic_step persistent capture");
+            }
+            if (!c->dev_step_valid) e = launch_set_step(c->d_ctl, (unsigned int)s, c->stream);
+            if (e == cudaSuccess)
+                e = c->persist_graph ? cudaGraphLaunch(c->persist_graph, c->stream)
+                                     : launch_persistent(a, c->pcfg, det, c->period, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "pic_step persistent launch");
+            c->dev_step_valid = true;
+            c->launches += 1;
+            c->step = s + c->period;
+            left -= c->period;
+            continue;
+        }
+        if (graphs && !persist && c->period > 0 && s % c->period == 0 && left >= c->period) {
             const int which = any_source(c, s, c->period) ? 0 : 1;
             if (!c->period_graph[which]) {
                 e = capture_period(c, which);
@@ -1837,6 +1887,8 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
         if (g) cudaGraphExecDestroy(g);
         g = nullptr;
     }
+    if (c->persist_graph) cudaGraphExecDestroy(c->persist_graph);
+    c->persist_graph = nullptr;
     for (pic_tune_entry &r : res)
         r.chosen = (r.blocks_per_sm == best_c.bps && r.ring_stages == best_c.ring &&
                     r.hist_mode == best_c.hm && r.consumer_warps == best_c.nw) ? 1 : 0;

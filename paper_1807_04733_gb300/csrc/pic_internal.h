@@ -103,7 +103,8 @@ struct DevCtl {
     unsigned int cur;        // current particle buffer (0/1)
     unsigned int timeout_where;
     unsigned int step;       // time step of graph-replayed steps
-    unsigned int pad[2];
+    unsigned int bar_count;  // grid barrier of the persistent kernel: arrivals,
+    unsigned int bar_gen;    //   and its generation
 };
 
 struct Args {            // everything a kernel needs, passed by value
@@ -147,6 +148,7 @@ struct Args {            // everything a kernel needs, passed by value
     uint32_t flags;
     int n_e;
     int moment_every;
+    int compact_every;
     uint32_t step;                           // time step (plain launches)
     const unsigned int *step_dev;            // graph replay: the step is read here
     int bump_step;                           // this kernel's last block advances *step_dev
@@ -239,6 +241,17 @@ cudaError_t launch_flux_w(const Args &a, int w0, int w1, int w_now, const long l
                           cudaStream_t st);
 // set the device step counter read by graph-replayed steps
 cudaError_t launch_set_step(DevCtl *ctl, unsigned int step, cudaStream_t s);
+// the persistent kernel: n_steps whole steps of every stack in one cooperative
+// launch (the step read from and advanced in device memory)
+struct PersistCfg {
+    int grid = 0, ring = 0;
+    size_t smem = 0;
+    bool wsm = false;        // weighted densities privatised in shared memory
+    bool ok = false;
+};
+cudaError_t configure_persistent(const Args &a, bool det, PersistCfg *pc);
+cudaError_t launch_persistent(const Args &a, const PersistCfg &pc, bool det, int n_steps,
+                              cudaStream_t s);
 
 // adjoint replay (pic_adjoint.cu); pass = 1 or 2
 cudaError_t configure_adjoint(const Args &a, int pass, LaunchCfg *cfg);

@@ -4,6 +4,8 @@
 // fluxes through the cell faces.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "pic_step.cuh"
 
 namespace pic {
@@ -172,14 +174,13 @@ __global__ void __launch_bounds__(TPB) k_state_hist_w(const Args a, int s0, int 
     }
 }
 
-// Weighted densities at the end of a density step: every live carrier adds
-// its weight to its (spin, bin, cell) entry.  One block owns a contiguous
-// chunk of tiles; with SM the stack's histogram is privatised in shared
-// memory and flushed once per stack segment, otherwise added in global
-// memory.  Launched after the step's last kernel: in a graph replay that
-// kernel has already advanced the device step counter.
+// Weighted densities at the end of density step `step`: every live carrier
+// adds its weight to its (spin, bin, cell) entry.  One block owns a
+// contiguous chunk of tiles; with SM the stack's histogram is privatised in
+// shared memory and flushed once per stack segment, otherwise added in
+// global memory.
 template <bool SM>
-__global__ void __launch_bounds__(TPB) k_wdep(const Args a)
+__device__ __forceinline__ void phase_wdep(const Args &a, uint32_t step)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned long long *s_h = reinterpret_cast<unsigned long long *>(smem);
@@ -187,7 +188,6 @@ __global__ void __launch_bounds__(TPB) k_wdep(const Args a)
     __shared__ long long s_nsl[PIC_MAX_STACKS];
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
     const int tid = threadIdx.x;
-    const uint32_t step = a.step_dev ? __ldcg(a.step_dev) - 1u : a.step;
     const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
     Plan p;
     make_plan(a, s_tpref, s_nsl, p);
@@ -197,12 +197,12 @@ __global__ void __launch_bounds__(TPB) k_wdep(const Args a)
         return a.nhw + st.n_off + (long long)tout * 2 * a.n_e * st.n_cells;
     };
     auto flush = [&](int s) {
-        __syncthreads();
+        cta_sync();
         const int nb = 2 * a.n_e * a.stacks[s].n_cells;
         unsigned long long *gh = hist(s);
         for (int i = tid; i < nb; i += TPB)
             if (s_h[i]) atomicAdd(&gh[i], s_h[i]);
-        __syncthreads();
+        cta_sync();
     };
     int seg = -1;
     unsigned long long *gh = nullptr;
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(TPB) k_wdep(const Args a)
             if (SM) {
                 if (seg >= 0) flush(seg);
                 for (int i = tid; i < 2 * a.n_e * a.stacks[s].n_cells; i += TPB) s_h[i] = 0ull;
-                __syncthreads();
+                cta_sync();
             }
             gh = hist(s);
             seg = s;
@@ -238,6 +238,14 @@ __global__ void __launch_bounds__(TPB) k_wdep(const Args a)
         }
     }
     if (SM && seg >= 0) flush(seg);
+}
+
+// Launched after the step's last kernel: in a graph replay that kernel has
+// already advanced the device step counter.
+template <bool SM>
+__global__ void __launch_bounds__(TPB) k_wdep(const Args a)
+{
+    phase_wdep<SM>(a, a.step_dev ? __ldcg(a.step_dev) - 1u : a.step);
 }
 
 cudaError_t launch_flux_w(const Args &a, int w0, int w1, int w_now, const long long *now, int ncm,
@@ -416,6 +424,167 @@ cudaError_t launch_slow(const Args &a0, const LaunchCfg &c, bool det, bool dep, 
         else { k_event<false, false><<<g, TPB, sm, s>>>(ae); k_place<false, false><<<gp, TPB, smp, s>>>(a); }
     }
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// The persistent kernel: whole steps of every stack in one cooperative launch
+// (batched stacks, use_graph = 2).  Blocks of 288 threads run the streaming
+// pass with all nine warps (eight consumers and the producer) and every other
+// pass on warps 0-7 (the passes' 256-thread barriers become a named barrier
+// of those warps); a grid barrier separates the passes.  The step is read
+// from and advanced in device memory, so the launch replays from a graph.
+// ---------------------------------------------------------------------------
+
+// Grid barrier: every block resident (a cooperative launch).  Sense by
+// generation; the wait is bounded in polls, after which the status says
+// PIC_ERR_TIMEOUT and every later barrier of the launch passes at once.
+__device__ __forceinline__ void grid_sync(const Args &a)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int *gen = &a.ctl->bar_gen;
+        const unsigned int g = *gen;
+        __threadfence();
+        if (atomicAdd(&a.ctl->bar_count, 1u) == gridDim.x - 1) {
+            a.ctl->bar_count = 0u;           // the next arrivals follow the new generation
+            __threadfence();
+            atomicAdd(&a.ctl->bar_gen, 1u);
+        } else {
+            unsigned int it = 0;
+            while (*gen == g) {
+                if (*(volatile unsigned int *)&a.ctl->status != 0u) break;
+                if (++it > a.spin_limit) {
+                    atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+                    a.ctl->timeout_where = 5u;
+                    break;
+                }
+                if (it > 64) __nanosleep(256);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// a source half step with carriers in some stack (uniform: device data)
+__device__ __forceinline__ bool any_source(const Args &a, long long h)
+{
+    for (int s = 0; s < a.n_stacks; ++s)
+        if (a.inj[a.stacks[s].inj_off + h] > 0) return true;
+    return false;
+}
+
+template <bool DET, bool WSM>
+__global__ void __launch_bounds__(stream_threads<8>(), 2) k_period(const Args a, int n_steps)
+{
+    __shared__ int s_stop;
+    const bool low = threadIdx.x < TPB;      // the warps of the 256-thread passes
+    for (int i = 0; i < n_steps; ++i) {
+        // stop after a failure (a decision of the whole block)
+        if (threadIdx.x == 0) s_stop = *(volatile unsigned int *)&a.ctl->status != 0u;
+        __syncthreads();
+        if (s_stop) break;
+        const uint32_t s = __ldcg(a.step_dev);
+        const bool dep = ((s + 1) % (uint32_t)a.moment_every) == 0;
+        if (any_source(a, 2 * (long long)s)) {
+            if (low) phase_inject<0>(a, 0, 0);
+            grid_sync(a);
+        }
+        if (dep) phase_stream<DET, true, false, 8>(a);
+        else phase_stream<DET, false, false, 8>(a);
+        grid_sync(a);
+        if (low) {
+            if (dep) phase_event<DET, true>(a);
+            else phase_event<DET, false>(a);
+        }
+        grid_sync(a);
+        if (low) {
+            if (dep) phase_place<DET, true>(a);
+            else phase_place<DET, false>(a);
+        }
+        grid_sync(a);
+        if (any_source(a, 2 * (long long)s + 1)) {
+            if (low) phase_inject<0>(a, 1, dep ? 1 : 0);
+            grid_sync(a);
+        }
+        if (dep && a.w[0]) {
+            if (low) phase_wdep<WSM>(a, s);
+            grid_sync(a);
+        }
+        if (((s + 1) % (uint32_t)a.compact_every) == 0) {
+            if (low) phase_compact<0>(a);
+            grid_sync(a);
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            *const_cast<unsigned int *>(a.step_dev) = s + 1u;
+            __threadfence();
+        }
+        grid_sync(a);
+    }
+}
+
+cudaError_t configure_persistent(const Args &a, bool det, PersistCfg *pc)
+{
+    int dev = 0, sms = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    // dynamic shared memory: the largest pass
+    const size_t tiles = (size_t)(2 * a.n_stacks + 1) * 8 + 16;
+    const size_t fixed_dep = (size_t)a.ftab_max * sizeof(FastEnt) + tiles +
+                             (size_t)(a.nbin_max + a.gbin_max) * 4 + (size_t)a.gbin_max * 16 + 8;
+    const int gmax = 16 * sms;
+    const size_t other = std::max({event_smem(a, true, 0, gmax), place_smem(a, true, 0)});
+    const size_t wsm = (size_t)a.nbin_max * 8;
+    const bool wsm_ok = a.w[0] && wsm + (size_t)(2 * PIC_MAX_STACKS + 1) * 8 + 4096 <= (size_t)optin;
+    PersistCfg best;
+    for (int ring = 8; ring >= 2; --ring) {
+        size_t sm = std::max(fixed_dep + (size_t)ring * 3 * TILE_BYTES, other);
+        if (wsm_ok) sm = std::max(sm, wsm);
+        int o = 0;
+        auto k = det ? (wsm_ok ? k_period<true, true> : k_period<true, false>)
+                     : (wsm_ok ? k_period<false, true> : k_period<false, false>);
+        e = occupancy(k, sm, &o, stream_threads<8>());
+        if (e != cudaSuccess) return e;
+        if (o < 1) continue;
+        // the most resident blocks, then the deepest ring
+        if (!best.ok || o > best.grid / sms) {
+            best.grid = sms * o;
+            best.ring = ring;
+            best.smem = sm;
+            best.wsm = wsm_ok;
+            best.ok = true;
+        }
+    }
+    *pc = best;
+    return best.ok ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+cudaError_t launch_persistent(const Args &a0, const PersistCfg &pc, bool det, int n_steps,
+                              cudaStream_t s)
+{
+    Args a = a0;
+    a.ring = pc.ring;
+    a.grid_fast = pc.grid;
+    a.bump_step = 0;
+    const bool wsm_ok = pc.wsm;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)pc.grid);
+    cfg.blockDim = dim3((unsigned)stream_threads<8>());
+    cfg.dynamicSmemBytes = pc.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (det) {
+        if (wsm_ok) return cudaLaunchKernelEx(&cfg, k_period<true, true>, a, n_steps);
+        return cudaLaunchKernelEx(&cfg, k_period<true, false>, a, n_steps);
+    }
+    if (wsm_ok) return cudaLaunchKernelEx(&cfg, k_period<false, true>, a, n_steps);
+    return cudaLaunchKernelEx(&cfg, k_period<false, false>, a, n_steps);
 }
 
 cudaError_t launch_inject(const Args &a, const LaunchCfg &c, int half, bool deposit,

@@ -191,6 +191,28 @@ __device__ __forceinline__ void add_flux(int32_t *sJ, int nf, int sg, int c0, in
     else         for (int f = c1 + 1; f <= c0; ++f) atomicAdd(&sJ[sg * nf + f], -1);
 }
 
+// Barrier of the threads that run a 256-thread pass: the whole block in an
+// ordinary launch; warps 0-7 in the persistent kernel, whose blocks have the
+// streaming pass's 288 threads (its producer warp sits out the other passes).
+// blockDim is uniform over a block, so the choice is too.
+__device__ __forceinline__ void cta_sync()
+{
+    if (blockDim.x == TPB) __syncthreads();
+    else asm volatile("bar.sync 2, %0;" ::"n"(TPB) : "memory");
+}
+
+__device__ __forceinline__ bool cta_sync_or(bool p)
+{
+    if (blockDim.x == TPB) return __syncthreads_or(p) != 0;
+    uint32_t r;
+    asm volatile("{\n .reg .pred q, o;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred o, 2, %2, q;\n"
+                 " selp.u32 %0, 1, 0, o;\n}\n"
+                 : "=r"(r)
+                 : "r"((uint32_t)p), "n"(TPB)
+                 : "memory");
+    return r != 0;
+}
+
 // Block-wide exclusive scan of small non-negative ints; returns the total.
 __device__ __forceinline__ int block_scan(int v, int &excl, int *s_w)
 {
@@ -202,7 +224,7 @@ __device__ __forceinline__ int block_scan(int v, int &excl, int *s_w)
         if (lane >= o) x += y;
     }
     if (lane == 31) s_w[wid] = x;
-    __syncthreads();
+    cta_sync();
     if (wid == 0) {
         int w = lane < TPB / 32 ? s_w[lane] : 0;
 #pragma unroll
@@ -212,10 +234,10 @@ __device__ __forceinline__ int block_scan(int v, int &excl, int *s_w)
         }
         if (lane < TPB / 32) s_w[lane] = w;        // inclusive warp totals
     }
-    __syncthreads();
+    cta_sync();
     excl = x - v + (wid ? s_w[wid - 1] : 0);
     const int total = s_w[TPB / 32 - 1];
-    __syncthreads();
+    cta_sync();
     return total;
 }
 
@@ -225,11 +247,11 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = v;
-    __syncthreads();
+    cta_sync();
     unsigned long long t = 0;
     if (threadIdx.x == 0)
         for (int i = 0; i < TPB / 32; ++i) t += s_r[i];
-    __syncthreads();
+    cta_sync();
     return t;  // valid in thread 0
 }
 
@@ -314,7 +336,7 @@ __device__ __forceinline__ void make_plan(const Args &a, long long *s_tpref,
 {
     for (int i = threadIdx.x; i < a.n_stacks; i += TPB)
         s_nsl[i] = (long long)a.cnt[i].n_slots;
-    __syncthreads();
+    cta_sync();
     if (threadIdx.x == 0) {
         long long acc = 0;
         for (int i = 0; i < a.n_stacks; ++i) {
@@ -323,7 +345,7 @@ __device__ __forceinline__ void make_plan(const Args &a, long long *s_tpref,
         }
         s_tpref[a.n_stacks] = acc;
     }
-    __syncthreads();
+    cta_sync();
     p.T = s_tpref[a.n_stacks];
     p.t0 = p.T * blockIdx.x / gridDim.x;
     p.t1 = p.T * (blockIdx.x + 1) / gridDim.x;
@@ -342,13 +364,13 @@ __device__ __forceinline__ int stack_of(const long long *s_tpref, int n, long lo
 // Last-block-done: returns true in every thread of the block that finished last.
 __device__ __forceinline__ bool last_block(const Args &a, int *s_flag)
 {
-    __syncthreads();
+    cta_sync();
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int t = atomicAdd(&a.ctl->done, 1u);
         *s_flag = (t == gridDim.x - 1);
     }
-    __syncthreads();
+    cta_sync();
     const bool last = *s_flag != 0;
     if (last) __threadfence();
     return last;
@@ -358,9 +380,9 @@ __device__ __forceinline__ void load_stack(const Args &a, int s, Stk &k, DevStac
                                            TabEnt *s_ent, uint32_t *s_T, float *s_edge,
                                            uint32_t *s_p0)
 {
-    __syncthreads();
+    cta_sync();
     if (threadIdx.x == 0) *s_st = a.stacks[s];
-    __syncthreads();
+    cta_sync();
     const DevStack &st = *s_st;
     for (int i = threadIdx.x; i < st.tab_n; i += TPB) s_ent[i] = a.ent[st.ent_off + i];
     for (int i = threadIdx.x; i < st.T_n; i += TPB) s_T[i] = a.T_thr[st.T_off + i];
@@ -472,7 +494,7 @@ __device__ __forceinline__ long long look_back_place(const Args &a, unsigned int
 __device__ __forceinline__ long long make_tiles(const Args &a, long long *s_tpref, long long *s_nsl)
 {
     for (int i = threadIdx.x; i < a.n_stacks; i += TPB) s_nsl[i] = (long long)a.cnt[i].n_slots;
-    __syncthreads();
+    cta_sync();
     if (threadIdx.x == 0) {
         long long acc = 0;
         for (int i = 0; i < a.n_stacks; ++i) {
@@ -481,7 +503,7 @@ __device__ __forceinline__ long long make_tiles(const Args &a, long long *s_tpre
         }
         s_tpref[a.n_stacks] = acc;
     }
-    __syncthreads();
+    cta_sync();
     return s_tpref[a.n_stacks];
 }
 
@@ -571,7 +593,7 @@ template <int NW>
 constexpr int stream_threads() { return 32 * NW + 32; }
 
 template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0>
-__global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW, ADJ>()) k_stream(const Args a)
+__device__ __forceinline__ void phase_stream(const Args &a)
 {
     constexpr int NT = 32 * NW;              // consumer threads
     constexpr int G = TILE / NT;             // slots per consumer thread and tile
@@ -637,6 +659,10 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW, ADJ>()) k_
     // ---------------- producer warp ----------------
     if (warp == NW) {
         if (lane == 0) {
+            // the bulk copies (async proxy) read global memory written with
+            // ordinary stores by earlier passes: within one persistent launch
+            // that order needs this fence (between launches it is implied)
+            asm volatile("fence.proxy.async;" ::: "memory");
             long long issued = 0;
             int stg = 0;
             uint32_t phase = 0;          // completions of stage stg so far, mod 2
@@ -929,6 +955,12 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW, ADJ>()) k_
     if (tid == 0) a.qcnt[b] = (uint32_t)s_qn;
 }
 
+template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0>
+__global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW, ADJ>()) k_stream(const Args a)
+{
+    phase_stream<DET, DEPN, WAGG, NW, ADJ>(a);
+}
+
 // ---------------------------------------------------------------------------
 // k_event: the general step for the queued (eventful) carriers.
 //
@@ -946,7 +978,7 @@ __global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW, ADJ>()) k_
 #define PIC_SLOW_MIN_BLOCKS 2      // resident blocks per SM of the event pass
 #endif
 template <bool DET, bool DEPN, int ADJ = 0>
-__global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a)
+__device__ __forceinline__ void phase_event(const Args &a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     TabEnt *s_ent = reinterpret_cast<TabEnt *>(smem);
@@ -996,7 +1028,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
         run += tot;
     }
     if (tid == 0) s_qpre[Gf] = run;
-    __syncthreads();
+    cta_sync();
     const long long M = s_qpre[Gf];
     const long long i0 = M * b / G, i1 = M * (b + 1) / G;
 
@@ -1025,7 +1057,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
     Tally ty{};
 
     auto flush_segment = [&](int s) {
-        __syncthreads();
+        cta_sync();
         const DevStack &st = s_st;
         const int nf = st.n_cells + 1;
         if (!ADJ) {
@@ -1075,7 +1107,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
             if (q == 0 && tid == 0 && v) atomicAdd(&a.cnt[s].live, 0ull - v);
         }
         ty = Tally{};
-        __syncthreads();
+        cta_sync();
     };
 
     // the general step for item i of the concatenated queue, of stack s
@@ -1227,7 +1259,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
                 for (int q = tid; q < s_st.T_n; q += TPB) s_gT[q] = 0.0;
             }
             if (tid == 0) s_next = (unsigned long long)lo;
-            __syncthreads();
+            cta_sync();
 #pragma unroll 1
             for (;;) {
                 unsigned long long base = 0;
@@ -1251,6 +1283,12 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
     }
 }
 
+template <bool DET, bool DEPN, int ADJ = 0>
+__global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a)
+{
+    phase_event<DET, DEPN, ADJ>(a);
+}
+
 // ---------------------------------------------------------------------------
 // k_place: slots and ids of the secondaries staged by k_event.
 //
@@ -1262,7 +1300,7 @@ __global__ void __launch_bounds__(TPB, PIC_SLOW_MIN_BLOCKS) k_event(const Args a
 // bounded wait.  Every block publishes its own count before it waits.
 // ---------------------------------------------------------------------------
 template <bool DET, bool DEPN, int ADJ = 0>
-__global__ void __launch_bounds__(TPB) k_place(const Args a)
+__device__ __forceinline__ void phase_place(const Args &a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     // births per (spin, cell) of this step (the births-minus-removals
@@ -1363,7 +1401,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
         for (long long wb = w0; wb < w1; wb += TPB) {
             const long long w = wb + tid;
             uint32_t bits = w < w1 ? a.spawn_bits[w] : 0u;
-            if (!__syncthreads_or(bits != 0u)) continue;     // no secondary here
+            if (!cta_sync_or(bits != 0u)) continue;     // no secondary here
             int excl;
             const int tot = block_scan(__popc(bits), excl, s_w);
             if (bits) {
@@ -1431,7 +1469,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
 
     // deposits and boundary tallies of the placed secondaries of stack s
     auto flush = [&](int s) {
-        __syncthreads();
+        cta_sync();
         const DevStack &st = a.stacks[s];
         const int nf = st.n_cells + 1;
         if (!ADJ) {
@@ -1472,7 +1510,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
             if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
         }
         ty = Tally{};
-        __syncthreads();
+        cta_sync();
     };
 
     // staged secondaries in tiles [tl0, tl1): the block's count (thread 0)
@@ -1522,7 +1560,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
                 s_cl = c_last;
             }
         }
-        __syncthreads();
+        cta_sync();
         (void)c_first;
         for (int s = s_first; s <= s_last; ++s) {
             const long long sg0 = s_tpref[s] > t0 ? s_tpref[s] : t0;
@@ -1543,7 +1581,7 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
                 if (vmom)
                     for (int q = tid; q < 2 * nc; q += TPB) s_v[q] = 0ull;
             }
-            __syncthreads();
+            cta_sync();
             const long long n = place(s, sg0, sg1, prefix);
             if (sg1 == s_tpref[s + 1] && tid == 0)
                 a.cnt[s].spawn_total = (unsigned long long)(prefix + n);
@@ -1571,11 +1609,17 @@ __global__ void __launch_bounds__(TPB) k_place(const Args a)
     }
 }
 
+template <bool DET, bool DEPN, int ADJ = 0>
+__global__ void __launch_bounds__(TPB) k_place(const Args a)
+{
+    phase_place<DET, DEPN, ADJ>(a);
+}
+
 // ---------------------------------------------------------------------------
 // k_inject: Source(dt/2) for half step h = 2*step + half (Eq. Strang-source)
 // ---------------------------------------------------------------------------
 template <int ADJ = 0>
-__global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int deposit)
+__device__ __forceinline__ void phase_inject(const Args &a, int half, int deposit)
 {
     __shared__ long long s_pref[PIC_MAX_STACKS + 1];
     __shared__ long long s_n[PIC_MAX_STACKS];
@@ -1594,13 +1638,13 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
         s_q[s] = 0;
         s_wsum[s] = 0;
     }
-    __syncthreads();
+    cta_sync();
     if (tid == 0) {
         long long acc = 0;
         for (int s = 0; s < a.n_stacks; ++s) { s_pref[s] = acc; acc += s_n[s]; }
         s_pref[a.n_stacks] = acc;
     }
-    __syncthreads();
+    cta_sync();
     const long long total = s_pref[a.n_stacks];
     const int tj = (int)(step / (uint32_t)a.moment_every);
     const int tout = (int)((step + 1) / (uint32_t)a.moment_every) - 1;
@@ -1684,7 +1728,7 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
             }
         }
     }
-    __syncthreads();
+    cta_sync();
     for (int s = tid; s < a.n_stacks; s += TPB) {
         if (s_q[s]) atomicAdd(&a.cnt[s].led[L_Q_INJECTED], s_q[s]);
         if (s_wsum[s]) atomicAdd(&a.cnt[s].w_injected, s_wsum[s]);
@@ -1710,11 +1754,17 @@ __global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int depo
     }
 }
 
+template <int ADJ = 0>
+__global__ void __launch_bounds__(TPB) k_inject(const Args a, int half, int deposit)
+{
+    phase_inject<ADJ>(a, half, deposit);
+}
+
 // ---------------------------------------------------------------------------
 // k_compact: stable removal of dead slots (k = 0) into the other buffer
 // ---------------------------------------------------------------------------
 template <int ADJ = 0>
-__global__ void __launch_bounds__(TPB) k_compact(const Args a)
+__device__ __forceinline__ void phase_compact(const Args &a)
 {
     __shared__ long long s_tpref[PIC_MAX_STACKS + 1];
     __shared__ long long s_nsl[PIC_MAX_STACKS];
@@ -1783,7 +1833,7 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
                 if (tid == 0) s_prefix = pre;
             }
         }
-        __syncthreads();
+        cta_sync();
         pre_first = s_prefix;
         (void)c_first;
         // phase 2: scatter live slots, stable, into the other buffer
@@ -1854,6 +1904,12 @@ __global__ void __launch_bounds__(TPB) k_compact(const Args a)
             a.ctl->epoch = ep + 1u;
         }
     }
+}
+
+template <int ADJ = 0>
+__global__ void __launch_bounds__(TPB) k_compact(const Args a)
+{
+    phase_compact<ADJ>(a);
 }
 
 // ---------------------------------------------------------------------------

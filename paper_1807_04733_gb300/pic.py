@@ -185,7 +185,8 @@ def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hi
     p.compact_every = wl.compact_every; p.moment_every = wl.moment_every
     p.n_steps_max = wl.n_steps if n_steps_max is None else n_steps_max
     p.blocks_per_sm = blocks_per_sm; p.hist_mode = hist_mode; p.ring_stages = ring_stages
-    p.use_graph = 1 if use_graph else 0
+    # True/1: graph-replayed periods; 2 or "persistent": one persistent launch per period
+    p.use_graph = 2 if use_graph in (2, "persistent") else (1 if use_graph else 0)
     p.stack_base = stack_base
     p.consumer_warps = consumer_warps
     return p

@@ -73,3 +73,85 @@ def test_graph_steps_bitexact_batched_and_adjoint():
     assert torch.allclose(a_T, b_T, rtol=1e-12, atol=1e-9)
     plain.close()
     graph.close()
+
+
+# ---------------------------------------------------------------------------
+# One persistent launch per period (use_graph = 2): every block resident, the
+# passes of each step separated by grid barriers, the launch itself replayed
+# from a graph.  Bit-exact with single launches.
+# ---------------------------------------------------------------------------
+def full_state(ctx, wl):
+    out = state(ctx, len(wl.stacks))
+    for s in range(len(wl.stacks)):
+        out.append((ctx.gen_moments(s).cpu().numpy(),))
+        if wl.flags & W.FLAG_VELOCITY:
+            out.append((ctx.vel_moments(s).cpu().numpy(),))
+        if wl.flags & W.FLAG_WEIGHTS:
+            nw, Jw, wi = ctx.weighted_moments(s)
+            out.append((nw.cpu().numpy(), Jw.cpu().numpy(), wi, ctx.weights(s)))
+    return out
+
+
+def same_full(a, b):
+    assert len(a) == len(b)
+    same([x for x in a if len(x) == 4 and isinstance(x[2], dict)],
+         [x for x in b if len(x) == 4 and isinstance(x[2], dict)])
+    for x, y in zip(a, b):
+        for u, v in zip(x, y):
+            if isinstance(u, np.ndarray):
+                assert np.array_equal(u, v)
+            elif not isinstance(u, dict):
+                assert u == v
+
+
+@pytest.mark.parametrize("chunks", [[400], [5, 50, 13, 100, 232]])
+def test_persistent_launch_bitexact_single_stack(chunks):
+    wl = W.spin_valve(True, n0=20_000, capacity=40_000, n_steps=400, flags=DET,
+                      moment_every=3, compact_every=7)
+    plain = pic.Context(wl)
+    pers = pic.Context(wl, use_graph=2)
+    for n in chunks:
+        plain.step(n)
+        pers.step(n)
+        same(state(plain, 1), state(pers, 1))
+    plain.close()
+    pers.close()
+
+
+def test_persistent_launch_one_launch_per_period_batched():
+    """Six batched stacks through the pulse, moments every step, compaction
+    every 50: one launch per 50-step period, results equal single launches,
+    and the adjoint afterwards equals the single-launch run's."""
+    wl = W.batched(n_stacks=6, scale=2e-3, n_steps=200, flags=DET | W.FLAG_VELOCITY)
+    plain = pic.Context(wl)
+    pers = pic.Context(wl, use_graph=2)
+    plain.step(200)
+    pers.step(200)
+    assert pers.launches == 4                 # 200 steps = 4 periods of 50
+    same_full(full_state(plain, wl), full_state(pers, wl))
+    S, ne = 6, wl.n_e
+    ncm = pers.n_cells_max
+    _, n_out, _ = pers.shape(0)
+    rng = np.random.default_rng(2)
+    gn = torch.from_numpy((rng.integers(-1024, 1025, (S, n_out, 2, ne, ncm)) / 1024.0)
+                          .astype(np.float32)).cuda()
+    gJ = torch.zeros((S, n_out, 2, ncm + 1), dtype=torch.float32, device="cuda")
+    a_tau, a_T = plain.grad(gn, gJ)
+    b_tau, b_T = pers.grad(gn, gJ)
+    assert torch.allclose(a_tau, b_tau, rtol=1e-12, atol=1e-9)
+    assert torch.allclose(a_T, b_T, rtol=1e-12, atol=1e-9)
+    plain.close()
+    pers.close()
+
+
+def test_persistent_launch_weights():
+    wl = W.config(0, scale=0.02, flags=DET | W.FLAG_WEIGHTS).replace(n_steps=250)
+    st = wl.stacks[0]
+    st.e_bias = np.arange(1, wl.n_e + 1, dtype=np.float64)
+    plain = pic.Context(wl)
+    pers = pic.Context(wl, use_graph=2)
+    plain.step(250)
+    pers.step(250)
+    same_full(full_state(plain, wl), full_state(pers, wl))
+    plain.close()
+    pers.close()
