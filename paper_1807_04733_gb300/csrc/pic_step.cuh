@@ -255,6 +255,30 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;  // valid in thread 0
 }
 
+// Block sums of N per-thread counts in one reduction (one barrier instead
+// of two per count): thread q < N receives the sum of count q.  s_w holds
+// (TPB / 32) x N words.  A warp's sum of a count stays below 2^32 (a thread
+// counts at most its share of a launch's items, times 59 quanta).
+template <int N>
+__device__ __forceinline__ unsigned long long block_sums(const uint32_t (&v)[N],
+                                                         unsigned long long *s_w)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int q = 0; q < N; ++q) {
+        uint32_t x = v[q];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) s_w[warp * N + q] = x;
+    }
+    cta_sync();
+    unsigned long long t = 0;
+    if (threadIdx.x < N)
+        for (int w = 0; w < TPB / 32; ++w) t += s_w[w * N + threadIdx.x];
+    cta_sync();
+    return t;
+}
+
 // Status word of the look-back: epoch:32 | flag:2 | value:30
 constexpr unsigned long long FLAG_A = 1ull, FLAG_P = 2ull;
 __device__ __forceinline__ void publish(unsigned long long *w, unsigned int ep,
@@ -1002,6 +1026,7 @@ __device__ __forceinline__ void phase_event(const Args &a)
     __shared__ DevStack s_st;
     __shared__ int s_w[TPB / 32];
     __shared__ unsigned long long s_r[TPB / 32];
+    __shared__ unsigned long long s_r8[(TPB / 32) * 8];    // block sums of the ledger counts
     __shared__ unsigned long long s_next;
     __shared__ long long s_cut;
 
@@ -1097,14 +1122,13 @@ __device__ __forceinline__ void phase_event(const Args &a)
         unsigned long long *L = a.cnt[s].led;
         const uint32_t vals[8] = {ty.absorbed, ty.bath, ty.hits, ty.trans, ty.trunc,
                                   ty.spawn_drop, ty.q_drop, ty.changed};
-        const int idx[8] = {L_ABSORBED, L_Q_BATH, L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED,
-                            L_SPAWN_DROPPED, L_Q_DROPPED, L_CHANGED};
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const unsigned long long v = block_sum_u64(vals[q], s_r);
-            if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
+        const unsigned long long v = block_sums<8>(vals, s_r8);
+        if (tid < 8 && v) {
+            const int idx[8] = {L_ABSORBED, L_Q_BATH, L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED,
+                                L_SPAWN_DROPPED, L_Q_DROPPED, L_CHANGED};
+            atomicAdd(&L[idx[tid]], v);
             // removed carriers leave the live count
-            if (q == 0 && tid == 0 && v) atomicAdd(&a.cnt[s].live, 0ull - v);
+            if (tid == 0) atomicAdd(&a.cnt[s].live, 0ull - v);
         }
         ty = Tally{};
         cta_sync();
@@ -1315,6 +1339,7 @@ __device__ __forceinline__ void phase_place(const Args &a)
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     __shared__ int s_w[TPB / 32];
     __shared__ unsigned long long s_r[TPB / 32];
+    __shared__ unsigned long long s_r8[(TPB / 32) * 8];    // block sums of the ledger counts
     __shared__ long long s_pre[2], s_cl;
     __shared__ int s_flag;
 
@@ -1502,12 +1527,11 @@ __device__ __forceinline__ void phase_place(const Args &a)
         }
         unsigned long long *L = a.cnt[s].led;
         const uint32_t vals[5] = {ty.hits, ty.trans, ty.trunc, ty.spawn_drop, ty.q_drop};
-        const int idx[5] = {L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED, L_SPAWN_DROPPED,
-                            L_Q_DROPPED};
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-            const unsigned long long v = block_sum_u64(vals[q], s_r);
-            if (tid == 0 && v) atomicAdd(&L[idx[q]], v);
+        const unsigned long long v = block_sums<5>(vals, s_r8);
+        if (tid < 5 && v) {
+            const int idx[5] = {L_IFACE_HITS, L_IFACE_TRANSMIT, L_TRUNCATED, L_SPAWN_DROPPED,
+                                L_Q_DROPPED};
+            atomicAdd(&L[idx[tid]], v);
         }
         ty = Tally{};
         cta_sync();
