@@ -570,11 +570,13 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 // label and, with PIC_F_VELOCITY_MOMENTS, velocity) into shared-memory
 // histograms flushed once per block and stack segment.
 //
-// ADJ = 1, 2: the same pass in the two replays of the adjoint, with the
-// per-slot reward (a fourth array of the ring): a finished carrier earns the
-// flux weights of the faces it crossed and, on a density step, the weight of
-// its bin; pass 2 also adds its reward-to-go to the no-scattering sum of its
-// table entry.
+// ADJ = 1, 2: the same pass in the two replays of the adjoint: a finished
+// carrier earns the flux weights of the faces it crossed and, on a density
+// step, the weight of its bin.  Pass 1 adds a nonzero reward to the slot's
+// sum in memory (most carriers earn none in a step); pass 2 streams the
+// slots' rewards-to-go as a further array of the ring, subtracts the
+// rewards and adds each reward-to-go to the no-scattering sum of its table
+// entry.
 // ---------------------------------------------------------------------------
 // resident blocks per SM the register budget must allow: four of 288
 // threads (eight consumer warps, 56 registers) or five of 160 (four consumer
@@ -585,11 +587,12 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 #ifndef PIC_STREAM_MIN_BLOCKS_4
 #define PIC_STREAM_MIN_BLOCKS_4 5
 #endif
-// the replays carry the slots' rewards as well: three blocks (72 registers)
+// the second replay carries the slots' rewards-to-go as well: three blocks
+// (72 registers); the first fits four
 template <int NW, int ADJ>
 constexpr int stream_min_blocks()
 {
-    return ADJ ? 3 : (NW == 8 ? PIC_STREAM_MIN_BLOCKS_8 : PIC_STREAM_MIN_BLOCKS_4);
+    return ADJ == 2 ? 3 : ADJ == 1 ? 4 : (NW == 8 ? PIC_STREAM_MIN_BLOCKS_8 : PIC_STREAM_MIN_BLOCKS_4);
 }
 
 template <int NW>
@@ -622,7 +625,10 @@ __device__ __forceinline__ void phase_stream(const Args &a)
     constexpr int NT = 32 * NW;              // consumer threads
     constexpr int G = TILE / NT;             // slots per consumer thread and tile
     constexpr int NC = G / 4;                // Philox calls (and float4s) per thread
-    constexpr int STG = ADJ ? 5 : 3;         // ring arrays: z, (mu, packed) [, reward]
+    // ring arrays: z, (mu, packed) and, in pass 2, the reward-to-go (pass 1
+    // only adds to the rewards: it does so in memory, for the carriers that
+    // earn one)
+    constexpr int STG = ADJ == 2 ? 5 : 3;
     static_assert(G % 4 == 0 && G <= 8, "4 or 8 slots per thread");
     extern __shared__ __align__(128) unsigned char smem[];
     float *ring = reinterpret_cast<float *>(smem);                      // a.ring x STG x TILE
@@ -706,7 +712,7 @@ __device__ __forceinline__ void phase_stream(const Args &a)
                 mbar_expect_tx(&s_full[stg], STG * TILE_BYTES);
                 bulk_load(dst, Z + off, TILE_BYTES, &s_full[stg]);
                 bulk_load(dst + TILE, MP + 2 * off, 2 * TILE_BYTES, &s_full[stg]);
-                if (ADJ) bulk_load(dst + 3 * TILE, a.acc[cur] + off, 2 * TILE_BYTES, &s_full[stg]);
+                if (ADJ == 2) bulk_load(dst + 3 * TILE, a.acc[cur] + off, 2 * TILE_BYTES, &s_full[stg]);
                 issued = i + 1;
                 if (++stg == nring) { stg = 0; phase ^= 1u; }
             }
@@ -828,8 +834,8 @@ __device__ __forceinline__ void phase_stream(const Args &a)
         const uint4 *rmp = reinterpret_cast<const uint4 *>(rz + TILE);   // (mu, packed) pairs
         float zin[G], min_[G];
         uint32_t pin[G];
-        long long av[ADJ ? G : 1];           // replay: the slots' rewards
-        if (ADJ) {
+        long long av[ADJ == 2 ? G : 1];      // pass 2: the slots' rewards-to-go
+        if (ADJ == 2) {
             const longlong2 *racc = reinterpret_cast<const longlong2 *>(rz + 3 * TILE);
 #pragma unroll
             for (int c = 0; c < G / 2; ++c) {
@@ -895,8 +901,15 @@ __device__ __forceinline__ void phase_stream(const Args &a)
                     if (ADJ == 2 && av[j] != 0)
                         atomicAdd(&s_sr[(layer * 2 + sg) * ne + (int)k - 1], (unsigned long long)av[j]);
                     if (r != 0) {
-                        av[j] = ADJ == 1 ? av[j] + r : av[j] - r;
-                        achg = true;
+                        if (ADJ == 1) {
+                            // pass 1: added in memory (this thread owns the slot)
+                            atomicAdd(reinterpret_cast<unsigned long long *>(a.acc[cur]) + (gZs - Z) +
+                                          slot0 + i0 + j,
+                                      (unsigned long long)r);
+                        } else {
+                            av[j] -= r;
+                            achg = true;
+                        }
                     }
                 }
             }
@@ -930,7 +943,7 @@ __device__ __forceinline__ void phase_stream(const Args &a)
             for (int j = 0; j < G; ++j)
                 if (i0 + j < nvalid) gZ[j] = zo[j];
         }
-        if (ADJ && achg) {
+        if (ADJ == 2 && achg) {
             long long *gA = a.acc[cur] + (gZs - Z) + slot0 + i0;
             if (i0 + G <= nvalid) {
 #pragma unroll
@@ -1159,7 +1172,7 @@ __device__ __forceinline__ void phase_event(const Args &a)
         const int c_start = ADJ ? cell_of(a, S, z) : 0;     // the replay's flux reward
         // adjoint: the slot's reward sum; in pass 2 the reward-to-go R
         // that weights every decision of this step
-        const long long R = ADJ ? a.acc[cur][gslot] : 0;
+        const long long R = ADJ == 2 ? a.acc[cur][gslot] : 0;
         const double Rd = ADJ == 2 ? (double)R * a.inv_q : 0.0;
         flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, key_x, S.ctr_hi,
                               step, SUB_IF, ty, Rd, s_gT);
@@ -1253,7 +1266,8 @@ __device__ __forceinline__ void phase_event(const Args &a)
                 if (DEPN) rw += dep_w(a, s, tout, sg, k, c_end);
             }
         }
-        if (ADJ && rw != 0) a.acc[cur][gslot] = ADJ == 1 ? R + rw : R - rw;
+        if (ADJ == 1 && rw != 0) a.acc[cur][gslot] += rw;
+        if (ADJ == 2 && rw != 0) a.acc[cur][gslot] = R - rw;
         Z[gslot] = z;
         if (__float_as_uint(mu) != __float_as_uint(mu_in) || pk != pk_in) {
             ++ty.changed;
@@ -1972,7 +1986,7 @@ static cudaError_t pick_stream_ring(size_t fixed, int blocks_per_sm, int ring_re
     int best = -1;
     for (int r = 2; r <= MAX_RING; ++r) {
         if (ring_req > 0 && r != ring_req) continue;
-        const size_t sm = fixed + (size_t)r * (ADJ ? 5 : 3) * TILE_BYTES;
+        const size_t sm = fixed + (size_t)r * (ADJ == 2 ? 5 : 3) * TILE_BYTES;
         int o1 = 0, o2 = 0;
         cudaError_t e = occupancy(k_stream<false, DEPN, WAGG, NW, ADJ>, sm, &o1, stream_threads<NW>());
         if (e == cudaSuccess) e = occupancy(k_stream<true, DEPN, WAGG, NW, ADJ>, sm, &o2, stream_threads<NW>());
@@ -1986,6 +2000,13 @@ static cudaError_t pick_stream_ring(size_t fixed, int blocks_per_sm, int ring_re
     }
     return best < 0 ? cudaErrorInvalidConfiguration : cudaSuccess;
 }
+// Waves of resident blocks in the event pass's grid (its blocks take equal
+// shares of the queue and never wait on one another).  One wave: a block's
+// fixed work (queue prefix, tables, histograms) is paid once per SM slot,
+// which matters when the queue is short (densities every step).
+#ifndef PIC_EVENT_WAVES
+#define PIC_EVENT_WAVES 1
+#endif
 template <bool DEPN, int ADJ = 0>
 static cudaError_t event_cfg(size_t sm, int *grid, int sms)
 {
@@ -1995,7 +2016,7 @@ static cudaError_t event_cfg(size_t sm, int *grid, int sms)
     if (e != cudaSuccess) return e;
     const int o = o1 < o2 ? o1 : o2;
     if (o < 1) return cudaErrorInvalidConfiguration;
-    *grid = sms * o * 2;        // no block waits on another: more blocks than fit
+    *grid = sms * o * PIC_EVENT_WAVES;
     return cudaSuccess;
 }
 
