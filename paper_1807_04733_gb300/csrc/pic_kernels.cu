@@ -233,7 +233,7 @@ __device__ __forceinline__ void phase_wdep(const Args &a, uint32_t step)
             const int sg = (int)((pk >> 8) & 1u);
             const int b = (sg * a.n_e + (k - 1)) * st.n_cells + cell_of(a, tmp, a.z[cur][g]);
             const unsigned long long w = a.w[cur][g];
-            if (SM) atomicAdd(&s_h[b], w);
+            if (SM) add_u64_split(&s_h[b], w);
             else atomicAdd(&gh[b], w);
         }
     }

@@ -279,6 +279,18 @@ __device__ __forceinline__ unsigned long long block_sums(const uint32_t (&v)[N],
     return t;
 }
 
+// 64-bit shared-memory sum as two native 32-bit atomic additions: the low
+// word's old value gives the carry into the high word exactly, so the pair
+// holds the sum modulo 2^64 (whatever the order of the additions).
+__device__ __forceinline__ void add_u64_split(unsigned long long *p, unsigned long long v)
+{
+    uint32_t *w = reinterpret_cast<uint32_t *>(p);
+    const uint32_t lo = (uint32_t)v;
+    const uint32_t old = atomicAdd(&w[0], lo);
+    const uint32_t hi = (uint32_t)(v >> 32) + (uint32_t)(old + lo < old);
+    if (hi) atomicAdd(&w[1], hi);
+}
+
 // Status word of the look-back: epoch:32 | flag:2 | value:30
 constexpr unsigned long long FLAG_A = 1ull, FLAG_P = 2ull;
 __device__ __forceinline__ void publish(unsigned long long *w, unsigned int ep,
@@ -899,7 +911,7 @@ __device__ __forceinline__ void phase_stream(const Args &a)
                     long long r = s_gp[sg * nc + c1] - s_gp[sg * nc + c0];
                     if (DEPN) r += s_gn[(sg * ne + (int)k - 1) * nc + c1];
                     if (ADJ == 2 && av[j] != 0)
-                        atomicAdd(&s_sr[(layer * 2 + sg) * ne + (int)k - 1], (unsigned long long)av[j]);
+                        add_u64_split(&s_sr[(layer * 2 + sg) * ne + (int)k - 1], (unsigned long long)av[j]);
                     if (r != 0) {
                         if (ADJ == 1) {
                             // pass 1: added in memory (this thread owns the slot)
@@ -922,7 +934,7 @@ __device__ __forceinline__ void phase_stream(const Args &a)
                     const int c1 = cu < nc - 1 ? cu : nc - 1;
                     bin = (sg * ne + (int)k - 1) * nc + c1;
                     atomicAdd(&s_gs[c1], (pk >> 13) & 0xFFu);
-                    if (vmom) atomicAdd(&s_v[sg * nc + c1], (unsigned long long)vel_q(w));
+                    if (vmom) add_u64_split(&s_v[sg * nc + c1], (unsigned long long)vel_q(w));
                 }
                 if (!WAGG && bin >= 0) atomicAdd(&s_n[bin], 1u);
                 if (WAGG) {
@@ -1149,13 +1161,11 @@ __device__ __forceinline__ void phase_event(const Args &a)
 
     // the general step for item i of the concatenated queue, of stack s
     // (whose tables are loaded); f: its streaming block
-    auto item = [&](int s, long long i, int f) {
+    auto item = [&](int s, long long i, int f, const float4 rec) {
         const DevStack &st = s_st;
-        const long long q = i - s_qpre[f];
         const long long fpos0 = chunk_lo(T, f, Gf) * TILE;
         const long long sbase = st.base - s_tpref[s] * TILE;     // position -> slot
         const bool room0 = (st.cap - s_nsl[s]) <= 0;
-        const float4 rec = a.qrec[fpos0 + q];
         float z = rec.x, mu = rec.y;
         uint32_t pk = __float_as_uint(rec.z);
         const long long vpos = fpos0 + __float_as_uint(rec.w);
@@ -1259,7 +1269,7 @@ __device__ __forceinline__ void phase_event(const Args &a)
                 atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
                 atomicAdd(&s_gs[c_end], (pk >> 13) & 0xFFu);
                 if (vmom)
-                    atomicAdd(&s_v[sg * S.n_cells + c_end], (unsigned long long)vel_q(__fmul_rn(e.v, mu)));
+                    add_u64_split(&s_v[sg * S.n_cells + c_end], (unsigned long long)vel_q(__fmul_rn(e.v, mu)));
             }
             if (ADJ) {
                 rw = flux_w(a, s, tj, sg, c_start, c_end);
@@ -1298,22 +1308,37 @@ __device__ __forceinline__ void phase_event(const Args &a)
             }
             if (tid == 0) s_next = (unsigned long long)lo;
             cta_sync();
-#pragma unroll 1
-            for (;;) {
+            // A warp takes 32 items at a time and loads the records of its
+            // next batch while it runs the current one.
+            auto grab = [&](long long &i, int &f, float4 &rec) -> bool {
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(&s_next, 32ull);
                 base = __shfl_sync(0xffffffffu, base, 0);
-                if ((long long)base >= hi) break;
-                // the batch's first streaming block, then at most a step or two
-                // (a streaming block queues thousands of items)
-                int f = 0;
-                if (lane == 0) f = fast_block_of((long long)base);
-                f = __shfl_sync(0xffffffffu, f, 0);
-                const long long i = (long long)base + lane;
+                if ((long long)base >= hi) return false;
+                // the batch's first streaming block, then at most a step or
+                // two (a streaming block queues thousands of items)
+                int ff = 0;
+                if (lane == 0) ff = fast_block_of((long long)base);
+                ff = __shfl_sync(0xffffffffu, ff, 0);
+                i = (long long)base + lane;
                 if (i < hi) {
-                    while (s_qpre[f + 1] <= i) ++f;
-                    item(s, i, f);
+                    while (s_qpre[ff + 1] <= i) ++ff;
+                    rec = a.qrec[chunk_lo(T, ff, Gf) * TILE + (i - s_qpre[ff])];
                 }
+                f = ff;
+                return true;
+            };
+            long long i_next = 0;
+            int f_next = 0;
+            float4 rec_next = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool more = grab(i_next, f_next, rec_next);
+#pragma unroll 1
+            while (more) {
+                const long long i = i_next;
+                const int f = f_next;
+                const float4 rec = rec_next;
+                more = grab(i_next, f_next, rec_next);
+                if (i < hi) item(s, i, f, rec);
             }
             flush_segment(s);
             lo = hi;
@@ -1485,8 +1510,8 @@ __device__ __forceinline__ void phase_place(const Args &a)
                                 if (vmom) {
                                     const int ls = (int)((pk >> 9) & 0xFu);
                                     const float v = a.ent[stg.ent_off + (ls * 2 + sg) * a.n_e + (k - 1)].v;
-                                    atomicAdd(&s_v[sg * stg.n_cells + c1],
-                                              (unsigned long long)vel_q(__fmul_rn(v, r.y)));
+                                    add_u64_split(&s_v[sg * stg.n_cells + c1],
+                                                  (unsigned long long)vel_q(__fmul_rn(v, r.y)));
                                 }
                             }
                         }
