@@ -252,6 +252,18 @@ pic_status pic_step(pic_ctx *ctx, int n_steps);
 pic_status pic_moments(pic_ctx *ctx, int stack, uint32_t *n_dev, int32_t *J_dev,
                        pic_ledger *ledger_host);
 
+/* One moment window of one stack (Eq. firstmoment), into caller-owned
+ * buffers in host memory (pageable or pinned) or device memory: n_out (may
+ * be NULL) receives uint32 [2][n_e][n_cells] and J_out (may be NULL) int32
+ * [2][n_cells+1] of window `window` (0 <= window < n_out), the layouts of
+ * one window of pic_moments; ledger_host (host, may be NULL) as there.  The
+ * copy moves one window only, not the whole run.  A window not reached yet
+ * holds zeros (densities) and the crossings so far (fluxes).  Synchronises
+ * the context stream; PIC_ERR_ARG for a bad stack or window; returns any
+ * pending device status. */
+pic_status pic_moment_window(pic_ctx *ctx, int stack, int window, uint32_t *n_out,
+                             int32_t *J_out, pic_ledger *ledger_host);
+
 /* Generation map of one stack (Figs. 5(b) and 7(b),(d), Sec. V): g_dev
  * (device, caller-owned, overwritten) receives uint64 [n_out][n_cells], the
  * generation labels (1 for a primary, the parent's + 1 for a secondary,

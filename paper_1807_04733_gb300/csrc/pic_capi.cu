@@ -1264,6 +1264,30 @@ pic_status pic_moments(pic_ctx *c, int stack, uint32_t *n_dev, int32_t *J_dev, p
     return st;
 }
 
+pic_status pic_moment_window(pic_ctx *c, int stack, int window, uint32_t *n_out, int32_t *J_out,
+                             pic_ledger *led)
+{
+    if (!c) return PIC_ERR_ARG;
+    if (stack < 0 || stack >= c->n_stacks) return fail(c, PIC_ERR_ARG, "stack index out of range");
+    const HostStack &h = c->hs[stack];
+    const DevStack &d = c->ds[stack];
+    if (window < 0 || window >= h.n_out) return fail(c, PIC_ERR_ARG, "window index out of range");
+    cudaError_t e = J_out ? derive_fluxes(c) : cudaSuccess;
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_moment_window fluxes");
+    const size_t nn = (size_t)2 * c->p.n_e * h.n_cells;
+    const size_t nj = (size_t)2 * (h.n_cells + 1);
+    // the buffers may be host or device memory (unified addressing)
+    if (n_out) e = cudaMemcpyAsync(n_out, c->d_nh + d.n_off + (size_t)window * nn, 4 * nn, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && J_out)
+        e = cudaMemcpyAsync(J_out, c->d_J + d.J_off + (size_t)window * nj, 4 * nj, cudaMemcpyDefault, c->stream);
+    DevCounters hc{};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hc, c->d_cnt + stack, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pic_moment_window copy");
+    const pic_status st = device_status(c);
+    if (led) std::memcpy(led, hc.led, sizeof(pic_ledger));
+    return st;
+}
+
 pic_status pic_weighted_moments(pic_ctx *c, int stack, uint64_t *nw_dev, int64_t *Jw_dev,
                                 uint64_t *w_injected_host)
 {

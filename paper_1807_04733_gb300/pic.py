@@ -30,7 +30,8 @@ STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_ALLOC", 3: "PIC_ERR_CAPACIT
 REC_DTYPE = np.dtype([("z", "<f4"), ("mu", "<f4"), ("id", "<u4"), ("packed", "<u4")])
 
 # symbols declared in include/pic.h
-EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_gen_moments",
+EXPORTS = ("pic_init", "pic_excite", "pic_step", "pic_moments", "pic_moment_window",
+           "pic_gen_moments",
            "pic_vel_moments", "pic_weighted_moments", "pic_weights", "pic_set_weights", "pic_grad",
            "pic_records",
            "pic_set_records", "pic_save", "pic_load", "pic_sync", "pic_derive_tables", "pic_shape", "pic_profile",
@@ -129,6 +130,7 @@ def lib():
         L.pic_excite.argtypes = [P, C.c_int, C.POINTER(pic_pulse)]
         L.pic_step.argtypes = [P, C.c_int]
         L.pic_moments.argtypes = [P, C.c_int, P, P, C.POINTER(pic_ledger)]
+        L.pic_moment_window.argtypes = [P, C.c_int, C.c_int, P, P, C.POINTER(pic_ledger)]
         L.pic_gen_moments.argtypes = [P, C.c_int, P]
         L.pic_vel_moments.argtypes = [P, C.c_int, P]
         L.pic_weighted_moments.argtypes = [P, C.c_int, P, P, C.POINTER(C.c_uint64)]
@@ -267,6 +269,14 @@ def pic_moments(ctx, stack, n_dev_ptr, J_dev_ptr):
     led = pic_ledger()
     _check(lib().pic_moments(ctx, stack, C.c_void_p(n_dev_ptr or 0) if n_dev_ptr else None,
                              C.c_void_p(J_dev_ptr) if J_dev_ptr else None, C.byref(led)), ctx)
+    return led.as_dict()
+
+
+def pic_moment_window(ctx, stack, window, n_ptr, J_ptr):
+    """One moment window into host or device buffers (addresses); the ledger."""
+    led = pic_ledger()
+    _check(lib().pic_moment_window(ctx, stack, window, C.c_void_p(n_ptr) if n_ptr else None,
+                                   C.c_void_p(J_ptr) if J_ptr else None, C.byref(led)), ctx)
     return led.as_dict()
 
 
