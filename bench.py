@@ -595,7 +595,7 @@ def main():
     # replicas: every rank runs its own copy with its own seed (weak scaling)
     wl = wl.replace(seed=wl.seed + rank)
     tune_steps = 0 if args.no_autotune else args.autotune_steps
-    total = pre + 140 * tune_steps + period * (args.warmup + 2 * args.steps) + 1
+    total = pre + 140 * tune_steps + period * (args.warmup + 3 * args.steps) + 1
     ctx = pic.Context(wl, n_steps_max=max(wl.n_steps, total), blocks_per_sm=args.blocks_per_sm,
                       hist_mode=args.hist_mode, ring_stages=args.ring)
     stream = ctx.stream
@@ -628,7 +628,6 @@ def main():
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    pic.pic_profile(ctx.ctx, True)
     clk.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -641,13 +640,27 @@ def main():
     torch.cuda.synchronize()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
-    ktimes = pic.pic_profile_read(ctx.ctx)
-    pic.pic_profile(ctx.ctx, False)
     led1 = [ctx.ledger(s) for s in range(len(wl.stacks))]
     if dist is not None:
         dist.barrier()
     delta = {k: sum(b[k] - a[k] for a, b in zip(led0, led1)) for k in led1[0]}
     ps = delta["particle_steps"]
+
+    # ---- kernel breakdown: as many steps again, with CUDA events around
+    # every launch (kept out of the timed region above: they cost ~2 %) ----
+    pic.pic_profile(ctx.ctx, True)
+    ek0 = torch.cuda.Event(enable_timing=True)
+    ek1 = torch.cuda.Event(enable_timing=True)
+    ek0.record(stream)
+    for _ in range(args.steps):
+        ctx.step(period)
+    ek1.record(stream)
+    torch.cuda.synchronize()
+    ms_k = ek0.elapsed_time(ek1)
+    ktimes = pic.pic_profile_read(ctx.ctx)
+    pic.pic_profile(ctx.ctx, False)
+    led2 = [ctx.ledger(s) for s in range(len(wl.stacks))]
+    delta_k = {k: sum(b[k] - a[k] for a, b in zip(led1, led2)) for k in led2[0]}
 
     # ---- end-to-end region: the C-ABI with host buffers, every step the
     # window just finished (densities and fluxes) and the ledger read back
@@ -664,7 +677,7 @@ def main():
         led = pic.pic_moment_window(ctx.ctx, 0, w, n_host.data_ptr(), J_host.data_ptr())
         ps_e2e = led["particle_steps"]
     e2e_s = time.perf_counter() - t
-    ps_e2e -= led1[0]["particle_steps"]
+    ps_e2e -= led2[0]["particle_steps"]
     d2h = n_host.numel() * 4 + J_host.numel() * 4 + 13 * 8
     # the run's inputs (tables, excitation) are host buffers copied once by
     # pic_init / pic_excite; a step has no inputs of its own
@@ -676,7 +689,7 @@ def main():
     ms_max, ps_all = shard.reduce_measurement(ms, float(ps), dist, "cuda")
     e2e_ms, ps_e2e_all = shard.reduce_measurement(e2e_s * 1e3, float(ps_e2e), dist, "cuda")
 
-    roofline = roofline_of(delta, ktimes, ms)
+    roofline = roofline_of(delta_k, ktimes, ms_k)
 
     line = {
         "metric": METRIC, "value": ps_all / (ms_max * 1e-3), "unit": UNIT,
