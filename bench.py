@@ -647,7 +647,7 @@ def main():
     ps = delta["particle_steps"]
 
     # ---- kernel breakdown: as many steps again, with CUDA events around
-    # every launch (kept out of the timed region above: they cost ~2 %) ----
+    # every launch (kept out of the timed region above) ----
     pic.pic_profile(ctx.ctx, True)
     ek0 = torch.cuda.Event(enable_timing=True)
     ek1 = torch.cuda.Event(enable_timing=True)
