@@ -677,6 +677,7 @@ def main():
         led = pic.pic_moment_window(ctx.ctx, 0, w, n_host.data_ptr(), J_host.data_ptr())
         ps_e2e = led["particle_steps"]
     e2e_s = time.perf_counter() - t
+    ev_e2e = led["eventful"] - led2[0]["eventful"] if args.steps else 0
     ps_e2e -= led2[0]["particle_steps"]
     d2h = n_host.numel() * 4 + J_host.numel() * 4 + 13 * 8
     # the run's inputs (tables, excitation) are host buffers copied once by
@@ -704,6 +705,9 @@ def main():
         "e2e": {"value": ps_e2e_all / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": d2h,
                 "h2d_bytes_once": h2d_once,
+                # eventful carriers per carrier-step here (ledger_delta gives the
+                # timed region's): the state relaxes as the run goes on
+                "eventful_fraction": ev_e2e / ps_e2e if ps_e2e else None,
                 "note": "pic_step then pic_moment_window into pinned host buffers every step; "
                         "the tables and the excitation are the run's only inputs, copied from "
                         "host buffers once (pic_init, pic_excite)"},
