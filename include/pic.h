@@ -397,7 +397,7 @@ pic_status pic_profile_read(pic_ctx *ctx, pic_kernel_times *out);
  *   n_alive (host, written): number of live slots.
  *   cuda_stream: cudaStream_t the work is ordered on; the call synchronises it.
  * n must be below 2^30 (the look-back words carry 30-bit counts); larger n,
- * NULL pointers or a misaligned packed array return PIC_ERR_ARG.  Every
+ * NULL pointers or a misaligned input array return PIC_ERR_ARG.  Every
  * call looks up the array's device address on the current device (so a
  * device reset between calls is harmless).  Calls share the array: each call
  * resets the part that must start from zero, and calls whose kernels overlap

@@ -66,7 +66,10 @@ extern "C" pic_status pic_compact_static(const float *z, const float *mu, const 
     if (n >= (int64_t(1) << 30)) return PIC_ERR_ARG;
     if (n > 0 && (!z || !mu || !id || !packed || !z_out || !mu_out || !id_out || !packed_out))
         return PIC_ERR_ARG;
-    if (n > 0 && (reinterpret_cast<uintptr_t>(packed) & 15u)) return PIC_ERR_ARG;
+    // the kernel reads the inputs in 16-byte vectors
+    if (n > 0 && ((reinterpret_cast<uintptr_t>(packed) | reinterpret_cast<uintptr_t>(z) |
+                   reinterpret_cast<uintptr_t>(mu) | reinterpret_cast<uintptr_t>(id)) & 15u))
+        return PIC_ERR_ARG;
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -1841,25 +1841,51 @@ __device__ __forceinline__ void phase_compact(const Args &a)
     Plan p;
     make_plan(a, s_tpref, s_nsl, p);
 
-    auto alive4 = [&](int s, long long t, uint32_t &mask) {
-        const DevStack &st = a.stacks[s];
-        const long long nsl = s_nsl[s];
-        const long long slot0 = (t - s_tpref[s]) * TILE + (long long)tid * VEC;
-        mask = 0;
-        if (slot0 < nsl) {
-            uint4 p4;
-            if (a.mp_stride == 2) {
-                const uint4 *q = reinterpret_cast<const uint4 *>(a.mu[cur] + 2 * (st.base + slot0));
-                const uint4 q01 = q[0], q23 = q[1];
-                p4 = make_uint4(q01.y, q01.w, q23.y, q23.w);
-            } else {
-                p4 = *reinterpret_cast<const uint4 *>(a.pk[cur] + st.base + slot0);
-            }
-            const uint32_t *pp = &p4.x;
+    // Slots are taken in groups of TPB * CV (one tile): warp w takes the
+    // 32 * CV slots [w * 32 CV, (w + 1) * 32 CV) of a group as CV rows of 32, lane l
+    // the slot l of each row, so that loads and the stores of the live slots
+    // are coalesced; a slot's rank is the live slots of the earlier warps
+    // (one block scan of the warps' counts), of the earlier rows and of the
+    // lower lanes of its row (ballots).  A group lies in one stack; lim = the
+    // first slot not in it, or the stack's slot count; nothing at or past lim
+    // is read.
+    constexpr int CV = 4;
+    constexpr long long GT = (long long)TPB * CV / TILE;      // tiles per group
+    const int warp = tid >> 5, lane = tid & 31;
+    const unsigned int lt = (1u << lane) - 1u;
+    uint32_t pkv[CV], bal[CV];
+    auto alive_rows = [&](const DevStack &st, long long g0, long long lim) -> int {
+        int n = 0;
+        const long long sl0 = g0 + warp * (32 * CV) + lane;
+        const uint32_t *P = a.pk[cur] + (st.base + sl0) * S;
+        const int left = lim - sl0 > 32 * CV ? 32 * CV : (int)(lim - sl0);   // rows i with i*32 < left
 #pragma unroll
-            for (int j = 0; j < VEC; ++j)
-                if (slot0 + j < nsl && (pp[j] & 0xFFu)) mask |= 1u << j;
+        for (int i = 0; i < CV; ++i) {
+            pkv[i] = i * 32 < left ? P[i * 32 * S] : 0u;
+            bal[i] = __ballot_sync(0xffffffffu, (pkv[i] & 0xFFu) != 0u);
+            n += __popc(bal[i]);
         }
+        return n;                     // the warp's live slots
+    };
+    // exclusive prefix of the warps' counts and the group's total
+    auto warp_scan = [&](int n, int &excl) -> int {
+        if (lane == 0) s_w[warp] = n;
+        cta_sync();
+        int pre = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < TPB / 32; ++w) {
+            const int v = s_w[w];
+            pre += w < warp ? v : 0;
+            tot += v;
+        }
+        cta_sync();
+        excl = pre;
+        return tot;
+    };
+    // the groups of stack s inside this block's chunk: [ta, tb) tiles
+    auto seg_tiles = [&](int s, long long &ta, long long &tb) {
+        ta = p.t0 > s_tpref[s] ? p.t0 : s_tpref[s];
+        tb = p.t1 < s_tpref[s + 1] ? p.t1 : s_tpref[s + 1];
     };
 
     if (p.t0 < p.t1) {
@@ -1869,16 +1895,20 @@ __device__ __forceinline__ void phase_compact(const Args &a)
         // phase 1: count the first segment (if it needs the look-back) and the
         // last segment (its count is what later blocks need)
         long long c_first = 0, c_last = 0;
-        for (long long t = p.t0; t < p.t1; ++t) {
-            const int s = stack_of(s_tpref, a.n_stacks, t);
+        for (int s = s_first; s <= s_last; ++s) {
             const bool need = (s == s_first && first_inside) || s == s_last;
-            if (!need) { t = s_tpref[s + 1] - 1; continue; }
-            uint32_t m;
-            alive4(s, t, m);
-            int excl;
-            const int tot = block_scan(__popc(m), excl, s_w);
-            if (s == s_first) c_first += tot;
-            if (s == s_last) c_last += tot;
+            if (!need) continue;
+            const DevStack &st = a.stacks[s];
+            long long ta, tb;
+            seg_tiles(s, ta, tb);
+            for (long long t = ta; t < tb; t += GT) {
+                const long long g0 = (t - s_tpref[s]) * TILE;
+                const long long ge = ((t + GT < tb ? t + GT : tb) - s_tpref[s]) * TILE;
+                int excl;
+                const int tot = warp_scan(alive_rows(st, g0, ge < s_nsl[s] ? ge : s_nsl[s]), excl);
+                if (s == s_first) c_first += tot;
+                if (s == s_last) c_last += tot;
+            }
         }
         long long pre_first = 0;
         if (tid < 32) {
@@ -1900,59 +1930,63 @@ __device__ __forceinline__ void phase_compact(const Args &a)
         pre_first = s_prefix;
         (void)c_first;
         // phase 2: scatter live slots, stable, into the other buffer
-        int seg = -1;
-        long long run = 0;
-        for (long long t = p.t0; t < p.t1; ++t) {
-            const int s = stack_of(s_tpref, a.n_stacks, t);
-            if (s != seg) {
-                if (seg >= 0 && s_tpref[seg + 1] <= p.t1 && tid == 0)
-                    a.cnt[seg].alive_total = (unsigned long long)run;
-                seg = s;
-                run = (s == s_first) ? pre_first : 0;
-            }
-            uint32_t m;
-            alive4(s, t, m);
-            int excl;
-            const int tot = block_scan(__popc(m), excl, s_w);
-            if (m) {
-                const DevStack &st = a.stacks[s];
-                const long long src = st.base + (t - s_tpref[s]) * TILE + (long long)tid * VEC;
+        for (int s = s_first; s <= s_last; ++s) {
+            const DevStack &st = a.stacks[s];
+            long long ta, tb;
+            seg_tiles(s, ta, tb);
+            if (ta >= tb) continue;
+            long long run = (s == s_first) ? pre_first : 0;
+            for (long long t = ta; t < tb; t += GT) {
+                const long long g0 = (t - s_tpref[s]) * TILE;
+                const long long ge = ((t + GT < tb ? t + GT : tb) - s_tpref[s]) * TILE;
+                const long long lim = ge < s_nsl[s] ? ge : s_nsl[s];
+                const long long sl0 = g0 + warp * (32 * CV) + lane;  // this lane's first slot
+                const int left = lim - sl0 > 32 * CV ? 32 * CV : (int)(lim - sl0);
+                const float *Zc = a.z[cur] + st.base + sl0;
+                const float *Mc = a.mu[cur] + (st.base + sl0) * S;
+                const uint32_t *Ic = a.id[cur] + st.base + sl0;
+                float zv[CV], muv[CV];
+                uint32_t idv[CV];
+#pragma unroll
+                for (int i = 0; i < CV; ++i) {
+                    const bool in = i * 32 < left;
+                    zv[i] = in ? Zc[i * 32] : 0.f;
+                    muv[i] = in ? Mc[i * 32 * S] : 0.f;
+                    idv[i] = in ? Ic[i * 32] : 0u;
+                }
+                int excl;
+                const int tot = warp_scan(alive_rows(st, g0, lim), excl);
                 long long d = st.base + run + excl;
 #pragma unroll
-                for (int j = 0; j < VEC; ++j) {
-                    if (!((m >> j) & 1u)) continue;
-                    a.z[nxt][d] = a.z[cur][src + j];
-                    if (S == 2) {
-                        *reinterpret_cast<uint2 *>(a.mu[nxt] + 2 * d) =
-                            *reinterpret_cast<const uint2 *>(a.mu[cur] + 2 * (src + j));
-                    } else {
-                        a.mu[nxt][d] = a.mu[cur][src + j];
-                        a.pk[nxt][d] = a.pk[cur][src + j];
+                for (int i = 0; i < CV; ++i) {
+                    const long long src = st.base + sl0 + i * 32;
+                    if ((bal[i] >> lane) & 1u) {
+                        const long long o = d + __popc(bal[i] & lt);
+                        a.z[nxt][o] = zv[i];
+                        if (S == 2) {
+                            *reinterpret_cast<uint2 *>(a.mu[nxt] + 2 * o) =
+                                make_uint2(__float_as_uint(muv[i]), pkv[i]);
+                        } else {
+                            a.mu[nxt][o] = muv[i];
+                            a.pk[nxt][o] = pkv[i];
+                        }
+                        a.id[nxt][o] = idv[i];
+                        if (!ADJ && a.w[0]) a.w[nxt][o] = a.w[cur][src];
+                        if (ADJ) a.acc[nxt][o] = a.acc[cur][src];
+                    } else if (ADJ == 1 && i * 32 < left) {
+                        // pass 1: a removed carrier's own reward is final
+                        const unsigned long long id = (unsigned long long)idv[i] |
+                                                      ((unsigned long long)(pkv[i] >> 21) << 32);
+                        if (id < (unsigned long long)st.n_ids) a.tot[st.id_off + (long long)id] = a.acc[cur][src];
+                        else atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_STATE);
                     }
-                    a.id[nxt][d] = a.id[cur][src + j];
-                    if (!ADJ && a.w[0]) a.w[nxt][d] = a.w[cur][src + j];
-                    if (ADJ) a.acc[nxt][d] = a.acc[cur][src + j];
-                    ++d;
+                    d += __popc(bal[i]);
                 }
+                run += tot;
             }
-            if (ADJ == 1) {
-                // pass 1: a removed carrier's own reward is final
-                const DevStack &st = a.stacks[s];
-                const long long slot0 = (t - s_tpref[s]) * TILE + (long long)tid * VEC;
-                const long long src = st.base + slot0;
-#pragma unroll
-                for (int j = 0; j < VEC; ++j) {
-                    if (slot0 + j >= s_nsl[s] || ((m >> j) & 1u)) continue;
-                    const unsigned long long id = (unsigned long long)a.id[cur][src + j] |
-                                                  ((unsigned long long)(a.pk[cur][(src + j) * S] >> 21) << 32);
-                    if (id < (unsigned long long)st.n_ids) a.tot[st.id_off + (long long)id] = a.acc[cur][src + j];
-                    else atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_STATE);
-                }
-            }
-            run += tot;
+            if (s_tpref[s + 1] <= p.t1 && tid == 0)
+                a.cnt[s].alive_total = (unsigned long long)run;
         }
-        if (seg >= 0 && s_tpref[seg + 1] <= p.t1 && tid == 0)
-            a.cnt[seg].alive_total = (unsigned long long)run;
     }
 
     if (last_block(a, &s_flag)) {
