@@ -232,7 +232,9 @@ class OraclePool:
 def cpu_sample(args, wl, pre):
     """Oracle replicas of a scaled copy of the workload on the host cores."""
     cores = max(1, min(os.cpu_count() or 1, 64))
-    scale = 1e-3 * args.scale if args.config == 4 else 1e-2 * args.scale
+    # the large workload: 1.25e6 slots (20 MB of state) per replica, beyond
+    # what the host cores' caches hold together
+    scale = 3.125e-3 * args.scale if args.config == 4 else 1e-2 * args.scale
     n_each = max(1, int(round(wl.stacks[0].capacity * scale)))
     return cores, scale, n_each
 
