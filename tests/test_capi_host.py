@@ -54,6 +54,19 @@ def test_init_rejects_bad_arguments_without_a_device():
     assert e.value.status == 1
 
 
+def test_compact_static_rejects_misaligned_inputs_without_a_device():
+    # the compaction reads its inputs in 16-byte vectors: any input array
+    # off a 16-byte boundary is an argument error, found before any device
+    # work (the addresses are never dereferenced)
+    good = 1 << 20
+    for bad in range(4):
+        ptrs = [good] * 4
+        ptrs[bad] = good + 4
+        with pytest.raises(pic.PicError) as e:
+            pic.pic_compact_static(*ptrs, 1000, good, good, good, good)
+        assert e.value.status == 1
+
+
 WORKLOADS = [
     W.config(0, scale=0.01),
     W.spin_valve(True, n0=1000, capacity=4000, n_steps=300),
