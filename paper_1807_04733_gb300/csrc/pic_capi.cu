@@ -845,7 +845,7 @@ cudaError_t enqueue_step(pic_ctx *c, const Args &a0, int s, bool inj0, bool inj1
         Args b = a;
         b.bump_step = graph && !inj1;
         e = timed(c, 4, [&] { return launch_slow(b, lc, det, dep, st); });
-        ++launches;
+        launches += 2;                   // the event and placement passes
     }
     if (e == cudaSuccess && inj1) {
         Args b = a;
@@ -995,7 +995,10 @@ pic_status pic_step(pic_ctx *c, int n_steps)
                 }
                 if (e != cudaSuccess) return cuda_fail(c, e, "pic_step persistent capture");
             }
-            if (!c->dev_step_valid) e = launch_set_step(c->d_ctl, (unsigned int)s, c->stream);
+            if (!c->dev_step_valid) {
+                e = launch_set_step(c->d_ctl, (unsigned int)s, c->stream);
+                c->launches += 1;
+            }
             if (e == cudaSuccess)
                 e = c->persist_graph ? cudaGraphLaunch(c->persist_graph, c->stream)
                                      : launch_persistent(a, c->pcfg, det, c->period, c->stream);
@@ -1012,7 +1015,10 @@ pic_status pic_step(pic_ctx *c, int n_steps)
                 e = capture_period(c, which);
                 if (e != cudaSuccess) return cuda_fail(c, e, "pic_step graph capture");
             }
-            if (!c->dev_step_valid) e = launch_set_step(c->d_ctl, (unsigned int)s, c->stream);
+            if (!c->dev_step_valid) {
+                e = launch_set_step(c->d_ctl, (unsigned int)s, c->stream);
+                c->launches += 1;
+            }
             if (e == cudaSuccess) e = cudaGraphLaunch(c->period_graph[which], c->stream);
             if (e != cudaSuccess) return cuda_fail(c, e, "pic_step graph launch");
             c->dev_step_valid = true;

@@ -127,7 +127,8 @@ def test_persistent_launch_one_launch_per_period_batched():
     pers = pic.Context(wl, use_graph=2)
     plain.step(200)
     pers.step(200)
-    assert pers.launches == 4                 # 200 steps = 4 periods of 50
+    # 200 steps = 4 periods of 50, after the kernel that sets the device step
+    assert pers.launches == 5
     same_full(full_state(plain, wl), full_state(pers, wl))
     S, ne = 6, wl.n_e
     ncm = pers.n_cells_max
