@@ -315,6 +315,12 @@ template <bool DEPN, bool WAGG>
 cudaError_t stream_cfg(size_t fixed, int blocks_per_sm, int ring_req, int nw, int *ring,
                        int *blocks, size_t *smem)
 {
+    // 16: two groups of eight warps (the density-step pass only)
+    if (nw == 16) {
+        if constexpr (DEPN)
+            return pick_stream_ring<DEPN, WAGG, 8, 0, 2>(fixed, blocks_per_sm, ring_req, ring, blocks, smem);
+        return cudaErrorInvalidValue;
+    }
     return nw == 4 ? pick_stream_ring<DEPN, WAGG, 4>(fixed, blocks_per_sm, ring_req, ring, blocks, smem)
                    : pick_stream_ring<DEPN, WAGG, 8>(fixed, blocks_per_sm, ring_req, ring, blocks, smem);
 }
@@ -347,8 +353,25 @@ cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_m
         e = stream_cfg<true, false>(fixed_dep, blocks_per_sm, 0, 8, &cfg->ring_fast_dep, &o_dep,
                                     &cfg->smem_fast_dep);
     if (e != cudaSuccess) return e;
+    int nw_dep = 8;
+    if (o_dep == 1) {
+        // room for one block per SM only (large histograms): a second group
+        // of eight consumer warps in the same block shares them
+        int ring2 = 0, o2 = 0;
+        size_t sm2 = 0;
+        e = hist_mode == 1
+                ? stream_cfg<true, true>(fixed_dep, blocks_per_sm, 0, 16, &ring2, &o2, &sm2)
+                : stream_cfg<true, false>(fixed_dep, blocks_per_sm, 0, 16, &ring2, &o2, &sm2);
+        if (e == cudaSuccess && o2 >= 1) {
+            nw_dep = 16;
+            cfg->ring_fast_dep = ring2;
+            cfg->smem_fast_dep = sm2;
+        }
+        e = cudaSuccess;
+        cudaGetLastError();
+    }
     cfg->nw_fast = nw_plain;
-    cfg->nw_fast_dep = 8;
+    cfg->nw_fast_dep = nw_dep;
     cfg->grid_fast = sms * o_plain;
     cfg->grid_fast_dep = sms * o_dep;
     const int gf_max = cfg->grid_fast > cfg->grid_fast_dep ? cfg->grid_fast : cfg->grid_fast_dep;
@@ -373,6 +396,12 @@ namespace {
 template <bool DET, bool DEPN, bool WAGG>
 void stream_launch(const Args &a, int g, int nw, size_t sm, cudaStream_t s)
 {
+    if constexpr (DEPN) {
+        if (nw == 16) {
+            k_stream<DET, DEPN, WAGG, 8, 0, 2><<<g, stream_threads<16>(), sm, s>>>(a);
+            return;
+        }
+    }
     if (nw == 4) k_stream<DET, DEPN, WAGG, 4><<<g, stream_threads<4>(), sm, s>>>(a);
     else k_stream<DET, DEPN, WAGG, 8><<<g, stream_threads<8>(), sm, s>>>(a);
 }

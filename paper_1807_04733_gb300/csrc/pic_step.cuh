@@ -631,10 +631,14 @@ __device__ __forceinline__ unsigned long long stream_sum_u64(unsigned long long 
 template <int NW>
 constexpr int stream_threads() { return 32 * NW + 32; }
 
-template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0>
+template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0, int GR = 1>
 __device__ __forceinline__ void phase_stream(const Args &a)
 {
-    constexpr int NT = 32 * NW;              // consumer threads
+    // GR groups of NW consumer warps take the tiles of the ring in turn (two
+    // groups where the density-step histograms leave room for one block per
+    // SM); each group covers a whole tile
+    constexpr int NT = 32 * NW;              // consumer threads of a group
+    constexpr int NTT = NT * GR;             // consumer threads
     constexpr int G = TILE / NT;             // slots per consumer thread and tile
     constexpr int NC = G / 4;                // Philox calls (and float4s) per thread
     // ring arrays: z, (mu, packed) and, in pass 2, the reward-to-go (pass 1
@@ -659,14 +663,14 @@ __device__ __forceinline__ void phase_stream(const Args &a)
     long long *s_nsl = s_tpref + a.n_stacks + 1;
     __shared__ __align__(8) unsigned long long s_full[MAX_RING], s_empty[MAX_RING];
     __shared__ DevStack s_st;
-    __shared__ unsigned long long s_r[NW];
+    __shared__ unsigned long long s_r[NW * GR];
     __shared__ int s_qn, s_abort;
 
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
     const int b = blockIdx.x, G_ = gridDim.x, tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const unsigned int lt_mask = (1u << lane) - 1u;
-    for (int i = tid; i < a.n_stacks; i += NT + 32) {
+    for (int i = tid; i < a.n_stacks; i += NTT + 32) {
         s_nsl[i] = (long long)a.cnt[i].n_slots;
         // the carriers advanced in this step: every live one (the counts
         // change only in the source, event and placement kernels)
@@ -699,7 +703,7 @@ __device__ __forceinline__ void phase_stream(const Args &a)
     const float *MP = a.mu[cur];         // mu and packed, interleaved
 
     // ---------------- producer warp ----------------
-    if (warp == NW) {
+    if (warp == NW * GR) {
         if (lane == 0) {
             // the bulk copies (async proxy) read global memory written with
             // ordinary stores by earlier passes: within one persistent launch
@@ -745,7 +749,9 @@ __device__ __forceinline__ void phase_stream(const Args &a)
     const float half = a.half_dt;
     const long long pos0 = t0 * TILE;                // queue region of this block
     const bool vmom = DEPN && !ADJ && (a.flags & PIC_F_VELOCITY_MOMENTS);
-    const int i0 = G * tid;                          // the thread's first slot in a tile
+    const int grp = GR > 1 ? warp / NW : 0;          // the thread's group
+    const int ltid = tid - grp * NT;                 // its index within the group
+    const int i0 = G * ltid;                         // its first slot in a tile
     int seg_stack = -1, nc = 1, ne = a.n_e;
     long long seg_t0 = 0, seg_t1 = -1;               // tiles of the current stack
     int nsl = 0;
@@ -754,12 +760,12 @@ __device__ __forceinline__ void phase_stream(const Args &a)
     uint32_t n_queued = 0;
 
     auto flush = [&](int s) {
-        stream_sync<NW>();
+        stream_sync<NW * GR>();
         const DevStack &st = s_st;
         if (ADJ == 2) {
             // the no-scattering score of an entry times the sum of the
             // reward-to-go of the carriers that passed the test with it
-            for (int i = tid; i < st.tab_n; i += NT) {
+            for (int i = tid; i < st.tab_n; i += NTT) {
                 const long long v = (long long)s_sr[i];
                 if (v) atomicAdd(&a.g_ent[st.ent_off + i], (double)v * a.inv_q * a.aent[st.ent_off + i].noscat);
             }
@@ -767,28 +773,28 @@ __device__ __forceinline__ void phase_stream(const Args &a)
         if (DEPN && !ADJ) {
             const int nbins = 2 * a.n_e * st.n_cells;
             uint32_t *gN = a.n_hist + st.n_off + (long long)tout * nbins;
-            for (int i = tid; i < nbins; i += NT) {
+            for (int i = tid; i < nbins; i += NTT) {
                 const uint32_t v = s_n[i];
                 if (v) atomicAdd(&gN[i], v);
             }
             unsigned long long *gG = a.g_hist + st.n_off / (2 * a.n_e) + (long long)tout * st.n_cells;
-            for (int i = tid; i < st.n_cells; i += NT) {
+            for (int i = tid; i < st.n_cells; i += NTT) {
                 const uint32_t v = s_gs[i];
                 if (v) atomicAdd(&gG[i], (unsigned long long)v);
             }
             if (vmom) {
                 unsigned long long *gV = reinterpret_cast<unsigned long long *>(a.v_hist) +
                                          st.n_off / a.n_e + (long long)tout * 2 * st.n_cells;
-                for (int i = tid; i < 2 * st.n_cells; i += NT) {
+                for (int i = tid; i < 2 * st.n_cells; i += NTT) {
                     const unsigned long long v = s_v[i];
                     if (v) atomicAdd(&gV[i], v);
                 }
             }
         }
-        const unsigned long long v1 = stream_sum_u64<NW>(n_queued, s_r);
+        const unsigned long long v1 = stream_sum_u64<NW * GR>(n_queued, s_r);
         if (tid == 0 && v1) atomicAdd(&a.cnt[s].led[L_EVENTFUL], v1);
         n_queued = 0;
-        stream_sync<NW>();
+        stream_sync<NW * GR>();
     };
 
     int stg = 0;
@@ -799,26 +805,26 @@ __device__ __forceinline__ void phase_stream(const Args &a)
             // a new stack segment: its tables, histograms and constants
             const int s = stack_of(s_tpref, a.n_stacks, t);
             if (seg_stack >= 0) flush(seg_stack);
-            stream_sync<NW>();
+            stream_sync<NW * GR>();
             if (tid == 0) s_st = a.stacks[s];
-            stream_sync<NW>();
+            stream_sync<NW * GR>();
             const DevStack &st = s_st;
-            for (int q = tid; q < st.ftab_n; q += NT) s_ent[q] = a.fent[st.fent_off + q];
+            for (int q = tid; q < st.ftab_n; q += NTT) s_ent[q] = a.fent[st.fent_off + q];
             if (DEPN && !ADJ) {
-                for (int q = tid; q < 2 * a.n_e * st.n_cells; q += NT) s_n[q] = 0u;
-                for (int q = tid; q < st.n_cells; q += NT) s_gs[q] = 0u;
+                for (int q = tid; q < 2 * a.n_e * st.n_cells; q += NTT) s_n[q] = 0u;
+                for (int q = tid; q < st.n_cells; q += NTT) s_gs[q] = 0u;
                 if (vmom)
-                    for (int q = tid; q < 2 * st.n_cells; q += NT) s_v[q] = 0ull;
+                    for (int q = tid; q < 2 * st.n_cells; q += NTT) s_v[q] = 0ull;
             }
             if (ADJ == 2)
-                for (int q = tid; q < st.tab_n; q += NT) s_sr[q] = 0ull;
+                for (int q = tid; q < st.tab_n; q += NTT) s_sr[q] = 0ull;
             if (ADJ) {
                 const long long *gp = a.gpot + (long long)(s * a.n_out + tj) * 2 * a.ncm;
-                for (int q = tid; q < 2 * st.n_cells; q += NT)
+                for (int q = tid; q < 2 * st.n_cells; q += NTT)
                     s_gp[q] = gp[(q / st.n_cells) * a.ncm + q % st.n_cells];
                 if (DEPN) {
                     const int rows = 2 * a.n_e;
-                    for (int q = tid; q < rows * st.n_cells; q += NT)
+                    for (int q = tid; q < rows * st.n_cells; q += NTT)
                         s_gn[q] = a.gn ? a.gn[((long long)(s * a.n_out + tout) * rows + q / st.n_cells) * a.ncm +
                                               q % st.n_cells]
                                        : 0;
@@ -831,10 +837,14 @@ __device__ __forceinline__ void phase_stream(const Args &a)
             seg_t1 = s_tpref[s + 1];
             nsl = (int)s_nsl[s];
             gZs = Z + st.base;
-            stream_sync<NW>();
+            stream_sync<NW * GR>();
         }
         const int slot0 = (int)(t - seg_t0) * TILE;  // first slot of the tile in its stack
         const int nvalid = nsl - slot0;              // valid slots of the tile (>= 1)
+        if (GR > 1 && (int)(i % GR) != grp) {           // the other group's tile
+            if (++stg == nring) { stg = 0; phase ^= 1u; }
+            continue;
+        }
         // after a failed wait every later wait is skipped: the warps run the
         // same control flow to the end (results are invalid, the status says so)
         if (!*(volatile int *)&s_abort && !mbar_wait(&s_full[stg], phase, a.spin_limit)) {
@@ -851,7 +861,7 @@ __device__ __forceinline__ void phase_stream(const Args &a)
             const longlong2 *racc = reinterpret_cast<const longlong2 *>(rz + 3 * TILE);
 #pragma unroll
             for (int c = 0; c < G / 2; ++c) {
-                const longlong2 v = racc[(G / 2) * tid + c];
+                const longlong2 v = racc[(G / 2) * ltid + c];
                 av[2 * c] = v.x;
                 av[2 * c + 1] = v.y;
             }
@@ -859,8 +869,8 @@ __device__ __forceinline__ void phase_stream(const Args &a)
         bool achg = false;
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            const float4 z4 = reinterpret_cast<const float4 *>(rz)[NC * tid + c];
-            const uint4 q01 = rmp[2 * (NC * tid + c)], q23 = rmp[2 * (NC * tid + c) + 1];
+            const float4 z4 = reinterpret_cast<const float4 *>(rz)[NC * ltid + c];
+            const uint4 q01 = rmp[2 * (NC * ltid + c)], q23 = rmp[2 * (NC * ltid + c) + 1];
             zin[4 * c] = z4.x; zin[4 * c + 1] = z4.y; zin[4 * c + 2] = z4.z; zin[4 * c + 3] = z4.w;
             min_[4 * c] = __uint_as_float(q01.x); min_[4 * c + 1] = __uint_as_float(q01.z);
             min_[4 * c + 2] = __uint_as_float(q23.x); min_[4 * c + 3] = __uint_as_float(q23.z);
@@ -880,7 +890,7 @@ __device__ __forceinline__ void phase_stream(const Args &a)
         uint32_t xw[G];
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-            const uint4 x = philox_rk(make_uint4((uint32_t)(slot0 >> 2) + (uint32_t)(NC * tid + c),
+            const uint4 x = philox_rk(make_uint4((uint32_t)(slot0 >> 2) + (uint32_t)(NC * ltid + c),
                                                  ctr_hi, step, SUB_TEST), a);
             xw[4 * c] = x.x; xw[4 * c + 1] = x.y; xw[4 * c + 2] = x.z; xw[4 * c + 3] = x.w;
         }
@@ -1000,14 +1010,15 @@ __device__ __forceinline__ void phase_stream(const Args &a)
         }
     }
     if (seg_stack >= 0) flush(seg_stack);
-    stream_sync<NW>();
+    stream_sync<NW * GR>();
     if (tid == 0) a.qcnt[b] = (uint32_t)s_qn;
 }
 
-template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0>
-__global__ void __launch_bounds__(32 * NW + 32, stream_min_blocks<NW, ADJ>()) k_stream(const Args a)
+template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0, int GR = 1>
+__global__ void __launch_bounds__(32 * NW * GR + 32, GR > 1 ? 1 : stream_min_blocks<NW, ADJ>())
+    k_stream(const Args a)
 {
-    phase_stream<DET, DEPN, WAGG, NW, ADJ>(a);
+    phase_stream<DET, DEPN, WAGG, NW, ADJ, GR>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -2038,7 +2049,7 @@ static cudaError_t occupancy(K kernel, size_t smem, int *blocks, int threads = T
 // (with and without fused multiply-add) fitting: the most resident blocks per
 // SM such that at least three tiles per SM are in flight, then the deepest
 // ring (blocks_per_sm, ring_req: 0 = free).
-template <bool DEPN, bool WAGG, int NW, int ADJ = 0>
+template <bool DEPN, bool WAGG, int NW, int ADJ = 0, int GR = 1>
 static cudaError_t pick_stream_ring(size_t fixed, int blocks_per_sm, int ring_req, int *ring,
                                     int *blocks, size_t *smem)
 {
@@ -2047,8 +2058,8 @@ static cudaError_t pick_stream_ring(size_t fixed, int blocks_per_sm, int ring_re
         if (ring_req > 0 && r != ring_req) continue;
         const size_t sm = fixed + (size_t)r * (ADJ == 2 ? 5 : 3) * TILE_BYTES;
         int o1 = 0, o2 = 0;
-        cudaError_t e = occupancy(k_stream<false, DEPN, WAGG, NW, ADJ>, sm, &o1, stream_threads<NW>());
-        if (e == cudaSuccess) e = occupancy(k_stream<true, DEPN, WAGG, NW, ADJ>, sm, &o2, stream_threads<NW>());
+        cudaError_t e = occupancy(k_stream<false, DEPN, WAGG, NW, ADJ, GR>, sm, &o1, stream_threads<NW * GR>());
+        if (e == cudaSuccess) e = occupancy(k_stream<true, DEPN, WAGG, NW, ADJ, GR>, sm, &o2, stream_threads<NW * GR>());
         if (e != cudaSuccess) return e;
         int o = o1 < o2 ? o1 : o2;
         if (blocks_per_sm > 0 && o > blocks_per_sm) o = blocks_per_sm;

@@ -25,9 +25,11 @@ def same_records(a, b):
     return len(a) == len(b) and np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
 
-def compare_run(wl, checkpoints, hist_mode=0, stacks=None, set_recs=None):
+def compare_run(wl, checkpoints, hist_mode=0, stacks=None, set_recs=None, dep_warps=None):
     """Step the GPU context and the oracle to each checkpoint and compare."""
     ctx = pic.Context(wl, hist_mode=hist_mode)
+    if dep_warps is not None:
+        assert ctx.launch_config()["warps_step_moments"] == dep_warps
     idx = range(len(wl.stacks)) if stacks is None else stacks
     refs = {s: OracleSim(wl, stack=s) for s in idx}
     if set_recs is not None:
@@ -91,6 +93,17 @@ def test_det_bitexact_spin_valve(ap):
 def test_det_bitexact_warp_aggregated_histogram():
     wl = W.config(0, scale=0.02, flags=DET).replace(n_steps=150)
     compare_run(wl, [150], hist_mode=1)
+
+
+@pytest.mark.parametrize("hist_mode", [0, 1])
+def test_det_bitexact_large_histograms(hist_mode):
+    """The large workload's grid (315 cells, 60 energy bins: 151 KB of
+    density histogram) leaves room for one density-step block per SM, which
+    then runs two groups of eight consumer warps sharing the histograms;
+    densities every other step."""
+    wl = W.config(4, scale=1e-4, flags=DET).replace(n_steps=120, moment_every=2,
+                                                     compact_every=25)
+    compare_run(wl, [2, 61, 120], hist_mode=hist_mode, dep_warps=16)
 
 
 @pytest.mark.parametrize("rep", range(2))
