@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--hist-mode", type=int, default=0)
     ap.add_argument("--ring", type=int, default=0)
+    ap.add_argument("--event-pass", type=int, default=0, choices=(0, 1),
+                    help="ordinary steps: 0 general step inside the streaming pass where it "
+                         "applies, 1 separate event pass (the autotuner may change it)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-adjoint", action="store_true")
@@ -116,12 +119,13 @@ def measured_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
-# ncu DRAM traffic of the step kernels (k_stream + k_event + k_place), bytes
-# per live carrier-step, from one steady-state capture of each on this
-# workload scaled to 1/20; the traffic grows in proportion to the carriers
-# advanced.  Valid only for the kernel source whose hash is given: reported
-# as null once the kernels change.
-NCU_TRAFFIC = {"bytes_per_particle_step": 16.72, "src_sha": "c97ac892f7313c30"}
+# ncu DRAM traffic of the step kernels, bytes per live carrier-step, from one
+# steady-state capture of each on this workload scaled to 1/20, for the two
+# forms of an ordinary step: "separate" (k_stream + k_event + k_place) and
+# "fused" (k_stream with the general step inside + k_place); the traffic grows
+# in proportion to the carriers advanced.  Valid only for the kernel source
+# whose hash is given: reported as null once the kernels change.
+NCU_TRAFFIC = {"separate": None, "fused": None, "src_sha": None}
 
 
 def kernel_sha():
@@ -392,7 +396,7 @@ def batched_leg(args):
     # after the pulse window, then used for the timed one
     tune = {}
     if not args.no_autotune:
-        scratch = pic.Context(wl, n_steps_max=200 + 140 * 2)
+        scratch = pic.Context(wl, n_steps_max=200 + 200 * 2)
         scratch.step(200)
         trials = scratch.autotune(2)
         cfg = scratch.launch_config()
@@ -455,9 +459,11 @@ def batched_leg(args):
 # ---------------------------------------------------------------------------
 # roofline of the step kernels and timed legs of other configurations
 # ---------------------------------------------------------------------------
-def roofline_of(delta, ktimes, ms):
+def roofline_of(delta, ktimes, ms, fused=False):
     """The step kernels: the streaming pass (k_stream), the event pass
-    (k_event) and the placement of secondaries (k_place); one launch of each
+    (k_event) and the placement of secondaries (k_place), or, fused (the
+    ordinary steps of a context whose launch configuration has the general
+    step inside the streaming pass), k_stream and k_place; one launch of each
     per time step, timed together with CUDA events on the context stream;
     "per launch" = per time step."""
     peak, peak_kind = measured_peak()
@@ -472,10 +478,13 @@ def roofline_of(delta, ktimes, ms):
     achieved = (alg / n_k) / (k_ms / n_k * 1e-3) / 1e9
     achieved_s = (strict / n_k) / (k_ms / n_k * 1e-3) / 1e9
     traffic = None
-    if NCU_TRAFFIC and NCU_TRAFFIC.get("src_sha") == kernel_sha():
-        traffic = NCU_TRAFFIC["bytes_per_particle_step"] * delta["particle_steps"] / n_k
+    form = "fused" if fused else "separate"
+    if NCU_TRAFFIC.get(form) and NCU_TRAFFIC.get("src_sha") == kernel_sha():
+        traffic = NCU_TRAFFIC[form] * delta["particle_steps"] / n_k
+    kernel = ("k_stream (general step inside) + k_place; density steps k_stream+k_event+k_place"
+              if fused else "k_stream+k_event+k_place")
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": traffic, "kernel": "k_stream+k_event+k_place",
+            "frac": achieved / peak, "traffic": traffic, "kernel": kernel, "form": form,
             "peak_source": peak_kind,
             "byte_count": "per carrier-step 20 B (16 B read, z written) + 12 B per eventful "
                           "carrier + 16 B per placed secondary",
@@ -501,7 +510,7 @@ def timed_leg(wl, pre, n_timed, chunk, capacity=None, autotune_steps=0):
     roofline."""
     import torch
     from paper_1807_04733_gb300 import pic
-    n_max = pre + 140 * autotune_steps + n_timed + 1
+    n_max = pre + 200 * autotune_steps + n_timed + 1
     ctx = pic.Context(wl, n_steps_max=max(wl.n_steps, n_max), capacity=capacity)
     left = pre
     while left > 0:
@@ -530,8 +539,10 @@ def timed_leg(wl, pre, n_timed, chunk, capacity=None, autotune_steps=0):
     pic.pic_profile(ctx.ctx, False)
     led1 = [ctx.ledger(s) for s in range(S)]
     delta = {k: sum(b[k] - a[k] for a, b in zip(led0, led1)) for k in led1[0]}
+    lcfg = ctx.launch_config()
     out = {"value": delta["particle_steps"] / (ms * 1e-3), "unit": UNIT, "ms": ms,
-           "time_steps": n_timed, "roofline": roofline_of(delta, kt, ms),
+           "time_steps": n_timed,
+           "roofline": roofline_of(delta, kt, ms, fused=lcfg["grid_step_fused"] > 0),
            "saturation": saturation(delta), "ledger_delta": delta,
            "kernel_ms": {k: v[1] for k, v in kt.items() if v[0]},
            "launch_config": ctx.launch_config(), "autotune": tune}
@@ -597,9 +608,9 @@ def main():
     # replicas: every rank runs its own copy with its own seed (weak scaling)
     wl = wl.replace(seed=wl.seed + rank)
     tune_steps = 0 if args.no_autotune else args.autotune_steps
-    total = pre + 140 * tune_steps + period * (args.warmup + 3 * args.steps) + 1
+    total = pre + 200 * tune_steps + period * (args.warmup + 3 * args.steps) + 1
     ctx = pic.Context(wl, n_steps_max=max(wl.n_steps, total), blocks_per_sm=args.blocks_per_sm,
-                      hist_mode=args.hist_mode, ring_stages=args.ring)
+                      hist_mode=args.hist_mode, ring_stages=args.ring, event_pass=args.event_pass)
     stream = ctx.stream
     # set-up: the pulse window (inputs resident in HBM before timing)
     left = pre
@@ -692,7 +703,7 @@ def main():
     ms_max, ps_all = shard.reduce_measurement(ms, float(ps), dist, "cuda")
     e2e_ms, ps_e2e_all = shard.reduce_measurement(e2e_s * 1e3, float(ps_e2e), dist, "cuda")
 
-    roofline = roofline_of(delta_k, ktimes, ms_k)
+    roofline = roofline_of(delta_k, ktimes, ms_k, fused=ctx.launch_config()["grid_step_fused"] > 0)
 
     line = {
         "metric": METRIC, "value": ps_all / (ms_max * 1e-3), "unit": UNIT,

@@ -111,6 +111,13 @@ typedef struct {
                                carriers, 4 or 8 (each thread then takes 8 or 4
                                consecutive slots of a 1024-slot tile); 0 = 8.
                                Results do not depend on it. */
+    int32_t event_pass;     /* 0: the ordinary steps of a single-stack context
+                               with eight consumer warps run the general step
+                               of the eventful carriers inside the streaming
+                               pass (extra warps fed through a shared-memory
+                               ring, while the carriers' sectors are in L2);
+                               1: always a separate event pass after the
+                               streaming pass.  Results do not depend on it. */
 } pic_params;
 
 /* Launch configuration a context chose (pic_launch_info). */
@@ -125,6 +132,10 @@ typedef struct {
      * streaming pass with density weights, its ring depth and shared memory */
     int32_t grid_adj_step[2], ring_adj_step[2];
     int64_t smem_adj_step[2];
+    /* the streaming pass with the general step inside (event_pass 0); grid
+     * 0: ordinary steps use the separate event pass */
+    int32_t grid_step_fused, ring_step_fused;
+    int64_t smem_step_fused;
 } pic_launch_info;
 
 /* One laterally homogeneous layer stack (Sec. II: 1-D transport along z).
@@ -419,6 +430,7 @@ typedef struct {
     double ns_per_particle_step;  /* device time of the trial / carriers advanced */
     int32_t consumer_warps; /* warps of the streaming pass on the carriers (4 or 8),
                                i.e. 8 or 4 consecutive slots per thread */
+    int32_t event_pass;     /* 0 the general step inside the streaming pass, 1 separate */
 } pic_tune_entry;
 
 /* Time candidate launch configurations of the step kernels on the running
@@ -428,10 +440,12 @@ typedef struct {
  * run), timed with CUDA events on the context stream and divided by the
  * carriers advanced.  Candidates: 8 or 4 consumer warps per block of the
  * streaming pass (4 or 8 slots per thread), 1 to 6 (8 with four warps)
- * resident blocks per SM, ring depth 2, 3, 4, 6 or 8 where it fits, and both
- * deposit modes when the trial contains density steps.  entries (host, may be NULL): up to
- * max_entries results in the order tried; *n_entries (may be NULL): their
- * number.  Needs steps left: up to 140 * trial_steps.  Synchronises. */
+ * resident blocks per SM, ring depth 2, 3, 4, 6 or 8 where it fits, both
+ * deposit modes when the trial contains density steps, and (eight consumer
+ * warps, a single stack) the general step inside the streaming pass or in a
+ * separate pass.  entries (host, may be NULL): up to max_entries results in
+ * the order tried; *n_entries (may be NULL): their number.  Needs steps left:
+ * up to 200 * trial_steps.  Synchronises. */
 pic_status pic_autotune(pic_ctx *ctx, int trial_steps, pic_tune_entry *entries,
                         int max_entries, int *n_entries);
 

@@ -185,6 +185,9 @@ bool valid_params(const pic_params *p, std::string &why)
     if (p->consumer_warps != 0 && p->consumer_warps != 4 && p->consumer_warps != 8) {
         why = "consumer_warps must be 0, 4 or 8"; return false;
     }
+    if (p->event_pass != 0 && p->event_pass != 1) {
+        why = "event_pass must be 0 or 1"; return false;
+    }
     if (p->stack_base < 0 || p->stack_base > 65535) { why = "stack_base out of range"; return false; }
     return true;
 }
@@ -677,6 +680,7 @@ pic_status pic_init(pic_ctx **out, const pic_params *p, const pic_stack_desc *st
     a.spin_limit = 1u << 24;
 
     e = configure(a, p->blocks_per_sm, p->ring_stages, p->hist_mode, p->consumer_warps, &c->lc);
+    if (p->event_pass == 1) c->lc.grid_fused = 0;
     if (e != cudaSuccess) {
         g_init_error = std::string("kernel configuration (moment grid too large for shared "
                                    "memory, or no device): ") + cudaGetErrorString(e);
@@ -837,15 +841,29 @@ cudaError_t enqueue_step(pic_ctx *c, const Args &a0, int s, bool inj0, bool inj1
         e = timed(c, 0, [&] { return launch_inject(a, lc, 0, false, st); });
         ++launches;
     }
-    if (e == cudaSuccess) {
-        e = timed(c, dep ? 2 : 1, [&] { return launch_fast(a, lc, det, dep, c->p.hist_mode, st); });
-        ++launches;
-    }
-    if (e == cudaSuccess) {
-        Args b = a;
-        b.bump_step = graph && !inj1;
-        e = timed(c, 4, [&] { return launch_slow(b, lc, det, dep, st); });
-        launches += 2;                   // the event and placement passes
+    if (!dep && lc.grid_fused > 0) {
+        // the fused form: the streaming pass runs the general step too
+        if (e == cudaSuccess) {
+            e = timed(c, 1, [&] { return launch_fused(a, lc, det, st); });
+            ++launches;
+        }
+        if (e == cudaSuccess) {
+            Args b = a;
+            b.bump_step = graph && !inj1;
+            e = timed(c, 4, [&] { return launch_place_fused(b, lc, det, st); });
+            ++launches;
+        }
+    } else {
+        if (e == cudaSuccess) {
+            e = timed(c, dep ? 2 : 1, [&] { return launch_fast(a, lc, det, dep, c->p.hist_mode, st); });
+            ++launches;
+        }
+        if (e == cudaSuccess) {
+            Args b = a;
+            b.bump_step = graph && !inj1;
+            e = timed(c, 4, [&] { return launch_slow(b, lc, det, dep, st); });
+            launches += 2;               // the event and placement passes
+        }
     }
     if (e == cudaSuccess && inj1) {
         Args b = a;
@@ -1049,6 +1067,7 @@ uint64_t fingerprint(const pic_ctx *c)
 {
     pic_params p = c->p;
     p.blocks_per_sm = 0; p.hist_mode = 0; p.ring_stages = 0; p.use_graph = 0; p.consumer_warps = 0;
+    p.event_pass = 0;
     uint64_t h = fnv1a(&p, sizeof(p));
     h = fnv1a(&c->n_stacks, sizeof(c->n_stacks), h);
     for (const HostStack &s : c->hs) {
@@ -1822,6 +1841,9 @@ pic_status pic_launch_config(const pic_ctx *c, pic_launch_info *out)
         out->ring_adj_step[i] = r ? c->rp.lc[i].ring_fast_dep : 0;
         out->smem_adj_step[i] = r ? (int64_t)c->rp.lc[i].smem_fast_dep : 0;
     }
+    out->grid_step_fused = c->lc.grid_fused;
+    out->ring_step_fused = c->lc.grid_fused ? c->lc.ring_fused : 0;
+    out->smem_step_fused = c->lc.grid_fused ? (int64_t)c->lc.smem_fused : 0;
     return PIC_OK;
 }
 
@@ -1831,13 +1853,17 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
     if (!c) return PIC_ERR_ARG;
     if (trial_steps < 1) return fail(c, PIC_ERR_ARG, "pic_autotune: trial_steps < 1");
     if (c->profiling) return fail(c, PIC_ERR_STATE, "pic_autotune: profiling is on");
-    struct Cand { int bps, ring, hm, nw; };
+    struct Cand { int bps, ring, hm, nw, ev; };
     std::vector<Cand> cands;
     const bool dep_in_trial = trial_steps >= c->p.moment_every;
+    // the fused form exists for one stack and eight consumer warps, with at
+    // most PIC_EV_MIN_BLOCKS blocks per SM
+    const bool fusable = c->n_stacks == 1;
     for (int hm = 0; hm <= (dep_in_trial ? 1 : 0); ++hm)
         for (int nw : {8, 4})
-            for (int bps = 1; bps <= (nw == 4 ? 8 : 6); ++bps)
-                for (int ring : {2, 3, 4, 6, 8}) cands.push_back({bps, ring, hm, nw});
+            for (int ev = (nw == 8 && fusable ? 0 : 1); ev <= 1; ++ev)
+                for (int bps = 1; bps <= (ev == 0 ? 3 : nw == 4 ? 8 : 6); ++bps)
+                    for (int ring : {2, 3, 4, 6, 8}) cands.push_back({bps, ring, hm, nw, ev});
     if ((int64_t)c->step + (int64_t)trial_steps * (int64_t)cands.size() > c->p.n_steps_max)
         return fail(c, PIC_ERR_ARG, "pic_autotune: not enough steps left for the trials");
     const int use_graph = c->p.use_graph;
@@ -1861,7 +1887,8 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
     const pic_params keep_p = c->p;
     double best = 0.0;
     LaunchCfg best_lc = keep;
-    Cand best_c{keep_p.blocks_per_sm, keep_p.ring_stages, keep_p.hist_mode, keep_p.consumer_warps};
+    Cand best_c{keep_p.blocks_per_sm, keep_p.ring_stages, keep_p.hist_mode, keep_p.consumer_warps,
+                keep_p.event_pass};
     std::vector<pic_tune_entry> res;
     for (size_t i = 0; i < cands.size() && e == cudaSuccess; ++i) {
         const Cand &k = cands[i];
@@ -1875,9 +1902,11 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
                                    lc.grid_compact});
         // a candidate whose ring leaves fewer resident blocks than asked for
         // is another candidate's duplicate
+        if (k.ev == 1) lc.grid_fused = 0;
         if (gmax > c->n_status || lc.ring_fast != k.ring || lc.grid_fast != sms * k.bps ||
             lc.grid_fast_dep == 0)
             continue;
+        if (k.ev == 0 && (lc.grid_fused != sms * k.bps || lc.ring_fused != k.ring)) continue;
         c->lc = lc;
         c->p.hist_mode = k.hm;
         uint64_t ps0 = 0, ps1 = 0;
@@ -1892,7 +1921,7 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[0], ev[1]);
         if (e != cudaSuccess) break;
         const double ns = ps1 > ps0 ? 1e6 * (double)ms / (double)(ps1 - ps0) : 1e30;
-        res.push_back(pic_tune_entry{k.bps, k.ring, k.hm, 0, ns, k.nw});
+        res.push_back(pic_tune_entry{k.bps, k.ring, k.hm, 0, ns, k.nw, k.ev});
         if (res.size() == 1 || ns < best) {
             best = ns;
             best_lc = lc;
@@ -1912,6 +1941,7 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
     c->p.ring_stages = best_c.ring;
     c->p.hist_mode = best_c.hm;
     c->p.consumer_warps = best_c.nw;
+    c->p.event_pass = best_c.ev;
     // graphs captured with the old configuration are stale
     for (cudaGraphExec_t &g : c->period_graph) {
         if (g) cudaGraphExecDestroy(g);
@@ -1921,7 +1951,8 @@ pic_status pic_autotune(pic_ctx *c, int trial_steps, pic_tune_entry *entries, in
     c->persist_graph = nullptr;
     for (pic_tune_entry &r : res)
         r.chosen = (r.blocks_per_sm == best_c.bps && r.ring_stages == best_c.ring &&
-                    r.hist_mode == best_c.hm && r.consumer_warps == best_c.nw) ? 1 : 0;
+                    r.hist_mode == best_c.hm && r.consumer_warps == best_c.nw &&
+                    r.event_pass == best_c.ev) ? 1 : 0;
     if (entries)
         for (int i = 0; i < (int)res.size() && i < max_entries; ++i) entries[i] = res[i];
     if (n_entries) *n_entries = (int)res.size();

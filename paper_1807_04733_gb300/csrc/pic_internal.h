@@ -208,6 +208,9 @@ struct LaunchCfg {
     int grid_compact, grid_inject;
     int ring_fast, ring_fast_dep;
     size_t smem_fast, smem_fast_dep, smem_slow, smem_slow_dep, smem_place, smem_place_dep;
+    // the fused streaming pass (plain steps of a single stack; grid 0: not used)
+    int grid_fused, ring_fused;
+    size_t smem_fused;
 };
 // blocks_per_sm, ring, nw: 0 = chosen from the occupancy
 cudaError_t configure(const Args &a, int blocks_per_sm, int ring, int hist_mode, int nw,
@@ -218,6 +221,11 @@ cudaError_t launch_fast(const Args &a, const LaunchCfg &c, bool deterministic, b
                         int hist_mode, cudaStream_t s);
 cudaError_t launch_slow(const Args &a, const LaunchCfg &c, bool deterministic, bool deposit,
                         cudaStream_t s);
+// a plain step in the fused form: the streaming pass with its event warps
+// (Args a), then the placement (Args b, which may advance the step counter)
+cudaError_t launch_fused(const Args &a, const LaunchCfg &c, bool deterministic, cudaStream_t s);
+cudaError_t launch_place_fused(const Args &b, const LaunchCfg &c, bool deterministic,
+                               cudaStream_t s);
 cudaError_t launch_compact(const Args &a, const LaunchCfg &c, cudaStream_t s);
 // live carriers of stacks [s0, s1) counted per (spin, cell) into out (int32,
 // per stack at out + stack_off(s) ...): mode 0 = the windows' births-minus-

@@ -308,6 +308,11 @@ cudaError_t launch_state_hist(const Args &a, int s0, int s1, int mode, int win, 
 // ---------------------------------------------------------------------------
 // host-side launch helpers
 // ---------------------------------------------------------------------------
+// plain steps of a single stack in the fused form (0: separate event pass)
+#ifndef PIC_FUSED_STEP
+#define PIC_FUSED_STEP 1
+#endif
+
 namespace {
 
 // k_stream's configuration for one deposit variant and consumer-warp count
@@ -372,6 +377,28 @@ cudaError_t configure(const Args &a, int blocks_per_sm, int ring_req, int hist_m
     }
     cfg->nw_fast = nw_plain;
     cfg->nw_fast_dep = nw_dep;
+    // the fused form, for the plain steps of a single stack with eight
+    // consumer warps: the general step's tables, the removals histogram and
+    // the event ring besides the streaming pass's own shared memory
+    cfg->grid_fused = 0;
+    cfg->ring_fused = 0;
+    cfg->smem_fused = 0;
+#if PIC_FUSED_STEP
+    if (a.n_stacks == 1 && nw_plain == 8) {
+        const size_t fixed_ev = fixed + 16 + (size_t)a.tab_max * sizeof(TabEnt) + (size_t)a.T_max * 4 +
+                                (size_t)a.jbin_max * 4 + 16 + (size_t)EV_CAP * (16 + 4 + 4);
+        int rf = 0, of = 0;
+        size_t sf = 0;
+        e = pick_stream_ring<false, false, 8, 0, 1, true>(fixed_ev, blocks_per_sm, ring_req, &rf, &of, &sf);
+        if (e == cudaSuccess && of >= 1) {
+            cfg->grid_fused = sms * of;
+            cfg->ring_fused = rf;
+            cfg->smem_fused = sf;
+        }
+        e = cudaSuccess;
+        cudaGetLastError();
+    }
+#endif
     cfg->grid_fast = sms * o_plain;
     cfg->grid_fast_dep = sms * o_dep;
     const int gf_max = cfg->grid_fast > cfg->grid_fast_dep ? cfg->grid_fast : cfg->grid_fast_dep;
@@ -452,6 +479,26 @@ cudaError_t launch_slow(const Args &a0, const LaunchCfg &c, bool det, bool dep, 
         if (dep) { k_event<false, true><<<g, TPB, sm, s>>>(ae); k_place<false, true><<<gp, TPB, smp, s>>>(a); }
         else { k_event<false, false><<<g, TPB, sm, s>>>(ae); k_place<false, false><<<gp, TPB, smp, s>>>(a); }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fused(const Args &a0, const LaunchCfg &c, bool det, cudaStream_t s)
+{
+    Args a = a0;
+    a.ring = c.ring_fused;
+    a.bump_step = 0;                     // the placement pass ends the step
+    constexpr int nthr = stream_threads_of<8, 1, true>();
+    if (det) k_stream<true, false, false, 8, 0, 1, true><<<c.grid_fused, nthr, c.smem_fused, s>>>(a);
+    else k_stream<false, false, false, 8, 0, 1, true><<<c.grid_fused, nthr, c.smem_fused, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_place_fused(const Args &b0, const LaunchCfg &c, bool det, cudaStream_t s)
+{
+    Args b = b0;
+    b.grid_fast = c.grid_fused;          // the streaming blocks whose secondaries it places
+    if (det) k_place<true, false><<<c.grid_place, TPB, c.smem_place, s>>>(b);
+    else k_place<false, false><<<c.grid_place, TPB, c.smem_place, s>>>(b);
     return cudaGetLastError();
 }
 

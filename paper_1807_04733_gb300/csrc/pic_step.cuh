@@ -561,6 +561,165 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
+// Shared memory and step constants of the general step (the event pass, and
+// the event warps of the streaming pass in its fused form).
+struct EvEnv {
+    float *Z, *MU;                       // current buffer: depths, (mu, packed) pairs
+    uint32_t step;
+    float half;
+    int cur, tj, tout;
+    bool vmom;
+    int32_t *s_J;                        // removals per (spin, cell)
+    uint32_t *s_n, *s_gs;                // density steps: histograms
+    unsigned long long *s_v;
+    double *s_g, *s_gT;                  // adjoint pass 2: gradient bins
+};
+
+// The general step of one queued carrier (record rec: its depth, mu, packed
+// word and position within its streaming block's tiles), of stack s whose
+// tables S holds; f: its streaming block, whose first position is fpos0;
+// tile0: the stack's first tile; room0: the stack's buffer was full before
+// the step (secondaries are dropped).  TW: the slot's scattering-test word
+// is given (xs_in, drawn by the streaming pass) instead of drawn again.
+template <bool DET, bool DEPN, int ADJ, bool TW = false>
+__device__ __forceinline__ void event_item(const Args &a, const DevStack &st, const Stk &S,
+                                           const EvEnv &E, Tally &ty, int s, int f,
+                                           long long fpos0, long long tile0, bool room0,
+                                           const float4 rec, uint32_t xs_in = 0u)
+{
+    const int cur = E.cur, tj = E.tj, tout = E.tout;
+    const uint32_t step = E.step;
+    const float half = E.half;
+    const bool vmom = E.vmom;
+    float *Z = E.Z, *MU = E.MU;
+    int32_t *s_J = E.s_J;
+    uint32_t *s_n = E.s_n, *s_gs = E.s_gs;
+    unsigned long long *s_v = E.s_v;
+    double *s_g = E.s_g, *s_gT = E.s_gT;
+    (void)cur; (void)tj; (void)tout; (void)vmom; (void)s_J; (void)s_n; (void)s_gs; (void)s_v;
+    (void)s_g; (void)s_gT;
+    const long long sbase = st.base - tile0 * TILE;          // position -> slot
+    float z = rec.x, mu = rec.y;
+    uint32_t pk = __float_as_uint(rec.z);
+    const long long vpos = fpos0 + __float_as_uint(rec.w);
+    const long long gslot = sbase + vpos;
+    const long long slot = vpos - tile0 * TILE;       // slot within the stack
+    int k = (int)(pk & 0xFFu);
+    const float mu_in = mu;
+    const uint32_t pk_in = pk;
+    const int sg = (int)((pk >> 8) & 1u);
+    int layer = (int)((pk >> 9) & 0xFu);
+    const uint32_t key_x = (uint32_t)slot;              // draws keyed by the slot
+    TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
+    float lo = S.edge[layer], hi = S.edge[layer + 1];
+    const int c_start = ADJ ? cell_of(a, S, z) : 0;     // the replay's flux reward
+    // adjoint: the slot's reward sum; in pass 2 the reward-to-go R
+    // that weights every decision of this step
+    const long long R = ADJ == 2 ? a.acc[cur][gslot] : 0;
+    const double Rd = ADJ == 2 ? (double)R * a.inv_q : 0.0;
+    flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, key_x, S.ctr_hi,
+                          step, SUB_IF, ty, Rd, s_gT);
+    const int tb = (layer * 2 + sg) * S.n_e + (k - 1);     // entry of the test
+    // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes):
+    // the slot group's test word, then the carrier's event words
+    uint32_t xs = xs_in;
+    if (!TW) {
+        const uint4 xg = philox_rk(make_uint4((uint32_t)(slot >> 2), S.ctr_hi, step,
+                                              SUB_TEST), a);
+        xs = (slot & 3) == 0 ? xg.x : (slot & 3) == 1 ? xg.y : (slot & 3) == 2 ? xg.z : xg.w;
+    }
+    bool dead = false;
+    if (ADJ == 2 && !(xs < e.P) && Rd != 0.0) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * Rd);
+    if (xs < e.P) {
+        const uint4 x = philox_rk(make_uint4(key_x, S.ctr_hi, step, SUB_EVT), a);
+        const bool inel = x.y < e.Q;
+        // scores of the test (scattered) and of the channel
+        if (ADJ == 2 && Rd != 0.0) {
+            const AdjEnt &ae = a.aent[st.ent_off + tb];
+            atomicAdd(&s_g[tb], (inel ? ae.scat_inel : ae.scat_el) * Rd);
+        }
+        if (k == 1 && (inel || (a.flags & PIC_F_LOWEST_BIN_ANY))) {
+            dead = true;
+            ++ty.absorbed;
+            ++ty.bath;
+        } else {
+            mu = mu_of(x.z);
+            if (inel) {
+                const int kp = 1 + (int)__umulhi(x.w, (uint32_t)(k - 1));
+                const int ks = k - kp;
+                k = kp;
+                e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
+                if (a.flags & PIC_F_NO_SECONDARIES) {
+                    ty.bath += (uint32_t)ks;
+                } else if (room0) {
+                    ++ty.spawn_drop;
+                    ty.q_drop += (uint32_t)ks;
+                    if (a.flags & PIC_F_STRICT_CAPACITY)
+                        atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
+                } else {
+                    // secondary: same place, spin from P0, isotropic
+                    const uint4 y = philox_rk(make_uint4(key_x, S.ctr_hi, step, SUB_SEC), a);
+                    const uint32_t g0 = (pk >> 13) & 0xFFu;
+                    const int sgs = y.x < S.p0[layer] ? 0 : 1;
+                    const uint32_t gen = g0 < 255u ? g0 + 1u : 255u;
+                    float zs = z, mus = mu_of(y.y), los = lo, his = hi;
+                    int ls = layer;
+                    TabEnt es = S.ent[(ls * 2 + sgs) * S.n_e + (ks - 1)];
+                    Tally ts{};
+                    flight<DET>(a, S, zs, mus, ls, es, los, his, sgs, ks, half, key_x,
+                                S.ctr_hi, step, SUB_SIF, ts);
+                    // the secondary's boundary events ride in the (not yet
+                    // used) id_hi bits until it is placed
+                    const uint32_t pks = (uint32_t)ks | ((uint32_t)sgs << 8) |
+                                         ((uint32_t)ls << 9) | (gen << 13) |
+                                         (ts.hits << 21) | (ts.trans << 25) |
+                                         (ts.trunc << 29);
+                    a.stage[vpos] = make_float4(zs, mus, __uint_as_float(pks), z);
+                    if (ADJ == 2) a.stage_l[vpos] = (uint32_t)layer;
+                    atomicOr(&a.spawn_bits[vpos >> 5], 1u << (vpos & 31));
+                    atomicAdd(&a.fspawn[f], 1u);
+                }
+            }
+        }
+    }
+    long long rw = 0;        // adjoint: reward of the step
+    if (dead) {
+        pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
+        const int c_end = cell_of(a, S, z);
+        // a removal, where the carrier stopped (with its weight)
+        if (!ADJ) {
+            atomicAdd(&s_J[sg * (S.n_cells + 1) + c_end], -1);
+            if (a.w[0])
+                atomicAdd(reinterpret_cast<unsigned long long *>(a.bdw) + st.J_off +
+                              ((long long)tj * 2 + sg) * (S.n_cells + 1) + c_end,
+                          0ull - (unsigned long long)a.w[cur][gslot]);
+        }
+        if (ADJ) rw = flux_w(a, s, tj, sg, c_start, c_end);
+    } else {
+        flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, key_x, S.ctr_hi,
+                              step, SUB_IF + 16, ty, Rd, s_gT);
+        const int c_end = cell_of(a, S, z);
+        pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
+        if (DEPN && !ADJ) {
+            atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
+            atomicAdd(&s_gs[c_end], (pk >> 13) & 0xFFu);
+            if (vmom)
+                add_u64_split(&s_v[sg * S.n_cells + c_end], (unsigned long long)vel_q(__fmul_rn(e.v, mu)));
+        }
+        if (ADJ) {
+            rw = flux_w(a, s, tj, sg, c_start, c_end);
+            if (DEPN) rw += dep_w(a, s, tout, sg, k, c_end);
+        }
+    }
+    if (ADJ == 1 && rw != 0) a.acc[cur][gslot] += rw;
+    if (ADJ == 2 && rw != 0) a.acc[cur][gslot] = R - rw;
+    Z[gslot] = z;
+    if (__float_as_uint(mu) != __float_as_uint(mu_in) || pk != pk_in) {
+        ++ty.changed;
+        *reinterpret_cast<uint2 *>(MU + 2 * gslot) = make_uint2(__float_as_uint(mu), pk);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // k_stream: the streaming pass (Transport(dt/2) -> Scattering(dt) ->
 // Transport(dt/2) for every carrier that neither scatters nor meets a
@@ -589,6 +748,16 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 // slots' rewards-to-go as a further array of the ring, subtracts the
 // rewards and adds each reward-to-go to the no-scattering sum of its table
 // entry.
+//
+// EV (the fused form, plain steps of a single stack): PIC_EV_WARPS further
+// warps run the general step of the block's own eventful carriers while the
+// consumers stream on, so that the scattered updates of a carrier's depth and
+// (mu, packed) pair land in sectors the pass has just read or written, still
+// in L2, instead of in a separate pass after the whole buffer has gone
+// through.  A consumer hands each eventful carrier's record to a
+// shared-memory ring after the tile's depths are stored; every ring entry has
+// a sequence word (2p: free for position p; 2p + 1: holds position p), so the
+// consumers and the event warps wait only on the entries they write or read.
 // ---------------------------------------------------------------------------
 // resident blocks per SM the register budget must allow: four of 288
 // threads (eight consumer warps, 56 registers) or five of 160 (four consumer
@@ -601,6 +770,14 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
 #endif
 // the second replay carries the slots' rewards-to-go as well: three blocks
 // (72 registers); the first fits four
+#ifndef PIC_EV_WARPS
+#define PIC_EV_WARPS 2             // event warps of the fused streaming pass
+#endif
+#ifndef PIC_EV_MIN_BLOCKS
+#define PIC_EV_MIN_BLOCKS 3        // its resident blocks per SM (56 registers)
+#endif
+constexpr int EV_CAP = 512;        // entries of its event ring (a power of two)
+
 template <int NW, int ADJ>
 constexpr int stream_min_blocks()
 {
@@ -631,9 +808,10 @@ __device__ __forceinline__ unsigned long long stream_sum_u64(unsigned long long 
 template <int NW>
 constexpr int stream_threads() { return 32 * NW + 32; }
 
-template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0, int GR = 1>
+template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0, int GR = 1, bool EV = false>
 __device__ __forceinline__ void phase_stream(const Args &a)
 {
+    static_assert(!EV || (!DEPN && ADJ == 0 && GR == 1), "fused form: plain steps only");
     // GR groups of NW consumer warps take the tiles of the ring in turn (two
     // groups where the density-step histograms leave room for one block per
     // SM); each group covers a whole tile
@@ -661,16 +839,34 @@ __device__ __forceinline__ void phase_stream(const Args &a)
         (reinterpret_cast<uintptr_t>(s_gs + (DEPN && !ADJ ? a.gbin_max : 0)) + 7) & ~uintptr_t(7));
     long long *s_tpref = reinterpret_cast<long long *>(s_v + (DEPN && !ADJ ? 2 * a.gbin_max : 0));
     long long *s_nsl = s_tpref + a.n_stacks + 1;
+    // fused form: the stack's tables of the general step, its removals per
+    // (spin, cell) and the event ring (records and their sequence words)
+    TabEnt *s_tab = reinterpret_cast<TabEnt *>(
+        (reinterpret_cast<uintptr_t>(s_nsl + a.n_stacks) + 15) & ~uintptr_t(15));
+    uint32_t *s_T = reinterpret_cast<uint32_t *>(s_tab + (EV ? a.tab_max : 0));
+    int32_t *s_J = reinterpret_cast<int32_t *>(s_T + (EV ? a.T_max : 0));
+    float4 *s_erec = reinterpret_cast<float4 *>(
+        (reinterpret_cast<uintptr_t>(s_J + (EV ? a.jbin_max : 0)) + 15) & ~uintptr_t(15));
+    uint32_t *s_eseq = reinterpret_cast<uint32_t *>(s_erec + (EV ? EV_CAP : 0));
+    uint32_t *s_ews = s_eseq + (EV ? EV_CAP : 0);        // the records' test words
     __shared__ __align__(8) unsigned long long s_full[MAX_RING], s_empty[MAX_RING];
     __shared__ DevStack s_st;
     __shared__ unsigned long long s_r[NW * GR];
     __shared__ int s_qn, s_abort;
+    // fused form: ring positions reserved and claimed, consumer warps done,
+    // the final count once they are, the event warps' ledger sums
+    __shared__ unsigned int s_etail, s_eclaim, s_cdone, s_efin_n;
+    __shared__ int s_efin;
+    __shared__ unsigned long long s_ev8[EV ? 8 : 1];
+    __shared__ DevStack s_est;
+    __shared__ float s_eedge[EV ? PIC_MAX_LAYERS + 1 : 1];
+    __shared__ uint32_t s_ep0[EV ? PIC_MAX_LAYERS : 1];
 
     const int cur = (int)*(volatile unsigned int *)&a.ctl->cur;
     const int b = blockIdx.x, G_ = gridDim.x, tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const unsigned int lt_mask = (1u << lane) - 1u;
-    for (int i = tid; i < a.n_stacks; i += NTT + 32) {
+    for (int i = tid; i < a.n_stacks; i += (int)blockDim.x) {
         s_nsl[i] = (long long)a.cnt[i].n_slots;
         // the carriers advanced in this step: every live one (the counts
         // change only in the source, event and placement kernels)
@@ -684,7 +880,14 @@ __device__ __forceinline__ void phase_stream(const Args &a)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_qn = 0;
         s_abort = 0;
+        if (EV) {
+            s_etail = s_eclaim = s_cdone = s_efin_n = 0u;
+            s_efin = 0;
+            for (int k = 0; k < 8; ++k) s_ev8[k] = 0ull;
+        }
     }
+    if (EV)
+        for (int i = tid; i < EV_CAP; i += (int)blockDim.x) s_eseq[i] = 2u * (uint32_t)i;   // free for i
     __syncthreads();
     if (tid == 0) {
         long long acc = 0;
@@ -740,6 +943,119 @@ __device__ __forceinline__ void phase_stream(const Args &a)
             }
         }
         return;
+    }
+
+    // ---------------- event warps (fused form) ----------------
+    if constexpr (EV) {
+        if (warp > NW) {
+            constexpr int NET = 32 * PIC_EV_WARPS;
+            const int etid = tid - 32 * (NW + 1);
+            auto ev_sync = [] { asm volatile("bar.sync 3, %0;" ::"n"(NET) : "memory"); };
+            if (etid == 0) s_est = a.stacks[0];
+            ev_sync();
+            const DevStack &st = s_est;
+            for (int i = etid; i < st.tab_n; i += NET) s_tab[i] = a.ent[st.ent_off + i];
+            for (int i = etid; i < st.T_n; i += NET) s_T[i] = a.T_thr[st.T_off + i];
+            if (etid <= st.n_layers) s_eedge[etid] = st.edge[etid];
+            if (etid < st.n_layers) s_ep0[etid] = st.p0_thr[etid];
+            const int nf = st.n_cells + 1;
+            for (int i = etid; i < 2 * nf; i += NET) s_J[i] = 0;
+            Stk S{};
+            S.ent = s_tab; S.T = s_T; S.edge = s_eedge; S.p0 = s_ep0;
+            S.n_layers = st.n_layers; S.n_cells = st.n_cells; S.n_e = a.n_e;
+            S.ctr_hi = (uint32_t)a.stack_base << 16;
+            S.aT = nullptr;
+            const uint32_t step = step_now(a);
+            const int tj = (int)(step / (uint32_t)a.moment_every);
+            const EvEnv env{Z, a.mu[cur], step, a.half_dt, cur, tj, 0, false, s_J,
+                            nullptr, nullptr, nullptr, nullptr, nullptr};
+            const bool room0 = (st.cap - s_nsl[0]) <= 0;
+            const long long tile0 = s_tpref[0];
+            Tally ty{};
+            ev_sync();
+#pragma unroll 1
+            for (;;) {
+                // 32 ring positions at a time; a lane waits for its record,
+                // or for the end of the queue before its position
+                unsigned int base = 0;
+                if (lane == 0) {
+                    // claim once 32 records are reserved past the claims (or
+                    // the ring is closed), polling one word with back-off
+                    unsigned int ns = 32, it = 0;
+                    const unsigned long long tw0 = global_ns();
+                    while (*(volatile unsigned int *)&s_etail - *(volatile unsigned int *)&s_eclaim < 32u &&
+                           !*(volatile int *)&s_efin && !*(volatile int *)&s_abort) {
+                        __nanosleep(ns);
+                        if (ns < 512) ns *= 2;
+                        if (++it > a.spin_limit || ((it & 255u) == 0 && global_ns() - tw0 > PIC_WAIT_NS)) {
+                            atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+                            a.ctl->timeout_where = 5u;
+                            s_abort = 1;
+                        }
+                    }
+                    base = atomicAdd(&s_eclaim, 32u);
+                }
+                base = __shfl_sync(0xffffffffu, base, 0);
+                const uint32_t pos = base + (uint32_t)lane;
+                volatile uint32_t *sq = s_eseq + (pos & (EV_CAP - 1));
+                bool have = false;
+                unsigned int it = 0;
+                unsigned long long t_start = 0;
+                for (;;) {
+                    if (*sq == 2u * pos + 1u) { have = true; break; }
+                    if (*(volatile int *)&s_efin && pos >= *(volatile unsigned int *)&s_efin_n) break;
+                    if (*(volatile int *)&s_abort) break;
+                    if (it == 0) t_start = global_ns();
+                    if (++it > a.spin_limit || ((it & 255u) == 0 && global_ns() - t_start > PIC_WAIT_NS)) {
+                        atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+                        a.ctl->timeout_where = 5u;
+                        s_abort = 1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                float4 rec = make_float4(0.f, 0.f, 0.f, 0.f);
+                uint32_t xs = 0u;
+                if (have) {
+                    __threadfence_block();
+                    rec = s_erec[pos & (EV_CAP - 1)];
+                    xs = s_ews[pos & (EV_CAP - 1)];
+                    __threadfence_block();
+                    *sq = 2u * (pos + (uint32_t)EV_CAP);         // free for pos + EV_CAP
+                }
+                const unsigned int any = __ballot_sync(0xffffffffu, have);
+                if (have)
+                    event_item<DET, false, 0, true>(a, st, S, env, ty, 0, b, t0 * TILE, tile0, room0,
+                                                    rec, xs);
+                if (!any) break;
+            }
+            // the event warps' ledger counts and removals
+            const uint32_t vals[8] = {ty.absorbed, ty.bath, ty.hits, ty.trans, ty.trunc,
+                                      ty.spawn_drop, ty.q_drop, ty.changed};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t v = __reduce_add_sync(0xffffffffu, vals[k]);
+                if (lane == 0 && v) atomicAdd(&s_ev8[k], (unsigned long long)v);
+            }
+            ev_sync();
+            {
+                int32_t *gB = a.bd_hist + st.J_off + (long long)tj * 2 * nf;
+                for (int i = etid; i < 2 * nf; i += NET) {
+                    const int v = s_J[i];
+                    if (v) atomicAdd(&gB[i], v);
+                }
+            }
+            if (etid < 8) {
+                const unsigned long long v = s_ev8[etid];
+                const int idx[8] = {L_ABSORBED, L_Q_BATH, L_IFACE_HITS, L_IFACE_TRANSMIT,
+                                    L_TRUNCATED, L_SPAWN_DROPPED, L_Q_DROPPED, L_CHANGED};
+                if (v) {
+                    atomicAdd(&a.cnt[0].led[idx[etid]], v);
+                    if (etid == 0) atomicAdd(&a.cnt[0].live, 0ull - v);   // removed carriers
+                }
+            }
+            return;
+        }
     }
 
     // ---------------- consumer warps ----------------
@@ -990,7 +1306,41 @@ __device__ __forceinline__ void phase_stream(const Args &a)
                 bal[q] = __ballot_sync(0xffffffffu, (cnt >> q) & 1u);
                 tot += __popc(bal[q]) << q;
             }
-            if (tot) {
+            if (tot && EV) {
+                // fused form: into the event ring, after the depths above
+                unsigned int base = 0;
+                if (lane == 0) base = atomicAdd(&s_etail, (unsigned int)tot);
+                base = __shfl_sync(0xffffffffu, base, 0);
+                uint32_t p = base;
+#pragma unroll
+                for (int r = 0; r < NB; ++r) p += (uint32_t)__popc(bal[r] & lt_mask) << r;
+                n_queued += cnt;
+                const uint32_t rel = (uint32_t)((t - t0) * TILE) + (uint32_t)i0;
+#pragma unroll
+                for (int j = 0; j < G; ++j) {
+                    if (!((slowbits >> j) & 1u)) continue;
+                    volatile uint32_t *sq = s_eseq + (p & (EV_CAP - 1));
+                    unsigned int it = 0;
+                    unsigned long long t_start = 0;
+                    while (*sq != 2u * p && !*(volatile int *)&s_abort) {
+                        if (it == 0) t_start = global_ns();
+                        if (++it > a.spin_limit ||
+                            ((it & 255u) == 0 && global_ns() - t_start > PIC_WAIT_NS)) {
+                            atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_TIMEOUT);
+                            a.ctl->timeout_where = 6u;
+                            s_abort = 1;
+                        }
+                        __nanosleep(32);
+                    }
+                    if (*(volatile int *)&s_abort) break;
+                    s_erec[p & (EV_CAP - 1)] = make_float4(zin[j], min_[j], __uint_as_float(pin[j]),
+                                                           __uint_as_float(rel + (uint32_t)j));
+                    s_ews[p & (EV_CAP - 1)] = xw[j];
+                    __threadfence_block();       // the record and this tile's depths first
+                    *sq = 2u * p + 1u;
+                    ++p;
+                }
+            } else if (tot) {
                 int base = 0;
                 if (lane == 0) base = atomicAdd(&s_qn, tot);
                 base = __shfl_sync(0xffffffffu, base, 0);
@@ -1009,16 +1359,33 @@ __device__ __forceinline__ void phase_stream(const Args &a)
             }
         }
     }
+    if (EV) {
+        // the last consumer warp to finish closes the ring: no position at or
+        // after the final count will be written
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            if (atomicAdd(&s_cdone, 1u) == (unsigned int)(NW - 1)) {
+                *(volatile unsigned int *)&s_efin_n = *(volatile unsigned int *)&s_etail;
+                __threadfence_block();
+                *(volatile int *)&s_efin = 1;
+            }
+        }
+    }
     if (seg_stack >= 0) flush(seg_stack);
     stream_sync<NW * GR>();
     if (tid == 0) a.qcnt[b] = (uint32_t)s_qn;
 }
 
-template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0, int GR = 1>
-__global__ void __launch_bounds__(32 * NW * GR + 32, GR > 1 ? 1 : stream_min_blocks<NW, ADJ>())
+template <int NW, int GR, bool EV>
+constexpr int stream_threads_of() { return 32 * NW * GR + 32 + (EV ? 32 * PIC_EV_WARPS : 0); }
+
+template <bool DET, bool DEPN, bool WAGG, int NW, int ADJ = 0, int GR = 1, bool EV = false>
+__global__ void __launch_bounds__(stream_threads_of<NW, GR, EV>(),
+                                  EV ? PIC_EV_MIN_BLOCKS : GR > 1 ? 1 : stream_min_blocks<NW, ADJ>())
     k_stream(const Args a)
 {
-    phase_stream<DET, DEPN, WAGG, NW, ADJ, GR>(a);
+    phase_stream<DET, DEPN, WAGG, NW, ADJ, GR, EV>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -1172,129 +1539,12 @@ __device__ __forceinline__ void phase_event(const Args &a)
 
     // the general step for item i of the concatenated queue, of stack s
     // (whose tables are loaded); f: its streaming block
+    const EvEnv env{Z, MU, step, half, cur, tj, tout, vmom, s_J, s_n, s_gs, s_v, s_g, s_gT};
     auto item = [&](int s, long long i, int f, const float4 rec) {
-        const DevStack &st = s_st;
-        const long long fpos0 = chunk_lo(T, f, Gf) * TILE;
-        const long long sbase = st.base - s_tpref[s] * TILE;     // position -> slot
-        const bool room0 = (st.cap - s_nsl[s]) <= 0;
-        float z = rec.x, mu = rec.y;
-        uint32_t pk = __float_as_uint(rec.z);
-        const long long vpos = fpos0 + __float_as_uint(rec.w);
-        const long long gslot = sbase + vpos;
-        const long long slot = vpos - s_tpref[s] * TILE;       // slot within the stack
-        int k = (int)(pk & 0xFFu);
-        const float mu_in = mu;
-        const uint32_t pk_in = pk;
-        const int sg = (int)((pk >> 8) & 1u);
-        int layer = (int)((pk >> 9) & 0xFu);
-        const uint32_t key_x = (uint32_t)slot;              // draws keyed by the slot
-        TabEnt e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
-        float lo = S.edge[layer], hi = S.edge[layer + 1];
-        const int c_start = ADJ ? cell_of(a, S, z) : 0;     // the replay's flux reward
-        // adjoint: the slot's reward sum; in pass 2 the reward-to-go R
-        // that weights every decision of this step
-        const long long R = ADJ == 2 ? a.acc[cur][gslot] : 0;
-        const double Rd = ADJ == 2 ? (double)R * a.inv_q : 0.0;
-        flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, key_x, S.ctr_hi,
-                              step, SUB_IF, ty, Rd, s_gT);
-        const int tb = (layer * 2 + sg) * S.n_e + (k - 1);     // entry of the test
-        // Scattering(dt): Monte-Carlo test against tau_eff (Eq. lifetimes):
-        // the slot group's test word, then the carrier's event words
-        const uint4 xg = philox_rk(make_uint4((uint32_t)(slot >> 2), S.ctr_hi, step,
-                                              SUB_TEST), a);
-        const uint32_t xs = (slot & 3) == 0 ? xg.x : (slot & 3) == 1 ? xg.y
-                          : (slot & 3) == 2 ? xg.z : xg.w;
-        bool dead = false;
-        if (ADJ == 2 && !(xs < e.P) && Rd != 0.0) atomicAdd(&s_g[tb], a.aent[st.ent_off + tb].noscat * Rd);
-        if (xs < e.P) {
-            const uint4 x = philox_rk(make_uint4(key_x, S.ctr_hi, step, SUB_EVT), a);
-            const bool inel = x.y < e.Q;
-            // scores of the test (scattered) and of the channel
-            if (ADJ == 2 && Rd != 0.0) {
-                const AdjEnt &ae = a.aent[st.ent_off + tb];
-                atomicAdd(&s_g[tb], (inel ? ae.scat_inel : ae.scat_el) * Rd);
-            }
-            if (k == 1 && (inel || (a.flags & PIC_F_LOWEST_BIN_ANY))) {
-                dead = true;
-                ++ty.absorbed;
-                ++ty.bath;
-            } else {
-                mu = mu_of(x.z);
-                if (inel) {
-                    const int kp = 1 + (int)__umulhi(x.w, (uint32_t)(k - 1));
-                    const int ks = k - kp;
-                    k = kp;
-                    e = S.ent[(layer * 2 + sg) * S.n_e + (k - 1)];
-                    if (a.flags & PIC_F_NO_SECONDARIES) {
-                        ty.bath += (uint32_t)ks;
-                    } else if (room0) {
-                        ++ty.spawn_drop;
-                        ty.q_drop += (uint32_t)ks;
-                        if (a.flags & PIC_F_STRICT_CAPACITY)
-                            atomicCAS(&a.ctl->status, 0u, (unsigned int)PIC_ERR_CAPACITY);
-                    } else {
-                        // secondary: same place, spin from P0, isotropic
-                        const uint4 y = philox_rk(make_uint4(key_x, S.ctr_hi, step, SUB_SEC), a);
-                        const uint32_t g0 = (pk >> 13) & 0xFFu;
-                        const int sgs = y.x < S.p0[layer] ? 0 : 1;
-                        const uint32_t gen = g0 < 255u ? g0 + 1u : 255u;
-                        float zs = z, mus = mu_of(y.y), los = lo, his = hi;
-                        int ls = layer;
-                        TabEnt es = S.ent[(ls * 2 + sgs) * S.n_e + (ks - 1)];
-                        Tally ts{};
-                        flight<DET>(a, S, zs, mus, ls, es, los, his, sgs, ks, half, key_x,
-                                    S.ctr_hi, step, SUB_SIF, ts);
-                        // the secondary's boundary events ride in the (not yet
-                        // used) id_hi bits until it is placed
-                        const uint32_t pks = (uint32_t)ks | ((uint32_t)sgs << 8) |
-                                             ((uint32_t)ls << 9) | (gen << 13) |
-                                             (ts.hits << 21) | (ts.trans << 25) |
-                                             (ts.trunc << 29);
-                        a.stage[vpos] = make_float4(zs, mus, __uint_as_float(pks), z);
-                        if (ADJ == 2) a.stage_l[vpos] = (uint32_t)layer;
-                        atomicOr(&a.spawn_bits[vpos >> 5], 1u << (vpos & 31));
-                        atomicAdd(&a.fspawn[f], 1u);
-                    }
-                }
-            }
-        }
-        long long rw = 0;        // adjoint: reward of the step
-        if (dead) {
-            pk = (pk & ~0x1FFFu) | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
-            const int c_end = cell_of(a, S, z);
-            // a removal, where the carrier stopped (with its weight)
-            if (!ADJ) {
-                atomicAdd(&s_J[sg * (S.n_cells + 1) + c_end], -1);
-                if (a.w[0])
-                    atomicAdd(reinterpret_cast<unsigned long long *>(a.bdw) + st.J_off +
-                                  ((long long)tj * 2 + sg) * (S.n_cells + 1) + c_end,
-                              0ull - (unsigned long long)a.w[cur][gslot]);
-            }
-            if (ADJ) rw = flux_w(a, s, tj, sg, c_start, c_end);
-        } else {
-            flight<DET, ADJ == 2>(a, S, z, mu, layer, e, lo, hi, sg, k, half, key_x, S.ctr_hi,
-                                  step, SUB_IF + 16, ty, Rd, s_gT);
-            const int c_end = cell_of(a, S, z);
-            pk = (pk & ~0x1FFFu) | (uint32_t)k | ((uint32_t)sg << 8) | ((uint32_t)layer << 9);
-            if (DEPN && !ADJ) {
-                atomicAdd(&s_n[(sg * S.n_e + (k - 1)) * S.n_cells + c_end], 1u);
-                atomicAdd(&s_gs[c_end], (pk >> 13) & 0xFFu);
-                if (vmom)
-                    add_u64_split(&s_v[sg * S.n_cells + c_end], (unsigned long long)vel_q(__fmul_rn(e.v, mu)));
-            }
-            if (ADJ) {
-                rw = flux_w(a, s, tj, sg, c_start, c_end);
-                if (DEPN) rw += dep_w(a, s, tout, sg, k, c_end);
-            }
-        }
-        if (ADJ == 1 && rw != 0) a.acc[cur][gslot] += rw;
-        if (ADJ == 2 && rw != 0) a.acc[cur][gslot] = R - rw;
-        Z[gslot] = z;
-        if (__float_as_uint(mu) != __float_as_uint(mu_in) || pk != pk_in) {
-            ++ty.changed;
-            *reinterpret_cast<uint2 *>(MU + 2 * gslot) = make_uint2(__float_as_uint(mu), pk);
-        }
-        };
+        (void)i;
+        event_item<DET, DEPN, ADJ>(a, s_st, S, env, ty, s, f, chunk_lo(T, f, Gf) * TILE, s_tpref[s],
+                                   (s_st.cap - s_nsl[s]) <= 0, rec);
+    };
 
     if (i0 < i1) {
         const int s_first = stack_of(s_tpref, a.n_stacks, tile_of(i0));
@@ -2049,7 +2299,7 @@ static cudaError_t occupancy(K kernel, size_t smem, int *blocks, int threads = T
 // (with and without fused multiply-add) fitting: the most resident blocks per
 // SM such that at least three tiles per SM are in flight, then the deepest
 // ring (blocks_per_sm, ring_req: 0 = free).
-template <bool DEPN, bool WAGG, int NW, int ADJ = 0, int GR = 1>
+template <bool DEPN, bool WAGG, int NW, int ADJ = 0, int GR = 1, bool EV = false>
 static cudaError_t pick_stream_ring(size_t fixed, int blocks_per_sm, int ring_req, int *ring,
                                     int *blocks, size_t *smem)
 {
@@ -2058,8 +2308,9 @@ static cudaError_t pick_stream_ring(size_t fixed, int blocks_per_sm, int ring_re
         if (ring_req > 0 && r != ring_req) continue;
         const size_t sm = fixed + (size_t)r * (ADJ == 2 ? 5 : 3) * TILE_BYTES;
         int o1 = 0, o2 = 0;
-        cudaError_t e = occupancy(k_stream<false, DEPN, WAGG, NW, ADJ, GR>, sm, &o1, stream_threads<NW * GR>());
-        if (e == cudaSuccess) e = occupancy(k_stream<true, DEPN, WAGG, NW, ADJ, GR>, sm, &o2, stream_threads<NW * GR>());
+        constexpr int nthr = stream_threads_of<NW, GR, EV>();
+        cudaError_t e = occupancy(k_stream<false, DEPN, WAGG, NW, ADJ, GR, EV>, sm, &o1, nthr);
+        if (e == cudaSuccess) e = occupancy(k_stream<true, DEPN, WAGG, NW, ADJ, GR, EV>, sm, &o2, nthr);
         if (e != cudaSuccess) return e;
         int o = o1 < o2 ? o1 : o2;
         if (blocks_per_sm > 0 && o > blocks_per_sm) o = blocks_per_sm;

@@ -47,7 +47,8 @@ class pic_params(C.Structure):
                 ("moment_every", C.c_int32), ("n_steps_max", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("hist_mode", C.c_int32),
                 ("ring_stages", C.c_int32), ("use_graph", C.c_int32),
-                ("stack_base", C.c_int32), ("consumer_warps", C.c_int32)]
+                ("stack_base", C.c_int32), ("consumer_warps", C.c_int32),
+                ("event_pass", C.c_int32)]
 
 
 class pic_stack_desc(C.Structure):
@@ -83,7 +84,9 @@ class pic_launch_info(C.Structure):
                 ("smem_step", C.c_int64), ("smem_step_moments", C.c_int64),
                 ("warps_step", C.c_int32), ("warps_step_moments", C.c_int32),
                 ("grid_adj_step", C.c_int32 * 2), ("ring_adj_step", C.c_int32 * 2),
-                ("smem_adj_step", C.c_int64 * 2)]
+                ("smem_adj_step", C.c_int64 * 2),
+                ("grid_step_fused", C.c_int32), ("ring_step_fused", C.c_int32),
+                ("smem_step_fused", C.c_int64)]
 
     def as_dict(self):
         out = {}
@@ -96,7 +99,8 @@ class pic_launch_info(C.Structure):
 class pic_tune_entry(C.Structure):
     _fields_ = [("blocks_per_sm", C.c_int32), ("ring_stages", C.c_int32),
                 ("hist_mode", C.c_int32), ("chosen", C.c_int32),
-                ("ns_per_particle_step", C.c_double), ("consumer_warps", C.c_int32)]
+                ("ns_per_particle_step", C.c_double), ("consumer_warps", C.c_int32),
+                ("event_pass", C.c_int32)]
 
     def as_dict(self):
         return {n: (float(getattr(self, n)) if n.startswith("ns") else int(getattr(self, n)))
@@ -179,7 +183,7 @@ def _check(status, ctx=None):
 # marshalling of the workload description
 # ---------------------------------------------------------------------------
 def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hist_mode=0,
-                ring_stages=0, use_graph=0, stack_base=0, consumer_warps=0):
+                ring_stages=0, use_graph=0, stack_base=0, consumer_warps=0, event_pass=0):
     p = pic_params()
     p.n_e = wl.n_e; p.dt = wl.dt; p.dz = wl.dz
     p.seed = wl.seed if seed is None else seed
@@ -191,6 +195,7 @@ def make_params(wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0, hi
     p.use_graph = 2 if use_graph in (2, "persistent") else (1 if use_graph else 0)
     p.stack_base = stack_base
     p.consumer_warps = consumer_warps
+    p.event_pass = event_pass
     return p
 
 
@@ -380,7 +385,7 @@ def pic_launch_config(ctx):
     return info.as_dict()
 
 
-def pic_autotune(ctx, trial_steps, max_entries=64):
+def pic_autotune(ctx, trial_steps, max_entries=256):
     buf = (pic_tune_entry * max_entries)()
     n = C.c_int(0)
     _check(lib().pic_autotune(ctx, trial_steps, buf, max_entries, C.byref(n)), ctx)
@@ -418,13 +423,13 @@ class Context:
 
     def __init__(self, wl, n_steps_max=None, flags=None, seed=None, blocks_per_sm=0,
                  hist_mode=0, stream=None, excite=True, capacity=None, ring_stages=0,
-                 use_graph=False, stack_base=0, consumer_warps=0):
+                 use_graph=False, stack_base=0, consumer_warps=0, event_pass=0):
         import torch
         self.wl = wl
         self.torch = torch
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.params = make_params(wl, n_steps_max, flags, seed, blocks_per_sm, hist_mode,
-                                  ring_stages, use_graph, stack_base, consumer_warps)
+                                  ring_stages, use_graph, stack_base, consumer_warps, event_pass)
         self._tabs = [_Tables(st) for st in wl.stacks]
         self.stacks = [make_stack(st, capacity) for st in wl.stacks]
         self.ctx = pic_init(self.params, self.stacks, [t.c for t in self._tabs],

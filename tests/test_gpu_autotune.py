@@ -15,7 +15,7 @@ DET = W.FLAG_DETERMINISTIC
 
 
 def test_autotune_keeps_results_and_picks_fastest():
-    wl = W.spin_valve(False, n0=30_000, capacity=90_000, n_steps=1000, flags=DET,
+    wl = W.spin_valve(False, n0=30_000, capacity=90_000, n_steps=1300, flags=DET,
                       moment_every=3, compact_every=7)
     plain = pic.Context(wl)
     tuned = pic.Context(wl, use_graph=True)
@@ -27,11 +27,15 @@ def test_autotune_keeps_results_and_picks_fastest():
     # both shapes of the streaming pass were timed: 8 consumer warps with 4
     # slots per thread and 4 with 8
     assert {t["consumer_warps"] for t in trials} == {4, 8}
+    # and the general step inside the streaming pass or in a pass of its own
+    assert {t["event_pass"] for t in trials} == {0, 1}
+    assert all(t["blocks_per_sm"] <= 3 for t in trials if t["event_pass"] == 0)
     best = min(trials, key=lambda t: t["ns_per_particle_step"])
     assert best["chosen"] == 1
     info = tuned.launch_config()
     assert info["ring_step"] == best["ring_stages"]
     assert info["warps_step"] == best["consumer_warps"]
+    assert (info["grid_step_fused"] > 0) == (best["event_pass"] == 0)
     done = tuned.shape(0)[2]
     end = max(900, done)
     plain.step(done - 100)

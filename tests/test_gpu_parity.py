@@ -25,9 +25,14 @@ def same_records(a, b):
     return len(a) == len(b) and np.array_equal(a.view(np.uint32), b.view(np.uint32))
 
 
-def compare_run(wl, checkpoints, hist_mode=0, stacks=None, set_recs=None, dep_warps=None):
-    """Step the GPU context and the oracle to each checkpoint and compare."""
-    ctx = pic.Context(wl, hist_mode=hist_mode)
+def compare_run(wl, checkpoints, hist_mode=0, stacks=None, set_recs=None, dep_warps=None,
+                event_pass=0):
+    """Step the GPU context and the oracle to each checkpoint and compare.
+    A single-stack context runs its ordinary steps with the general step
+    inside the streaming pass unless event_pass is 1."""
+    ctx = pic.Context(wl, hist_mode=hist_mode, event_pass=event_pass)
+    fused = ctx.launch_config()["grid_step_fused"]
+    assert (fused > 0) == (len(wl.stacks) == 1 and event_pass == 0)
     if dep_warps is not None:
         assert ctx.launch_config()["warps_step_moments"] == dep_warps
     idx = range(len(wl.stacks)) if stacks is None else stacks
@@ -55,10 +60,10 @@ def compare_run(wl, checkpoints, hist_mode=0, stacks=None, set_recs=None, dep_wa
     return led
 
 
-@pytest.mark.parametrize("rep", range(3))
-def test_det_bitexact_bilayer_through_capacity(rep):
+@pytest.mark.parametrize("rep,event_pass", [(0, 0), (1, 0), (2, 0), (0, 1)])
+def test_det_bitexact_bilayer_through_capacity(rep, event_pass):
     wl = W.config(0, scale=0.02, flags=DET).replace(n_steps=300)
-    led = compare_run(wl, [1, 40, 99, 100, 101, 180, 300])
+    led = compare_run(wl, [1, 40, 99, 100, 101, 180, 300], event_pass=event_pass)
     assert led["spawn_dropped"] > 0          # capacity was reached
     assert led["injected"] == 2000
 
@@ -112,10 +117,12 @@ def test_det_bitexact_batched_stacks(rep):
     compare_run(wl, [1, 77, 200])
 
 
-def test_det_bitexact_many_tiles_and_blocks():
+@pytest.mark.parametrize("event_pass", [0, 1])
+def test_det_bitexact_many_tiles_and_blocks(event_pass):
     """1.2M carriers (hundreds of tiles, every block a multi-tile chunk) with
     fast scattering so that every tile spawns; ragged count (not a multiple
-    of the 4-wide vectors or of the tile)."""
+    of the 4-wide vectors or of the tile).  Every other step is ordinary (the
+    general step inside the streaming pass, or in its own pass)."""
     N = 1_200_003
     wl = W.bilayer(n0=0, capacity=3_000_000, n_steps=12, flags=DET, compact_every=5,
                    moment_every=2)
@@ -128,7 +135,7 @@ def test_det_bitexact_many_tiles_and_blocks():
     r["id"] = np.arange(N, dtype=np.uint32)
     k = rng.integers(1, 31, N)
     r["packed"] = pack(k, rng.integers(0, 2, N), (r["z"] >= 15).astype(np.uint32), 1)
-    compare_run(wl, [1, 5, 12], set_recs={0: (r, N)})
+    compare_run(wl, [1, 5, 12], set_recs={0: (r, N)}, event_pass=event_pass)
 
 
 def test_edge_empty_and_single():
