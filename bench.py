@@ -125,7 +125,7 @@ def measured_peak():
 # "fused" (k_stream with the general step inside + k_place); the traffic grows
 # in proportion to the carriers advanced.  Valid only for the kernel source
 # whose hash is given: reported as null once the kernels change.
-NCU_TRAFFIC = {"separate": None, "fused": None, "src_sha": None}
+NCU_TRAFFIC = {"separate": 16.71, "fused": 14.82, "src_sha": "02ad247dd84327d3"}
 
 
 def kernel_sha():
