@@ -1648,6 +1648,21 @@ __device__ __forceinline__ void phase_place(const Args &a)
     const int b = blockIdx.x, Gs = gridDim.x, Gf = a.grid_fast, tid = threadIdx.x;
     const bool vmom = DEPN && !ADJ && (a.flags & PIC_F_VELOCITY_MOMENTS);
     const long long T = make_tiles(a, s_tpref, s_nsl);
+    {
+        // every stack's buffer was full before the step: the event pass
+        // dropped every secondary, so nothing is staged, counted or placed;
+        // one block ends the launch (the epoch of the look-back words, the
+        // device step counter)
+        bool full = true;
+        for (int s = 0; s < a.n_stacks && full; ++s) full = a.stacks[s].cap - s_nsl[s] <= 0;
+        if (full) {
+            if (b == 0 && tid == 0) {
+                a.ctl->epoch = ep + 1u;
+                bump_step(a);
+            }
+            return;
+        }
+    }
     const int fb0 = (int)((long long)Gf * b / Gs), fb1 = (int)((long long)Gf * (b + 1) / Gs);
     const long long t0 = chunk_lo(T, fb0, Gf), t1 = chunk_lo(T, fb1, Gf);
     const uint32_t step = step_now(a);
