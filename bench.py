@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--hist-mode", type=int, default=0)
     ap.add_argument("--ring", type=int, default=0)
+    ap.add_argument("--graph", type=int, default=1, choices=(0, 1),
+                    help="1: the main line replays whole periods from CUDA graphs (use_graph); "
+                         "0: one launch per kernel")
     ap.add_argument("--event-pass", type=int, default=0, choices=(0, 1),
                     help="ordinary steps: 0 general step inside the streaming pass where it "
                          "applies, 1 separate event pass (the autotuner may change it)")
@@ -107,6 +110,7 @@ def config_dict(wl, period, pre, args):
         "pre_roll_time_steps": pre,
         "build": "deterministic (no FMA)" if args.deterministic else "fast (FMA)",
         "l2": "inputs larger than L2 (16 B x capacity of particle state)",
+        "launch": "whole periods replayed from CUDA graphs" if args.graph else "one launch per kernel",
     }
 
 
@@ -125,7 +129,7 @@ def measured_peak():
 # "fused" (k_stream with the general step inside + k_place); the traffic grows
 # in proportion to the carriers advanced.  Valid only for the kernel source
 # whose hash is given: reported as null once the kernels change.
-NCU_TRAFFIC = {"separate": 16.71, "fused": 14.82, "src_sha": "02ad247dd84327d3"}
+NCU_TRAFFIC = {"separate": 16.71, "fused": 14.81, "src_sha": "08f98d9f613e9f16"}
 
 
 def kernel_sha():
@@ -610,7 +614,8 @@ def main():
     tune_steps = 0 if args.no_autotune else args.autotune_steps
     total = pre + 200 * tune_steps + period * (args.warmup + 3 * args.steps) + 1
     ctx = pic.Context(wl, n_steps_max=max(wl.n_steps, total), blocks_per_sm=args.blocks_per_sm,
-                      hist_mode=args.hist_mode, ring_stages=args.ring, event_pass=args.event_pass)
+                      hist_mode=args.hist_mode, ring_stages=args.ring, event_pass=args.event_pass,
+                      use_graph=bool(args.graph))
     stream = ctx.stream
     # set-up: the pulse window (inputs resident in HBM before timing)
     left = pre
