@@ -1737,16 +1737,41 @@ __device__ __forceinline__ void phase_place(const Args &a)
         Stk tmp;
         tmp.n_cells = stg.n_cells;
         long long run = prefix;
+        // q consecutive bitmap words per thread: PW where the words left fill
+        // the block that way, fewer (down to one) near the end of the range,
+        // so that a short range still spreads over all the threads
+        constexpr int PW = 8;
         const long long w0 = tl0 * (TILE / 32), w1 = tl1 * (TILE / 32);
-        for (long long wb = w0; wb < w1; wb += TPB) {
-            const long long w = wb + tid;
-            uint32_t bits = w < w1 ? a.spawn_bits[w] : 0u;
-            if (!cta_sync_or(bits != 0u)) continue;     // no secondary here
+        for (long long wb = w0; wb < w1;) {
+            const long long left = w1 - wb;
+            const int q = left >= (long long)PW * TPB ? PW : (int)((left + TPB - 1) / TPB);
+            const long long span = left < (long long)q * TPB ? left : (long long)q * TPB;
+            const long long wt = wb + (long long)q * tid, we = wb + span;
+            uint32_t wd[PW];
+#pragma unroll
+            for (int u = 0; u < PW; ++u) wd[u] = (u < q && wt + u < we) ? a.spawn_bits[wt + u] : 0u;
+            int cnt = 0;
+#pragma unroll
+            for (int u = 0; u < PW; ++u) cnt += __popc(wd[u]);
+            if (!cta_sync_or(cnt != 0)) {               // no secondary here
+                wb += span;
+                continue;
+            }
             int excl;
-            const int tot = block_scan(__popc(bits), excl, s_w);
-            if (bits) {
-                a.spawn_bits[w] = 0u;
-                long long g = run + excl;
+            const int tot = block_scan(cnt, excl, s_w);
+            if (cnt) {
+#pragma unroll
+                for (int u = 0; u < PW; ++u)
+                    if (wd[u]) a.spawn_bits[wt + u] = 0u;
+            }
+            long long g = run + excl;
+#pragma unroll 1
+            for (int u = 0; u < q; ++u) {
+                uint32_t bits = wd[0];                  // word u, by selects (no local array)
+#pragma unroll
+                for (int v = 1; v < PW; ++v)
+                    if (u == v) bits = wd[v];
+                const long long w = wt + u;
                 while (bits) {
                     const int j = __ffs(bits) - 1;
                     bits &= bits - 1u;
@@ -1799,6 +1824,7 @@ __device__ __forceinline__ void phase_place(const Args &a)
                 }
             }
             run += tot;
+            wb += span;
         }
         const unsigned long long kk = block_sum_u64(kept, s_r);
         if (tid == 0 && kk) atomicAdd(&a.cnt[s].led[L_SPAWNED], kk);
@@ -2356,6 +2382,9 @@ static cudaError_t event_cfg(size_t sm, int *grid, int sms)
     return cudaSuccess;
 }
 
+#ifndef PIC_PLACE_DEP_BLOCKS
+#define PIC_PLACE_DEP_BLOCKS 2     // resident placement blocks per SM on density steps
+#endif
 template <bool DEPN, int ADJ = 0>
 static cudaError_t place_cfg(size_t sm, int *grid, int sms)
 {
@@ -2363,8 +2392,11 @@ static cudaError_t place_cfg(size_t sm, int *grid, int sms)
     cudaError_t e = occupancy(k_place<false, DEPN, ADJ>, sm, &o1);
     if (e == cudaSuccess) e = occupancy(k_place<true, DEPN, ADJ>, sm, &o2);
     if (e != cudaSuccess) return e;
-    const int o = o1 < o2 ? o1 : o2;
+    int o = o1 < o2 ? o1 : o2;
     if (o < 1) return cudaErrorInvalidConfiguration;
+    // density steps: every block that places a secondary zeroes and flushes
+    // the whole histogram, so fewer blocks than fit
+    if (DEPN && o > PIC_PLACE_DEP_BLOCKS) o = PIC_PLACE_DEP_BLOCKS;
     *grid = sms * o;            // look-back: every block resident
     return cudaSuccess;
 }
