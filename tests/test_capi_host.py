@@ -54,6 +54,18 @@ def test_init_rejects_bad_arguments_without_a_device():
     assert e.value.status == 1
 
 
+@pytest.mark.parametrize("field,value", [("event_pass", 2), ("event_pass", -1),
+                                         ("consumer_warps", 6), ("hist_mode", 3)])
+def test_init_rejects_bad_launch_options_without_a_device(field, value):
+    wl = W.config(0, scale=0.01)
+    p = pic.make_params(wl)
+    setattr(p, field, value)
+    tabs = pic._Tables(wl.stacks[0])
+    with pytest.raises(pic.PicError) as e:
+        pic.pic_init(p, [pic.make_stack(wl.stacks[0])], [tabs.c])
+    assert e.value.status == 1
+
+
 def test_compact_static_rejects_misaligned_inputs_without_a_device():
     # the compaction reads its inputs in 16-byte vectors: any input array
     # off a 16-byte boundary is an argument error, found before any device
